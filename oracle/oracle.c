@@ -1,0 +1,351 @@
+/*
+ * Oracle for the Jacobi-preconditioned CG solve over a CSR (AIJ) matrix.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, sequential CPU
+ * restatement of what the GPU path computes.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it; the
+ * product path never does.  It shares no code, header or table with the
+ * CUDA library.
+ *
+ * What it follows:
+ *  - MatMult on the MATAIJ (compressed sparse row) type, Sec. 4 of the
+ *    paper; the CSR traffic model of Challenge A7 (Sec. 3).
+ *  - VecAXPY y <- a x + y, VecAYPX y <- x + b y, VecDot and VecNorm(NORM_2)
+ *    as the paper's vector operations (Sec. 5.1, Sec. 2 stub routine).
+ *  - PCJACOBI (Sec. 5.3: Jacobi-preconditioned smoothers) and KSPCG
+ *    (Sec. 5.5: the CG method).  The paper names these methods but does not
+ *    print them; the iteration below is the textbook preconditioned CG of
+ *    Hestenes & Stiefel (1952) in the form of Saad, "Iterative Methods for
+ *    Sparse Linear Systems", 2nd ed., Algorithm 9.1.
+ *  - The single-precision-on-the-GPU plan of Response A7 (Sec. 4), read as
+ *    classical iterative refinement (Wilkinson; Moler 1967): FP64 residual,
+ *    FP32 inner PCG on the scaled residual, FP64 update.
+ *
+ * Readings where the paper is silent:
+ *  - Stopping test: unpreconditioned ||r||_2 <= rtol * ||b||_2, taken before
+ *    each iteration; the iteration count is the number of SpMVs after set-up.
+ *  - Breakdown: p.Ap <= 0 or r.z < 0 is an indefinite operator or
+ *    preconditioner; a NaN in any scalar is reported as such.
+ *  - FP32 inner reductions accumulate in FP32 by pairwise summation.
+ *
+ * Status codes (defined here independently of the CUDA library):
+ *   0 converged, 1 iteration limit, -1 bad argument, -4 missing or
+ *   non-positive diagonal, -5 indefinite, -6 NaN, -8 stagnation, -10 bad CSR.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_CONVERGED 0
+#define ORC_DIVERGED_ITS 1
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_DIAG (-4)
+#define ORC_ERR_INDEFINITE (-5)
+#define ORC_ERR_NAN (-6)
+#define ORC_ERR_STAGNATION (-8)
+#define ORC_ERR_CSR (-10)
+
+/* ---------------------------------------------------------------- CSR --- */
+
+/* Structural check: rowptr[0] = 0, rowptr non-decreasing, every column in
+ * [0, ncols) and strictly increasing within its row. */
+int orc_csr_check(int64_t n, int64_t ncols, const int32_t *rowptr, const int32_t *colidx)
+{
+    if (n < 0 || ncols < 0) return ORC_ERR_ARG;
+    if (rowptr[0] != 0) return ORC_ERR_CSR;
+    for (int64_t i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return ORC_ERR_CSR;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (colidx[k] < 0 || colidx[k] >= ncols) return ORC_ERR_CSR;
+            if (k > rowptr[i] && colidx[k] <= colidx[k - 1]) return ORC_ERR_CSR;
+        }
+    }
+    return 0;
+}
+
+/* MatMult: y_i = sum_k vals[k] * x[colidx[k]] over row i, in storage order. */
+void orc_spmv(int64_t n, const int32_t *rowptr, const int32_t *colidx,
+              const double *vals, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            s += vals[k] * x[colidx[k]];
+        y[i] = s;
+    }
+}
+
+/* The same product in binary32 (values, vector and sum all float). */
+void orc_spmv_f32(int64_t n, const int32_t *rowptr, const int32_t *colidx,
+                  const float *vals, const float *x, float *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float s = 0.0f;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            s += vals[k] * x[colidx[k]];
+        y[i] = s;
+    }
+}
+
+/* ------------------------------------------------------- vector ops --- */
+
+/* VecDot: sum_i x_i y_i, left to right. */
+double orc_dot(int64_t n, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+}
+
+/* VecNorm(NORM_2): sqrt(x . x). */
+double orc_norm2(int64_t n, const double *x)
+{
+    return sqrt(orc_dot(n, x, x));
+}
+
+/* Compensated dot product Dot2 (Ogita, Rump & Oishi, "Accurate sum and dot
+ * product", SIAM J. Sci. Comput. 26(6), 2005, Algorithm 5.3): the result is
+ * as accurate as if computed in twice the working precision and then
+ * rounded.  TwoProduct uses the fused multiply-add; TwoSum is Knuth's. */
+double orc_dot2(int64_t n, const double *x, const double *y)
+{
+    double p = 0.0, s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double h = x[i] * y[i];
+        double r = fma(x[i], y[i], -h);          /* exact error of the product */
+        double q = p + h;                        /* TwoSum(p, h) */
+        double z = q - p;
+        double e = (p - (q - z)) + (h - z);
+        p = q;
+        s += e + r;
+    }
+    return p + s;
+}
+
+/* VecAXPY: y <- alpha x + y. */
+void orc_axpy(int64_t n, double alpha, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = alpha * x[i] + y[i];
+}
+
+/* VecAYPX: y <- x + beta y. */
+void orc_aypx(int64_t n, double beta, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i] + beta * y[i];
+}
+
+/* Pairwise (cascade) sum of v[0..n) in binary32: split in halves down to
+ * blocks of at most 8, which are summed left to right. */
+static float pairwise_f32(const float *v, int64_t n)
+{
+    if (n <= 8) {
+        float s = 0.0f;
+        for (int64_t i = 0; i < n; ++i) s += v[i];
+        return s;
+    }
+    int64_t h = n / 2;
+    return pairwise_f32(v, h) + pairwise_f32(v + h, n - h);
+}
+
+/* FP32 dot with FP32 pairwise accumulation; tmp has n floats. */
+static float dot_f32(int64_t n, const float *x, const float *y, float *tmp)
+{
+    for (int64_t i = 0; i < n; ++i) tmp[i] = x[i] * y[i];
+    return pairwise_f32(tmp, n);
+}
+
+/* ------------------------------------------------------------ Jacobi --- */
+
+/* PCJACOBI set-up: dinv_i = 1 / a_ii.  Missing or non-positive a_ii is an
+ * error (the preconditioner would not be SPD). */
+int orc_jacobi_dinv(int64_t n, const int32_t *rowptr, const int32_t *colidx,
+                    const double *vals, double *dinv)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        int found = 0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (colidx[k] == i) { d = vals[k]; found = 1; }
+        if (!found || !(d > 0.0)) return ORC_ERR_DIAG;
+        dinv[i] = 1.0 / d;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ KSPCG --- */
+
+/*
+ * Jacobi-preconditioned CG, FP64.
+ *   x (in/out) initial guess -> solution; rtol relative to ||b||_2;
+ *   maxit iterations at most; rhist (optional, maxit+1 doubles) receives
+ *   ||r_k||_2 for k = 0..iters.
+ * Returns a status code; *iters = SpMVs done, *rnorm = last ||r||_2 of the
+ * recurrence.
+ *
+ *   r = b - A x;  z = D^-1 r;  p = z;  rho = r.z
+ *   for k = 0, 1, ...:
+ *       if ||r|| <= rtol ||b||: converged after k iterations
+ *       q = A p;  pi = p.q;  (pi <= 0: indefinite)
+ *       alpha = rho / pi;  x += alpha p;  r -= alpha q;  z = D^-1 r
+ *       rho' = r.z;  (rho' < 0: indefinite preconditioner)
+ *       beta = rho' / rho;  rho = rho';  p = z + beta p
+ */
+int orc_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+            const double *b, double *x, double rtol, int64_t maxit,
+            int64_t *iters, double *rnorm, double *rhist)
+{
+    *iters = 0;
+    *rnorm = 0.0;
+    if (n < 0 || maxit < 0 || !(rtol >= 0.0)) return ORC_ERR_ARG;
+    if (n == 0) return ORC_CONVERGED;
+    double *dinv = malloc(sizeof(double) * n);
+    double *r = malloc(sizeof(double) * n);
+    double *z = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n);
+    double *q = malloc(sizeof(double) * n);
+    int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
+    if (status == 0) {
+        orc_spmv(n, rowptr, colidx, vals, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        memcpy(p, z, sizeof(double) * n);
+        double rho = orc_dot(n, r, z);
+        double bnorm = orc_norm2(n, b);
+        int64_t k = 0;
+        status = ORC_DIVERGED_ITS;
+        for (;;) {
+            double rn = orc_norm2(n, r);
+            *rnorm = rn;
+            if (rhist) rhist[k] = rn;
+            if (isnan(rn) || isnan(rho)) { status = ORC_ERR_NAN; break; }
+            if (rn <= rtol * bnorm) { status = ORC_CONVERGED; break; }
+            if (k >= maxit) break;
+            orc_spmv(n, rowptr, colidx, vals, p, q);
+            double pi = orc_dot(n, p, q);
+            if (isnan(pi)) { status = ORC_ERR_NAN; break; }
+            if (pi <= 0.0) { status = ORC_ERR_INDEFINITE; break; }
+            double alpha = rho / pi;
+            orc_axpy(n, alpha, p, x);
+            orc_axpy(n, -alpha, q, r);
+            for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            double rho_new = orc_dot(n, r, z);
+            ++k;
+            if (rho_new < 0.0) { *rnorm = orc_norm2(n, r); status = ORC_ERR_INDEFINITE; break; }
+            double beta = rho_new / rho;
+            rho = rho_new;
+            orc_aypx(n, beta, z, p);
+        }
+        *iters = k;
+    }
+    free(dinv); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/*
+ * The same iteration entirely in binary32 (storage, arithmetic and
+ * pairwise-accumulated reductions), from x = 0.  vals32/dinv32 are the
+ * rounded FP64 inputs.  rtol is relative to ||b||_2 computed in FP32.
+ */
+int orc_pcg_f32(int64_t n, const int32_t *rowptr, const int32_t *colidx, const float *vals32,
+                const float *dinv32, const float *b, float *x, float rtol, int64_t maxit,
+                int64_t *iters, float *rnorm)
+{
+    *iters = 0;
+    *rnorm = 0.0f;
+    if (n < 0 || maxit < 0 || !(rtol >= 0.0f)) return ORC_ERR_ARG;
+    if (n == 0) return ORC_CONVERGED;
+    float *r = malloc(sizeof(float) * n);
+    float *z = malloc(sizeof(float) * n);
+    float *p = malloc(sizeof(float) * n);
+    float *q = malloc(sizeof(float) * n);
+    float *t = malloc(sizeof(float) * n);
+    for (int64_t i = 0; i < n; ++i) { x[i] = 0.0f; r[i] = b[i]; }
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv32[i] * r[i];
+    memcpy(p, z, sizeof(float) * n);
+    float rho = dot_f32(n, r, z, t);
+    float bnorm = sqrtf(dot_f32(n, b, b, t));
+    int64_t k = 0;
+    int status = ORC_DIVERGED_ITS;
+    for (;;) {
+        float rn = sqrtf(dot_f32(n, r, r, t));
+        *rnorm = rn;
+        if (isnan(rn) || isnan(rho)) { status = ORC_ERR_NAN; break; }
+        if (rn <= rtol * bnorm) { status = ORC_CONVERGED; break; }
+        if (k >= maxit) break;
+        orc_spmv_f32(n, rowptr, colidx, vals32, p, q);
+        float pi = dot_f32(n, p, q, t);
+        if (isnan(pi)) { status = ORC_ERR_NAN; break; }
+        if (pi <= 0.0f) { status = ORC_ERR_INDEFINITE; break; }
+        float alpha = rho / pi;
+        for (int64_t i = 0; i < n; ++i) x[i] = alpha * p[i] + x[i];
+        for (int64_t i = 0; i < n; ++i) r[i] = -alpha * q[i] + r[i];
+        for (int64_t i = 0; i < n; ++i) z[i] = dinv32[i] * r[i];
+        float rho_new = dot_f32(n, r, z, t);
+        ++k;
+        if (rho_new < 0.0f) { status = ORC_ERR_INDEFINITE; break; }
+        float beta = rho_new / rho;
+        rho = rho_new;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    *iters = k;
+    free(r); free(z); free(p); free(q); free(t);
+    return status;
+}
+
+/*
+ * Mixed precision: FP32 inner PCG inside FP64 iterative refinement.
+ *   loop: r = b - A x (FP64);  stop if ||r|| <= rtol ||b||;
+ *         stagnation if ||r|| > ||r_prev|| / 2;
+ *         s = ||r||;  solve A d = r / s with FP32 PCG to inner_rtol;
+ *         x += s d (FP64).
+ * Returns a status; *outer = refinement steps taken, *inner = FP32 PCG
+ * iterations summed over them, *rnorm = last FP64 residual norm.
+ */
+int orc_pcg_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                  const double *b, double *x, double rtol, double inner_rtol,
+                  int64_t inner_maxit, int64_t outer_maxit,
+                  int64_t *outer, int64_t *inner, double *rnorm)
+{
+    *outer = 0;
+    *inner = 0;
+    *rnorm = 0.0;
+    if (n < 0 || inner_maxit < 0 || outer_maxit < 0 || !(rtol >= 0.0)) return ORC_ERR_ARG;
+    if (n == 0) return ORC_CONVERGED;
+    double *dinv = malloc(sizeof(double) * n);
+    int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
+    if (status != 0) { free(dinv); return status; }
+    int64_t nnz = rowptr[n];
+    float *vals32 = malloc(sizeof(float) * (nnz > 0 ? nnz : 1));
+    float *dinv32 = malloc(sizeof(float) * n);
+    float *r32 = malloc(sizeof(float) * n);
+    float *d32 = malloc(sizeof(float) * n);
+    double *r = malloc(sizeof(double) * n);
+    for (int64_t k = 0; k < nnz; ++k) vals32[k] = (float)vals[k];
+    for (int64_t i = 0; i < n; ++i) dinv32[i] = (float)dinv[i];
+    double bnorm = orc_norm2(n, b);
+    double prev = INFINITY;
+    status = ORC_DIVERGED_ITS;
+    for (int64_t it = 0;; ++it) {
+        orc_spmv(n, rowptr, colidx, vals, x, r);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+        double rn = orc_norm2(n, r);
+        *rnorm = rn;
+        *outer = it;
+        if (isnan(rn)) { status = ORC_ERR_NAN; break; }
+        if (rn <= rtol * bnorm) { status = ORC_CONVERGED; break; }
+        if (rn > 0.5 * prev) { status = ORC_ERR_STAGNATION; break; }
+        if (it >= outer_maxit) break;
+        prev = rn;
+        for (int64_t i = 0; i < n; ++i) r32[i] = (float)(r[i] / rn);
+        int64_t kin = 0;
+        float rin = 0.0f;
+        int st = orc_pcg_f32(n, rowptr, colidx, vals32, dinv32, r32, d32, (float)inner_rtol,
+                             inner_maxit, &kin, &rin);
+        *inner += kin;
+        if (st < 0) { status = st; break; }
+        for (int64_t i = 0; i < n; ++i) x[i] += rn * (double)d32[i];
+    }
+    free(dinv); free(vals32); free(dinv32); free(r32); free(d32); free(r);
+    return status;
+}

@@ -1,0 +1,82 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case copies the oracle into a temporary directory, plants one mistake
+in the copy of oracle.c (a dropped term, a wrong sign, index or operand, a
+wrong preconditioner), builds it with gcc and runs the pins against it: at
+least one pin must fail.  The committed oracle is never modified.
+"""
+import importlib.util
+import os
+import shutil
+import sys
+
+import pytest
+
+import test_oracle_pins as P
+
+ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+
+MUTANTS = {
+    "spmv_row_index_for_column": ("s += vals[k] * x[colidx[k]];\n        y[i] = s;\n    }\n}\n\n/* The same product in binary32",
+                                  "s += vals[k] * x[i];\n        y[i] = s;\n    }\n}\n\n/* The same product in binary32"),
+    "spmv_skips_last_entry": ("double s = 0.0;\n        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)",
+                              "double s = 0.0;\n        for (int64_t k = rowptr[i]; k + 1 < rowptr[i + 1]; ++k)"),
+    "residual_update_sign": ("orc_axpy(n, -alpha, q, r);", "orc_axpy(n, alpha, q, r);"),
+    "beta_inverted": ("double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    "no_preconditioner_in_loop": ("for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];\n            double rho_new",
+                                  "for (int64_t i = 0; i < n; ++i) z[i] = r[i];\n            double rho_new"),
+    "dinv_not_inverted": ("dinv[i] = 1.0 / d;", "dinv[i] = d;"),
+    "aypx_roles_swapped": ("y[i] = x[i] + beta * y[i];", "y[i] = beta * x[i] + y[i];"),
+    "norm_without_sqrt": ("return sqrt(orc_dot(n, x, x));", "return orc_dot(n, x, x);"),
+    "pi_from_wrong_operands": ("double pi = orc_dot(n, p, q);", "double pi = orc_dot(n, q, q);"),
+    "x_update_with_z": ("orc_axpy(n, alpha, p, x);", "orc_axpy(n, alpha, z, x);"),
+    "rho_unpreconditioned": ("double rho = orc_dot(n, r, z);", "double rho = orc_dot(n, r, r);"),
+    "dot2_drops_product_error": ("s += e + r;", "s += e;"),
+    "f32_residual_sign": ("r[i] = -alpha * q[i] + r[i];", "r[i] = alpha * q[i] + r[i];"),
+    "mixed_update_unscaled": ("x[i] += rn * (double)d32[i];", "x[i] += (double)d32[i];"),
+    "csr_check_allows_duplicates": ("colidx[k] <= colidx[k - 1]", "colidx[k] < colidx[k - 1]"),
+}
+
+PINS = [
+    lambda o: P.test_spmv_dense_bruteforce_nonsymmetric_rectangular(o),
+    lambda o: P.test_spmv_exact_inputs_bitwise(o),
+    lambda o: P.test_spmv_laplacian_row_sums(o),
+    lambda o: P.test_csr_check(o),
+    lambda o: P.test_dot_norm_exact(o),
+    lambda o: P.test_dot2_is_twice_working_precision(o),
+    lambda o: P.test_axpy_aypx_roles(o),
+    lambda o: P.test_jacobi_dinv(o),
+    lambda o: P.test_pcg_iterates_are_krylov_minimisers(o, 3),
+    lambda o: P.test_pcg_finite_termination(o, lambda: P.I.lap2d5(2), 3),
+    lambda o: P.test_pcg_iteration_bound_2d(o),
+    lambda o: P.test_pcg_diagonal_matrix_one_step(o),
+    lambda o: P.test_pcg_f32_close_to_fp64(o),
+    lambda o: P.test_mixed_refinement_reaches_fp64_accuracy(o),
+]
+
+
+def _load_mutant(tmp_path, name, old, new):
+    d = tmp_path / f"oracle_{name}"
+    shutil.copytree(ORACLE_DIR, d, ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp"))
+    src = (d / "oracle.c").read_text()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    (d / "oracle.c").write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}", d / "__init__.py")
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    mod.build()
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    caught = []
+    for pin in PINS:
+        try:
+            pin(mut)
+        except Exception:          # an assertion, or a failure to converge
+            caught.append(pin)
+    assert caught, f"no pin fails with mutation {name}"

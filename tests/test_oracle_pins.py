@@ -1,0 +1,336 @@
+"""Pins that tie the CPU oracle to mathematics, not to itself (CPU only).
+
+* SpMV: dense brute force in extended precision with Higham's componentwise
+  bound |fl(a.x) - a.x| <= gamma_m |a|.|x| (Accuracy and Stability of
+  Numerical Algorithms, Sec. 3.1); exact integer inputs (bitwise); row sums
+  of the Dirichlet Laplacian; a non-symmetric, rectangular pattern so that a
+  transposed operand cannot pass.
+* Vector ops: exact inputs (bitwise), roles of alpha/beta in AXPY/AYPX.
+* PCG: the k-th iterate equals the minimiser of the A-norm error over the
+  Jacobi-preconditioned Krylov space (computed by dense Galerkin projection);
+  finite termination after #distinct eigenvalues steps; the CG iteration
+  bound from the closed-form condition number; dense solves; manufactured
+  solutions; breakdown, limit and degenerate cases.
+* Mixed precision: agreement with the FP64 solve and the outer-step count.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2011_00715_gb300 import inputs as I
+
+U = 2.0 ** -53
+
+
+def gamma(m):
+    return m * U / (1 - m * U)
+
+
+# ------------------------------------------------------------------ SpMV --
+
+def test_spmv_dense_bruteforce_nonsymmetric_rectangular(orc):
+    A = I.random_csr(150, 220, 9, seed=21)          # 150 x 220, non-symmetric
+    x = I.uniform_pm1(4, 0, 220)
+    d = np.zeros((150, 220), dtype=np.longdouble)
+    rows = np.repeat(np.arange(150), np.diff(A.rowptr))
+    d[rows, A.colidx] = A.vals
+    exact = d @ x.astype(np.longdouble)
+    y = orc.spmv(A, x)
+    absdot = np.abs(d) @ np.abs(x).astype(np.longdouble)
+    m = np.diff(A.rowptr)
+    bound = np.array([gamma(int(mi)) for mi in m]) * absdot.astype(float)
+    assert np.all(np.abs(y - exact.astype(float)) <= bound + 1e-300)
+    # the transposed product is a different vector
+    assert np.abs(y - (d.T[:150, :150] @ x[:150].astype(np.longdouble)).astype(float)).max() > 1e-3
+
+
+def test_spmv_exact_inputs_bitwise(orc):
+    A = I.exact_csr(300, 8, seed=3)
+    x = I.exact_vector(300, seed=4)
+    y = orc.spmv(A, x)
+    k = np.round(x * 2 ** 20).astype(np.int64)
+    for i in range(A.n):
+        s = 0
+        for t in range(A.rowptr[i], A.rowptr[i + 1]):
+            s += int(A.vals[t]) * int(k[A.colidx[t]])
+        assert y[i] == s / 2 ** 20
+
+
+def test_spmv_laplacian_row_sums(orc):
+    A = I.lap3d7(9)
+    y = orc.spmv(A, np.ones(A.n))
+    c = np.arange(A.n)
+    x, yy, z = c % 9, (c // 9) % 9, c // 81
+    missing = sum((v == 0).astype(int) + (v == 8) for v in (x, yy, z))
+    assert np.array_equal(y, missing.astype(float))
+
+
+def test_spmv_f32_matches_rounded_double(orc):
+    A = I.exact_csr(200, 6, seed=8)
+    x = I.exact_vector(200, seed=9)
+    # exact inputs with <= 24 significant bits: the FP32 product is exact too
+    x = np.round(x * 2 ** 12) / 2 ** 12
+    assert np.array_equal(orc.spmv_f32(A, x).astype(np.float64), orc.spmv(A, x))
+
+
+def test_csr_check(orc):
+    A = I.lap2d5(4)
+    assert orc.csr_check(A.n, A.n, A.rowptr, A.colidx) == 0
+    bad = A.rowptr.copy(); bad[3] = bad[4] + 1
+    assert orc.csr_check(A.n, A.n, bad, A.colidx) == orc.ERR_CSR
+    badc = A.colidx.copy(); badc[5] = A.n
+    assert orc.csr_check(A.n, A.n, A.rowptr, badc) == orc.ERR_CSR
+    unsorted = A.colidx.copy(); unsorted[[0, 1]] = unsorted[[1, 0]]
+    assert orc.csr_check(A.n, A.n, A.rowptr, unsorted) == orc.ERR_CSR
+    bad0 = A.rowptr.copy(); bad0[0] = 1
+    assert orc.csr_check(A.n, A.n, bad0, A.colidx) == orc.ERR_CSR
+    dup = A.colidx.copy(); dup[1] = dup[0]                 # repeated column in row 0
+    assert orc.csr_check(A.n, A.n, A.rowptr, dup) == orc.ERR_CSR
+    neg = A.colidx.copy(); neg[0] = -1
+    assert orc.csr_check(A.n, A.n, A.rowptr, neg) == orc.ERR_CSR
+
+
+# ------------------------------------------------------------ vector ops --
+
+def test_dot_norm_exact(orc):
+    x = I.exact_vector(10000, seed=1)
+    y = np.round(I.uniform_pm1(2, 0, 10000) * 8)
+    kx = np.round(x * 2 ** 20).astype(np.int64)
+    exact = int(np.sum(kx * y.astype(np.int64))) / 2 ** 20
+    assert orc.dot(x, y) == exact
+    assert orc.dot2(x, y) == exact
+    assert orc.norm2(np.array([3.0, 4.0])) == 5.0
+    v = np.array([1.0, 2.0, 2.0, 4.0, 10.0])             # sum of squares 125
+    assert orc.norm2(v) == math.sqrt(125.0)
+
+
+def test_dot2_is_twice_working_precision(orc):
+    # ill-conditioned dot: huge cancellation; Dot2 error <= u|s| + gamma^2 |x|.|y|
+    rng_x = I.uniform_pm1(3, 0, 2000) * np.exp(20 * I.uniform01(3, 1, np.arange(2000)))
+    y = I.uniform_pm1(3, 2, 2000)
+    x = np.concatenate([rng_x, -rng_x[:1000]])
+    y = np.concatenate([y, y[:1000]])
+    exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y))
+    s2 = orc.dot2(x, y)
+    n = len(x)
+    bound = U * abs(float(exact)) + gamma(n) ** 2 * float(np.abs(x) @ np.abs(y))
+    assert abs(Fraction(s2) - exact) <= Fraction(bound)
+    # (1 + 2^-30)^2 - (1 + 2^-29) = 2^-60 exactly; the rounded product loses
+    # that term, so a plain dot returns 0 and Dot2 must return 2^-60
+    a = 1.0 + 2.0 ** -30
+    x = np.array([a, -(1.0 + 2.0 ** -29)])
+    y = np.array([a, 1.0])
+    assert orc.dot(x, y) == 0.0
+    assert orc.dot2(x, y) == 2.0 ** -60
+
+
+def test_axpy_aypx_roles(orc):
+    x = np.array([1.0, 2.0, -3.0])
+    y = np.array([10.0, 20.0, 30.0])
+    assert np.array_equal(orc.axpy(2.0, x, y), [12.0, 24.0, 24.0])      # 2x + y
+    assert np.array_equal(orc.aypx(2.0, x, y), [21.0, 42.0, 57.0])      # x + 2y
+
+
+def test_jacobi_dinv(orc):
+    A = I.var5(5, 4, seed=2)
+    st, dinv = orc.jacobi_dinv(A)
+    assert st == 0 and np.array_equal(dinv, 1.0 / np.diag(A.to_dense()))
+    B = I.random_csr(10, 10, 2, seed=1)                 # no guaranteed diagonal
+    d = B.to_dense()
+    st, _ = orc.jacobi_dinv(B)
+    assert st == (0 if np.all(np.diag(d) > 0) and all(
+        i in B.colidx[B.rowptr[i]:B.rowptr[i + 1]] for i in range(10)) else orc.ERR_DIAG)
+
+
+# ------------------------------------------------------------------- PCG --
+
+def krylov_minimiser(A, b, k):
+    """Dense reference for the k-th PCG iterate from x0 = 0: the minimiser
+    of ||x - x*||_A over span{z0, (D^-1 A) z0, ..., (D^-1 A)^(k-1) z0},
+    z0 = D^-1 b, by Galerkin projection on an orthonormal basis."""
+    d = A.to_dense()
+    dinv = 1.0 / np.diag(d)
+    v = dinv * b
+    basis = []
+    for _ in range(k):
+        basis.append(v)
+        v = dinv * (d @ v)
+    Q, _ = np.linalg.qr(np.array(basis).T)
+    y = np.linalg.solve(Q.T @ d @ Q, Q.T @ b)
+    return Q @ y
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_pcg_iterates_are_krylov_minimisers(orc, k):
+    A = I.var5(8, 7, seed=31, sigma=0.5)                # non-constant diagonal
+    b = orc.spmv(A, I.xstar(A.n, 5))
+    r = orc.pcg(A, b, rtol=0.0, maxit=k)
+    assert r["status"] == orc.DIVERGED_ITS and r["iters"] == k
+    ref = krylov_minimiser(A, b, k)
+    assert np.linalg.norm(r["x"] - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_pcg_energy_error_monotone_and_history(orc):
+    A = I.var7(4, 4, 4, seed=5)
+    d = A.to_dense()
+    xs = I.xstar(A.n, 6)
+    b = d @ xs
+    errs = []
+    for k in range(0, 25):
+        r = orc.pcg(A, b, rtol=0.0, maxit=k, history=True)
+        e = r["x"] - xs
+        errs.append(math.sqrt(e @ d @ e))
+        # recurrence residual matches the true residual on this small case
+        assert abs(r["rhist"][-1] - np.linalg.norm(b - d @ r["x"])) <= 1e-10 * np.linalg.norm(b)
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-12) for i in range(len(errs) - 1))
+    assert errs[-1] < 1e-6 * errs[0]
+
+
+@pytest.mark.parametrize("maker,steps", [
+    (lambda: I.lap2d5(2), 3),        # eigenvalues {2, 4, 4, 6}: 3 distinct
+    (lambda: I.lap3d7(2), 4),        # {3, 5, 7, 9}
+    (lambda: I.lap2d5(6, 1), 6),     # 1D tridiagonal: 6 distinct
+])
+def test_pcg_finite_termination(orc, maker, steps):
+    A = maker()
+    b = orc.spmv(A, I.xstar(A.n, 1))
+    r = orc.pcg(A, b, rtol=1e-12, maxit=50)
+    assert r["status"] == orc.CONVERGED and r["iters"] == steps
+    r1 = orc.pcg(A, b, rtol=1e-12, maxit=steps - 1)
+    assert r1["status"] == orc.DIVERGED_ITS and r1["rnorm"] > 1e-6 * np.linalg.norm(b)
+
+
+def cg_bound(kappa, rtol):
+    """||r_k||/||b|| <= 2 sqrt(kappa) ((sqrt k - 1)/(sqrt k + 1))^k from x0 = 0."""
+    s = math.sqrt(kappa)
+    return math.ceil(math.log(2 * s / rtol) / math.log((s + 1) / (s - 1)))
+
+
+def test_pcg_iteration_bound_2d(orc):
+    N = 64
+    lmin = 4 - 4 * math.cos(math.pi / (N + 1))
+    lmax = 4 + 4 * math.cos(math.pi / (N + 1))
+    assert abs(lmax / lmin - 1711.7) < 0.1
+    bound = cg_bound(lmax / lmin, 1e-8)
+    assert bound == 473
+    A = I.lap2d5(N)
+    xs = I.xstar(A.n, 1)
+    b = orc.spmv(A, xs)
+    r = orc.pcg(A, b, rtol=1e-8, maxit=2000)
+    assert r["status"] == orc.CONVERGED and 50 < r["iters"] <= bound
+    tr = b - orc.spmv(A, r["x"])
+    assert np.linalg.norm(tr) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-3)
+    assert np.linalg.norm(r["x"] - xs) <= (lmax / lmin) * 1e-8 * np.linalg.norm(xs)
+
+
+def test_pcg_iteration_bound_3d(orc):
+    N = 24
+    c = math.cos(math.pi / (N + 1))
+    kappa = (6 + 6 * c) / (6 - 6 * c)
+    A = I.lap3d7(N)
+    b = orc.spmv(A, I.xstar(A.n, 2))
+    r = orc.pcg(A, b, rtol=1e-10, maxit=5000)
+    assert r["status"] == orc.CONVERGED and r["iters"] <= cg_bound(kappa, 1e-10)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: I.random_csr(200, 200, 5, seed=8, symmetric=True, diag_shift=0.1),
+    lambda: I.var27(6, 5, 4, seed=3, sigma=1.0),
+])
+def test_pcg_against_dense_solve(orc, maker):
+    A = maker()
+    d = A.to_dense()
+    b = I.uniform_pm1(9, 0, A.n)
+    r = orc.pcg(A, b, rtol=1e-12, maxit=10000)
+    assert r["status"] == orc.CONVERGED
+    ref = np.linalg.solve(d, b)
+    kappa = np.linalg.cond(d)
+    assert np.linalg.norm(r["x"] - ref) <= kappa * 1e-12 * 1.01 * np.linalg.norm(ref)
+    assert np.linalg.norm(b - d @ r["x"]) <= 1e-12 * np.linalg.norm(b) * (1 + 1e-3)
+
+
+def test_pcg_manufactured_solution(orc):
+    A = I.var27(10, seed=3, sigma=1.0)
+    xs = I.xstar(A.n, 3)
+    b = orc.spmv(A, xs)
+    r = orc.pcg(A, b, rtol=1e-12, maxit=10000)
+    assert r["status"] == orc.CONVERGED
+    assert np.linalg.norm(r["x"] - xs) <= 1e-7 * np.linalg.norm(xs)
+
+
+def test_pcg_diagonal_matrix_one_step(orc):
+    # Jacobi is the exact inverse of a diagonal operator: one iteration
+    n = 50
+    dvals = 0.5 + 10 * I.uniform01(4, 0, np.arange(n))
+    A = I.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), dvals)
+    b = I.uniform_pm1(4, 1, n)
+    r = orc.pcg(A, b, rtol=1e-14, maxit=10)
+    assert r["status"] == orc.CONVERGED and r["iters"] == 1
+    assert np.allclose(r["x"], b / dvals, rtol=1e-15, atol=0)
+
+
+def test_pcg_degenerate_cases(orc):
+    A = I.lap2d5(5)
+    # zero right-hand side: converged before any iteration, x stays 0
+    r = orc.pcg(A, np.zeros(A.n), 1e-8, 100)
+    assert r["status"] == orc.CONVERGED and r["iters"] == 0 and not r["x"].any()
+    # initial guess equal to the solution
+    xs = I.xstar(A.n, 2)
+    b = orc.spmv(A, xs)
+    r = orc.pcg(A, b, 1e-8, 100, x0=xs)
+    assert r["status"] == orc.CONVERGED and r["iters"] == 0
+    # iteration limit
+    r = orc.pcg(A, b, 1e-14, 3)
+    assert r["status"] == orc.DIVERGED_ITS and r["iters"] == 3
+    # empty system
+    E = I.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert orc.pcg(E, np.zeros(0), 1e-8, 10)["status"] == orc.CONVERGED
+    # NaN in the right-hand side
+    bn = b.copy(); bn[3] = np.nan
+    assert orc.pcg(A, bn, 1e-8, 10)["status"] == orc.ERR_NAN
+    # indefinite with a positive diagonal: [[1, 2], [2, 1]] has eigenvalue -1
+    B = I.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+              np.array([1.0, 2.0, 2.0, 1.0]))
+    assert orc.pcg(B, np.array([1.0, -1.0]), 1e-10, 10)["status"] == orc.ERR_INDEFINITE
+    # non-positive and missing diagonals
+    C = I.CSR(2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, -2.0]))
+    assert orc.pcg(C, np.ones(2), 1e-10, 10)["status"] == orc.ERR_DIAG
+    M = I.CSR(2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, 1.0]))
+    assert orc.pcg(M, np.ones(2), 1e-10, 10)["status"] == orc.ERR_DIAG
+
+
+# ------------------------------------------------------- mixed precision --
+
+def test_pcg_f32_close_to_fp64(orc):
+    A = I.var7(10, 10, 10, seed=3)
+    b = I.uniform_pm1(1, 0, A.n)
+    r32 = orc.pcg_f32(A, b, 1e-5, 5000)
+    r64 = orc.pcg(A, b, 1e-5, 5000)
+    assert r32["status"] == orc.CONVERGED
+    assert abs(r32["iters"] - r64["iters"]) <= 3
+    ref = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(r32["x"] - ref) <= 1e-3 * np.linalg.norm(ref)
+
+
+def test_mixed_refinement_reaches_fp64_accuracy(orc):
+    A = I.var27(12, seed=3, sigma=1.0)
+    xs = I.xstar(A.n, 3)
+    b = orc.spmv(A, xs)
+    ref = orc.pcg(A, b, 1e-10, 10000)
+    m = orc.pcg_mixed(A, b, 1e-10, inner_rtol=1e-4)
+    assert m["status"] == orc.CONVERGED
+    # true FP64 residual by construction
+    assert np.linalg.norm(b - orc.spmv(A, m["x"])) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(m["x"] - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    # each outer step gains about inner_rtol: ceil(log(rtol)/log(eta)) + 2
+    assert m["outer"] <= math.ceil(math.log(1e-10) / math.log(1e-4)) + 2
+
+
+def test_mixed_zero_rhs_and_bad_diag(orc):
+    A = I.lap2d5(4)
+    m = orc.pcg_mixed(A, np.zeros(A.n), 1e-10)
+    assert m["status"] == orc.CONVERGED and m["outer"] == 0
+    C = I.CSR(2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 0.0]))
+    assert orc.pcg_mixed(C, np.ones(2), 1e-10)["status"] == orc.ERR_DIAG
