@@ -1,0 +1,332 @@
+/*
+ * gbs.h -- C ABI of the GB300 Jacobi-preconditioned CG library.
+ *
+ * The library solves A x = b for a sparse symmetric positive definite A in
+ * compressed sparse row (AIJ) form with the conjugate-gradient method and a
+ * Jacobi (diagonal) preconditioner, entirely on one GPU.  The objects and
+ * calls follow the PETSc usage the paper describes: objects are created,
+ * filled with data, then handed to a solver (Sec. 2, Listing 1); every call
+ * returns an error code and passes outputs through pointers (Sec. 2,
+ * Listing 4: VecAXPY(rk,-1.0,r), VecNorm(rk,NORM_2,&norm)); a Mat of type
+ * MATAIJ holds CSR data and Vec holds a dense vector (Sec. 4).
+ *
+ * Conventions for every function below:
+ *  - Return value: GBS_OK (0) on success, a positive status for a solve that
+ *    ended without converging but left valid output, or a negative GBS_ERR_*
+ *    code.  On a negative code no output argument is written unless stated.
+ *  - Handles are opaque pointers owned by the library; *_destroy frees them
+ *    and accepts NULL.  A handle must not be used after its context is
+ *    destroyed.
+ *  - Index arrays are int32 (rowptr has nrows+1 entries, colidx nnz
+ *    entries); vector lengths and sizes are int64.
+ *  - "memspace" says where a caller pointer lives: GBS_MEM_HOST (pageable or
+ *    pinned host memory) or GBS_MEM_DEVICE (device memory of the context's
+ *    GPU).  The library never queries pointer attributes (Sec. 3, Challenge
+ *    A5: those queries cost about 0.3 us each); the caller states it.
+ *  - Work is queued on the context's CUDA stream.  Calls that return host
+ *    scalars (dot, norm, solve results) synchronise that stream; all others
+ *    are asynchronous with respect to the host.
+ *  - Not thread-safe per context: one host thread drives a context at a time.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status --- */
+enum {
+    GBS_OK = 0,
+    GBS_DIVERGED_ITS = 1,      /* iteration limit reached; x holds the last iterate */
+    GBS_ERR_ARG = -1,          /* bad argument: NULL, size mismatch, aliasing, dtype */
+    GBS_ERR_OOM = -2,          /* device or pinned host allocation failed */
+    GBS_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    GBS_ERR_DIAG = -4,         /* Jacobi: a diagonal entry is missing or <= 0 */
+    GBS_ERR_INDEFINITE = -5,   /* CG breakdown: p.Ap <= 0 or r.z < 0 */
+    GBS_ERR_NAN = -6,          /* a NaN appeared in a solver scalar */
+    GBS_ERR_TIMEOUT = -7,      /* a device-side wait gave up (cooperative barrier) */
+    GBS_ERR_STAGNATION = -8,   /* mixed mode: an outer step reduced ||r|| by less than 2x */
+    GBS_ERR_BUDGET = -9,       /* server: the request alone exceeds the memory budget */
+    GBS_ERR_CSR = -10,         /* malformed CSR: rowptr, column range or order */
+    GBS_ERR_NOT_FOUND = -11,   /* server: unknown ticket */
+    GBS_ERR_UNSUPPORTED = -12  /* valid request the library does not implement */
+};
+
+enum { GBS_MEM_HOST = 0, GBS_MEM_DEVICE = 1 };
+enum { GBS_F64 = 0, GBS_F32 = 1 };
+
+/* Precision of a solve (Response A7, Sec. 4: single precision on the GPU,
+ * with the flags carried by the solve). */
+enum {
+    GBS_MODE_FP64 = 0,   /* every step in FP64 */
+    GBS_MODE_MIXED = 1   /* FP32 inner PCG (FP32 SpMV, vectors and reductions)
+                            inside FP64 iterative refinement: FP64 is kept
+                            for r = b - A x, the update x += s d and the
+                            convergence norms */
+};
+
+/* How a solve is launched. */
+enum {
+    GBS_ALG_AUTO = 0,        /* library choice */
+    GBS_ALG_PERSISTENT = 1,  /* one cooperative kernel per solve; the iteration
+                                loop, reductions and convergence test run on
+                                the device (Challenge A1: no host round trip
+                                per dot product) */
+    GBS_ALG_PEROP = 2,       /* one kernel per vector/matrix operation, scalars
+                                kept on the device, convergence read by the
+                                host every iteration: the library-call-per-op
+                                pattern of PETSc's GPU back-end */
+    GBS_ALG_GRAPH = 3        /* GBS_ALG_PEROP's kernels captured once into a
+                                CUDA graph of several iterations and replayed
+                                (Challenge A1: CUDA graphs) */
+};
+
+typedef struct gbs_ctx_s *gbs_ctx;
+typedef struct gbs_mat_s *gbs_mat;
+typedef struct gbs_vec_s *gbs_vec;
+typedef struct gbs_pc_s *gbs_pc;
+typedef struct gbs_server_s *gbs_server;
+
+/* Solver options.  gbs_opts_default fills the defaults noted per field. */
+typedef struct {
+    int mode;                /* GBS_MODE_FP64 (default) or GBS_MODE_MIXED */
+    int algorithm;           /* GBS_ALG_* (default GBS_ALG_AUTO) */
+    double inner_rtol;       /* MIXED: relative tolerance of each FP32 inner
+                                solve (default 1e-4) */
+    int outer_maxit;         /* MIXED: refinement steps at most (default 30) */
+    int barrier_timeout_ms;  /* device-side waits give up after this many
+                                milliseconds with GBS_ERR_TIMEOUT (default 2000) */
+    int graph_iters;         /* GBS_ALG_GRAPH: iterations per captured graph (default 16) */
+    int fault_skip_arrival;  /* testing only: if >= 0, that CTA of the next
+                                persistent solve does not arrive at its first
+                                grid barrier, so the barrier times out (default -1) */
+    int reserved[8];
+} gbs_opts;
+
+/* Result of the last solve on a context. */
+typedef struct {
+    int status;          /* GBS_OK, GBS_DIVERGED_ITS or a negative GBS_ERR_* */
+    int iters;           /* CG iterations (SpMVs after set-up); MIXED: summed
+                            over all inner solves */
+    int outer_iters;     /* MIXED: refinement steps; FP64: 0 */
+    double rnorm;        /* final ||r||_2: recurrence residual in FP64 mode,
+                            true FP64 residual ||b - A x||_2 in MIXED mode */
+    double bnorm;        /* ||b||_2 */
+    double device_ms;    /* device time of the solve (CUDA events) */
+} gbs_solve_info;
+
+/* Library version string (static storage). */
+const char *gbs_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *gbs_status_string(int status);
+
+/* Fill *opts with the defaults.  GBS_ERR_ARG if opts is NULL. */
+int gbs_opts_default(gbs_opts *opts);
+
+/* ----------------------------------------------------------- context --- */
+
+/* Create a context bound to CUDA device `device` and the CUDA stream
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream is borrowed: the caller keeps it alive until gbs_ctx_destroy.
+ * `opts` may be NULL for defaults.  Errors: GBS_ERR_ARG, GBS_ERR_CUDA,
+ * GBS_ERR_OOM. */
+int gbs_ctx_create(int device, void *cuda_stream, const gbs_opts *opts, gbs_ctx *out);
+
+/* Destroy a context and the scratch memory it owns.  Matrices, vectors,
+ * preconditioners and servers created on it must be destroyed first. */
+int gbs_ctx_destroy(gbs_ctx ctx);
+
+/* Replace the context's stream (borrowed, as above). */
+int gbs_ctx_set_stream(gbs_ctx ctx, void *cuda_stream);
+
+/* Replace the context's default solver options (copied). */
+int gbs_ctx_set_opts(gbs_ctx ctx, const gbs_opts *opts);
+
+/* Block until all work queued on the context's stream has finished. */
+int gbs_ctx_synchronize(gbs_ctx ctx);
+
+/* Number of this library's kernel launches on the context so far (a
+ * counter kept by the host code; used to report launch counts). */
+int gbs_ctx_launch_count(gbs_ctx ctx, int64_t *count);
+
+/* ------------------------------------------------------------ matrix --- */
+
+/* MatCreate + MatSetType(MATAIJ) + fill (Sec. 4): copy a CSR matrix into
+ * library-owned device memory.  rowptr[nrows+1], colidx[nnz] (int32),
+ * vals[nnz] (FP64), nnz = rowptr[nrows]; all three arrays in `memspace`
+ * (host arrays are staged through pinned memory).  The caller keeps
+ * ownership of its arrays; the library keeps none of their pointers.
+ * Validation on the device: rowptr[0] = 0, rowptr non-decreasing, every
+ * column in [0, ncols), columns strictly increasing within a row
+ * (GBS_ERR_CSR otherwise).  The Jacobi diagonal D^-1 and the FP32 copy
+ * of the values (for GBS_MODE_MIXED) are prepared here as well.
+ * Errors: GBS_ERR_ARG, GBS_ERR_CSR, GBS_ERR_OOM, GBS_ERR_CUDA. */
+int gbs_mat_create_aij(gbs_ctx ctx, int64_t nrows, int64_t ncols, const int32_t *rowptr,
+                       const int32_t *colidx, const double *vals, int memspace, gbs_mat *out);
+
+/* Replace the values of an existing matrix (same sparsity pattern), e.g. a
+ * new Jacobian with the old structure.  vals[nnz] in `memspace`. */
+int gbs_mat_set_values(gbs_mat A, const double *vals, int memspace);
+
+/* Sizes of a matrix; any output pointer may be NULL. */
+int gbs_mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz);
+
+/* Free a matrix (NULL is allowed). */
+int gbs_mat_destroy(gbs_mat A);
+
+/* MatMult: y = A x.  x has ncols entries, y has nrows entries, same dtype
+ * (GBS_F64 uses the FP64 values, GBS_F32 the FP32 copy).  y must not alias
+ * x (GBS_ERR_ARG).  Asynchronous. */
+int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y);
+
+/* ------------------------------------------------------------ vector --- */
+
+/* VecCreate: a device vector of n entries of `dtype`, owned by the library,
+ * zero-filled.  Errors: GBS_ERR_ARG, GBS_ERR_OOM. */
+int gbs_vec_create(gbs_ctx ctx, int64_t n, int dtype, gbs_vec *out);
+
+/* Wrap caller-owned device memory (n entries of `dtype`) without copying
+ * (VecCreate...WithArray, Sec. 2).  The caller keeps ownership and must keep
+ * the memory alive until gbs_vec_destroy.  dev_ptr must be aligned to the
+ * element size (GBS_ERR_ARG otherwise). */
+int gbs_vec_wrap(gbs_ctx ctx, void *dev_ptr, int64_t n, int dtype, gbs_vec *out);
+
+/* Free a vector handle (and its memory if the library owns it). */
+int gbs_vec_destroy(gbs_vec v);
+
+/* Length and device pointer of a vector (outputs may be NULL). */
+int gbs_vec_get_info(gbs_vec v, int64_t *n, int *dtype, void **dev_ptr);
+
+/* Copy n entries of the vector's dtype from `src` (in `memspace`) into v.
+ * Asynchronous for device and pinned host sources. */
+int gbs_vec_set_values(gbs_vec v, const void *src, int memspace);
+
+/* Copy the vector's n entries into `dst` (in `memspace`).  Synchronises the
+ * stream when dst is host memory. */
+int gbs_vec_get_values(gbs_vec v, void *dst, int memspace);
+
+/* VecSet: v_i = alpha. */
+int gbs_vec_set(gbs_vec v, double alpha);
+
+/* VecCopy: y <- x (same length; dtypes may differ, converting on the GPU). */
+int gbs_vec_copy(gbs_vec x, gbs_vec y);
+
+/* VecAXPY: y <- alpha x + y (Sec. 5.1: 2 flops, 3 memory accesses per entry). */
+int gbs_vec_axpy(gbs_vec y, double alpha, gbs_vec x);
+
+/* VecAYPX: y <- x + beta y. */
+int gbs_vec_aypx(gbs_vec y, double beta, gbs_vec x);
+
+/* VecPointwiseMult: w_i = x_i y_i. */
+int gbs_vec_pointwise_mult(gbs_vec w, gbs_vec x, gbs_vec y);
+
+/* VecDot: *out = x . y, reduced on the device in a fixed order (so repeated
+ * calls give identical bits).  FP32 vectors accumulate in FP32.
+ * Synchronises the stream. */
+int gbs_vec_dot(gbs_vec x, gbs_vec y, double *out);
+
+/* VecNorm(NORM_2): *out = ||x||_2.  Synchronises the stream. */
+int gbs_vec_norm2(gbs_vec x, double *out);
+
+/* ---------------------------------------------------- preconditioner --- */
+
+/* PCJACOBI (Sec. 5.3): z = D^-1 r with D = diag(A).  GBS_ERR_DIAG if a
+ * diagonal entry is missing or not positive.  The pc borrows A. */
+int gbs_pc_jacobi_create(gbs_mat A, gbs_pc *out);
+
+/* PCApply: z = D^-1 r (vectors of A's size, same dtype). */
+int gbs_pc_apply(gbs_pc pc, gbs_vec r, gbs_vec z);
+
+int gbs_pc_destroy(gbs_pc pc);
+
+/* ------------------------------------------------------------ solver --- */
+
+/* KSPSolve with KSPCG + PCJACOBI (Sec. 5.5, Sec. 5.3), using the context's
+ * options.  b (FP64, nrows) is read; x (FP64, nrows) is the initial guess on
+ * entry and the solution on exit.  Stops when ||r||_2 <= rtol ||b||_2 (the
+ * test is taken before each iteration) or after maxit iterations.
+ * Returns GBS_OK (converged), GBS_DIVERGED_ITS (limit reached, x valid) or
+ * GBS_ERR_DIAG / GBS_ERR_INDEFINITE / GBS_ERR_NAN / GBS_ERR_TIMEOUT /
+ * GBS_ERR_STAGNATION / GBS_ERR_ARG / GBS_ERR_CUDA.  iters and rnorm may be
+ * NULL.  Synchronises the stream once, at the end. */
+int gbs_ksp_solve_cg(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, int *iters,
+                     double *rnorm);
+
+/* The same with explicit options (NULL = the context's) and the full
+ * result in *info (may be NULL). */
+int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
+                        const gbs_opts *opts, gbs_solve_info *info);
+
+/* Result of the last solve issued on the context. */
+int gbs_ksp_last_info(gbs_ctx ctx, gbs_solve_info *info);
+
+/* Batched solve of independent systems in one persistent launch (Response
+ * A6, Sec. 4: many different-size problems at once; Challenge F2 / Sec. 4:
+ * multiple right-hand sides raise arithmetic intensity).  System s has
+ * matrix A[s] (all on ctx), right-hand sides B[s] and solutions X[s]:
+ * FP64 vectors of nrows(A[s]) * nrhs[s] entries, column-major (column c at
+ * offset c * nrows).  X[s] holds the initial guesses on entry.  Each
+ * column is an independent CG solve with tolerance rtol[s].  Results per
+ * (system, column), flattened in system order: iters[], rnorm[], status[]
+ * each with sum(nrhs) entries (any may be NULL).  Returns GBS_OK if every
+ * column converged, else the first non-zero column status.  `mode` is
+ * GBS_MODE_FP64 or GBS_MODE_MIXED.  Each column's result is independent of
+ * the other systems in the batch. */
+int gbs_ksp_solve_cg_batched(gbs_ctx ctx, int nsys, const gbs_mat *A, const gbs_vec *B,
+                             gbs_vec *X, const int *nrhs, const double *rtol, int maxit,
+                             int mode, int *iters, double *rnorm, int *status);
+
+/* ----------------------------------------------------------- serving --- */
+
+/* A serving engine: solve requests are admitted against a device-memory
+ * budget, their CSR and Krylov state stay on the device, and a persistent
+ * batched kernel advances all admitted requests together; requests that
+ * arrive while others run join as slots and memory free up (continuous
+ * batching).  hbm_budget_bytes bounds the device memory held by admitted
+ * requests.  max_slots bounds concurrent requests (0 = library default). */
+int gbs_server_create(gbs_ctx ctx, size_t hbm_budget_bytes, int max_slots, int mode,
+                      gbs_server *out);
+
+int gbs_server_destroy(gbs_server srv);
+
+/* Submit a request: host CSR (rowptr/colidx/vals as in gbs_mat_create_aij),
+ * k right-hand sides b[nrows * k] (host, column-major), tolerance rtol,
+ * iteration limit maxit.  The arrays are copied before return.  Returns a
+ * ticket in *ticket.  GBS_ERR_BUDGET if the request alone can never fit the
+ * budget; otherwise it is queued until memory and a slot are free. */
+int gbs_server_submit(gbs_server srv, int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
+                      const double *vals, int k, const double *b, double rtol, int maxit,
+                      uint64_t *ticket);
+
+/* Advance the engine without blocking for long: admit queued requests,
+ * launch or continue device work, retire finished requests.  Returns the
+ * number of requests retired by this call in *retired (may be NULL). */
+int gbs_server_progress(gbs_server srv, int *retired);
+
+/* *done = 1 if the request has finished (its result can be fetched). */
+int gbs_server_poll(gbs_server srv, uint64_t ticket, int *done);
+
+/* Drive the engine until the request has finished. */
+int gbs_server_wait(gbs_server srv, uint64_t ticket);
+
+/* Copy a finished request's solution (host, nrows * k, column-major) and
+ * per-column iters/rnorm/status (k entries each; any may be NULL), then
+ * release it.  GBS_ERR_NOT_FOUND for unknown or already fetched tickets. */
+int gbs_server_fetch(gbs_server srv, uint64_t ticket, double *x, int *iters, double *rnorm,
+                     int *status);
+
+/* Engine counters: queued, running and finished requests, device bytes in
+ * use (outputs may be NULL). */
+int gbs_server_stats(gbs_server srv, int *queued, int *running, int *finished,
+                     size_t *bytes_in_use);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBS_H */

@@ -1,0 +1,784 @@
+// Contexts, CSR matrices, vectors, Jacobi preconditioner, vector kernels
+// and MatMult of the GB300 Jacobi-PCG library.
+//
+// Objects follow the PETSc front-end the paper describes (Sec. 4: Mat of
+// type MATAIJ, Vec; Sec. 2: create, fill, solve).  Every kernel here is
+// bandwidth-bound: no tensor cores (the path is sparse), coalesced loads,
+// grids sized in multiples of the SM count.
+
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "gbs_impl.cuh"
+
+static const char *kVersion = "gbs 0.1 (sm_103a)";
+
+int gbs_cuda_fail(cudaError_t e)
+{
+    (void)cudaGetLastError();  // clear a sticky launch error where possible
+    if (e == cudaErrorMemoryAllocation) return GBS_ERR_OOM;
+    return GBS_ERR_CUDA;
+}
+
+extern "C" const char *gbs_version(void) { return kVersion; }
+
+extern "C" const char *gbs_status_string(int s)
+{
+    switch (s) {
+    case GBS_OK: return "converged";
+    case GBS_DIVERGED_ITS: return "iteration limit reached";
+    case GBS_ERR_ARG: return "bad argument";
+    case GBS_ERR_OOM: return "out of memory";
+    case GBS_ERR_CUDA: return "CUDA error";
+    case GBS_ERR_DIAG: return "diagonal entry missing or not positive";
+    case GBS_ERR_INDEFINITE: return "indefinite operator or preconditioner";
+    case GBS_ERR_NAN: return "NaN in a solver scalar";
+    case GBS_ERR_TIMEOUT: return "device-side wait timed out";
+    case GBS_ERR_STAGNATION: return "iterative refinement stagnated";
+    case GBS_ERR_BUDGET: return "request exceeds the memory budget";
+    case GBS_ERR_CSR: return "malformed CSR matrix";
+    case GBS_ERR_NOT_FOUND: return "unknown ticket";
+    case GBS_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int gbs_opts_default(gbs_opts *o)
+{
+    if (!o) return GBS_ERR_ARG;
+    memset(o, 0, sizeof(*o));
+    o->mode = GBS_MODE_FP64;
+    o->algorithm = GBS_ALG_AUTO;
+    o->inner_rtol = 1e-4;
+    o->outer_maxit = 30;
+    o->barrier_timeout_ms = 2000;
+    o->graph_iters = 16;
+    o->fault_skip_arrival = -1;
+    return GBS_OK;
+}
+
+static int opts_valid(const gbs_opts *o)
+{
+    if (o->mode != GBS_MODE_FP64 && o->mode != GBS_MODE_MIXED) return 0;
+    if (o->algorithm < GBS_ALG_AUTO || o->algorithm > GBS_ALG_GRAPH) return 0;
+    if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)) return 0;
+    if (o->outer_maxit < 0 || o->barrier_timeout_ms <= 0 || o->graph_iters <= 0) return 0;
+    return 1;
+}
+
+void gbs_count_launch(gbs_ctx ctx, int n) { ctx->launches += n; }
+
+// ------------------------------------------------------------------ ctx --
+
+extern "C" int gbs_ctx_create(int device, void *stream, const gbs_opts *opts, gbs_ctx *out)
+{
+    if (!out) return GBS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    GBS_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return GBS_ERR_ARG;
+    gbs_opts o;
+    gbs_opts_default(&o);
+    if (opts) {
+        if (!opts_valid(opts)) return GBS_ERR_ARG;
+        o = *opts;
+    }
+    GBS_CUDA_TRY(cudaSetDevice(device));
+    gbs_ctx c = (gbs_ctx)calloc(1, sizeof(*c));
+    if (!c) return GBS_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    c->opts = o;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess) {
+        c->num_sms = prop.multiProcessorCount;
+        c->coop_supported = prop.cooperativeLaunch;
+        e = cudaMallocHost(&c->pinned, 4096);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->devsmall, 4096);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        if (c->pinned) cudaFreeHost(c->pinned);
+        if (c->devsmall) cudaFree(c->devsmall);
+        free(c);
+        return gbs_cuda_fail(e);
+    }
+    c->last.status = GBS_OK;
+    *out = c;
+    return GBS_OK;
+}
+
+extern "C" int gbs_ctx_destroy(gbs_ctx c)
+{
+    if (!c) return GBS_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->devsmall) cudaFree(c->devsmall);
+    cudaEventDestroy(c->ev0);
+    cudaEventDestroy(c->ev1);
+    free(c);
+    return GBS_OK;
+}
+
+extern "C" int gbs_ctx_set_stream(gbs_ctx c, void *stream)
+{
+    if (!c) return GBS_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return GBS_OK;
+}
+
+extern "C" int gbs_ctx_set_opts(gbs_ctx c, const gbs_opts *o)
+{
+    if (!c || !o || !opts_valid(o)) return GBS_ERR_ARG;
+    c->opts = *o;
+    return GBS_OK;
+}
+
+extern "C" int gbs_ctx_synchronize(gbs_ctx c)
+{
+    if (!c) return GBS_ERR_ARG;
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GBS_OK;
+}
+
+extern "C" int gbs_ctx_launch_count(gbs_ctx c, int64_t *count)
+{
+    if (!c || !count) return GBS_ERR_ARG;
+    *count = c->launches;
+    return GBS_OK;
+}
+
+int gbs_ctx_reserve(gbs_ctx c, size_t bytes, void **out)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes > c->scratch_bytes) {
+        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (c->scratch) cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+        GBS_CUDA_TRY(cudaMalloc(&c->scratch, bytes));
+        c->scratch_bytes = bytes;
+    }
+    *out = c->scratch;
+    return GBS_OK;
+}
+
+// --------------------------------------------------------------- matrix --
+
+// Per-row structure check and Jacobi set-up: one thread per row.
+// flags bit 0: malformed CSR; bit 1: a diagonal missing or <= 0.
+__global__ void k_csr_validate(int64_t n, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                               const int32_t *colidx, const double *vals, double *dinv,
+                               float *dinv32, int *flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bad = 0;
+    const int32_t b = rowptr[i], e = rowptr[i + 1];
+    if (i == 0 && b != 0) bad |= 1;
+    if (e < b || b < 0 || (int64_t)e > nnz) bad |= 1;
+    double d = 0.0;
+    int found = 0;
+    if (!(bad & 1)) {
+        int32_t prev = -1;
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t c = colidx[k];
+            if (c < 0 || c >= ncols || c <= prev) { bad |= 1; break; }
+            prev = c;
+            if (c == i) { d = vals[k]; found = 1; }
+        }
+    }
+    if (!found || !(d > 0.0)) {
+        bad |= 2;
+        dinv[i] = 0.0;
+        dinv32[i] = 0.0f;
+    } else {
+        dinv[i] = 1.0 / d;
+        dinv32[i] = (float)(1.0 / d);
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+__global__ void k_diag_refresh(int64_t n, const int32_t *rowptr, const int32_t *colidx,
+                               const double *vals, double *dinv, float *dinv32, int *flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    int found = 0;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+        if (colidx[k] == i) { d = vals[k]; found = 1; }
+    if (!found || !(d > 0.0)) {
+        dinv[i] = 0.0;
+        dinv32[i] = 0.0f;
+        atomicOr(flags, 2);
+    } else {
+        dinv[i] = 1.0 / d;
+        dinv32[i] = (float)(1.0 / d);
+    }
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double *a, float *b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+static int grid_for(gbs_ctx c, int64_t n, int per_sm = 4)
+{
+    int64_t g = (n + GBS_BLOCK - 1) / GBS_BLOCK;
+    const int64_t cap = (int64_t)c->num_sms * per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+// Split rows into tiles: at most GBS_TILE_ROWS rows and GBS_TILE_NNZ
+// nonzeros each; a longer row is a tile of its own.
+static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &tiles, int *maxrow)
+{
+    tiles.clear();
+    tiles.push_back(0);
+    int64_t start = 0;
+    int mr = 0;
+    while (start < n) {
+        int64_t end = start;
+        while (end < n && end - start < GBS_TILE_ROWS) {
+            const int64_t rn = rowptr[end + 1] - rowptr[end];
+            if (rn > mr) mr = (int)rn;
+            if (end > start && rowptr[end + 1] - rowptr[start] > GBS_TILE_NNZ) break;
+            ++end;
+            if (rn > GBS_TILE_NNZ) break;  // a long row stays alone
+        }
+        tiles.push_back((int32_t)end);
+        start = end;
+    }
+    *maxrow = mr;
+}
+
+static void mat_free(gbs_mat A)
+{
+    if (!A) return;
+    cudaFree(A->rowptr);
+    cudaFree(A->colidx);
+    cudaFree(A->vals);
+    cudaFree(A->vals32);
+    cudaFree(A->dinv);
+    cudaFree(A->dinv32);
+    cudaFree(A->tiles);
+    free(A);
+}
+
+extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const int32_t *rowptr,
+                                  const int32_t *colidx, const double *vals, int memspace,
+                                  gbs_mat *out)
+{
+    if (!c || !out || nrows < 0 || ncols < 0 || !rowptr) return GBS_ERR_ARG;
+    if (memspace != GBS_MEM_HOST && memspace != GBS_MEM_DEVICE) return GBS_ERR_ARG;
+    if (nrows >= (int64_t)INT32_MAX || ncols >= (int64_t)INT32_MAX) return GBS_ERR_ARG;
+    *out = nullptr;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    // the row pointers are needed on the host for tiling
+    std::vector<int32_t> hrp((size_t)nrows + 1);
+    if (memspace == GBS_MEM_HOST) {
+        memcpy(hrp.data(), rowptr, sizeof(int32_t) * (nrows + 1));
+    } else {
+        GBS_CUDA_TRY(cudaMemcpyAsync(hrp.data(), rowptr, sizeof(int32_t) * (nrows + 1),
+                                     cudaMemcpyDeviceToHost, c->stream));
+        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    if (hrp[0] != 0) return GBS_ERR_CSR;
+    for (int64_t i = 0; i < nrows; ++i)
+        if (hrp[i + 1] < hrp[i]) return GBS_ERR_CSR;
+    const int64_t nnz = hrp[nrows];
+    if (nnz > 0 && (!colidx || !vals)) return GBS_ERR_ARG;
+
+    gbs_mat A = (gbs_mat)calloc(1, sizeof(*A));
+    if (!A) return GBS_ERR_OOM;
+    A->ctx = c;
+    A->n = nrows;
+    A->ncols = ncols;
+    A->nnz = nnz;
+    std::vector<int32_t> tiles;
+    make_tiles(hrp.data(), nrows, tiles, &A->max_row_nnz);
+    A->ntiles = (int64_t)tiles.size() - 1;
+    // allocations padded to 16 bytes so vector loads never leave the buffer
+    const size_t pad_nnz = (size_t)((nnz + 4) & ~(int64_t)3);
+    const size_t pad_n = (size_t)((nrows + 4) & ~(int64_t)3);
+    cudaError_t e = cudaMalloc(&A->rowptr, sizeof(int32_t) * (pad_n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&A->colidx, sizeof(int32_t) * pad_nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&A->vals, sizeof(double) * pad_nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&A->dinv, sizeof(double) * pad_n);
+    if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
+    if (e == cudaSuccess) e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(A->colidx, 0, sizeof(int32_t) * pad_nnz, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A->vals, 0, sizeof(double) * pad_nnz, c->stream);
+    const cudaMemcpyKind kind =
+        memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(A->rowptr, hrp.data(), sizeof(int32_t) * (nrows + 1),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(A->colidx, colidx, sizeof(int32_t) * nnz, kind, c->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(A->vals, vals, sizeof(double) * nnz, kind, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(A->tiles, tiles.data(), sizeof(int32_t) * tiles.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    int *devflags = (int *)c->devsmall;
+    if (e == cudaSuccess) e = cudaMemsetAsync(devflags, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess && nrows > 0) {
+        const int g = (int)((nrows + 255) / 256);
+        k_csr_validate<<<g, 256, 0, c->stream>>>(nrows, ncols, nnz, A->rowptr, A->colidx,
+                                                  A->vals, A->dinv, A->dinv32, devflags);
+        gbs_count_launch(c);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pinned, devflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        mat_free(A);
+        return gbs_cuda_fail(e);
+    }
+    const int flags = *(volatile int *)c->pinned;
+    if (flags & 1) {
+        mat_free(A);
+        return GBS_ERR_CSR;
+    }
+    A->diag_ok = (flags & 2) ? 0 : 1;
+    if (nrows != ncols) A->diag_ok = 0;
+    *out = A;
+    return GBS_OK;
+}
+
+int gbs_mat_ensure_f32(gbs_mat A)
+{
+    if (A->vals32 || A->nnz == 0) {
+        if (!A->vals32) GBS_CUDA_TRY(cudaMalloc(&A->vals32, 16));
+        return GBS_OK;
+    }
+    gbs_ctx c = A->ctx;
+    const size_t pad_nnz = (size_t)((A->nnz + 4) & ~(int64_t)3);
+    GBS_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float) * pad_nnz));
+    GBS_CUDA_TRY(cudaMemsetAsync(A->vals32, 0, sizeof(float) * pad_nnz, c->stream));
+    k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals, A->vals32);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+extern "C" int gbs_mat_set_values(gbs_mat A, const double *vals, int memspace)
+{
+    if (!A || (!vals && A->nnz > 0)) return GBS_ERR_ARG;
+    if (memspace != GBS_MEM_HOST && memspace != GBS_MEM_DEVICE) return GBS_ERR_ARG;
+    gbs_ctx c = A->ctx;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    if (A->nnz > 0)
+        GBS_CUDA_TRY(cudaMemcpyAsync(A->vals, vals, sizeof(double) * A->nnz,
+                                     memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice
+                                                              : cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    int *devflags = (int *)c->devsmall;
+    GBS_CUDA_TRY(cudaMemsetAsync(devflags, 0, sizeof(int), c->stream));
+    if (A->n > 0) {
+        k_diag_refresh<<<(int)((A->n + 255) / 256), 256, 0, c->stream>>>(
+            A->n, A->rowptr, A->colidx, A->vals, A->dinv, A->dinv32, devflags);
+        gbs_count_launch(c);
+        GBS_CUDA_TRY(cudaGetLastError());
+    }
+    if (A->vals32 && A->nnz > 0) {
+        k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals,
+                                                                       A->vals32);
+        gbs_count_launch(c);
+        GBS_CUDA_TRY(cudaGetLastError());
+    }
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, devflags, sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    A->diag_ok = ((*(volatile int *)c->pinned) & 2) || A->n != A->ncols ? 0 : 1;
+    return GBS_OK;
+}
+
+extern "C" int gbs_mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz)
+{
+    if (!A) return GBS_ERR_ARG;
+    if (nrows) *nrows = A->n;
+    if (ncols) *ncols = A->ncols;
+    if (nnz) *nnz = A->nnz;
+    return GBS_OK;
+}
+
+extern "C" int gbs_mat_destroy(gbs_mat A)
+{
+    if (!A) return GBS_OK;
+    cudaSetDevice(A->ctx->device);
+    cudaStreamSynchronize(A->ctx->stream);
+    mat_free(A);
+    return GBS_OK;
+}
+
+// ------------------------------------------------------------- MatMult --
+
+template <typename V>
+struct StoreEpi {
+    V *y;
+    __device__ __forceinline__ void operator()(int64_t row, V s) const { y[row] = s; }
+};
+
+template <typename V>
+__global__ void __launch_bounds__(GBS_BLOCK) k_spmv(int64_t ntiles, const int32_t *tiles,
+                                                    const int32_t *rowptr, const int32_t *colidx,
+                                                    const V *vals, const V *x, V *y)
+{
+    __shared__ GbsTile<V> tl;
+    __shared__ V s_red[GBS_WARPS];
+    StoreEpi<V> epi{y};
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+        gbs_spmv_tile<V>(rowptr, colidx, vals, x, tiles[t], tiles[t + 1], tl, s_red, epi);
+}
+
+extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
+{
+    if (!A || !x || !y) return GBS_ERR_ARG;
+    if (x->n != A->ncols || y->n != A->n || x->dtype != y->dtype) return GBS_ERR_ARG;
+    if (x->data == y->data && A->n > 0) return GBS_ERR_ARG;
+    gbs_ctx c = A->ctx;
+    if (A->n == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const int64_t g64 = A->ntiles < (int64_t)c->num_sms * 8 ? A->ntiles : (int64_t)c->num_sms * 8;
+    const int g = (int)g64;
+    if (x->dtype == GBS_F64) {
+        k_spmv<double><<<g, GBS_BLOCK, 0, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx,
+                                                       A->vals, (const double *)x->data,
+                                                       (double *)y->data);
+    } else {
+        int st = gbs_mat_ensure_f32(A);
+        if (st) return st;
+        k_spmv<float><<<g, GBS_BLOCK, 0, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx,
+                                                      A->vals32, (const float *)x->data,
+                                                      (float *)y->data);
+    }
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+// --------------------------------------------------------------- vector --
+
+static size_t dsize(int dtype) { return dtype == GBS_F64 ? 8 : 4; }
+
+extern "C" int gbs_vec_create(gbs_ctx c, int64_t n, int dtype, gbs_vec *out)
+{
+    if (!c || !out || n < 0 || (dtype != GBS_F64 && dtype != GBS_F32)) return GBS_ERR_ARG;
+    *out = nullptr;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    gbs_vec v = (gbs_vec)calloc(1, sizeof(*v));
+    if (!v) return GBS_ERR_OOM;
+    const size_t bytes = dsize(dtype) * (size_t)((n + 4) & ~(int64_t)3);
+    cudaError_t e = cudaMalloc(&v->data, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->data, 0, bytes, c->stream);
+    if (e != cudaSuccess) {
+        if (v->data) cudaFree(v->data);
+        free(v);
+        return gbs_cuda_fail(e);
+    }
+    v->ctx = c;
+    v->n = n;
+    v->dtype = dtype;
+    v->owned = 1;
+    *out = v;
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_wrap(gbs_ctx c, void *ptr, int64_t n, int dtype, gbs_vec *out)
+{
+    if (!c || !out || n < 0 || (dtype != GBS_F64 && dtype != GBS_F32)) return GBS_ERR_ARG;
+    if (n > 0 && !ptr) return GBS_ERR_ARG;
+    if (((uintptr_t)ptr) % dsize(dtype) != 0) return GBS_ERR_ARG;
+    gbs_vec v = (gbs_vec)calloc(1, sizeof(*v));
+    if (!v) return GBS_ERR_OOM;
+    v->ctx = c;
+    v->data = ptr;
+    v->n = n;
+    v->dtype = dtype;
+    v->owned = 0;
+    *out = v;
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_destroy(gbs_vec v)
+{
+    if (!v) return GBS_OK;
+    if (v->owned && v->data) {
+        cudaSetDevice(v->ctx->device);
+        cudaStreamSynchronize(v->ctx->stream);
+        cudaFree(v->data);
+    }
+    free(v);
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_get_info(gbs_vec v, int64_t *n, int *dtype, void **p)
+{
+    if (!v) return GBS_ERR_ARG;
+    if (n) *n = v->n;
+    if (dtype) *dtype = v->dtype;
+    if (p) *p = v->data;
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_set_values(gbs_vec v, const void *src, int memspace)
+{
+    if (!v || (!src && v->n > 0)) return GBS_ERR_ARG;
+    if (memspace != GBS_MEM_HOST && memspace != GBS_MEM_DEVICE) return GBS_ERR_ARG;
+    if (v->n == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(v->ctx->device));
+    GBS_CUDA_TRY(cudaMemcpyAsync(v->data, src, dsize(v->dtype) * v->n,
+                                 memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice
+                                                          : cudaMemcpyDeviceToDevice,
+                                 v->ctx->stream));
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_get_values(gbs_vec v, void *dst, int memspace)
+{
+    if (!v || (!dst && v->n > 0)) return GBS_ERR_ARG;
+    if (memspace != GBS_MEM_HOST && memspace != GBS_MEM_DEVICE) return GBS_ERR_ARG;
+    if (v->n == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(v->ctx->device));
+    GBS_CUDA_TRY(cudaMemcpyAsync(dst, v->data, dsize(v->dtype) * v->n,
+                                 memspace == GBS_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                          : cudaMemcpyDeviceToDevice,
+                                 v->ctx->stream));
+    if (memspace == GBS_MEM_HOST) GBS_CUDA_TRY(cudaStreamSynchronize(v->ctx->stream));
+    return GBS_OK;
+}
+
+// Separately rounded multiply and add (no fused multiply-add), so each
+// standalone vector operation is the correctly rounded sequence of its
+// definition.
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+
+// Elementwise kernels.  op: 0 set, 1 copy(y=x), 2 axpy(y=a x+y), 3 aypx(y=x+a y),
+// 4 pointwise (y = x * w), 5 jacobi (y = dinv * x).
+template <typename TX, typename TY>
+__global__ void k_elementwise(int op, int64_t n, double a, const TX *__restrict__ x,
+                              const TY *__restrict__ w, TY *__restrict__ y)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        switch (op) {
+        case 0: y[i] = (TY)a; break;
+        case 1: y[i] = (TY)x[i]; break;
+        case 2: y[i] = rn_add(rn_mul((TY)a, (TY)x[i]), y[i]); break;
+        case 3: y[i] = rn_add((TY)x[i], rn_mul((TY)a, y[i])); break;
+        case 4: y[i] = rn_mul((TY)x[i], w[i]); break;
+        }
+    }
+}
+
+static int launch_elementwise(int op, gbs_vec y, double a, gbs_vec x, gbs_vec w)
+{
+    gbs_ctx c = y->ctx;
+    if (y->n == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const int g = grid_for(c, y->n, 8);
+    const void *xd = x ? x->data : nullptr;
+    const void *wd = w ? w->data : nullptr;
+    const int xt = x ? x->dtype : y->dtype;
+    if (y->dtype == GBS_F64) {
+        if (xt == GBS_F64)
+            k_elementwise<double, double><<<g, GBS_BLOCK, 0, c->stream>>>(
+                op, y->n, a, (const double *)xd, (const double *)wd, (double *)y->data);
+        else
+            k_elementwise<float, double><<<g, GBS_BLOCK, 0, c->stream>>>(
+                op, y->n, a, (const float *)xd, (const double *)wd, (double *)y->data);
+    } else {
+        if (xt == GBS_F64)
+            k_elementwise<double, float><<<g, GBS_BLOCK, 0, c->stream>>>(
+                op, y->n, a, (const double *)xd, (const float *)wd, (float *)y->data);
+        else
+            k_elementwise<float, float><<<g, GBS_BLOCK, 0, c->stream>>>(
+                op, y->n, a, (const float *)xd, (const float *)wd, (float *)y->data);
+    }
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_set(gbs_vec v, double a)
+{
+    if (!v) return GBS_ERR_ARG;
+    return launch_elementwise(0, v, a, nullptr, nullptr);
+}
+
+extern "C" int gbs_vec_copy(gbs_vec x, gbs_vec y)
+{
+    if (!x || !y || x->n != y->n || x->ctx != y->ctx) return GBS_ERR_ARG;
+    if (x->data == y->data) return GBS_OK;
+    return launch_elementwise(1, y, 0.0, x, nullptr);
+}
+
+extern "C" int gbs_vec_axpy(gbs_vec y, double a, gbs_vec x)
+{
+    if (!x || !y || x->n != y->n || x->dtype != y->dtype) return GBS_ERR_ARG;
+    return launch_elementwise(2, y, a, x, nullptr);
+}
+
+extern "C" int gbs_vec_aypx(gbs_vec y, double b, gbs_vec x)
+{
+    if (!x || !y || x->n != y->n || x->dtype != y->dtype) return GBS_ERR_ARG;
+    return launch_elementwise(3, y, b, x, nullptr);
+}
+
+extern "C" int gbs_vec_pointwise_mult(gbs_vec w, gbs_vec x, gbs_vec y)
+{
+    if (!w || !x || !y || w->n != x->n || x->n != y->n) return GBS_ERR_ARG;
+    if (w->dtype != x->dtype || x->dtype != y->dtype) return GBS_ERR_ARG;
+    return launch_elementwise(4, w, 0.0, x, y);
+}
+
+// Dot product in two fixed-order stages within one launch: each CTA sums a
+// grid-stride slice (thread partials, then a shuffle tree), the last CTA to
+// finish adds the CTA partials in index order.  Result in out[0] (T).
+template <typename T>
+__global__ void __launch_bounds__(GBS_BLOCK) k_dot(int64_t n, const T *__restrict__ x,
+                                                   const T *__restrict__ y, T *partials,
+                                                   unsigned int *counter, T *out)
+{
+    __shared__ T s_red[GBS_WARPS];
+    __shared__ bool s_last;
+    T acc[1] = {T(0)};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += x[i] * y[i];
+    gbs_block_sum<T, 1>(acc, s_red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc[0];
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        T tot[1];
+        gbs_grid_sum<T, 1>(partials, 0, gridDim.x, tot, s_red);
+        if (threadIdx.x == 0) {
+            out[0] = tot[0];
+            *counter = 0;
+        }
+    }
+}
+
+static int vec_dot_impl(gbs_vec x, gbs_vec y, double *out)
+{
+    gbs_ctx c = x->ctx;
+    if (x->n == 0) {
+        *out = 0.0;
+        return GBS_OK;
+    }
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const int g = grid_for(c, x->n, 4);
+    void *scr = nullptr;
+    int st = gbs_ctx_reserve(c, 64 + 8 * (size_t)g + 16, &scr);
+    if (st) return st;
+    unsigned int *counter = (unsigned int *)scr;
+    double *res = (double *)((char *)scr + 16);
+    void *partials = (char *)scr + 64;
+    GBS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, c->stream));
+    if (x->dtype == GBS_F64)
+        k_dot<double><<<g, GBS_BLOCK, 0, c->stream>>>(x->n, (const double *)x->data,
+                                                      (const double *)y->data,
+                                                      (double *)partials, counter, res);
+    else
+        k_dot<float><<<g, GBS_BLOCK, 0, c->stream>>>(x->n, (const float *)x->data,
+                                                     (const float *)y->data, (float *)partials,
+                                                     counter, (float *)res);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, res, 8, cudaMemcpyDeviceToHost, c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (x->dtype == GBS_F64)
+        *out = *(volatile double *)c->pinned;
+    else
+        *out = (double)*(volatile float *)c->pinned;
+    return GBS_OK;
+}
+
+extern "C" int gbs_vec_dot(gbs_vec x, gbs_vec y, double *out)
+{
+    if (!x || !y || !out || x->n != y->n || x->dtype != y->dtype) return GBS_ERR_ARG;
+    return vec_dot_impl(x, y, out);
+}
+
+extern "C" int gbs_vec_norm2(gbs_vec x, double *out)
+{
+    if (!x || !out) return GBS_ERR_ARG;
+    double d = 0.0;
+    int st = vec_dot_impl(x, x, &d);
+    if (st) return st;
+    *out = x->dtype == GBS_F64 ? sqrt(d) : (double)sqrtf((float)d);
+    return GBS_OK;
+}
+
+// ------------------------------------------------------------- Jacobi --
+
+extern "C" int gbs_pc_jacobi_create(gbs_mat A, gbs_pc *out)
+{
+    if (!A || !out) return GBS_ERR_ARG;
+    *out = nullptr;
+    if (!A->diag_ok) return GBS_ERR_DIAG;
+    gbs_pc pc = (gbs_pc)calloc(1, sizeof(*pc));
+    if (!pc) return GBS_ERR_OOM;
+    pc->A = A;
+    *out = pc;
+    return GBS_OK;
+}
+
+template <typename T>
+__global__ void k_jacobi(int64_t n, const T *__restrict__ dinv, const T *__restrict__ r,
+                         T *__restrict__ z)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = dinv[i] * r[i];
+}
+
+extern "C" int gbs_pc_apply(gbs_pc pc, gbs_vec r, gbs_vec z)
+{
+    if (!pc || !r || !z || r->n != pc->A->n || z->n != r->n || r->dtype != z->dtype)
+        return GBS_ERR_ARG;
+    gbs_ctx c = pc->A->ctx;
+    if (r->n == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const int g = grid_for(c, r->n, 8);
+    if (r->dtype == GBS_F64)
+        k_jacobi<double><<<g, GBS_BLOCK, 0, c->stream>>>(r->n, pc->A->dinv,
+                                                         (const double *)r->data,
+                                                         (double *)z->data);
+    else
+        k_jacobi<float><<<g, GBS_BLOCK, 0, c->stream>>>(r->n, pc->A->dinv32,
+                                                        (const float *)r->data,
+                                                        (float *)z->data);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+extern "C" int gbs_pc_destroy(gbs_pc pc)
+{
+    free(pc);
+    return GBS_OK;
+}

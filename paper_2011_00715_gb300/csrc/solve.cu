@@ -1,0 +1,735 @@
+// Jacobi-preconditioned CG solves (KSPCG + PCJACOBI, Sec. 5.5 / 5.3 of the
+// paper) on one GPU.
+//
+// Persistent path: one cooperative kernel runs the whole solve.  Each CTA
+// owns a contiguous range of CSR tiles (rows); per iteration it
+//   S: forms q = A p on its rows with the p.q partial fused in the SpMV
+//      epilogue                                          -> grid barrier
+//   U: alpha = rho / p.q; x += alpha p; r -= alpha q; z = D^-1 r, with the
+//      r.z and r.r partials fused                         -> grid barrier
+//   P: beta = rho'/rho; p = z + beta p                    -> grid barrier
+// and tests convergence on the device (||r||_2 <= rtol ||b||_2 before each
+// iteration), so the host is not involved until the end (Challenge A1:
+// dot products otherwise force a host synchronisation each iteration).
+// Every CTA reduces the per-CTA partials in the same fixed order, so all
+// CTAs hold bitwise-identical scalars and take identical decisions.
+//
+// Mixed mode (Response A7: single precision on the GPU): the same kernel
+// shape with an outer iterative-refinement loop inside it: FP64
+// r = b - A x with ||r|| fused, FP32 inner PCG on r/||r|| (FP32 values,
+// vectors and reductions), FP64 update x += ||r|| d.
+//
+// Per-op path: the same arithmetic as one kernel per operation with
+// scalars kept on the device (the PETSc library-call-per-op pattern), and
+// the same sequence captured in a CUDA graph (Challenge A1).
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gbs_impl.cuh"
+
+namespace {
+
+constexpr int kSlots = 8;   // partial-sum slots per CTA
+
+template <typename T>
+struct TileSmem {
+    T red[4 * GBS_WARPS];
+    T bcast[4];
+};
+
+struct KernelShared {
+    int flag;
+};
+
+// Arguments of the persistent kernels.
+struct PcgArgs {
+    int64_t n;
+    int64_t ntiles;
+    const int32_t *tiles;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const double *vals;
+    const float *vals32;
+    const double *dinv;
+    const float *dinv32;
+    const double *b;
+    double *x;
+    // FP64 work vectors (FP64 mode: r, z, p, q; mixed: r holds b - A x)
+    double *r, *z, *p, *q;
+    // FP32 work vectors (mixed mode): rhs, solution, r, z, p, q
+    float *b32, *x32, *r32, *z32, *p32, *q32;
+    double *part64;   // kSlots * G
+    float *part32;    // kSlots * G
+    gbs_grid_barrier *bar;
+    gbs_result_dev *res;
+    double rtol;
+    double inner_rtol;
+    int maxit;
+    int outer_maxit;
+    int x0_zero;
+    int skip_cta;
+    unsigned long long timeout_ns;
+};
+
+// Row range of CTA c: tiles [c*T/G, (c+1)*T/G).
+__device__ __forceinline__ void cta_tiles(const PcgArgs &a, int64_t &t0, int64_t &t1)
+{
+    t0 = a.ntiles * blockIdx.x / gridDim.x;
+    t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+}
+
+// Inner PCG loop on (vals_T, dinv_T) for rhs bT, solution xT (in/out), work
+// vectors rT..qT, as described at the top of this file.  Returns a status;
+// all CTAs return the same one.  *iters receives the iteration count.
+template <typename T>
+__device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T *bT, T *xT, T *rT,
+                        T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
+                        int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no, GbsTile<T> &tl,
+                        TileSmem<T> &sm, int *s_flag)
+{
+    const int G = gridDim.x, c = blockIdx.x;
+    int64_t t0, t1;
+    cta_tiles(a, t0, t1);
+    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
+    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
+    *iters = 0;
+
+    // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b
+    T acc[3] = {T(0), T(0), T(0)};
+    if (!x0_zero) {
+        auto epi = [&](int64_t i, T s) {
+            const T bi = bT[i];
+            const T ri = bi - s;
+            const T zi = dinv[i] * ri;
+            rT[i] = ri;
+            zT[i] = zi;
+            pT[i] = zi;
+            acc[0] += ri * zi;
+            acc[1] += ri * ri;
+            acc[2] += bi * bi;
+        };
+        for (int64_t t = t0; t < t1; ++t)
+            gbs_spmv_tile<T>(a.rowptr, a.colidx, vals, xT, __ldg(a.tiles + t),
+                             __ldg(a.tiles + t + 1), tl, sm.red, epi);
+    } else {
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
+            const T bi = bT[i];
+            const T zi = dinv[i] * bi;
+            xT[i] = T(0);
+            rT[i] = bi;
+            zT[i] = zi;
+            pT[i] = zi;
+            acc[0] += bi * zi;
+            acc[1] += bi * bi;
+            acc[2] += bi * bi;
+        }
+    }
+    gbs_block_sum<T, 3>(acc, sm.red);
+    if (threadIdx.x == 0) {
+        part[0 * G + c] = acc[0];
+        part[1 * G + c] = acc[1];
+        part[2 * G + c] = acc[2];
+    }
+    const bool skip = (a.skip_cta == c) && (*barrier_no == 0);
+    if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, skip, s_flag)) return GBS_ERR_TIMEOUT;
+    T g3[3];
+    gbs_grid_sum<T, 3>(part, G, G, g3, sm.bcast);
+    T rho = g3[0], rr = g3[1];
+    const T bnorm = sqrt(g3[2]);
+    *bnorm_out = bnorm;
+
+    int k = 0;
+    int status;
+    for (;;) {
+        const T rn = sqrt(rr);
+        *rnorm_out = rn;
+        if (isnan(rn) || isnan(rho)) { status = GBS_ERR_NAN; break; }
+        if (rn <= rtol * bnorm) { status = GBS_OK; break; }
+        if (k >= maxit) { status = GBS_DIVERGED_ITS; break; }
+
+        // ---- S: q = A p, partial p.q
+        T pq[1] = {T(0)};
+        auto epi = [&](int64_t i, T s) {
+            qT[i] = s;
+            pq[0] += __ldcg(pT + i) * s;
+        };
+        for (int64_t t = t0; t < t1; ++t)
+            gbs_spmv_tile<T>(a.rowptr, a.colidx, vals, pT, __ldg(a.tiles + t),
+                             __ldg(a.tiles + t + 1), tl, sm.red, epi);
+        gbs_block_sum<T, 1>(pq, sm.red);
+        if (threadIdx.x == 0) part[3 * G + c] = pq[0];
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
+            return GBS_ERR_TIMEOUT;
+        T pi[1];
+        gbs_grid_sum<T, 1>(part + 3 * G, G, G, pi, sm.bcast);
+        if (isnan(pi[0])) { status = GBS_ERR_NAN; break; }
+        if (pi[0] <= T(0)) { status = GBS_ERR_INDEFINITE; break; }
+        const T alpha = rho / pi[0];
+
+        // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
+        T u[2] = {T(0), T(0)};
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
+            const T pi_ = pT[i];
+            xT[i] += alpha * pi_;
+            const T ri = rT[i] - alpha * qT[i];
+            const T zi = dinv[i] * ri;
+            rT[i] = ri;
+            zT[i] = zi;
+            u[0] += ri * zi;
+            u[1] += ri * ri;
+        }
+        gbs_block_sum<T, 2>(u, sm.red);
+        if (threadIdx.x == 0) {
+            part[4 * G + c] = u[0];
+            part[5 * G + c] = u[1];
+        }
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
+            return GBS_ERR_TIMEOUT;
+        T g2[2];
+        gbs_grid_sum<T, 2>(part + 4 * G, G, G, g2, sm.bcast);
+        ++k;
+        const T rho_new = g2[0];
+        rr = g2[1];
+        if (rho_new < T(0)) { *rnorm_out = sqrt(rr); status = GBS_ERR_INDEFINITE; break; }
+        const T beta = rho_new / rho;
+        rho = rho_new;
+
+        // ---- P: p = z + beta p
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) pT[i] = zT[i] + beta * pT[i];
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
+            return GBS_ERR_TIMEOUT;
+    }
+    *iters = k;
+    return status;
+}
+
+__global__ void __launch_bounds__(GBS_BLOCK) k_pcg_fp64(PcgArgs a)
+{
+    __shared__ GbsTile<double> tl;
+    __shared__ TileSmem<double> sm;
+    __shared__ int s_flag;
+    int iters = 0, barrier_no = 0;
+    double rn = 0.0, bn = 0.0;
+    int st = pcg_loop<double>(a, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol,
+                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, tl, sm,
+                              &s_flag);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.res->status = st;
+        a.res->iters = iters;
+        a.res->outer = 0;
+        a.res->rnorm = rn;
+        a.res->bnorm = bn;
+        a.res->timeout_where = st == GBS_ERR_TIMEOUT ? a.bar->where : -1;
+    }
+}
+
+// Mixed precision: FP64 iterative refinement around the FP32 inner loop.
+__global__ void __launch_bounds__(GBS_BLOCK) k_pcg_mixed(PcgArgs a)
+{
+    __shared__ GbsTile<double> tl64;
+    __shared__ TileSmem<double> sm64;
+    __shared__ TileSmem<float> sm32;
+    __shared__ int s_flag;
+    GbsTile<float> &tl32 = *reinterpret_cast<GbsTile<float> *>(&tl64);
+    const int G = gridDim.x, c = blockIdx.x;
+    int64_t t0, t1;
+    cta_tiles(a, t0, t1);
+    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
+    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
+    int barrier_no = 0, inner_total = 0, outer = 0, st = GBS_DIVERGED_ITS;
+    double rn = 0.0, bnorm = 0.0, prev = INFINITY;
+    for (int it = 0;; ++it) {
+        // ---- FP64 residual r = b - A x with r.r (and b.b once) fused
+        double acc[2] = {0.0, 0.0};
+        const bool first = it == 0;
+        if (first && a.x0_zero) {
+            for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
+                const double bi = a.b[i];
+                a.x[i] = 0.0;
+                a.r[i] = bi;
+                acc[0] += bi * bi;
+                acc[1] += bi * bi;
+            }
+        } else {
+            auto epi = [&](int64_t i, double s) {
+                const double bi = a.b[i];
+                const double ri = bi - s;
+                a.r[i] = ri;
+                acc[0] += ri * ri;
+                if (first) acc[1] += bi * bi;
+            };
+            for (int64_t t = t0; t < t1; ++t)
+                gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.x, __ldg(a.tiles + t),
+                                      __ldg(a.tiles + t + 1), tl64, sm64.red, epi);
+        }
+        gbs_block_sum<double, 2>(acc, sm64.red);
+        double *part = a.part64 + (it & 1) * 2 * G;
+        if (threadIdx.x == 0) {
+            part[c] = acc[0];
+            part[G + c] = acc[1];
+        }
+        const bool skip = (a.skip_cta == c) && (barrier_no == 0);
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, barrier_no++, skip, &s_flag)) {
+            st = GBS_ERR_TIMEOUT;
+            break;
+        }
+        double g2[2];
+        gbs_grid_sum<double, 2>(part, G, G, g2, sm64.bcast);
+        rn = sqrt(g2[0]);
+        if (first) bnorm = sqrt(g2[1]);
+        outer = it;
+        if (isnan(rn)) { st = GBS_ERR_NAN; break; }
+        if (rn <= a.rtol * bnorm) { st = GBS_OK; break; }
+        if (rn > 0.5 * prev) { st = GBS_ERR_STAGNATION; break; }
+        if (it >= a.outer_maxit) { st = GBS_DIVERGED_ITS; break; }
+        prev = rn;
+        // ---- scale to FP32 (own rows) and solve A d = r / ||r|| in FP32
+        const double inv = 1.0 / rn;
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) a.b32[i] = (float)(a.r[i] * inv);
+        int kin = 0;
+        float rin = 0.f, bin = 0.f;
+        const int sti = pcg_loop<float>(a, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
+                                        a.q32, a.part32, (float)a.inner_rtol, a.maxit, true, &kin,
+                                        &rin, &bin, &barrier_no, tl32, sm32, &s_flag);
+        inner_total += kin;
+        if (sti < 0) { st = sti; break; }
+        // ---- FP64 update x += ||r|| d (own rows), then a barrier so the next
+        // residual SpMV sees every row of x
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) a.x[i] += rn * (double)a.x32[i];
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, barrier_no++, false, &s_flag)) {
+            st = GBS_ERR_TIMEOUT;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.res->status = st;
+        a.res->iters = inner_total;
+        a.res->outer = outer;
+        a.res->rnorm = rn;
+        a.res->bnorm = bnorm;
+        a.res->timeout_where = st == GBS_ERR_TIMEOUT ? a.bar->where : -1;
+    }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Largest cooperative grid for a kernel, capped by the tile count.
+int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_BLOCK, 0) != cudaSuccess)
+        return -1;
+    if (per_sm < 1) return -1;
+    int64_t g = (int64_t)per_sm * c->num_sms;
+    if (g > ntiles) g = ntiles;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
+                         const gbs_opts *o, gbs_solve_info *info)
+{
+    gbs_ctx c = A->ctx;
+    const bool mixed = o->mode == GBS_MODE_MIXED;
+    if (mixed) {
+        int st = gbs_mat_ensure_f32(A);
+        if (st) return st;
+    }
+    const void *fn = mixed ? (const void *)k_pcg_mixed : (const void *)k_pcg_fp64;
+    const int G = coop_grid(c, fn, A->ntiles);
+    if (G < 0) return GBS_ERR_CUDA;
+    const int64_t n = A->n;
+    const size_t vec64 = align256(sizeof(double) * (size_t)n);
+    const size_t vec32 = align256(sizeof(float) * (size_t)n);
+    const size_t part = align256(sizeof(double) * kSlots * (size_t)G);
+    const size_t head = 512;  // barrier + result
+    const size_t total = head + 2 * part + (mixed ? vec64 + 6 * vec32 : 4 * vec64);
+    void *scr = nullptr;
+    int st = gbs_ctx_reserve(c, total, &scr);
+    if (st) return st;
+    char *base = (char *)scr;
+    PcgArgs a;
+    memset(&a, 0, sizeof(a));
+    a.bar = (gbs_grid_barrier *)base;
+    a.res = (gbs_result_dev *)(base + 256);
+    a.part64 = (double *)(base + head);
+    a.part32 = (float *)(base + head + part);
+    char *v = base + head + 2 * part;
+    if (mixed) {
+        a.r = (double *)v; v += vec64;
+        a.b32 = (float *)v; v += vec32;
+        a.x32 = (float *)v; v += vec32;
+        a.r32 = (float *)v; v += vec32;
+        a.z32 = (float *)v; v += vec32;
+        a.p32 = (float *)v; v += vec32;
+        a.q32 = (float *)v; v += vec32;
+    } else {
+        a.r = (double *)v; v += vec64;
+        a.z = (double *)v; v += vec64;
+        a.p = (double *)v; v += vec64;
+        a.q = (double *)v; v += vec64;
+    }
+    a.n = n;
+    a.ntiles = A->ntiles;
+    a.tiles = A->tiles;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.vals = A->vals;
+    a.vals32 = A->vals32;
+    a.dinv = A->dinv;
+    a.dinv32 = A->dinv32;
+    a.b = (const double *)b->data;
+    a.x = (double *)x->data;
+    a.rtol = rtol;
+    a.inner_rtol = o->inner_rtol;
+    a.maxit = maxit;
+    a.outer_maxit = o->outer_maxit;
+    a.x0_zero = 0;
+    a.skip_cta = o->fault_skip_arrival;
+    a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
+
+    GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
+    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    void *args[] = {&a};
+    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(GBS_BLOCK), args, 0, c->stream));
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    gbs_result_dev r;
+    memcpy(&r, c->pinned, sizeof(r));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->status = r.status;
+    info->iters = r.iters;
+    info->outer_iters = r.outer;
+    info->rnorm = r.rnorm;
+    info->bnorm = r.bnorm;
+    info->device_ms = ms;
+    return r.status;
+}
+
+// ----------------------------------------------------------------------
+// Per-op path: one kernel per operation, scalars on the device.
+// ----------------------------------------------------------------------
+
+namespace {
+
+struct OpScalars {
+    double rho, rr, bnorm, pi, alpha, beta;
+    int k, status, done, pad;
+    unsigned int counter[4];
+};
+
+struct OpArgs {
+    int64_t n, ntiles;
+    const int32_t *tiles, *rowptr, *colidx;
+    const double *vals, *dinv, *b;
+    double *x, *r, *z, *p, *q;
+    double *part;   // 3 * G
+    OpScalars *s;
+    double rtol;
+    int maxit;
+};
+
+// Last-CTA-done reduction of K partials into tot (fixed order).  Returns
+// true in the last CTA only.
+template <int K>
+__device__ bool op_reduce(double (&v)[K], double *part, unsigned int *counter, double *s_red,
+                          double (&tot)[K], bool *s_last)
+{
+    const int G = gridDim.x;
+    gbs_block_sum<double, K>(v, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[k * G + blockIdx.x] = v[k];
+        __threadfence();
+        *s_last = atomicAdd(counter, 1u) == (unsigned)G - 1;
+    }
+    __syncthreads();
+    if (!*s_last) return false;
+    __threadfence();
+    gbs_grid_sum<double, K>(part, G, G, tot, s_red);
+    if (threadIdx.x == 0) *counter = 0;
+    return true;
+}
+
+__device__ void op_check(OpScalars *s, double rtol, int maxit)
+{
+    const double rn = sqrt(s->rr);
+    if (isnan(rn) || isnan(s->rho)) { s->status = GBS_ERR_NAN; s->done = 1; }
+    else if (rn <= rtol * s->bnorm) { s->status = GBS_OK; s->done = 1; }
+    else if (s->k >= maxit) { s->status = GBS_DIVERGED_ITS; s->done = 1; }
+}
+
+__global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
+{
+    __shared__ GbsTile<double> tl;
+    __shared__ TileSmem<double> sm;
+    __shared__ bool s_last;
+    double acc[3] = {0.0, 0.0, 0.0};
+    auto epi = [&](int64_t i, double s) {
+        const double bi = a.b[i], ri = bi - s, zi = a.dinv[i] * ri;
+        a.r[i] = ri;
+        a.z[i] = zi;
+        a.p[i] = zi;
+        acc[0] += ri * zi;
+        acc[1] += ri * ri;
+        acc[2] += bi * bi;
+    };
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
+        gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.x, a.tiles[t], a.tiles[t + 1], tl,
+                              sm.red, epi);
+    double tot[3];
+    if (op_reduce<3>(acc, a.part, &a.s->counter[0], sm.red, tot, &s_last) && threadIdx.x == 0) {
+        a.s->rho = tot[0];
+        a.s->rr = tot[1];
+        a.s->bnorm = sqrt(tot[2]);
+        a.s->k = 0;
+        a.s->done = 0;
+        a.s->status = GBS_DIVERGED_ITS;
+        op_check(a.s, a.rtol, a.maxit);
+    }
+}
+
+__global__ void __launch_bounds__(GBS_BLOCK) k_op_spmv_pq(OpArgs a)
+{
+    if (a.s->done) return;
+    __shared__ GbsTile<double> tl;
+    __shared__ TileSmem<double> sm;
+    __shared__ bool s_last;
+    double pq[1] = {0.0};
+    auto epi = [&](int64_t i, double s) {
+        a.q[i] = s;
+        pq[0] += a.p[i] * s;
+    };
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
+        gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.p, a.tiles[t], a.tiles[t + 1], tl,
+                              sm.red, epi);
+    double tot[1];
+    if (op_reduce<1>(pq, a.part, &a.s->counter[1], sm.red, tot, &s_last) && threadIdx.x == 0) {
+        a.s->pi = tot[0];
+        if (isnan(tot[0])) { a.s->status = GBS_ERR_NAN; a.s->done = 1; }
+        else if (tot[0] <= 0.0) { a.s->status = GBS_ERR_INDEFINITE; a.s->done = 1; }
+        else a.s->alpha = a.s->rho / tot[0];
+    }
+}
+
+__global__ void __launch_bounds__(GBS_BLOCK) k_op_update(OpArgs a)
+{
+    if (a.s->done) return;
+    __shared__ double s_red[4 * GBS_WARPS];
+    __shared__ bool s_last;
+    const double alpha = a.s->alpha;
+    double u[2] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * GBS_BLOCK + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * GBS_BLOCK) {
+        a.x[i] += alpha * a.p[i];
+        const double ri = a.r[i] - alpha * a.q[i];
+        const double zi = a.dinv[i] * ri;
+        a.r[i] = ri;
+        a.z[i] = zi;
+        u[0] += ri * zi;
+        u[1] += ri * ri;
+    }
+    double tot[2];
+    if (op_reduce<2>(u, a.part, &a.s->counter[2], s_red, tot, &s_last) && threadIdx.x == 0) {
+        a.s->k += 1;
+        a.s->rr = tot[1];
+        if (tot[0] < 0.0) {
+            a.s->status = GBS_ERR_INDEFINITE;
+            a.s->done = 1;
+        } else {
+            a.s->beta = tot[0] / a.s->rho;
+            a.s->rho = tot[0];
+            op_check(a.s, a.rtol, a.maxit);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GBS_BLOCK) k_op_pupdate(OpArgs a)
+{
+    if (a.s->done) return;
+    const double beta = a.s->beta;
+    for (int64_t i = (int64_t)blockIdx.x * GBS_BLOCK + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * GBS_BLOCK)
+        a.p[i] = a.z[i] + beta * a.p[i];
+}
+
+int op_iteration(gbs_ctx c, const OpArgs &a, int gt, int gv, cudaStream_t s)
+{
+    k_op_spmv_pq<<<gt, GBS_BLOCK, 0, s>>>(a);
+    k_op_update<<<gv, GBS_BLOCK, 0, s>>>(a);
+    k_op_pupdate<<<gv, GBS_BLOCK, 0, s>>>(a);
+    gbs_count_launch(c, 3);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+}  // namespace
+
+int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, const gbs_opts *o,
+                    gbs_solve_info *info, int use_graph)
+{
+    gbs_ctx c = A->ctx;
+    if (o->mode != GBS_MODE_FP64) return GBS_ERR_UNSUPPORTED;
+    const int64_t n = A->n;
+    int gt = (int)(A->ntiles < (int64_t)c->num_sms * 4 ? A->ntiles : (int64_t)c->num_sms * 4);
+    int gv = (int)((n + GBS_BLOCK - 1) / GBS_BLOCK);
+    if (gv > c->num_sms * 4) gv = c->num_sms * 4;
+    if (gt < 1) gt = 1;
+    if (gv < 1) gv = 1;
+    const int G = gt > gv ? gt : gv;
+    const size_t vec64 = align256(sizeof(double) * (size_t)n);
+    const size_t part = align256(sizeof(double) * 3 * (size_t)G);
+    const size_t head = align256(sizeof(OpScalars));
+    void *scr = nullptr;
+    int st = gbs_ctx_reserve(c, head + part + 4 * vec64, &scr);
+    if (st) return st;
+    char *base = (char *)scr;
+    OpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.s = (OpScalars *)base;
+    a.part = (double *)(base + head);
+    char *v = base + head + part;
+    a.r = (double *)v; v += vec64;
+    a.z = (double *)v; v += vec64;
+    a.p = (double *)v; v += vec64;
+    a.q = (double *)v; v += vec64;
+    a.n = n;
+    a.ntiles = A->ntiles;
+    a.tiles = A->tiles;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.vals = A->vals;
+    a.dinv = A->dinv;
+    a.b = (const double *)b->data;
+    a.x = (double *)x->data;
+    a.rtol = rtol;
+    a.maxit = maxit;
+
+    GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
+    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    k_op_setup<<<gt, GBS_BLOCK, 0, c->stream>>>(a);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    volatile OpScalars *hs = (volatile OpScalars *)c->pinned;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+    int rc = GBS_OK;
+    if (use_graph) {
+        // capture graph_iters iterations once; the kernels are no-ops once done
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int i = 0; i < o->graph_iters; ++i) {
+                k_op_spmv_pq<<<gt, GBS_BLOCK, 0, cap>>>(a);
+                k_op_update<<<gv, GBS_BLOCK, 0, cap>>>(a);
+                k_op_pupdate<<<gv, GBS_BLOCK, 0, cap>>>(a);
+            }
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) rc = gbs_cuda_fail(e);
+    }
+    for (int64_t it = 0; rc == GBS_OK; ) {
+        cudaError_t e = cudaMemcpyAsync(c->pinned, a.s, sizeof(OpScalars), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
+        if (hs->done) break;
+        if (it > (int64_t)maxit + 1) { rc = GBS_ERR_CUDA; break; }  // cannot happen
+        if (use_graph) {
+            e = cudaGraphLaunch(exec, c->stream);
+            gbs_count_launch(c, 3 * o->graph_iters);
+            if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
+            it += o->graph_iters;
+        } else {
+            rc = op_iteration(c, a, gt, gv, c->stream);
+            it += 1;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (rc != GBS_OK) return rc;
+    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->status = hs->status;
+    info->iters = hs->k;
+    info->outer_iters = 0;
+    info->rnorm = sqrt(hs->rr);
+    info->bnorm = hs->bnorm;
+    info->device_ms = ms;
+    return hs->status;
+}
+
+// ----------------------------------------------------------------------
+// Public solve entry points
+// ----------------------------------------------------------------------
+
+extern "C" int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
+                                   const gbs_opts *opts, gbs_solve_info *info)
+{
+    if (!A || !b || !x) return GBS_ERR_ARG;
+    gbs_ctx c = A->ctx;
+    const gbs_opts *o = opts ? opts : &c->opts;
+    if (b->ctx != c || x->ctx != c) return GBS_ERR_ARG;
+    if (A->n != A->ncols || b->n != A->n || x->n != A->n) return GBS_ERR_ARG;
+    if (b->dtype != GBS_F64 || x->dtype != GBS_F64) return GBS_ERR_ARG;
+    if (b->data == x->data && A->n > 0) return GBS_ERR_ARG;
+    if (!(rtol >= 0.0) || maxit < 0) return GBS_ERR_ARG;
+    if (o->mode != GBS_MODE_FP64 && o->mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
+    gbs_solve_info tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    int st;
+    if (A->n == 0) {
+        st = GBS_OK;
+        tmp.status = GBS_OK;
+    } else if (!A->diag_ok) {
+        st = GBS_ERR_DIAG;
+        tmp.status = st;
+    } else {
+        GBS_CUDA_TRY(cudaSetDevice(c->device));
+        int alg = o->algorithm;
+        if (alg == GBS_ALG_AUTO) alg = GBS_ALG_PERSISTENT;
+        if (alg == GBS_ALG_PERSISTENT)
+            st = gbs_solve_persistent(A, b, x, rtol, maxit, o, &tmp);
+        else
+            st = gbs_solve_perop(A, b, x, rtol, maxit, o, &tmp, alg == GBS_ALG_GRAPH);
+        if (st == GBS_ERR_CUDA || st == GBS_ERR_OOM || st == GBS_ERR_UNSUPPORTED ||
+            st == GBS_ERR_ARG)
+            tmp.status = st;
+    }
+    c->last = tmp;
+    if (info) *info = tmp;
+    return st;
+}
+
+extern "C" int gbs_ksp_solve_cg(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
+                                int *iters, double *rnorm)
+{
+    gbs_solve_info info;
+    const int st = gbs_ksp_solve_cg_ex(A, b, x, rtol, maxit, nullptr, &info);
+    if (st >= GBS_OK || st == GBS_ERR_INDEFINITE || st == GBS_ERR_NAN ||
+        st == GBS_ERR_STAGNATION || st == GBS_ERR_TIMEOUT) {
+        if (iters) *iters = info.iters;
+        if (rnorm) *rnorm = info.rnorm;
+    }
+    return st;
+}
+
+extern "C" int gbs_ksp_last_info(gbs_ctx c, gbs_solve_info *info)
+{
+    if (!c || !info) return GBS_ERR_ARG;
+    *info = c->last;
+    return GBS_OK;
+}

@@ -1,0 +1,474 @@
+"""Python binding of the gbs C ABI (include/gbs.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays are
+numpy arrays (host memory) or torch tensors (host or CUDA); their memory
+space is stated to the library explicitly, never queried.  Negative status
+codes raise :class:`GbsError`, except from the solve calls, which return
+their status inside the result because breakdown and limit statuses are
+results, not misuse.
+
+The library must have been built (``paper_2011_00715_gb300.build.build()``
+or ``__graft_entry__.build()``); there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+GBS_OK = 0
+GBS_DIVERGED_ITS = 1
+GBS_ERR_ARG = -1
+GBS_ERR_OOM = -2
+GBS_ERR_CUDA = -3
+GBS_ERR_DIAG = -4
+GBS_ERR_INDEFINITE = -5
+GBS_ERR_NAN = -6
+GBS_ERR_TIMEOUT = -7
+GBS_ERR_STAGNATION = -8
+GBS_ERR_BUDGET = -9
+GBS_ERR_CSR = -10
+GBS_ERR_NOT_FOUND = -11
+GBS_ERR_UNSUPPORTED = -12
+
+GBS_MEM_HOST = 0
+GBS_MEM_DEVICE = 1
+GBS_F64 = 0
+GBS_F32 = 1
+GBS_MODE_FP64 = 0
+GBS_MODE_MIXED = 1
+GBS_ALG_AUTO = 0
+GBS_ALG_PERSISTENT = 1
+GBS_ALG_PEROP = 2
+GBS_ALG_GRAPH = 3
+
+
+class GbsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {gbs_status_string(status)} ({status})")
+
+
+class gbs_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("algorithm", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int),
+                ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
+                ("fault_skip_arrival", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class gbs_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("device_ms", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    outer_iters: int
+    rnorm: float
+    bnorm: float
+    device_ms: float
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32P = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "gbs_version": ([], ctypes.c_char_p),
+    "gbs_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gbs_opts_default": ([ctypes.POINTER(gbs_opts)], ctypes.c_int),
+    "gbs_ctx_create": ([ctypes.c_int, _VP, ctypes.POINTER(gbs_opts), ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_ctx_destroy": ([_VP], ctypes.c_int),
+    "gbs_ctx_set_stream": ([_VP, _VP], ctypes.c_int),
+    "gbs_ctx_set_opts": ([_VP, ctypes.POINTER(gbs_opts)], ctypes.c_int),
+    "gbs_ctx_synchronize": ([_VP], ctypes.c_int),
+    "gbs_ctx_launch_count": ([_VP, ctypes.POINTER(_I64)], ctypes.c_int),
+    "gbs_mat_create_aij": ([_VP, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_mat_set_values": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
+    "gbs_mat_get_info": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "gbs_mat_destroy": ([_VP], ctypes.c_int),
+    "gbs_mat_mult": ([_VP, _VP, _VP], ctypes.c_int),
+    "gbs_vec_create": ([_VP, _I64, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_vec_wrap": ([_VP, _VP, _I64, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_vec_destroy": ([_VP], ctypes.c_int),
+    "gbs_vec_get_info": ([_VP, ctypes.POINTER(_I64), _I32P, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_vec_set_values": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
+    "gbs_vec_get_values": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
+    "gbs_vec_set": ([_VP, ctypes.c_double], ctypes.c_int),
+    "gbs_vec_copy": ([_VP, _VP], ctypes.c_int),
+    "gbs_vec_axpy": ([_VP, ctypes.c_double, _VP], ctypes.c_int),
+    "gbs_vec_aypx": ([_VP, ctypes.c_double, _VP], ctypes.c_int),
+    "gbs_vec_pointwise_mult": ([_VP, _VP, _VP], ctypes.c_int),
+    "gbs_vec_dot": ([_VP, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gbs_vec_norm2": ([_VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gbs_pc_jacobi_create": ([_VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_pc_apply": ([_VP, _VP, _VP], ctypes.c_int),
+    "gbs_pc_destroy": ([_VP], ctypes.c_int),
+    "gbs_ksp_solve_cg": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _I32P,
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gbs_ksp_solve_cg_ex": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.POINTER(gbs_opts),
+                             ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
+    "gbs_ksp_last_info": ([_VP, ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
+    "gbs_ksp_solve_cg_batched": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_int,
+                                  ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "gbs_server_create": ([_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "gbs_server_destroy": ([_VP], ctypes.c_int),
+    "gbs_server_submit": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gbs_server_progress": ([_VP, _I32P], ctypes.c_int),
+    "gbs_server_poll": ([_VP, ctypes.c_uint64, _I32P], ctypes.c_int),
+    "gbs_server_wait": ([_VP, ctypes.c_uint64], ctypes.c_int),
+    "gbs_server_fetch": ([_VP, ctypes.c_uint64, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gbs_server_stats": ([_VP, _I32P, _I32P, _I32P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def lib():
+    """The loaded libgbs.so.  Raises if it has not been built: there is no
+    CPU fallback for any operation."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libgbs.so is not built ({path}); run "
+                              "paper_2011_00715_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise GbsError(st, where)
+    return st
+
+
+def _ptr_space(a):
+    """(pointer, memspace, keepalive) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, GBS_MEM_HOST, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (GBS_MEM_DEVICE if a.is_cuda else GBS_MEM_HOST), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_code(a) -> int:
+    s = str(a.dtype)
+    if s.endswith("float64"):
+        return GBS_F64
+    if s.endswith("float32"):
+        return GBS_F32
+    raise TypeError(f"unsupported dtype {a.dtype}")
+
+
+# ---------------------------------------------------------------- general --
+
+def gbs_version() -> str:
+    return lib().gbs_version().decode()
+
+
+def gbs_status_string(status: int) -> str:
+    return lib().gbs_status_string(int(status)).decode()
+
+
+def gbs_opts_default(**overrides) -> gbs_opts:
+    o = gbs_opts()
+    _check(lib().gbs_opts_default(ctypes.byref(o)), "gbs_opts_default")
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+# -------------------------------------------------------------------- ctx --
+
+def gbs_ctx_create(device: int = 0, stream=None, opts: gbs_opts | None = None):
+    """stream: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream)."""
+    h = _VP()
+    _check(lib().gbs_ctx_create(device, _VP(stream or 0), ctypes.byref(opts) if opts else None,
+                                ctypes.byref(h)), "gbs_ctx_create")
+    return h
+
+
+def gbs_ctx_destroy(ctx):
+    _check(lib().gbs_ctx_destroy(ctx), "gbs_ctx_destroy")
+
+
+def gbs_ctx_set_stream(ctx, stream):
+    _check(lib().gbs_ctx_set_stream(ctx, _VP(stream or 0)), "gbs_ctx_set_stream")
+
+
+def gbs_ctx_set_opts(ctx, opts: gbs_opts):
+    _check(lib().gbs_ctx_set_opts(ctx, ctypes.byref(opts)), "gbs_ctx_set_opts")
+
+
+def gbs_ctx_synchronize(ctx):
+    _check(lib().gbs_ctx_synchronize(ctx), "gbs_ctx_synchronize")
+
+
+def gbs_ctx_launch_count(ctx) -> int:
+    c = _I64()
+    _check(lib().gbs_ctx_launch_count(ctx, ctypes.byref(c)), "gbs_ctx_launch_count")
+    return c.value
+
+
+# ----------------------------------------------------------------- matrix --
+
+def gbs_mat_create_aij(ctx, nrows: int, ncols: int, rowptr, colidx, vals):
+    """rowptr/colidx int32, vals float64: all numpy/host or all CUDA tensors."""
+    p_rp, s_rp, _k1 = _ptr_space(rowptr)
+    p_ci, s_ci, _k2 = _ptr_space(colidx)
+    p_v, s_v, _k3 = _ptr_space(vals)
+    if not (s_rp == s_ci == s_v):
+        raise ValueError("rowptr, colidx and vals must live in the same memory space")
+    if str(rowptr.dtype).split(".")[-1] != "int32" or str(colidx.dtype).split(".")[-1] != "int32":
+        raise TypeError("rowptr and colidx must be int32")
+    if _dtype_code(vals) != GBS_F64:
+        raise TypeError("vals must be float64")
+    h = _VP()
+    _check(lib().gbs_mat_create_aij(ctx, nrows, ncols, _VP(p_rp), _VP(p_ci), _VP(p_v), s_rp,
+                                    ctypes.byref(h)), "gbs_mat_create_aij")
+    return h
+
+
+def gbs_mat_set_values(A, vals):
+    p, s, _k = _ptr_space(vals)
+    _check(lib().gbs_mat_set_values(A, _VP(p), s), "gbs_mat_set_values")
+
+
+def gbs_mat_get_info(A):
+    n, m, z = _I64(), _I64(), _I64()
+    _check(lib().gbs_mat_get_info(A, ctypes.byref(n), ctypes.byref(m), ctypes.byref(z)),
+           "gbs_mat_get_info")
+    return n.value, m.value, z.value
+
+
+def gbs_mat_destroy(A):
+    _check(lib().gbs_mat_destroy(A), "gbs_mat_destroy")
+
+
+def gbs_mat_mult(A, x, y):
+    _check(lib().gbs_mat_mult(A, x, y), "gbs_mat_mult")
+
+
+# ----------------------------------------------------------------- vector --
+
+def gbs_vec_create(ctx, n: int, dtype: int = GBS_F64):
+    h = _VP()
+    _check(lib().gbs_vec_create(ctx, n, dtype, ctypes.byref(h)), "gbs_vec_create")
+    return h
+
+
+def gbs_vec_wrap(ctx, tensor):
+    """Wrap a contiguous CUDA tensor (float64 or float32) without copying; the
+    caller keeps the tensor alive while the handle is used."""
+    p, s, _k = _ptr_space(tensor)
+    if s != GBS_MEM_DEVICE:
+        raise ValueError("gbs_vec_wrap needs device memory")
+    h = _VP()
+    _check(lib().gbs_vec_wrap(ctx, _VP(p), tensor.numel(), _dtype_code(tensor), ctypes.byref(h)),
+           "gbs_vec_wrap")
+    return h
+
+
+def gbs_vec_destroy(v):
+    _check(lib().gbs_vec_destroy(v), "gbs_vec_destroy")
+
+
+def gbs_vec_get_info(v):
+    n, d, p = _I64(), ctypes.c_int(), _VP()
+    _check(lib().gbs_vec_get_info(v, ctypes.byref(n), ctypes.byref(d), ctypes.byref(p)),
+           "gbs_vec_get_info")
+    return n.value, d.value, p.value
+
+
+def gbs_vec_set_values(v, src):
+    p, s, _k = _ptr_space(src)
+    _check(lib().gbs_vec_set_values(v, _VP(p), s), "gbs_vec_set_values")
+
+
+def gbs_vec_get_values(v, dst):
+    p, s, _k = _ptr_space(dst)
+    _check(lib().gbs_vec_get_values(v, _VP(p), s), "gbs_vec_get_values")
+    return dst
+
+
+def gbs_vec_set(v, alpha: float):
+    _check(lib().gbs_vec_set(v, float(alpha)), "gbs_vec_set")
+
+
+def gbs_vec_copy(x, y):
+    _check(lib().gbs_vec_copy(x, y), "gbs_vec_copy")
+
+
+def gbs_vec_axpy(y, alpha: float, x):
+    _check(lib().gbs_vec_axpy(y, float(alpha), x), "gbs_vec_axpy")
+
+
+def gbs_vec_aypx(y, beta: float, x):
+    _check(lib().gbs_vec_aypx(y, float(beta), x), "gbs_vec_aypx")
+
+
+def gbs_vec_pointwise_mult(w, x, y):
+    _check(lib().gbs_vec_pointwise_mult(w, x, y), "gbs_vec_pointwise_mult")
+
+
+def gbs_vec_dot(x, y) -> float:
+    out = ctypes.c_double()
+    _check(lib().gbs_vec_dot(x, y, ctypes.byref(out)), "gbs_vec_dot")
+    return out.value
+
+
+def gbs_vec_norm2(x) -> float:
+    out = ctypes.c_double()
+    _check(lib().gbs_vec_norm2(x, ctypes.byref(out)), "gbs_vec_norm2")
+    return out.value
+
+
+# --------------------------------------------------------- preconditioner --
+
+def gbs_pc_jacobi_create(A):
+    h = _VP()
+    _check(lib().gbs_pc_jacobi_create(A, ctypes.byref(h)), "gbs_pc_jacobi_create")
+    return h
+
+
+def gbs_pc_apply(pc, r, z):
+    _check(lib().gbs_pc_apply(pc, r, z), "gbs_pc_apply")
+
+
+def gbs_pc_destroy(pc):
+    _check(lib().gbs_pc_destroy(pc), "gbs_pc_destroy")
+
+
+# ----------------------------------------------------------------- solver --
+
+def _info(i: gbs_solve_info) -> SolveInfo:
+    return SolveInfo(i.status, i.iters, i.outer_iters, i.rnorm, i.bnorm, i.device_ms)
+
+
+_RESULT_STATUSES = (GBS_OK, GBS_DIVERGED_ITS, GBS_ERR_DIAG, GBS_ERR_INDEFINITE, GBS_ERR_NAN,
+                    GBS_ERR_TIMEOUT, GBS_ERR_STAGNATION)
+
+
+def gbs_ksp_solve_cg(A, b, x, rtol: float, maxit: int):
+    """Returns (status, iters, rnorm)."""
+    it = ctypes.c_int()
+    rn = ctypes.c_double()
+    st = lib().gbs_ksp_solve_cg(A, b, x, float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rn))
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_cg")
+    return st, it.value, rn.value
+
+
+def gbs_ksp_solve_cg_ex(A, b, x, rtol: float, maxit: int, opts: gbs_opts | None = None) -> SolveInfo:
+    info = gbs_solve_info()
+    st = lib().gbs_ksp_solve_cg_ex(A, b, x, float(rtol), int(maxit),
+                                   ctypes.byref(opts) if opts else None, ctypes.byref(info))
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_cg_ex")
+    return _info(info)
+
+
+def gbs_ksp_last_info(ctx) -> SolveInfo:
+    info = gbs_solve_info()
+    _check(lib().gbs_ksp_last_info(ctx, ctypes.byref(info)), "gbs_ksp_last_info")
+    return _info(info)
+
+
+def gbs_ksp_solve_cg_batched(ctx, mats, Bs, Xs, nrhs, rtols, maxit: int, mode: int):
+    """Returns (status, iters[], rnorm[], status[]) per (system, column)."""
+    ns = len(mats)
+    A = (_VP * ns)(*mats)
+    B = (_VP * ns)(*Bs)
+    X = (_VP * ns)(*Xs)
+    K = (ctypes.c_int * ns)(*[int(k) for k in nrhs])
+    R = (ctypes.c_double * ns)(*[float(r) for r in rtols])
+    tot = int(sum(int(k) for k in nrhs))
+    its = np.zeros(tot, dtype=np.int32)
+    rns = np.zeros(tot, dtype=np.float64)
+    sts = np.zeros(tot, dtype=np.int32)
+    st = lib().gbs_ksp_solve_cg_batched(ctx, ns, A, B, X, K, R, int(maxit), int(mode),
+                                        its.ctypes.data, rns.ctypes.data, sts.ctypes.data)
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_cg_batched")
+    return st, its, rns, sts
+
+
+# ---------------------------------------------------------------- serving --
+
+def gbs_server_create(ctx, hbm_budget_bytes: int, max_slots: int = 0, mode: int = GBS_MODE_MIXED):
+    h = _VP()
+    _check(lib().gbs_server_create(ctx, int(hbm_budget_bytes), int(max_slots), int(mode),
+                                   ctypes.byref(h)), "gbs_server_create")
+    return h
+
+
+def gbs_server_destroy(srv):
+    _check(lib().gbs_server_destroy(srv), "gbs_server_destroy")
+
+
+def gbs_server_submit(srv, nrows: int, rowptr, colidx, vals, k: int, b, rtol: float, maxit: int) -> int:
+    for a in (rowptr, colidx, vals, b):
+        if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("server inputs are contiguous host numpy arrays")
+    t = ctypes.c_uint64()
+    _check(lib().gbs_server_submit(srv, int(nrows), rowptr.ctypes.data, colidx.ctypes.data,
+                                   vals.ctypes.data, int(k), b.ctypes.data, float(rtol), int(maxit),
+                                   ctypes.byref(t)), "gbs_server_submit")
+    return t.value
+
+
+def gbs_server_progress(srv) -> int:
+    r = ctypes.c_int()
+    _check(lib().gbs_server_progress(srv, ctypes.byref(r)), "gbs_server_progress")
+    return r.value
+
+
+def gbs_server_poll(srv, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(lib().gbs_server_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(d)), "gbs_server_poll")
+    return bool(d.value)
+
+
+def gbs_server_wait(srv, ticket: int):
+    _check(lib().gbs_server_wait(srv, ctypes.c_uint64(ticket)), "gbs_server_wait")
+
+
+def gbs_server_fetch(srv, ticket: int, n: int, k: int):
+    """Returns (x[n*k], iters[k], rnorm[k], status[k])."""
+    x = np.empty(n * k)
+    its = np.zeros(k, dtype=np.int32)
+    rns = np.zeros(k)
+    sts = np.zeros(k, dtype=np.int32)
+    _check(lib().gbs_server_fetch(srv, ctypes.c_uint64(ticket), x.ctypes.data, its.ctypes.data,
+                                  rns.ctypes.data, sts.ctypes.data), "gbs_server_fetch")
+    return x, its, rns, sts
+
+
+def gbs_server_stats(srv):
+    q, r, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    b = ctypes.c_size_t()
+    _check(lib().gbs_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f),
+                                  ctypes.byref(b)), "gbs_server_stats")
+    return q.value, r.value, f.value, b.value

@@ -198,12 +198,15 @@ def _variable_stencil(dims, neighbour_offsets, scale_of, seed, sigma, stream0):
     pindex = {d: i for i, d in enumerate(positive)}
     weight = _link_weights(dims, seed, sigma, stream0)
     link = {}
+    w_min = math.inf
     for d in neighbour_offsets:
         if d in pindex:
             w = weight(pindex[d], x, y, z)
         else:
             nd = (-d[0], -d[1], -d[2])
             w = weight(pindex[nd], x + d[0], y + d[1], z + d[2])
+        if w.size:
+            w_min = min(w_min, float(w.min()))
         link[d] = scale_of(d) * w
     diag = np.zeros(n)
     for d in neighbour_offsets:          # fixed order: the stencil's own order
@@ -213,7 +216,9 @@ def _variable_stencil(dims, neighbour_offsets, scale_of, seed, sigma, stream0):
     def value_of(k, valid):
         d = offs[k]
         return diag if d == (0, 0, 0) else -link[d]
-    return _assemble(dims, offs, value_of)
+    m = _assemble(dims, offs, value_of)
+    m.meta["w_min"] = w_min            # smallest link weight (Dirichlet links included)
+    return m
 
 
 def _face_offsets(ndim):

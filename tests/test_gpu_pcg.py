@@ -1,0 +1,202 @@
+"""Jacobi-PCG parity: the CUDA solves against the CPU oracle.
+
+Tolerances: iteration counts within +-2 of the oracle; solutions within
+1e-8 relative of the oracle's FP64 solution at rtol 1e-10 (1e-6 at rtol
+1e-8); the true residual ||b - A x||_2, recomputed by the oracle's SpMV,
+within rtol ||b||_2 (1 + 1e-3).  At full size the oracle is too slow to
+solve, so the full-size cases check properties that hold at any size:
+the true residual, the forward error against the manufactured solution
+(<= kappa * rtol), and the closed-form CG iteration bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2011_00715_gb300 import gbs
+from paper_2011_00715_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ALGS = {"persistent": gbs.GBS_ALG_PERSISTENT, "perop": gbs.GBS_ALG_PEROP,
+        "graph": gbs.GBS_ALG_GRAPH}
+
+
+@pytest.fixture(scope="module")
+def S():
+    from gpu_util import Session
+    return Session()
+
+
+def solve(S, A, b, rtol, maxit, x0=None, **opts):
+    h = S.mat(A)
+    bv, bt = S.vec(b)
+    xv, xt = S.vec(np.zeros(A.n) if x0 is None else x0)
+    info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, rtol, maxit, gbs.gbs_opts_default(**opts))
+    x = S.host(xt)
+    gbs.gbs_vec_destroy(bv)
+    gbs.gbs_vec_destroy(xv)
+    gbs.gbs_mat_destroy(h)
+    return info, x
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def true_res(orc, A, b, x):
+    return np.linalg.norm(b - orc.spmv(A, x))
+
+
+def lambda_min(A):
+    """Smallest eigenvalue of the SPD matrix (scipy shift-invert Lanczos)."""
+    sp = pytest.importorskip("scipy.sparse")
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    S = sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.n, A.n))
+    return float(sla.eigsh(S, k=1, sigma=0, which="LM", return_eigenvectors=False)[0])
+
+
+def solution_tol(orc, A, b, x, x_ref, lmin):
+    """Two vectors whose residuals are r and r_ref differ by at most
+    (||r|| + ||r_ref||) / lambda_min: the 1e-8 target applies where the
+    conditioning allows it, this guarantee of the stopping rule elsewhere."""
+    bound = (true_res(orc, A, b, x) + true_res(orc, A, b, x_ref)) / (lmin * np.linalg.norm(x_ref))
+    return max(1e-8, bound)
+
+
+@pytest.mark.parametrize("alg", sorted(ALGS))
+def test_c1_lap2d5_64(S, orc, alg):
+    A = I.lap2d5(64)
+    b = orc.spmv(A, I.xstar(A.n, 1))
+    ref = orc.pcg(A, b, 1e-8, 10000)
+    info, x = solve(S, A, b, 1e-8, 10000, algorithm=ALGS[alg])
+    assert info.status == gbs.GBS_OK
+    assert abs(info.iters - ref["iters"]) <= 2
+    assert rel(x, ref["x"]) <= 1e-6
+    assert true_res(orc, A, b, x) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-3)
+    assert abs(info.bnorm - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("alg", sorted(ALGS))
+@pytest.mark.parametrize("maker", [lambda: I.lap3d7(40), lambda: I.var7(33, 27, 21, seed=7),
+                                   lambda: I.var27(22, seed=3)])
+def test_fp64_rtol_1e10(S, orc, alg, maker):
+    A = maker()
+    b = orc.spmv(A, I.xstar(A.n, 2))
+    ref = orc.pcg(A, b, 1e-10, 20000)
+    info, x = solve(S, A, b, 1e-10, 20000, algorithm=ALGS[alg])
+    assert info.status == gbs.GBS_OK
+    assert abs(info.iters - ref["iters"]) <= 2
+    assert rel(x, ref["x"]) <= 1e-8
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("maker", [lambda: I.var27(22, seed=3), lambda: I.lap3d7(40),
+                                   lambda: I.var5(150, 130, seed=4)])
+def test_mixed_matches_fp64_oracle(S, orc, maker):
+    A = maker()
+    b = orc.spmv(A, I.xstar(A.n, 3))
+    ref = orc.pcg(A, b, 1e-10, 20000)
+    info, x = solve(S, A, b, 1e-10, 20000, mode=gbs.GBS_MODE_MIXED)
+    assert info.status == gbs.GBS_OK, gbs.gbs_status_string(info.status)
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b)
+    assert rel(x, ref["x"]) <= solution_tol(orc, A, b, x, ref["x"], lambda_min(A))
+    assert 1 <= info.outer_iters <= math.ceil(math.log(1e-10) / math.log(1e-4)) + 2
+    assert abs(info.rnorm - true_res(orc, A, b, x)) <= 1e-3 * info.rnorm + 1e-300
+    m = orc.pcg_mixed(A, b, 1e-10, 1e-4)
+    assert m["status"] == 0 and abs(m["outer"] - info.outer_iters) <= 1
+
+
+def test_finite_termination_and_limits(S, orc):
+    A = I.lap2d5(2)
+    b = orc.spmv(A, I.xstar(4, 1))
+    info, _ = solve(S, A, b, 1e-12, 50)
+    assert info.status == gbs.GBS_OK and info.iters == 3
+    A = I.var7(12, 11, 10, seed=3)
+    b = orc.spmv(A, I.xstar(A.n, 4))
+    for k in (0, 1, 5):
+        info, x = solve(S, A, b, 1e-14, k)
+        ref = orc.pcg(A, b, 1e-14, k)
+        assert info.status == gbs.GBS_DIVERGED_ITS and info.iters == k
+        assert rel(x, ref["x"]) <= 1e-12 if k else np.array_equal(x, ref["x"])
+
+
+def test_degenerate_inputs(S, orc):
+    A = I.lap2d5(30)
+    info, x = solve(S, A, np.zeros(A.n), 1e-8, 100)
+    assert info.status == gbs.GBS_OK and info.iters == 0 and not x.any()
+    xs = I.xstar(A.n, 5)
+    b = orc.spmv(A, xs)
+    info, x = solve(S, A, b, 1e-8, 100, x0=xs)
+    assert info.status == gbs.GBS_OK and info.iters == 0
+    bn = b.copy(); bn[7] = np.nan
+    info, _ = solve(S, A, bn, 1e-8, 100)
+    assert info.status == gbs.GBS_ERR_NAN
+    B = I.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+              np.array([1.0, 2.0, 2.0, 1.0]))
+    info, _ = solve(S, B, np.array([1.0, -1.0]), 1e-10, 10)
+    assert info.status == gbs.GBS_ERR_INDEFINITE
+    info, _ = solve(S, B, np.array([1.0, -1.0]), 1e-10, 10, mode=gbs.GBS_MODE_MIXED)
+    assert info.status == gbs.GBS_ERR_INDEFINITE
+    C = I.CSR(2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 0.0]))
+    info, _ = solve(S, C, np.ones(2), 1e-10, 10)
+    assert info.status == gbs.GBS_ERR_DIAG
+    E = I.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    h = S.mat(E)
+    b0 = gbs.gbs_vec_create(S.ctx, 0)
+    x0 = gbs.gbs_vec_create(S.ctx, 0)
+    assert gbs.gbs_ksp_solve_cg(h, b0, x0, 1e-8, 10)[0] == gbs.GBS_OK
+    gbs.gbs_mat_destroy(h)
+
+
+def test_barrier_timeout_is_reported_and_context_survives(S, orc):
+    """One CTA does not arrive at the first grid barrier: every CTA gives up
+    after the short limit, the solve returns GBS_ERR_TIMEOUT, and the same
+    context then solves normally."""
+    A = I.lap3d7(24)
+    b = orc.spmv(A, I.xstar(A.n, 6))
+    for mode in (gbs.GBS_MODE_FP64, gbs.GBS_MODE_MIXED):
+        info, _ = solve(S, A, b, 1e-8, 1000, mode=mode, fault_skip_arrival=0,
+                        barrier_timeout_ms=50)
+        assert info.status == gbs.GBS_ERR_TIMEOUT
+    info, x = solve(S, A, b, 1e-8, 1000)
+    assert info.status == gbs.GBS_OK
+    assert true_res(orc, A, b, x) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-3)
+
+
+def test_c2_full_size_fp64(S, orc):
+    """128^3 7-point Laplacian, rtol 1e-10, the configuration the benchmark
+    times: true residual, forward error <= kappa rtol, and the CG bound."""
+    N = 128
+    A = I.lap3d7(N)
+    xs = I.xstar(A.n, 2)
+    b = orc.spmv(A, xs)
+    info, x = solve(S, A, b, 1e-10, 5000)
+    assert info.status == gbs.GBS_OK
+    c = math.cos(math.pi / (N + 1))
+    kappa = (1 + c) / (1 - c)
+    s = math.sqrt(kappa)
+    bound = math.ceil(math.log(2 * s / 1e-10) / math.log((s + 1) / (s - 1)))
+    assert info.iters <= bound
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
+    assert rel(x, xs) <= kappa * 1e-10
+
+
+def test_c3_full_size_mixed_vs_fp64(S, orc):
+    """96^3 27-point variable-coefficient operator at rtol 1e-10: mixed and
+    FP64 both reach the true FP64 residual and agree to 1e-8."""
+    A = I.var27(96, seed=3, sigma=1.0)
+    b = orc.spmv(A, I.xstar(A.n, 3))
+    i64, x64 = solve(S, A, b, 1e-10, 20000)
+    imx, xmx = solve(S, A, b, 1e-10, 20000, mode=gbs.GBS_MODE_MIXED)
+    assert i64.status == gbs.GBS_OK and imx.status == gbs.GBS_OK
+    nb = np.linalg.norm(b)
+    assert true_res(orc, A, b, x64) <= 1e-10 * nb * (1 + 1e-3)
+    assert true_res(orc, A, b, xmx) <= 1e-10 * nb
+    # lambda_min(A) >= w_min * lambda_min(unit-weight operator) (A minus
+    # w_min times the unit operator is a sum of PSD link terms); the unit
+    # 27-point operator has the closed-form minimum 14 - 6c - 6c^2 - 2c^3,
+    # c = cos(pi / (N + 1))
+    c = math.cos(math.pi / 97)
+    lmin = (14 - 6 * c - 6 * c * c - 2 * c ** 3) * float(A.meta["w_min"])
+    assert rel(xmx, x64) <= solution_tol(orc, A, b, xmx, x64, lmin)

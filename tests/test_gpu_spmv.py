@@ -1,0 +1,191 @@
+"""MatMult parity: the CUDA CSR SpMV against the CPU oracle.
+
+FP64 rows are accumulated left to right in storage order with fused
+multiply-adds: held to ||y - y_orc|| <= 1e-13 ||y_orc|| and, per row, to the
+componentwise bound 2 gamma_m (|A||x|)_i (m = nonzeros in the row), and
+bitwise on exact inputs.  FP32 rows round each product and sum separately
+in the oracle's order, so they are bitwise equal to the oracle's FP32
+product (rows longer than one tile are reduced by a tree and use the
+bounds instead).
+"""
+import numpy as np
+import pytest
+
+from paper_2011_00715_gb300 import gbs
+from paper_2011_00715_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def S():
+    from gpu_util import Session
+    return Session()
+
+
+def with_empty_and_long_rows(n=3000, seed=5):
+    """Random pattern with empty rows, rows of very different lengths and one
+    row longer than a tile (5000 entries)."""
+    a = {}
+    lens = (I.counter_u64(seed, 30, np.arange(n)) % np.uint64(40)).astype(int)
+    lens[::97] = 0
+    for i in range(n):
+        c = (I.counter_u64(seed, 31 + i % 7, np.arange(lens[i]) + 64 * i) % np.uint64(n)).astype(int)
+        v = I.uniform_pm1(seed, 50 + i, lens[i])
+        for cc, vv in zip(c.tolist(), v.tolist()):
+            a[(i, cc)] = vv
+    for j in range(5000):
+        a[(17, (j * 7) % n)] = 1.0 / (j + 1)
+    return I._from_dict(n, a, {"family": "mixed-lengths"})
+
+
+def run(S, A, x, dtype=np.float64):
+    h = S.mat(A)
+    xv, xt = S.vec(x, dtype)
+    yv, yt = S.zeros(A.n, dtype)
+    gbs.gbs_mat_mult(h, xv, yv)
+    y = S.host(yt)
+    for v in (xv, yv):
+        gbs.gbs_vec_destroy(v)
+    gbs.gbs_mat_destroy(h)
+    return y
+
+
+CASES = {
+    "lap2d5_64": lambda: I.lap2d5(64),
+    "lap3d7_20": lambda: I.lap3d7(20),              # 8000 rows, ragged last tile
+    "var27_13": lambda: I.var27(13, seed=3),        # 27 nnz/row: tiles split by nnz
+    "random_rect": lambda: I.random_csr(700, 1300, 11, seed=2),
+    "tiny": lambda: I.lap2d5(2),
+}
+
+
+def assert_within_bounds(orc, A, x, y, ref):
+    rows = np.diff(A.rowptr)
+    absA = I.CSR(A.n, A.rowptr, A.colidx, np.abs(A.vals))
+    absA.meta["ncols"] = A.meta.get("ncols", A.n)
+    g = 2 * rows * U / (1 - 2 * rows * U)
+    assert np.all(np.abs(y - ref) <= g * orc.spmv(absA, np.abs(x)))
+    assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_spmv_fp64(S, name, orc):
+    A = CASES[name]()
+    ncols = A.meta.get("ncols", A.n)
+    x = I.uniform_pm1(17, 0, ncols)
+    y = run(S, A, x)
+    assert_within_bounds(orc, A, x, y, orc.spmv(A, x))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_spmv_fp32_bitwise(S, name, orc):
+    A = CASES[name]()
+    ncols = A.meta.get("ncols", A.n)
+    x = I.uniform_pm1(18, 0, ncols).astype(np.float32)
+    y = run(S, A, x, np.float32)
+    ref = orc.spmv_f32(A, x)
+    assert np.array_equal(y, ref)
+
+
+def test_spmv_empty_and_long_rows(S, orc):
+    A = with_empty_and_long_rows()
+    x = I.uniform_pm1(19, 0, A.n)
+    y = run(S, A, x)
+    ref = orc.spmv(A, x)
+    rows = np.diff(A.rowptr)
+    assert np.all(y[rows == 0] == 0.0)
+    assert_within_bounds(orc, A, x, y, ref)
+    x32 = x.astype(np.float32)
+    y32 = run(S, A, x32, np.float32)
+    ref32 = orc.spmv_f32(A, x32)
+    short = rows <= 2048
+    assert np.array_equal(y32[short], ref32[short])
+
+
+def test_spmv_exact_inputs(S, orc):
+    A = I.exact_csr(5000, 9, seed=4)
+    x = I.exact_vector(5000, seed=6)
+    assert np.array_equal(run(S, A, x), orc.spmv(A, x))
+
+
+def test_spmv_device_resident_input_and_set_values(S, orc):
+    A = I.var7(30, 20, 10, seed=8)
+    h = S.mat(A, device=True)
+    x = I.uniform_pm1(3, 0, A.n)
+    xv, xt = S.vec(x)
+    yv, yt = S.zeros(A.n)
+    gbs.gbs_mat_mult(h, xv, yv)
+    assert_within_bounds(orc, A, x, S.host(yt), orc.spmv(A, x))
+    vals2 = A.vals * 2.0
+    gbs.gbs_mat_set_values(h, vals2)
+    gbs.gbs_mat_mult(h, xv, yv)
+    A2 = I.CSR(A.n, A.rowptr, A.colidx, vals2)
+    assert_within_bounds(orc, A2, x, S.host(yt), orc.spmv(A2, x))
+    assert gbs.gbs_mat_get_info(h) == (A.n, A.n, A.nnz)
+    gbs.gbs_mat_destroy(h)
+
+
+def test_spmv_argument_errors(S):
+    A = I.lap2d5(8)
+    h = S.mat(A)
+    xv, _xt = S.zeros(A.n)
+    yv, _yt = S.zeros(A.n + 1)
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.gbs_mat_mult(h, xv, yv)
+    assert e.value.status == gbs.GBS_ERR_ARG
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.gbs_mat_mult(h, xv, xv)              # aliasing
+    assert e.value.status == gbs.GBS_ERR_ARG
+    gbs.gbs_mat_destroy(h)
+
+
+def test_csr_validation_errors(S):
+    A = I.lap2d5(6)
+    bad = A.colidx.copy(); bad[3] = A.n
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.gbs_mat_create_aij(S.ctx, A.n, A.n, A.rowptr, bad, A.vals)
+    assert e.value.status == gbs.GBS_ERR_CSR
+    uns = A.colidx.copy(); uns[[0, 1]] = uns[[1, 0]]
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.gbs_mat_create_aij(S.ctx, A.n, A.n, A.rowptr, uns, A.vals)
+    assert e.value.status == gbs.GBS_ERR_CSR
+    rp = A.rowptr.copy(); rp[5] = rp[6] + 1
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.gbs_mat_create_aij(S.ctx, A.n, A.n, rp, A.colidx, A.vals)
+    assert e.value.status == gbs.GBS_ERR_CSR
+
+
+def test_empty_matrix(S):
+    E = I.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    h = S.mat(E)
+    xv = gbs.gbs_vec_create(S.ctx, 0)
+    yv = gbs.gbs_vec_create(S.ctx, 0)
+    gbs.gbs_mat_mult(h, xv, yv)
+    assert gbs.gbs_mat_get_info(h) == (0, 0, 0)
+    gbs.gbs_mat_destroy(h)
+
+
+def test_spmv_full_size_3d7_sampled(S, orc):
+    """128^3 7-point Laplacian (2,097,152 rows): sampled rows recomputed by
+    the oracle one by one."""
+    A = I.lap3d7(128)
+    x = I.uniform_pm1(2, 0, A.n)
+    y = run(S, A, x)
+    rows = np.unique((I.counter_u64(9, 0, np.arange(4000)) % np.uint64(A.n)).astype(np.int64))
+    rows = np.concatenate([rows, [0, A.n - 1]])
+    for i in rows:
+        b, e = A.rowptr[i], A.rowptr[i + 1]
+        sub = I.CSR(1, np.array([0, e - b], np.int32), A.colidx[b:e].copy(), A.vals[b:e].copy())
+        sub.meta["ncols"] = A.n
+        ref = orc.spmv(sub, x)[0]
+        absd = float(np.abs(A.vals[b:e]) @ np.abs(x[A.colidx[b:e]]))
+        m = e - b
+        assert abs(y[i] - ref) <= 2 * m * U / (1 - 2 * m * U) * absd
+    # a property at full size: A 1 = number of Dirichlet faces per row
+    ones = run(S, A, np.ones(A.n))
+    c = np.arange(A.n)
+    miss = sum((v == 0).astype(int) + (v == 127) for v in (c % 128, (c // 128) % 128, c // 16384))
+    assert np.array_equal(ones, miss.astype(float))

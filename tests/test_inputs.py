@@ -118,6 +118,27 @@ def test_var27_link_scaling_and_interior_row_sums():
     assert np.allclose(np.diag(B.to_dense()), 6 * 1 + 12 * 0.5 + 8 * 0.25)
 
 
+def test_var27_unit_weight_closed_form_eigenvalues():
+    # with unit weights the 27-point operator is 14 I minus a sum of tensor
+    # products of the 1D Dirichlet shift pair T (eigenvalues 2 cos theta):
+    # lambda = 14 - 2(cx+cy+cz) - 2(cx cy + cx cz + cy cz) - 2 cx cy cz
+    nx, ny, nz = 3, 4, 5
+    lam = []
+    for a in range(1, nx + 1):
+        for b in range(1, ny + 1):
+            for c in range(1, nz + 1):
+                cx, cy, cz = (math.cos(a * math.pi / (nx + 1)), math.cos(b * math.pi / (ny + 1)),
+                              math.cos(c * math.pi / (nz + 1)))
+                lam.append(14 - 2 * (cx + cy + cz) - 2 * (cx * cy + cx * cz + cy * cz)
+                           - 2 * cx * cy * cz)
+    A = I.var27(nx, ny, nz, seed=1, sigma=0.0)
+    assert A.meta["w_min"] == 1.0
+    assert np.allclose(np.linalg.eigvalsh(A.to_dense()), sorted(lam), atol=1e-12)
+    # Loewner bound used by the solver tests: lambda_min(A) >= w_min lambda_min(unit)
+    B = I.var27(nx, ny, nz, seed=3, sigma=1.0)
+    assert np.linalg.eigvalsh(B.to_dense()).min() >= B.meta["w_min"] * min(lam) * (1 - 1e-12)
+
+
 def test_random_and_exact_generators():
     A = I.random_csr(30, 30, 4, seed=5, symmetric=True, diag_shift=0.5)
     d = A.to_dense()
