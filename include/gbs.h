@@ -265,6 +265,40 @@ int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
 /* Result of the last solve issued on the context. */
 int gbs_ksp_last_info(gbs_ctx ctx, gbs_solve_info *info);
 
+/* Largest system gbs_ksp_solve_cg_noalloc accepts (rows). */
+#define GBS_NOALLOC_MAX_ROWS 262144
+
+/* FP64 Jacobi-PCG solve that allocates nothing (the paper has no
+ * counterpart: this is a library service).  It is meant for callers that
+ * cannot allocate device memory while they solve: latency-bound loops,
+ * where cudaMalloc/cudaFree may synchronise the whole device and take
+ * unbounded time, and processes whose device memory is held by another
+ * allocator's pool, where a fresh cudaMalloc can fail.  The matrix must
+ * have been created beforehand (that allocates, once).
+ *
+ * Same arithmetic, stopping rule and statuses as gbs_ksp_solve_cg_ex with
+ * GBS_MODE_FP64 and GBS_ALG_PERSISTENT.  b (read) and x (initial guess in,
+ * solution out) are caller-owned FP64 device arrays of nrows entries;
+ * *info receives the result.  The solver's workspace (four FP64 vectors of
+ * GBS_NOALLOC_MAX_ROWS entries, per-CTA partial sums, barrier and result
+ * record: about 8.1 MB) is one fixed array in the library's device image;
+ * every GPU that loads the library holds it until the process exits.
+ * Limits and behaviour:
+ *  - GBS_ERR_ARG if nrows > GBS_NOALLOC_MAX_ROWS, the matrix is not
+ *    square, b or x is NULL, or b == x.
+ *  - Every call on a device uses the same array and leaves its contents
+ *    behind; the call clears the parts that must start at zero.  Calls that
+ *    overlap on the GPU (other streams or threads of the same device) race
+ *    on the array: serialise them.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ *  - Calls no cudaMalloc, no cudaFree and no other allocating routine; it
+ *    uses the context's stream, events and pinned result buffer (created
+ *    with the context) and synchronises the stream once, at the end. */
+int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, double rtol, int maxit,
+                             gbs_solve_info *info);
+
 /* Batched solve of independent systems in one persistent launch (Response
  * A6, Sec. 4: many different-size problems at once; Challenge F2 / Sec. 4:
  * multiple right-hand sides raise arithmetic intensity).  System s has

@@ -28,6 +28,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "gbs_impl.cuh"
 
 namespace {
@@ -732,4 +734,125 @@ extern "C" int gbs_ksp_last_info(gbs_ctx c, gbs_solve_info *info)
     if (!c || !info) return GBS_ERR_ARG;
     *info = c->last;
     return GBS_OK;
+}
+
+// ----------------------------------------------------------------------
+// Allocation-free FP64 solve.
+//
+// Some callers cannot allocate device memory at solve time: latency-bound
+// loops (cudaMalloc and cudaFree may synchronise the whole device and take
+// unbounded time) and processes whose device memory is owned by another
+// allocator's pool, where a fresh cudaMalloc can fail.  This entry point
+// runs the same persistent FP64 kernel as gbs_ksp_solve_cg_ex, with its
+// whole workspace (r, z, p, q, the per-CTA partial sums, the grid barrier
+// and the result record) in the fixed array below instead of the
+// context's scratch.  The array is part of this library's device image:
+// every GPU that loads the library holds it until the process exits.
+// ----------------------------------------------------------------------
+
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = GBS_NOALLOC_MAX_ROWS;
+constexpr int kNoAllocMaxCtas = 2048;
+constexpr size_t kNoAllocHead = 512;  // barrier (offset 0) + result record (offset 256)
+constexpr size_t kNoAllocPart = sizeof(double) * kSlots * kNoAllocMaxCtas;
+constexpr size_t kNoAllocVec = sizeof(double) * kNoAllocMaxRows;
+constexpr size_t kNoAllocBytes = kNoAllocHead + kNoAllocPart + 4 * kNoAllocVec;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once (under a
+// lock, so concurrent first calls from several threads are safe).
+struct NoAllocSetup {
+    void *addr[64];
+    bool done[64];
+};
+NoAllocSetup g_noalloc_setup = {};
+std::mutex g_noalloc_lock;
+
+int noalloc_address(int device, void **out)
+{
+    if (device < 0 || device >= 64) return GBS_ERR_ARG;
+    std::lock_guard<std::mutex> guard(g_noalloc_lock);
+    if (!g_noalloc_setup.done[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return gbs_cuda_fail(e);
+        g_noalloc_setup.addr[device] = p;
+        g_noalloc_setup.done[device] = true;
+    }
+    *out = g_noalloc_setup.addr[device];
+    return GBS_OK;
+}
+
+}  // namespace
+
+extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, double rtol,
+                                        int maxit, gbs_solve_info *info)
+{
+    if (!A || !info || !(rtol >= 0.0) || maxit < 0) return GBS_ERR_ARG;
+    if (A->n != A->ncols) return GBS_ERR_ARG;
+    if (A->n > kNoAllocMaxRows) return GBS_ERR_ARG;
+    if (A->n > 0 && (!b || !x || b == x)) return GBS_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    if (A->n == 0) return GBS_OK;
+    if (!A->diag_ok) {
+        info->status = GBS_ERR_DIAG;
+        return GBS_ERR_DIAG;
+    }
+    gbs_ctx c = A->ctx;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    void *scr = nullptr;
+    int st = noalloc_address(c->device, &scr);
+    if (st) return st;
+    int G = coop_grid(c, (const void *)k_pcg_fp64, A->ntiles);
+    if (G < 0) return GBS_ERR_CUDA;
+    if (G > kNoAllocMaxCtas) G = kNoAllocMaxCtas;
+    char *base = (char *)scr;
+    PcgArgs a;
+    memset(&a, 0, sizeof(a));
+    a.bar = (gbs_grid_barrier *)base;
+    a.res = (gbs_result_dev *)(base + 256);
+    a.part64 = (double *)(base + kNoAllocHead);
+    char *v = base + kNoAllocHead + kNoAllocPart;
+    a.r = (double *)v;
+    a.z = (double *)(v + kNoAllocVec);
+    a.p = (double *)(v + 2 * kNoAllocVec);
+    a.q = (double *)(v + 3 * kNoAllocVec);
+    a.n = A->n;
+    a.ntiles = A->ntiles;
+    a.tiles = A->tiles;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.vals = A->vals;
+    a.dinv = A->dinv;
+    a.b = b;
+    a.x = x;
+    a.rtol = rtol;
+    a.maxit = maxit;
+    a.skip_cta = -1;
+    a.timeout_ns = (unsigned long long)c->opts.barrier_timeout_ms * 1000000ull;
+    // the barrier and the result record must start at zero; the vectors and
+    // partial sums are written before they are read
+    GBS_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocHead, c->stream));
+    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    void *args[] = {&a};
+    GBS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_fp64, dim3(G), dim3(GBS_BLOCK),
+                                             args, 0, c->stream));
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    gbs_result_dev r;
+    memcpy(&r, c->pinned, sizeof(r));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->status = r.status;
+    info->iters = r.iters;
+    info->outer_iters = 0;
+    info->rnorm = r.rnorm;
+    info->bnorm = r.bnorm;
+    info->device_ms = ms;
+    return r.status;
 }

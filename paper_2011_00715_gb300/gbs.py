@@ -117,6 +117,8 @@ _SIGS = {
     "gbs_ksp_solve_cg_ex": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.POINTER(gbs_opts),
                              ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
     "gbs_ksp_last_info": ([_VP, ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
+    "gbs_ksp_solve_cg_noalloc": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
     "gbs_ksp_solve_cg_batched": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_int,
                                   ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
     "gbs_server_create": ([_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -393,6 +395,23 @@ def gbs_ksp_solve_cg_ex(A, b, x, rtol: float, maxit: int, opts: gbs_opts | None 
 def gbs_ksp_last_info(ctx) -> SolveInfo:
     info = gbs_solve_info()
     _check(lib().gbs_ksp_last_info(ctx, ctypes.byref(info)), "gbs_ksp_last_info")
+    return _info(info)
+
+
+def gbs_ksp_solve_cg_noalloc(A, b, x, rtol: float, maxit: int) -> SolveInfo:
+    """Allocation-free FP64 solve: b and x are caller-owned CUDA float64
+    tensors of the matrix's size (see include/gbs.h for the limits)."""
+    pb, sb, _kb = _ptr_space(b)
+    px, sx, _kx = _ptr_space(x)
+    if sb != GBS_MEM_DEVICE or sx != GBS_MEM_DEVICE:
+        raise ValueError("b and x must be device tensors")
+    if _dtype_code(b) != GBS_F64 or _dtype_code(x) != GBS_F64:
+        raise TypeError("b and x must be float64")
+    info = gbs_solve_info()
+    st = lib().gbs_ksp_solve_cg_noalloc(A, _VP(pb), _VP(px), float(rtol), int(maxit),
+                                        ctypes.byref(info))
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_cg_noalloc")
     return _info(info)
 
 
