@@ -50,6 +50,10 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true", help="headline line only")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="budget of the bounded oracle sample")
+    p.add_argument("--quick", action="store_true",
+                   help="device-resident headline solve only (no e2e, extras or CPU baseline)")
+    p.add_argument("--maxit", type=int, default=20000,
+                   help="iteration cap of the headline solve (profiling runs use a small cap)")
     return p.parse_args()
 
 
@@ -178,10 +182,11 @@ def run_reference(args, rank, world):
     oracle.build()
     A, xs = c2_problem()
     b = oracle.spmv(A, xs)
-    # iteration count of the full solve from a cheap bound-free estimate:
-    # run the oracle's own full solve only if affordable, else use a sample
+    # one full, untimed oracle solve gives the iteration count that each
+    # timed step's bounded sample is extrapolated to
+    full = oracle.pcg(A, b, RTOL, MAXIT)
+    full_iters = int(full["iters"])
     per_step_budget = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
-    full_iters = 564  # oracle iteration count of this solve (measured once)
     for _ in range(args.warmup):
         oracle_rate(A, b, full_iters, per_step_budget / 2)
     vals = []
@@ -270,7 +275,7 @@ def run_gbs(args, rank, world, local):
 
     def step():
         gbs.gbs_vec_set(xv, 0.0)
-        infos.append(gbs.gbs_ksp_solve_cg_ex(Ah, bv, xv, RTOL, MAXIT, opts))
+        infos.append(gbs.gbs_ksp_solve_cg_ex(Ah, bv, xv, RTOL, args.maxit, opts))
 
     for _ in range(args.warmup):
         step()
@@ -328,7 +333,7 @@ def run_gbs(args, rank, world, local):
             "clocks": clk}
     gbs.gbs_vec_destroy(rv)
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.quick:
         line["e2e"] = e2e_c2(g, A, xs, args, infos[0].iters)
         if not args.no_extras:
             line["extras"] = extras(g, args, A, Ah, xsv)

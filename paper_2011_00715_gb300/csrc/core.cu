@@ -241,7 +241,7 @@ static int grid_for(gbs_ctx c, int64_t n, int per_sm = 4)
     return g < 1 ? 1 : (int)g;
 }
 
-// Split rows into tiles: at most GBS_TILE_ROWS rows and GBS_TILE_NNZ
+// Split rows into warp tiles: at most GBS_WT_ROWS rows and GBS_WT_NNZ
 // nonzeros each; a longer row is a tile of its own.
 static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &tiles, int *maxrow)
 {
@@ -251,12 +251,12 @@ static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &t
     int mr = 0;
     while (start < n) {
         int64_t end = start;
-        while (end < n && end - start < GBS_TILE_ROWS) {
+        while (end < n && end - start < GBS_WT_ROWS) {
             const int64_t rn = rowptr[end + 1] - rowptr[end];
             if (rn > mr) mr = (int)rn;
-            if (end > start && rowptr[end + 1] - rowptr[start] > GBS_TILE_NNZ) break;
+            if (end > start && rowptr[end + 1] - rowptr[start] > GBS_WT_NNZ) break;
             ++end;
-            if (rn > GBS_TILE_NNZ) break;  // a long row stays alone
+            if (rn > GBS_WT_NNZ) break;  // a long row stays alone
         }
         tiles.push_back((int32_t)end);
         start = end;
@@ -431,19 +431,43 @@ extern "C" int gbs_mat_destroy(gbs_mat A)
 template <typename V>
 struct StoreEpi {
     V *y;
-    __device__ __forceinline__ void operator()(int64_t row, V s) const { y[row] = s; }
+    uint64_t pol;
+    __device__ __forceinline__ void operator()(int64_t row, V s) const { gbs_st(y + row, s, pol); }
 };
 
+// MatMult over warp tiles: warp w of the grid takes tiles w, w + W, ...
 template <typename V>
 __global__ void __launch_bounds__(GBS_BLOCK) k_spmv(int64_t ntiles, const int32_t *tiles,
                                                     const int32_t *rowptr, const int32_t *colidx,
                                                     const V *vals, const V *x, V *y)
 {
-    __shared__ GbsTile<V> tl;
-    __shared__ V s_red[GBS_WARPS];
-    StoreEpi<V> epi{y};
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-        gbs_spmv_tile<V>(rowptr, colidx, vals, x, tiles[t], tiles[t + 1], tl, s_red, epi);
+    extern __shared__ __align__(16) unsigned char smem[];
+    GbsWarpTile<V> *wts = reinterpret_cast<GbsWarpTile<V> *>(smem);
+    GbsWarpTile<V> &wt = wts[threadIdx.x >> 5];
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
+    StoreEpi<V> epi{y, pk};
+    const int64_t nw = (int64_t)gridDim.x * GBS_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * GBS_WARPS + (threadIdx.x >> 5); t < ntiles; t += nw)
+        gbs_spmv_warp<V>(rowptr, colidx, vals, x, __ldg(tiles + t), __ldg(tiles + t + 1), wt, ps, pk,
+                         epi);
+}
+
+template <typename V>
+static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V *y)
+{
+    const size_t smem = sizeof(GbsWarpTile<V>) * GBS_WARPS;
+    GBS_CUDA_TRY(cudaFuncSetAttribute((const void *)k_spmv<V>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V>, GBS_BLOCK, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (A->ntiles + GBS_WARPS - 1) / GBS_WARPS;
+    const int64_t cap = (int64_t)c->num_sms * per_sm;
+    const int g = (int)(need < cap ? need : cap);
+    k_spmv<V><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx, vals, x, y);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
 }
 
 extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
@@ -454,22 +478,11 @@ extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
     gbs_ctx c = A->ctx;
     if (A->n == 0) return GBS_OK;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
-    const int64_t g64 = A->ntiles < (int64_t)c->num_sms * 8 ? A->ntiles : (int64_t)c->num_sms * 8;
-    const int g = (int)g64;
-    if (x->dtype == GBS_F64) {
-        k_spmv<double><<<g, GBS_BLOCK, 0, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx,
-                                                       A->vals, (const double *)x->data,
-                                                       (double *)y->data);
-    } else {
-        int st = gbs_mat_ensure_f32(A);
-        if (st) return st;
-        k_spmv<float><<<g, GBS_BLOCK, 0, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx,
-                                                      A->vals32, (const float *)x->data,
-                                                      (float *)y->data);
-    }
-    gbs_count_launch(c);
-    GBS_CUDA_TRY(cudaGetLastError());
-    return GBS_OK;
+    if (x->dtype == GBS_F64)
+        return spmv_launch<double>(c, A, A->vals, (const double *)x->data, (double *)y->data);
+    int st = gbs_mat_ensure_f32(A);
+    if (st) return st;
+    return spmv_launch<float>(c, A, A->vals32, (const float *)x->data, (float *)y->data);
 }
 
 // --------------------------------------------------------------- vector --

@@ -6,10 +6,12 @@
 
 #include "gbs.h"
 
-#define GBS_BLOCK 256          // threads per CTA of the tile kernels
-#define GBS_TILE_ROWS 256      // rows per CSR tile at most
-#define GBS_TILE_NNZ 2048      // nonzeros per CSR tile at most (longer rows: own tile)
+#define GBS_BLOCK 256          // threads per CTA of the standalone kernels
 #define GBS_WARPS (GBS_BLOCK / 32)
+#define GBS_PBLOCK 512         // threads per CTA of the persistent solver kernels
+#define GBS_PWARPS (GBS_PBLOCK / 32)
+#define GBS_WT_ROWS 32         // rows per warp tile at most
+#define GBS_WT_NNZ 512         // nonzeros per warp tile at most (a longer row is a tile of its own)
 
 #define GBS_CUDA_TRY(call)                                   \
     do {                                                     \
@@ -44,7 +46,7 @@ struct gbs_mat_s {
     double *dinv;               // 1 / a_ii (valid if diag_ok)
     float *dinv32;
     int diag_ok;
-    int32_t *tiles;             // row starts of the CSR tiles, ntiles + 1 entries
+    int32_t *tiles;             // row starts of the warp tiles, ntiles + 1 entries
     int64_t ntiles;
     int max_row_nnz;
 };
@@ -121,13 +123,75 @@ __device__ __forceinline__ int gbs_ld_relaxed_int(const int *p)
     return v;
 }
 
-// Streaming loads of matrix data: read once per iteration, not kept in L1.
-template <typename T>
-__device__ __forceinline__ T gbs_ld_stream(const T *p) { return __ldcs(p); }
+// L2 cache policies: matrix data is streamed once per iteration (evict
+// first, no L1 allocation); solver vectors are re-read every iteration and
+// should stay in the 126 MB L2 (evict last).
+__device__ __forceinline__ uint64_t gbs_policy_stream()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t gbs_policy_keep()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 
-// Sum v[0..K) over the CTA with a fixed shuffle tree; every thread gets the
-// totals.  s_red must hold K * GBS_WARPS values.  Deterministic.
-template <typename T, int K>
+// Read-only streaming loads (matrix arrays, unchanged during a launch).
+__device__ __forceinline__ int32_t gbs_ld_stream(const int32_t *p, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double gbs_ld_stream(const double *p, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
+                 : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float gbs_ld_stream(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+                 : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Coherent loads and stores of vectors with an L2 policy.  Vectors written
+// inside a persistent launch are read back with these (never through the
+// read-only path); the grid barrier's acquire makes other CTAs' writes
+// visible.
+__device__ __forceinline__ double gbs_ld(const double *p, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float gbs_ld(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void gbs_st(double *p, double v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void gbs_st(float *p, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol)
+                 : "memory");
+}
+
+// Sum v[0..K) over a CTA of NW warps with a fixed shuffle tree; every thread
+// gets the totals.  s_red must hold K * NW values.  Deterministic.
+template <typename T, int K, int NW = GBS_WARPS>
 __device__ __forceinline__ void gbs_block_sum(T (&v)[K], T *s_red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -137,16 +201,57 @@ __device__ __forceinline__ void gbs_block_sum(T (&v)[K], T *s_red)
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) s_red[k * GBS_WARPS + warp] = v[k];
+        for (int k = 0; k < K; ++k) s_red[k * NW + warp] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        T t = lane < GBS_WARPS ? s_red[k * GBS_WARPS + lane] : T(0);
+        T t = lane < NW ? s_red[k * NW + lane] : T(0);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         v[k] = t;
     }
     __syncthreads();
+}
+
+// Sum v[0..K) over a CTA of NT threads with few FP64 operations: every
+// thread stages its values in s_buf (K * NT entries), then warp k adds value
+// k (lane l takes entries l, l+32, ... left to right) and finishes with a
+// fixed shuffle tree.  Deterministic.  Requires K <= NT / 32.  The totals
+// are returned in s_out[0..K) after a CTA barrier.
+template <typename T, int K, int NT>
+__device__ __forceinline__ void gbs_block_sum_staged(const T (&v)[K], T *s_buf, T *s_out)
+{
+    static_assert(K <= NT / 32, "one warp per value");
+#pragma unroll
+    for (int k = 0; k < K; ++k) s_buf[k * NT + threadIdx.x] = v[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < K) {
+        T t = T(0);
+#pragma unroll
+        for (int j = lane; j < NT; j += 32) t += s_buf[warp * NT + j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) s_out[warp] = t;
+    }
+    __syncthreads();
+}
+
+// Warp-level version of gbs_grid_sum for warp 0 only: every lane of the
+// calling warp gets the K totals (same fixed order, no CTA barrier).
+template <typename T, int K>
+__device__ __forceinline__ void gbs_warp_grid_sum(const T *partials, int stride, int G,
+                                                  T (&out)[K])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T t = T(0);
+        for (int c = lane; c < G; c += 32) t += __ldcg(partials + k * stride + c);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        out[k] = t;
+    }
 }
 
 // Sum partials[k * stride + c] over c in [0, G) for k < K, in a fixed order
@@ -200,7 +305,7 @@ __device__ __forceinline__ bool gbs_grid_sync(gbs_grid_barrier *bar, unsigned lo
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         *s_flag = ok;
     }
@@ -217,70 +322,75 @@ __device__ __forceinline__ float gbs_mac(float a, float x, float s)
     return __fadd_rn(s, __fmul_rn(a, x));
 }
 
-// Shared memory of one CSR tile.
+// Shared memory of one warp tile.
 template <typename V>
-struct GbsTile {
-    int32_t rp[GBS_TILE_ROWS + 1];
-    int32_t col[GBS_TILE_NNZ];
-    V val[GBS_TILE_NNZ];
+struct GbsWarpTile {
+    int32_t col[GBS_WT_NNZ];
+    V val[GBS_WT_NNZ];
 };
 
-// One CSR tile: rows [r0, r1) of y = A v.  For each row, epi(row, sum) is
-// called by exactly one thread.  The tile's colidx/vals (contiguous in
-// CSR) are staged in shared memory with coalesced streaming loads; then
-// one thread per row accumulates its row left to right in storage order.
-// The gathers of v use ordinary coherent loads, never the read-only path:
-// inside a persistent kernel v changes between iterations (made visible
-// by the grid barrier's acquire).  A tile holding a single row longer than
-// GBS_TILE_NNZ is reduced by the whole CTA with a fixed tree.
-// s_red must hold GBS_WARPS values.
+// One warp tile: rows [r0, r1) (at most 32) of y = A v, computed by one
+// warp.  The tile's colidx/vals (contiguous in CSR) are staged in the
+// warp's shared memory with coalesced streaming loads, several in flight
+// per lane; then lane l accumulates row r0 + l left to right in storage
+// order and calls epi(row, sum).  A tile holding a single row longer than
+// GBS_WT_NNZ is reduced by the warp with a fixed shuffle tree.  No CTA-wide
+// synchronisation: warps progress independently.  The gathers of v are
+// coherent loads (v may have been written earlier in the same launch).
 template <typename V, typename Epi>
-__device__ __forceinline__ void gbs_spmv_tile(const int32_t *__restrict__ rowptr,
+__device__ __forceinline__ void gbs_spmv_warp(const int32_t *__restrict__ rowptr,
                                               const int32_t *__restrict__ colidx,
                                               const V *__restrict__ vals, const V *v, int64_t r0,
-                                              int64_t r1, GbsTile<V> &tl, V *s_red, Epi &epi)
+                                              int64_t r1, GbsWarpTile<V> &wt, uint64_t pol_stream,
+                                              uint64_t pol_keep, Epi &epi)
 {
+    const int lane = threadIdx.x & 31;
     const int nrows = (int)(r1 - r0);
-    for (int t = threadIdx.x; t <= nrows; t += GBS_BLOCK) tl.rp[t] = rowptr[r0 + t];
-    __syncthreads();
-    const int k0 = tl.rp[0], k1 = tl.rp[nrows];
-    if (k1 - k0 <= GBS_TILE_NNZ) {
-        constexpr int U = 4;
-        for (int base = k0 + threadIdx.x; base < k1; base += GBS_BLOCK * U) {
+    int beg = 0, end = 0;
+    if (lane < nrows) {
+        beg = gbs_ld_stream(rowptr + r0 + lane, pol_stream);
+        end = gbs_ld_stream(rowptr + r0 + lane + 1, pol_stream);
+    }
+    const int k0 = __shfl_sync(0xffffffffu, beg, 0);
+    const int k1 = __shfl_sync(0xffffffffu, end, nrows - 1);
+    if (k1 - k0 <= GBS_WT_NNZ) {
+        constexpr int U = 8;
+        for (int base = k0 + lane; base < k1; base += 32 * U) {
             int c[U];
             V a[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int k = base + u * GBS_BLOCK;
-                c[u] = k < k1 ? gbs_ld_stream(colidx + k) : 0;
-                a[u] = k < k1 ? gbs_ld_stream(vals + k) : V(0);
+                const int k = base + 32 * u;
+                c[u] = k < k1 ? gbs_ld_stream(colidx + k, pol_stream) : 0;
+                a[u] = k < k1 ? gbs_ld_stream(vals + k, pol_stream) : V(0);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int k = base + u * GBS_BLOCK;
+                const int k = base + 32 * u;
                 if (k < k1) {
-                    tl.col[k - k0] = c[u];
-                    tl.val[k - k0] = a[u];
+                    wt.col[k - k0] = c[u];
+                    wt.val[k - k0] = a[u];
                 }
             }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < nrows; t += GBS_BLOCK) {
-            const int e = tl.rp[t + 1] - k0;
+        __syncwarp();
+        if (lane < nrows) {
             V s = V(0);
+            const int e = end - k0;
 #pragma unroll 4
-            for (int k = tl.rp[t] - k0; k < e; ++k) s = gbs_mac(tl.val[k], v[tl.col[k]], s);
-            epi(r0 + t, s);
+            for (int k = beg - k0; k < e; ++k) s = gbs_mac(wt.val[k], gbs_ld(v + wt.col[k], pol_keep), s);
+            epi(r0 + lane, s);
         }
-        __syncthreads();
+        __syncwarp();
     } else {
         V s = V(0);
-        for (int k = k0 + threadIdx.x; k < k1; k += GBS_BLOCK)
-            s = gbs_mac(gbs_ld_stream(vals + k), v[gbs_ld_stream(colidx + k)], s);
-        V tot[1] = {s};
-        gbs_block_sum<V, 1>(tot, s_red);
-        if (threadIdx.x == 0) epi(r0, tot[0]);
-        __syncthreads();
+        for (int k = k0 + lane; k < k1; k += 32)
+            s = gbs_mac(gbs_ld_stream(vals + k, pol_stream),
+                        gbs_ld(v + gbs_ld_stream(colidx + k, pol_stream), pol_keep), s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) epi(r0, s);
+        __syncwarp();
     }
 }
 

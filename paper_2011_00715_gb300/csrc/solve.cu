@@ -2,7 +2,7 @@
 // paper) on one GPU.
 //
 // Persistent path: one cooperative kernel runs the whole solve.  Each CTA
-// owns a contiguous range of CSR tiles (rows); per iteration it
+// owns a contiguous range of warp tiles (rows); per iteration it
 //   S: forms q = A p on its rows with the p.q partial fused in the SpMV
 //      epilogue                                          -> grid barrier
 //   U: alpha = rho / p.q; x += alpha p; r -= alpha q; z = D^-1 r, with the
@@ -13,6 +13,8 @@
 // dot products otherwise force a host synchronisation each iteration).
 // Every CTA reduces the per-CTA partials in the same fixed order, so all
 // CTAs hold bitwise-identical scalars and take identical decisions.
+// Matrix arrays stream through L2 with an evict-first policy; the solver
+// vectors use evict-last so that they can stay in L2 across iterations.
 //
 // Mixed mode (Response A7: single precision on the GPU): the same kernel
 // shape with an outer iterative-refinement loop inside it: FP64
@@ -35,15 +37,22 @@
 namespace {
 
 constexpr int kSlots = 8;   // partial-sum slots per CTA
+constexpr size_t kPersistSmem = sizeof(GbsWarpTile<double>) * GBS_PWARPS;
 
 template <typename T>
-struct TileSmem {
-    T red[4 * GBS_WARPS];
-    T bcast[4];
+struct PcgSmall {
+    T buf[3 * GBS_PBLOCK];   // staged block sums
+    T out[4];
 };
 
-struct KernelShared {
-    int flag;
+// Control block written by thread 0 of each CTA after a grid reduction and
+// read by the CTA's other threads.  All CTAs compute it from the same
+// partials in the same order, so all take the same decisions.
+template <typename T>
+struct PcgCtl {
+    T alpha, beta;
+    int go;
+    int status;
 };
 
 // Arguments of the persistent kernels.
@@ -76,147 +85,222 @@ struct PcgArgs {
     unsigned long long timeout_ns;
 };
 
-// Row range of CTA c: tiles [c*T/G, (c+1)*T/G).
+// Warp tiles [t0, t1) of CTA c: an even split of the tile list.
 __device__ __forceinline__ void cta_tiles(const PcgArgs &a, int64_t &t0, int64_t &t1)
 {
     t0 = a.ntiles * blockIdx.x / gridDim.x;
     t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
 }
 
-// Inner PCG loop on (vals_T, dinv_T) for rhs bT, solution xT (in/out), work
-// vectors rT..qT, as described at the top of this file.  Returns a status;
-// all CTAs return the same one.  *iters receives the iteration count.
+// Status of the stopping test taken before each iteration (-100: go on).
+template <typename T>
+__device__ __forceinline__ int pcg_check(T rn, T rho, T tol, int k, int maxit)
+{
+    if (isnan(rn) || isnan(rho)) return GBS_ERR_NAN;
+    if (rn <= tol) return GBS_OK;
+    if (k >= maxit) return GBS_DIVERGED_ITS;
+    return -100;
+}
+
+// PCG loop on (vals_T, dinv_T) for rhs bT, solution xT (in/out), work
+// vectors rT..qT, as described at the top of this file.  Returns a status,
+// the same in every thread of every CTA.  The scalar recurrences (rho,
+// ||r||, alpha, beta, the stopping test) run in thread 0 of each CTA only;
+// *iters, *rnorm_out and *bnorm_out are valid in thread 0.
 template <typename T>
 __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T *bT, T *xT, T *rT,
                         T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
-                        int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no, GbsTile<T> &tl,
-                        TileSmem<T> &sm, int *s_flag)
+                        int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no,
+                        GbsWarpTile<T> &wt, PcgSmall<T> &sm, PcgCtl<T> &ctl, int *s_flag)
 {
-    const int G = gridDim.x, c = blockIdx.x;
+    const int G = gridDim.x, c = blockIdx.x, warp = threadIdx.x >> 5;
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     int64_t t0, t1;
     cta_tiles(a, t0, t1);
     const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
     const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
-    *iters = 0;
+    // scalar state, meaningful in thread 0 only
+    T rho = T(0), rr = T(0), bnorm = T(0);
+    int k = 0, status = GBS_DIVERGED_ITS;
 
     // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b
     T acc[3] = {T(0), T(0), T(0)};
     if (!x0_zero) {
         auto epi = [&](int64_t i, T s) {
-            const T bi = bT[i];
+            const T bi = gbs_ld(bT + i, pk);
             const T ri = bi - s;
-            const T zi = dinv[i] * ri;
-            rT[i] = ri;
-            zT[i] = zi;
-            pT[i] = zi;
+            const T zi = gbs_ld(dinv + i, pk) * ri;
+            gbs_st(rT + i, ri, pk);
+            gbs_st(zT + i, zi, pk);
+            gbs_st(pT + i, zi, pk);
             acc[0] += ri * zi;
             acc[1] += ri * ri;
             acc[2] += bi * bi;
         };
-        for (int64_t t = t0; t < t1; ++t)
-            gbs_spmv_tile<T>(a.rowptr, a.colidx, vals, xT, __ldg(a.tiles + t),
-                             __ldg(a.tiles + t + 1), tl, sm.red, epi);
+        for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
+            gbs_spmv_warp<T>(a.rowptr, a.colidx, vals, xT, __ldg(a.tiles + t),
+                             __ldg(a.tiles + t + 1), wt, ps, pk, epi);
     } else {
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
-            const T bi = bT[i];
-            const T zi = dinv[i] * bi;
-            xT[i] = T(0);
-            rT[i] = bi;
-            zT[i] = zi;
-            pT[i] = zi;
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK) {
+            const T bi = gbs_ld(bT + i, pk);
+            const T zi = gbs_ld(dinv + i, pk) * bi;
+            gbs_st(xT + i, T(0), pk);
+            gbs_st(rT + i, bi, pk);
+            gbs_st(zT + i, zi, pk);
+            gbs_st(pT + i, zi, pk);
             acc[0] += bi * zi;
             acc[1] += bi * bi;
             acc[2] += bi * bi;
         }
     }
-    gbs_block_sum<T, 3>(acc, sm.red);
+    gbs_block_sum_staged<T, 3, GBS_PBLOCK>(acc, sm.buf, sm.out);
     if (threadIdx.x == 0) {
-        part[0 * G + c] = acc[0];
-        part[1 * G + c] = acc[1];
-        part[2 * G + c] = acc[2];
+        part[0 * G + c] = sm.out[0];
+        part[1 * G + c] = sm.out[1];
+        part[2 * G + c] = sm.out[2];
     }
     const bool skip = (a.skip_cta == c) && (*barrier_no == 0);
     if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, skip, s_flag)) return GBS_ERR_TIMEOUT;
-    T g3[3];
-    gbs_grid_sum<T, 3>(part, G, G, g3, sm.bcast);
-    T rho = g3[0], rr = g3[1];
-    const T bnorm = sqrt(g3[2]);
-    *bnorm_out = bnorm;
+    if (warp == 0) {
+        T g3[3];
+        gbs_warp_grid_sum<T, 3>(part, G, G, g3);
+        if (threadIdx.x == 0) {
+            rho = g3[0];
+            rr = g3[1];
+            bnorm = sqrt(g3[2]);
+            const int s = pcg_check<T>(sqrt(rr), rho, rtol * bnorm, 0, maxit);
+            ctl.go = s == -100;
+            if (!ctl.go) status = s;
+        }
+    }
+    __syncthreads();
 
-    int k = 0;
-    int status;
-    for (;;) {
-        const T rn = sqrt(rr);
-        *rnorm_out = rn;
-        if (isnan(rn) || isnan(rho)) { status = GBS_ERR_NAN; break; }
-        if (rn <= rtol * bnorm) { status = GBS_OK; break; }
-        if (k >= maxit) { status = GBS_DIVERGED_ITS; break; }
-
+    // every thread also counts iterations itself, so the loop is finite even
+    // if the shared control block were ever wrong
+    for (int k_all = 0; ctl.go && k_all <= maxit; ++k_all) {
         // ---- S: q = A p, partial p.q
         T pq[1] = {T(0)};
         auto epi = [&](int64_t i, T s) {
-            qT[i] = s;
-            pq[0] += __ldcg(pT + i) * s;
+            gbs_st(qT + i, s, pk);
+            pq[0] += gbs_ld(pT + i, pk) * s;
         };
-        for (int64_t t = t0; t < t1; ++t)
-            gbs_spmv_tile<T>(a.rowptr, a.colidx, vals, pT, __ldg(a.tiles + t),
-                             __ldg(a.tiles + t + 1), tl, sm.red, epi);
-        gbs_block_sum<T, 1>(pq, sm.red);
-        if (threadIdx.x == 0) part[3 * G + c] = pq[0];
+        for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
+            gbs_spmv_warp<T>(a.rowptr, a.colidx, vals, pT, __ldg(a.tiles + t),
+                             __ldg(a.tiles + t + 1), wt, ps, pk, epi);
+        gbs_block_sum_staged<T, 1, GBS_PBLOCK>(pq, sm.buf, sm.out);
+        if (threadIdx.x == 0) part[3 * G + c] = sm.out[0];
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
-        T pi[1];
-        gbs_grid_sum<T, 1>(part + 3 * G, G, G, pi, sm.bcast);
-        if (isnan(pi[0])) { status = GBS_ERR_NAN; break; }
-        if (pi[0] <= T(0)) { status = GBS_ERR_INDEFINITE; break; }
-        const T alpha = rho / pi[0];
+        if (warp == 0) {
+            T pi[1];
+            gbs_warp_grid_sum<T, 1>(part + 3 * G, G, G, pi);
+            if (threadIdx.x == 0) {
+                if (isnan(pi[0])) status = GBS_ERR_NAN;
+                else if (pi[0] <= T(0)) status = GBS_ERR_INDEFINITE;
+                ctl.go = !(isnan(pi[0]) || pi[0] <= T(0));
+                ctl.alpha = rho / pi[0];
+            }
+        }
+        __syncthreads();
+        if (!ctl.go) break;
+        const T alpha = ctl.alpha;
 
         // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
         T u[2] = {T(0), T(0)};
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
-            const T pi_ = pT[i];
-            xT[i] += alpha * pi_;
-            const T ri = rT[i] - alpha * qT[i];
-            const T zi = dinv[i] * ri;
-            rT[i] = ri;
-            zT[i] = zi;
-            u[0] += ri * zi;
-            u[1] += ri * ri;
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 2 * GBS_PBLOCK) {
+            const int64_t i1 = i0 + GBS_PBLOCK;
+            const bool h1 = i1 < re;
+            const T p0 = gbs_ld(pT + i0, pk), x0 = gbs_ld(xT + i0, pk), r0 = gbs_ld(rT + i0, pk);
+            const T q0 = gbs_ld(qT + i0, pk), d0 = gbs_ld(dinv + i0, pk);
+            T p1 = T(0), x1 = T(0), r1 = T(0), q1 = T(0), d1 = T(0);
+            if (h1) {
+                p1 = gbs_ld(pT + i1, pk);
+                x1 = gbs_ld(xT + i1, pk);
+                r1 = gbs_ld(rT + i1, pk);
+                q1 = gbs_ld(qT + i1, pk);
+                d1 = gbs_ld(dinv + i1, pk);
+            }
+            const T rn0 = r0 - alpha * q0, zn0 = d0 * rn0;
+            gbs_st(xT + i0, x0 + alpha * p0, pk);
+            gbs_st(rT + i0, rn0, pk);
+            gbs_st(zT + i0, zn0, pk);
+            u[0] += rn0 * zn0;
+            u[1] += rn0 * rn0;
+            if (h1) {
+                const T rn1 = r1 - alpha * q1, zn1 = d1 * rn1;
+                gbs_st(xT + i1, x1 + alpha * p1, pk);
+                gbs_st(rT + i1, rn1, pk);
+                gbs_st(zT + i1, zn1, pk);
+                u[0] += rn1 * zn1;
+                u[1] += rn1 * rn1;
+            }
         }
-        gbs_block_sum<T, 2>(u, sm.red);
+        gbs_block_sum_staged<T, 2, GBS_PBLOCK>(u, sm.buf, sm.out);
         if (threadIdx.x == 0) {
-            part[4 * G + c] = u[0];
-            part[5 * G + c] = u[1];
+            part[4 * G + c] = sm.out[0];
+            part[5 * G + c] = sm.out[1];
         }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
-        T g2[2];
-        gbs_grid_sum<T, 2>(part + 4 * G, G, G, g2, sm.bcast);
-        ++k;
-        const T rho_new = g2[0];
-        rr = g2[1];
-        if (rho_new < T(0)) { *rnorm_out = sqrt(rr); status = GBS_ERR_INDEFINITE; break; }
-        const T beta = rho_new / rho;
-        rho = rho_new;
+        if (warp == 0) {
+            T g2[2];
+            gbs_warp_grid_sum<T, 2>(part + 4 * G, G, G, g2);
+            if (threadIdx.x == 0) {
+                ++k;
+                const T rho_new = g2[0];
+                rr = g2[1];
+                if (rho_new < T(0)) {
+                    status = GBS_ERR_INDEFINITE;
+                    ctl.go = 0;
+                } else {
+                    ctl.beta = rho_new / rho;
+                    rho = rho_new;
+                    const int s = pcg_check<T>(sqrt(rr), rho, rtol * bnorm, k, maxit);
+                    ctl.go = s == -100;
+                    if (!ctl.go) status = s;
+                }
+            }
+        }
+        __syncthreads();
+        if (!ctl.go) break;
+        const T beta = ctl.beta;
 
         // ---- P: p = z + beta p
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) pT[i] = zT[i] + beta * pT[i];
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 2 * GBS_PBLOCK) {
+            const int64_t i1 = i0 + GBS_PBLOCK;
+            const T z0 = gbs_ld(zT + i0, pk), p0 = gbs_ld(pT + i0, pk);
+            if (i1 < re) {
+                const T z1 = gbs_ld(zT + i1, pk), p1 = gbs_ld(pT + i1, pk);
+                gbs_st(pT + i1, z1 + beta * p1, pk);
+            }
+            gbs_st(pT + i0, z0 + beta * p0, pk);
+        }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
     }
     *iters = k;
+    *rnorm_out = sqrt(rr);
+    *bnorm_out = bnorm;
+    // the status decides the caller's control flow in every thread: hand
+    // thread 0's value to the whole CTA so that all threads take one path
+    if (threadIdx.x == 0) ctl.status = status;
+    __syncthreads();
+    status = ctl.status;
+    __syncthreads();
     return status;
 }
 
-__global__ void __launch_bounds__(GBS_BLOCK) k_pcg_fp64(PcgArgs a)
+__global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
 {
-    __shared__ GbsTile<double> tl;
-    __shared__ TileSmem<double> sm;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PcgSmall<double> sm;
+    __shared__ PcgCtl<double> ctl;
     __shared__ int s_flag;
+    GbsWarpTile<double> &wt = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
     int iters = 0, barrier_no = 0;
     double rn = 0.0, bn = 0.0;
     int st = pcg_loop<double>(a, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol,
-                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, tl, sm,
+                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, wt, sm, ctl,
                               &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.res->status = st;
@@ -229,78 +313,99 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_pcg_fp64(PcgArgs a)
 }
 
 // Mixed precision: FP64 iterative refinement around the FP32 inner loop.
-__global__ void __launch_bounds__(GBS_BLOCK) k_pcg_mixed(PcgArgs a)
+// The refinement scalars live in thread 0 of each CTA, like the inner ones.
+__global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
 {
-    __shared__ GbsTile<double> tl64;
-    __shared__ TileSmem<double> sm64;
-    __shared__ TileSmem<float> sm32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PcgSmall<double> sm64;
+    __shared__ PcgCtl<float> ctl32;
+    __shared__ double s_scale;
+    __shared__ int s_go;
     __shared__ int s_flag;
-    GbsTile<float> &tl32 = *reinterpret_cast<GbsTile<float> *>(&tl64);
-    const int G = gridDim.x, c = blockIdx.x;
+    GbsWarpTile<double> &wt64 = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
+    GbsWarpTile<float> &wt32 = reinterpret_cast<GbsWarpTile<float> *>(smem)[threadIdx.x >> 5];
+    PcgSmall<float> &sm32 = *reinterpret_cast<PcgSmall<float> *>(&sm64);
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
+    const int G = gridDim.x, c = blockIdx.x, warp = threadIdx.x >> 5;
     int64_t t0, t1;
     cta_tiles(a, t0, t1);
     const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
     const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
     int barrier_no = 0, inner_total = 0, outer = 0, st = GBS_DIVERGED_ITS;
-    double rn = 0.0, bnorm = 0.0, prev = INFINITY;
-    for (int it = 0;; ++it) {
+    double rn = 0.0, bnorm = 0.0, prev = INFINITY;   // thread 0
+    for (int it = 0; it <= a.outer_maxit; ++it) {
         // ---- FP64 residual r = b - A x with r.r (and b.b once) fused
         double acc[2] = {0.0, 0.0};
         const bool first = it == 0;
         if (first && a.x0_zero) {
-            for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) {
-                const double bi = a.b[i];
-                a.x[i] = 0.0;
-                a.r[i] = bi;
+            for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK) {
+                const double bi = gbs_ld(a.b + i, pk);
+                gbs_st(a.x + i, 0.0, pk);
+                gbs_st(a.r + i, bi, pk);
                 acc[0] += bi * bi;
                 acc[1] += bi * bi;
             }
         } else {
             auto epi = [&](int64_t i, double s) {
-                const double bi = a.b[i];
+                const double bi = gbs_ld(a.b + i, pk);
                 const double ri = bi - s;
-                a.r[i] = ri;
+                gbs_st(a.r + i, ri, pk);
                 acc[0] += ri * ri;
                 if (first) acc[1] += bi * bi;
             };
-            for (int64_t t = t0; t < t1; ++t)
-                gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.x, __ldg(a.tiles + t),
-                                      __ldg(a.tiles + t + 1), tl64, sm64.red, epi);
+            for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
+                gbs_spmv_warp<double>(a.rowptr, a.colidx, a.vals, a.x, __ldg(a.tiles + t),
+                                      __ldg(a.tiles + t + 1), wt64, ps, pk, epi);
         }
-        gbs_block_sum<double, 2>(acc, sm64.red);
+        gbs_block_sum_staged<double, 2, GBS_PBLOCK>(acc, sm64.buf, sm64.out);
         double *part = a.part64 + (it & 1) * 2 * G;
         if (threadIdx.x == 0) {
-            part[c] = acc[0];
-            part[G + c] = acc[1];
+            part[c] = sm64.out[0];
+            part[G + c] = sm64.out[1];
         }
         const bool skip = (a.skip_cta == c) && (barrier_no == 0);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, barrier_no++, skip, &s_flag)) {
             st = GBS_ERR_TIMEOUT;
             break;
         }
-        double g2[2];
-        gbs_grid_sum<double, 2>(part, G, G, g2, sm64.bcast);
-        rn = sqrt(g2[0]);
-        if (first) bnorm = sqrt(g2[1]);
-        outer = it;
-        if (isnan(rn)) { st = GBS_ERR_NAN; break; }
-        if (rn <= a.rtol * bnorm) { st = GBS_OK; break; }
-        if (rn > 0.5 * prev) { st = GBS_ERR_STAGNATION; break; }
-        if (it >= a.outer_maxit) { st = GBS_DIVERGED_ITS; break; }
-        prev = rn;
+        if (warp == 0) {
+            double g2[2];
+            gbs_warp_grid_sum<double, 2>(part, G, G, g2);
+            if (threadIdx.x == 0) {
+                rn = sqrt(g2[0]);
+                if (first) bnorm = sqrt(g2[1]);
+                outer = it;
+                int s = -100;
+                if (isnan(rn)) s = GBS_ERR_NAN;
+                else if (rn <= a.rtol * bnorm) s = GBS_OK;
+                else if (rn > 0.5 * prev) s = GBS_ERR_STAGNATION;
+                else if (it >= a.outer_maxit) s = GBS_DIVERGED_ITS;
+                s_go = s == -100;
+                if (!s_go) st = s;
+                prev = rn;
+                s_scale = 1.0 / rn;
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
         // ---- scale to FP32 (own rows) and solve A d = r / ||r|| in FP32
-        const double inv = 1.0 / rn;
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) a.b32[i] = (float)(a.r[i] * inv);
+        const double inv = s_scale;
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK)
+            gbs_st(a.b32 + i, (float)(gbs_ld(a.r + i, pk) * inv), pk);
         int kin = 0;
         float rin = 0.f, bin = 0.f;
         const int sti = pcg_loop<float>(a, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
                                         a.q32, a.part32, (float)a.inner_rtol, a.maxit, true, &kin,
-                                        &rin, &bin, &barrier_no, tl32, sm32, &s_flag);
+                                        &rin, &bin, &barrier_no, wt32, sm32, ctl32, &s_flag);
         inner_total += kin;
         if (sti < 0) { st = sti; break; }
         // ---- FP64 update x += ||r|| d (own rows), then a barrier so the next
         // residual SpMV sees every row of x
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_BLOCK) a.x[i] += rn * (double)a.x32[i];
+        if (threadIdx.x == 0) s_scale = rn;
+        __syncthreads();
+        const double scale = s_scale;
+        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK)
+            gbs_st(a.x + i, gbs_ld(a.x + i, pk) + scale * (double)gbs_ld(a.x32 + i, pk), pk);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, barrier_no++, false, &s_flag)) {
             st = GBS_ERR_TIMEOUT;
             break;
@@ -318,16 +423,62 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_pcg_mixed(PcgArgs a)
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Largest cooperative grid for a kernel, capped by the tile count.
+// Cooperative grid for a persistent kernel: as many co-resident CTAs as
+// fit, but no more than one CTA per GBS_PWARPS warp tiles (small systems
+// run on few CTAs, so their barriers are cheap).
 int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles)
 {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmem) !=
+        cudaSuccess)
+        return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_BLOCK, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, kPersistSmem) !=
+        cudaSuccess)
         return -1;
     if (per_sm < 1) return -1;
     int64_t g = (int64_t)per_sm * c->num_sms;
-    if (g > ntiles) g = ntiles;
+    const int64_t need = (ntiles + GBS_PWARPS - 1) / GBS_PWARPS;
+    if (g > need) g = need;
     return g < 1 ? 1 : (int)g;
+}
+
+// Launch a persistent kernel and read its result record (one host
+// synchronisation per solve).
+int launch_persistent(gbs_ctx c, const void *fn, int G, PcgArgs &a, gbs_solve_info *info)
+{
+    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    void *args[] = {&a};
+    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(GBS_PBLOCK), args, kPersistSmem,
+                                             c->stream));
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    gbs_result_dev r;
+    memcpy(&r, c->pinned, sizeof(r));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->status = r.status;
+    info->iters = r.iters;
+    info->outer_iters = r.outer;
+    info->rnorm = r.rnorm;
+    info->bnorm = r.bnorm;
+    info->device_ms = ms;
+    return r.status;
+}
+
+void fill_matrix_args(PcgArgs &a, gbs_mat A)
+{
+    a.n = A->n;
+    a.ntiles = A->ntiles;
+    a.tiles = A->tiles;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.vals = A->vals;
+    a.vals32 = A->vals32;
+    a.dinv = A->dinv;
+    a.dinv32 = A->dinv32;
 }
 
 }  // namespace
@@ -375,15 +526,7 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         a.p = (double *)v; v += vec64;
         a.q = (double *)v; v += vec64;
     }
-    a.n = n;
-    a.ntiles = A->ntiles;
-    a.tiles = A->tiles;
-    a.rowptr = A->rowptr;
-    a.colidx = A->colidx;
-    a.vals = A->vals;
-    a.vals32 = A->vals32;
-    a.dinv = A->dinv;
-    a.dinv32 = A->dinv32;
+    fill_matrix_args(a, A);
     a.b = (const double *)b->data;
     a.x = (double *)x->data;
     a.rtol = rtol;
@@ -393,27 +536,8 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     a.x0_zero = 0;
     a.skip_cta = o->fault_skip_arrival;
     a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
-
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
-    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    void *args[] = {&a};
-    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(GBS_BLOCK), args, 0, c->stream));
-    gbs_count_launch(c);
-    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
-    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
-                                 c->stream));
-    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    gbs_result_dev r;
-    memcpy(&r, c->pinned, sizeof(r));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    info->status = r.status;
-    info->iters = r.iters;
-    info->outer_iters = r.outer;
-    info->rnorm = r.rnorm;
-    info->bnorm = r.bnorm;
-    info->device_ms = ms;
-    return r.status;
+    return launch_persistent(c, fn, G, a, info);
 }
 
 // ----------------------------------------------------------------------
@@ -421,6 +545,8 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
 // ----------------------------------------------------------------------
 
 namespace {
+
+constexpr size_t kOpSmem = sizeof(GbsWarpTile<double>) * GBS_WARPS;
 
 struct OpScalars {
     double rho, rr, bnorm, pi, alpha, beta;
@@ -471,9 +597,11 @@ __device__ void op_check(OpScalars *s, double rtol, int maxit)
 
 __global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
 {
-    __shared__ GbsTile<double> tl;
-    __shared__ TileSmem<double> sm;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[4 * GBS_WARPS];
     __shared__ bool s_last;
+    GbsWarpTile<double> &wt = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     double acc[3] = {0.0, 0.0, 0.0};
     auto epi = [&](int64_t i, double s) {
         const double bi = a.b[i], ri = bi - s, zi = a.dinv[i] * ri;
@@ -484,11 +612,12 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
         acc[1] += ri * ri;
         acc[2] += bi * bi;
     };
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
-        gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.x, a.tiles[t], a.tiles[t + 1], tl,
-                              sm.red, epi);
+    const int64_t nw = (int64_t)gridDim.x * GBS_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * GBS_WARPS + (threadIdx.x >> 5); t < a.ntiles; t += nw)
+        gbs_spmv_warp<double>(a.rowptr, a.colidx, a.vals, a.x, a.tiles[t], a.tiles[t + 1], wt, ps,
+                              pk, epi);
     double tot[3];
-    if (op_reduce<3>(acc, a.part, &a.s->counter[0], sm.red, tot, &s_last) && threadIdx.x == 0) {
+    if (op_reduce<3>(acc, a.part, &a.s->counter[0], s_red, tot, &s_last) && threadIdx.x == 0) {
         a.s->rho = tot[0];
         a.s->rr = tot[1];
         a.s->bnorm = sqrt(tot[2]);
@@ -502,19 +631,22 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
 __global__ void __launch_bounds__(GBS_BLOCK) k_op_spmv_pq(OpArgs a)
 {
     if (a.s->done) return;
-    __shared__ GbsTile<double> tl;
-    __shared__ TileSmem<double> sm;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[4 * GBS_WARPS];
     __shared__ bool s_last;
+    GbsWarpTile<double> &wt = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     double pq[1] = {0.0};
     auto epi = [&](int64_t i, double s) {
         a.q[i] = s;
         pq[0] += a.p[i] * s;
     };
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
-        gbs_spmv_tile<double>(a.rowptr, a.colidx, a.vals, a.p, a.tiles[t], a.tiles[t + 1], tl,
-                              sm.red, epi);
+    const int64_t nw = (int64_t)gridDim.x * GBS_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * GBS_WARPS + (threadIdx.x >> 5); t < a.ntiles; t += nw)
+        gbs_spmv_warp<double>(a.rowptr, a.colidx, a.vals, a.p, a.tiles[t], a.tiles[t + 1], wt, ps,
+                              pk, epi);
     double tot[1];
-    if (op_reduce<1>(pq, a.part, &a.s->counter[1], sm.red, tot, &s_last) && threadIdx.x == 0) {
+    if (op_reduce<1>(pq, a.part, &a.s->counter[1], s_red, tot, &s_last) && threadIdx.x == 0) {
         a.s->pi = tot[0];
         if (isnan(tot[0])) { a.s->status = GBS_ERR_NAN; a.s->done = 1; }
         else if (tot[0] <= 0.0) { a.s->status = GBS_ERR_INDEFINITE; a.s->done = 1; }
@@ -563,14 +695,11 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_pupdate(OpArgs a)
         a.p[i] = a.z[i] + beta * a.p[i];
 }
 
-int op_iteration(gbs_ctx c, const OpArgs &a, int gt, int gv, cudaStream_t s)
+void op_iteration(const OpArgs &a, int gt, int gv, cudaStream_t s)
 {
-    k_op_spmv_pq<<<gt, GBS_BLOCK, 0, s>>>(a);
+    k_op_spmv_pq<<<gt, GBS_BLOCK, kOpSmem, s>>>(a);
     k_op_update<<<gv, GBS_BLOCK, 0, s>>>(a);
     k_op_pupdate<<<gv, GBS_BLOCK, 0, s>>>(a);
-    gbs_count_launch(c, 3);
-    GBS_CUDA_TRY(cudaGetLastError());
-    return GBS_OK;
 }
 
 }  // namespace
@@ -581,7 +710,12 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, con
     gbs_ctx c = A->ctx;
     if (o->mode != GBS_MODE_FP64) return GBS_ERR_UNSUPPORTED;
     const int64_t n = A->n;
-    int gt = (int)(A->ntiles < (int64_t)c->num_sms * 4 ? A->ntiles : (int64_t)c->num_sms * 4);
+    GBS_CUDA_TRY(cudaFuncSetAttribute((const void *)k_op_setup,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOpSmem));
+    GBS_CUDA_TRY(cudaFuncSetAttribute((const void *)k_op_spmv_pq,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOpSmem));
+    const int64_t tiles_blocks = (A->ntiles + GBS_WARPS - 1) / GBS_WARPS;
+    int gt = (int)(tiles_blocks < (int64_t)c->num_sms * 4 ? tiles_blocks : (int64_t)c->num_sms * 4);
     int gv = (int)((n + GBS_BLOCK - 1) / GBS_BLOCK);
     if (gv > c->num_sms * 4) gv = c->num_sms * 4;
     if (gt < 1) gt = 1;
@@ -617,7 +751,7 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, con
 
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
     GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    k_op_setup<<<gt, GBS_BLOCK, 0, c->stream>>>(a);
+    k_op_setup<<<gt, GBS_BLOCK, kOpSmem, c->stream>>>(a);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
     volatile OpScalars *hs = (volatile OpScalars *)c->pinned;
@@ -630,30 +764,29 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, con
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int i = 0; i < o->graph_iters; ++i) {
-                k_op_spmv_pq<<<gt, GBS_BLOCK, 0, cap>>>(a);
-                k_op_update<<<gv, GBS_BLOCK, 0, cap>>>(a);
-                k_op_pupdate<<<gv, GBS_BLOCK, 0, cap>>>(a);
-            }
+            for (int i = 0; i < o->graph_iters; ++i) op_iteration(a, gt, gv, cap);
             e = cudaStreamEndCapture(cap, &graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e != cudaSuccess) rc = gbs_cuda_fail(e);
     }
-    for (int64_t it = 0; rc == GBS_OK; ) {
+    for (int64_t it = 0; rc == GBS_OK;) {
         cudaError_t e = cudaMemcpyAsync(c->pinned, a.s, sizeof(OpScalars), cudaMemcpyDeviceToHost,
                                         c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
         if (hs->done) break;
-        if (it > (int64_t)maxit + 1) { rc = GBS_ERR_CUDA; break; }  // cannot happen
+        if (it > (int64_t)maxit + 1) { rc = GBS_ERR_CUDA; break; }  // device never finished
         if (use_graph) {
             e = cudaGraphLaunch(exec, c->stream);
             gbs_count_launch(c, 3 * o->graph_iters);
             if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
             it += o->graph_iters;
         } else {
-            rc = op_iteration(c, a, gt, gv, c->stream);
+            op_iteration(a, gt, gv, c->stream);
+            gbs_count_launch(c, 3);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
             it += 1;
         }
     }
@@ -736,7 +869,7 @@ extern "C" int gbs_ksp_last_info(gbs_ctx c, gbs_solve_info *info)
     return GBS_OK;
 }
 
-// ----------------------------------------------------------------------
+
 // Allocation-free FP64 solve.
 //
 // Some callers cannot allocate device memory at solve time: latency-bound
@@ -819,13 +952,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     a.z = (double *)(v + kNoAllocVec);
     a.p = (double *)(v + 2 * kNoAllocVec);
     a.q = (double *)(v + 3 * kNoAllocVec);
-    a.n = A->n;
-    a.ntiles = A->ntiles;
-    a.tiles = A->tiles;
-    a.rowptr = A->rowptr;
-    a.colidx = A->colidx;
-    a.vals = A->vals;
-    a.dinv = A->dinv;
+    fill_matrix_args(a, A);
     a.b = b;
     a.x = x;
     a.rtol = rtol;
@@ -835,24 +962,5 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     // the barrier and the result record must start at zero; the vectors and
     // partial sums are written before they are read
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocHead, c->stream));
-    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    void *args[] = {&a};
-    GBS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_fp64, dim3(G), dim3(GBS_BLOCK),
-                                             args, 0, c->stream));
-    gbs_count_launch(c);
-    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
-    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
-                                 c->stream));
-    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    gbs_result_dev r;
-    memcpy(&r, c->pinned, sizeof(r));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    info->status = r.status;
-    info->iters = r.iters;
-    info->outer_iters = 0;
-    info->rnorm = r.rnorm;
-    info->bnorm = r.bnorm;
-    info->device_ms = ms;
-    return r.status;
+    return launch_persistent(c, (const void *)k_pcg_fp64, G, a, info);
 }
