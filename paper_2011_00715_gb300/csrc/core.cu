@@ -146,6 +146,14 @@ extern "C" int gbs_ctx_synchronize(gbs_ctx c)
 {
     if (!c) return GBS_ERR_ARG;
     GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // word 1 of devsmall: set by an asynchronous MatMult whose bulk copy
+    // did not complete in time; reported here and cleared
+    GBS_CUDA_TRY(cudaMemcpy(c->pinned, (int *)c->devsmall + 1, sizeof(int),
+                            cudaMemcpyDeviceToHost));
+    if (*(volatile int *)c->pinned) {
+        GBS_CUDA_TRY(cudaMemset((int *)c->devsmall + 1, 0, sizeof(int)));
+        return GBS_ERR_TIMEOUT;
+    }
     return GBS_OK;
 }
 
@@ -264,6 +272,34 @@ static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &t
     *maxrow = mr;
 }
 
+// Pipeline geometry: every stage must hold the largest copied tile (the
+// 16-byte-aligned supersets of its values, column indices and row pointers).
+static GbsPipeCfg make_pipe_cfg(const std::vector<int32_t> &tiles, const int32_t *rowptr,
+                                int vsize)
+{
+    const int E = 16 / vsize;
+    int vcap = 0, ccap = 0, rcap = 0;
+    for (size_t t = 0; t + 1 < tiles.size(); ++t) {
+        const int r0 = tiles[t], r1 = tiles[t + 1], k0 = rowptr[r0], k1 = rowptr[r1];
+        if (k1 - k0 > GBS_WT_NNZ) continue;
+        const int v = ((k1 + E - 1) & ~(E - 1)) - (k0 & ~(E - 1));
+        const int c = ((k1 + 3) & ~3) - (k0 & ~3);
+        const int r = ((r1 + 4) & ~3) - (r0 & ~3);
+        if (v > vcap) vcap = v;
+        if (c > ccap) ccap = c;
+        if (r > rcap) rcap = r;
+    }
+    auto r16 = [](int b) { return (b + 15) & ~15; };
+    GbsPipeCfg cfg;
+    cfg.coloff = r16(vsize * vcap);
+    cfg.rpoff = cfg.coloff + r16(4 * ccap);
+    cfg.sbytes = cfg.rpoff + r16(4 * rcap);
+    if (cfg.sbytes < 16) cfg.sbytes = 16;
+    cfg.stages = GBS_WARP_STAGE_BYTES / cfg.sbytes;
+    if (cfg.stages > GBS_MAX_STAGES) cfg.stages = GBS_MAX_STAGES;
+    return cfg;   // at least 2 stages: a full tile needs at most 6320 bytes
+}
+
 static void mat_free(gbs_mat A)
 {
     if (!A) return;
@@ -274,6 +310,7 @@ static void mat_free(gbs_mat A)
     cudaFree(A->dinv);
     cudaFree(A->dinv32);
     cudaFree(A->tiles);
+    cudaFree(A->tdesc);
     free(A);
 }
 
@@ -318,7 +355,15 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     if (e == cudaSuccess) e = cudaMalloc(&A->vals, sizeof(double) * pad_nnz);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv, sizeof(double) * pad_n);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
+    A->pipe64 = make_pipe_cfg(tiles, hrp.data(), 8);
+    A->pipe32 = make_pipe_cfg(tiles, hrp.data(), 4);
+    std::vector<int32_t> tdesc(2 * tiles.size());
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        tdesc[2 * t] = tiles[t];
+        tdesc[2 * t + 1] = hrp[tiles[t]];
+    }
     if (e == cudaSuccess) e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
+    if (e == cudaSuccess) e = cudaMalloc(&A->tdesc, sizeof(int32_t) * tdesc.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(A->colidx, 0, sizeof(int32_t) * pad_nnz, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A->vals, 0, sizeof(double) * pad_nnz, c->stream);
     const cudaMemcpyKind kind =
@@ -332,6 +377,9 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
         e = cudaMemcpyAsync(A->vals, vals, sizeof(double) * nnz, kind, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(A->tiles, tiles.data(), sizeof(int32_t) * tiles.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(A->tdesc, tdesc.data(), sizeof(int32_t) * tdesc.size(),
                             cudaMemcpyHostToDevice, c->stream);
     int *devflags = (int *)c->devsmall;
     if (e == cudaSuccess) e = cudaMemsetAsync(devflags, 0, sizeof(int), c->stream);
@@ -432,30 +480,40 @@ template <typename V>
 struct StoreEpi {
     V *y;
     uint64_t pol;
-    __device__ __forceinline__ void operator()(int64_t row, V s) const { gbs_st(y + row, s, pol); }
+    __device__ __forceinline__ void operator()(int64_t row, V s, V) const { gbs_st(y + row, s, pol); }
 };
 
-// MatMult over warp tiles: warp w of the grid takes tiles w, w + W, ...
+// MatMult over warp tiles: CTA c takes an even share of the tiles, its
+// warps claim them one by one through their bulk-copy pipelines.  A copy
+// that does not complete within 2 s sets *err, which gbs_ctx_synchronize
+// reports as GBS_ERR_TIMEOUT.
 template <typename V>
-__global__ void __launch_bounds__(GBS_BLOCK) k_spmv(int64_t ntiles, const int32_t *tiles,
+__global__ void __launch_bounds__(GBS_BLOCK) k_spmv(int64_t ntiles, const int32_t *tdesc,
                                                     const int32_t *rowptr, const int32_t *colidx,
-                                                    const V *vals, const V *x, V *y)
+                                                    const V *vals, const V *x, V *y,
+                                                    GbsPipeCfg cfg, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    GbsWarpTile<V> *wts = reinterpret_cast<GbsWarpTile<V> *>(smem);
-    GbsWarpTile<V> &wt = wts[threadIdx.x >> 5];
+    __shared__ GbsWarpQ s_q[GBS_WARPS];
+    __shared__ int s_next;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    gbs_warpq_init(s_q[warp]);
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     StoreEpi<V> epi{y, pk};
-    const int64_t nw = (int64_t)gridDim.x * GBS_WARPS;
-    for (int64_t t = (int64_t)blockIdx.x * GBS_WARPS + (threadIdx.x >> 5); t < ntiles; t += nw)
-        gbs_spmv_warp<V>(rowptr, colidx, vals, x, __ldg(tiles + t), __ldg(tiles + t + 1), wt, ps, pk,
-                         epi);
+    uint32_t parity = 0;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const bool ok = gbs_spmv_pipe<V>(tdesc, t0, t1, &s_next, rowptr, colidx, vals, x,
+                                     smem + (size_t)warp * GBS_WARP_STAGE_BYTES, s_q[warp], parity,
+                                     cfg, ps, pk, 2000000000ull, epi);
+    if (!ok && lane == 0) atomicExch(err, 1);
 }
 
 template <typename V>
 static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V *y)
 {
-    const size_t smem = sizeof(GbsWarpTile<V>) * GBS_WARPS;
+    const size_t smem = (size_t)GBS_WARP_STAGE_BYTES * GBS_WARPS;
     GBS_CUDA_TRY(cudaFuncSetAttribute((const void *)k_spmv<V>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -464,7 +522,10 @@ static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V *y)
     const int64_t need = (A->ntiles + GBS_WARPS - 1) / GBS_WARPS;
     const int64_t cap = (int64_t)c->num_sms * per_sm;
     const int g = (int)(need < cap ? need : cap);
-    k_spmv<V><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tiles, A->rowptr, A->colidx, vals, x, y);
+    int *err = (int *)c->devsmall + 1;   // word 1 of the context's small device buffer
+    const GbsPipeCfg cfg = sizeof(V) == 8 ? A->pipe64 : A->pipe32;
+    k_spmv<V><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tdesc, A->rowptr, A->colidx, vals,
+                                                 x, y, cfg, err);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
     return GBS_OK;

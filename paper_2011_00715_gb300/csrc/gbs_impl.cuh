@@ -36,6 +36,18 @@ struct gbs_ctx_s {
     cudaEvent_t ev0, ev1;
 };
 
+// Geometry of the bulk-copy pipeline of one matrix for one value type,
+// computed on the host from the tile list so that every stage holds the
+// largest tile: GBS_WARP_STAGE_BYTES per warp divided into `stages` slots.
+#define GBS_MAX_STAGES 4
+#define GBS_WARP_STAGE_BYTES 12800
+struct GbsPipeCfg {
+    int stages;   // 2..GBS_MAX_STAGES
+    int sbytes;   // stride of one stage in bytes (multiple of 16)
+    int coloff;   // byte offset of the column indices in a stage
+    int rpoff;    // byte offset of the row pointers in a stage
+};
+
 struct gbs_mat_s {
     gbs_ctx ctx;
     int64_t n, ncols, nnz;
@@ -47,6 +59,8 @@ struct gbs_mat_s {
     float *dinv32;
     int diag_ok;
     int32_t *tiles;             // row starts of the warp tiles, ntiles + 1 entries
+    int32_t *tdesc;             // {row start, nonzero start} per tile, ntiles + 1 pairs
+    GbsPipeCfg pipe64, pipe32;  // pipeline geometry for FP64 and FP32 values
     int64_t ntiles;
     int max_row_nnz;
 };
@@ -307,6 +321,9 @@ __device__ __forceinline__ bool gbs_grid_sync(gbs_grid_barrier *bar, unsigned lo
             }
             __nanosleep(32);
         }
+        // a failure recorded by any CTA before it arrived (e.g. a bulk copy
+        // that did not complete) fails the barrier for everyone
+        if (ok && gbs_ld_relaxed_int(&bar->error) != 0) ok = 0;
         *s_flag = ok;
     }
     __syncthreads();
@@ -392,6 +409,221 @@ __device__ __forceinline__ void gbs_spmv_warp(const int32_t *__restrict__ rowptr
         if (lane == 0) epi(r0, s);
         __syncwarp();
     }
+}
+
+// ------------------------------------------------------------------------
+// Bulk-copy (TMA) staging of warp tiles.
+//
+// A warp tile's CSR slice -- rowptr[r0..r1], colidx[k0..k1), vals[k0..k1) --
+// is contiguous in memory.  Lane 0 copies the 16-byte-aligned superset of
+// each array into one of two shared-memory stages with cp.async.bulk,
+// completing on that stage's mbarrier, while the warp computes the other
+// stage: the next tile is always in flight.  Allocations are padded so the
+// rounded-up ranges never leave a buffer.
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t gbs_smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void gbs_mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gbs_smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void gbs_fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void gbs_mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gbs_smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool gbs_mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(gbs_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with parity `parity` to complete, for at most
+// timeout_ns.  Returns false on timeout.
+__device__ __forceinline__ bool gbs_mbar_wait(uint64_t *bar, uint32_t parity,
+                                              unsigned long long timeout_ns)
+{
+    if (gbs_mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gbs_globaltimer();
+    while (!gbs_mbar_try_wait(bar, parity))
+        if (gbs_globaltimer() - t0 > timeout_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void gbs_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(gbs_smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(gbs_smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// Per-warp pipeline bookkeeping in shared memory.
+struct GbsWarpQ {
+    uint64_t bar[GBS_MAX_STAGES];   // one mbarrier per stage (count 1)
+    int4 desc[GBS_MAX_STAGES];      // {r0, k0, r1, k1} of the tile in each stage
+    int tile[GBS_MAX_STAGES];       // tile held by each stage, relative to the range (-1: none)
+};
+
+__device__ __forceinline__ void gbs_warpq_init(GbsWarpQ &q)
+{
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < GBS_MAX_STAGES; ++j) gbs_mbar_init(&q.bar[j], 1);
+        gbs_fence_mbar_init();
+    }
+    __syncwarp();
+}
+
+// y = A v over the warp tiles [t_begin, t_end), shared by the warps of a
+// CTA: lane 0 of each warp claims the next unclaimed tile from *s_next
+// (a CTA-shared counter, zero on entry) one step ahead, loads its
+// descriptor while the previous copy is issued, and copies the tile's CSR
+// slice into the next free stage of the warp's ring (wsm, cfg.stages
+// stages), keeping cfg.stages - 1 tiles in flight; the warp then computes
+// the oldest stage: lane l accumulates row r0 + l left to right and calls
+// epi(row, sum, vdiag), vdiag being the gathered v[row] (the row's
+// diagonal entry's operand; 0 if the row has no diagonal entry).  A tile
+// holding one row longer than GBS_WT_NNZ is read directly and reduced with
+// a fixed shuffle tree.  parity carries the warp's mbarrier phase bits
+// across calls.  Returns false if a copy did not complete within
+// timeout_ns; the copies still in flight are then waited for (again with a
+// limit) before returning.
+template <typename V, typename Epi>
+__device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc, int64_t t_begin,
+                                              int64_t t_end, int *s_next,
+                                              const int32_t *__restrict__ rowptr,
+                                              const int32_t *__restrict__ colidx,
+                                              const V *__restrict__ vals, const V *v,
+                                              unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
+                                              const GbsPipeCfg &cfg, uint64_t pol_stream,
+                                              uint64_t pol_keep, unsigned long long timeout_ns,
+                                              Epi &epi)
+{
+    constexpr int E = 16 / (int)sizeof(V);   // values per 16 bytes
+    const int lane = threadIdx.x & 31;
+    const int NS = cfg.stages;
+    // lane 0: the next claimed tile and its descriptor, fetched one step ahead
+    int64_t t_pend = t_end;
+    int2 d_lo = make_int2(0, 0), d_hi = make_int2(0, 0);
+    auto claim = [&]() {
+        t_pend = t_begin + atomicAdd(s_next, 1);
+        if (t_pend < t_end) {
+            d_lo = __ldg(reinterpret_cast<const int2 *>(tdesc) + t_pend);
+            d_hi = __ldg(reinterpret_cast<const int2 *>(tdesc) + t_pend + 1);
+        }
+    };
+    // lane 0 only: start the copy of the pending tile into stage j, claim the next
+    auto issue = [&](int j) {
+        if (t_pend >= t_end) {
+            q.tile[j] = -1;
+            return;
+        }
+        const int r0 = d_lo.x, k0 = d_lo.y, r1 = d_hi.x, k1 = d_hi.y;
+        q.tile[j] = (int)(t_pend - t_begin);
+        q.desc[j] = make_int4(r0, k0, r1, k1);
+        claim();
+        if (k1 - k0 > GBS_WT_NNZ) return;
+        const int vb = k0 & ~(E - 1), ve = (k1 + E - 1) & ~(E - 1);
+        const int cb = k0 & ~3, ce = (k1 + 3) & ~3;
+        const int rb = r0 & ~3, re = (r1 + 4) & ~3;
+        const uint32_t bv = (uint32_t)(sizeof(V) * (ve - vb)), bc = 4u * (uint32_t)(ce - cb),
+                       br = 4u * (uint32_t)(re - rb);
+        unsigned char *st = wsm + (size_t)j * cfg.sbytes;
+        gbs_mbar_expect_tx(&q.bar[j], bv + bc + br);
+        gbs_bulk_g2s(st + cfg.rpoff, rowptr + rb, br, &q.bar[j], pol_stream);
+        if (bv) gbs_bulk_g2s(st, vals + vb, bv, &q.bar[j], pol_stream);
+        if (bc) gbs_bulk_g2s(st + cfg.coloff, colidx + cb, bc, &q.bar[j], pol_stream);
+    };
+    if (lane == 0) {
+        claim();
+        for (int j = 0; j < NS - 1; ++j) issue(j);
+    }
+    __syncwarp();
+    bool ok = true;
+    int m = 0;
+    for (;; ++m) {
+        const int j = m % NS;
+        if (lane == 0) issue((m + NS - 1) % NS);   // that stage was consumed at m - 1
+        __syncwarp();
+        if (q.tile[j] < 0) break;   // claims are monotonic: no later stage holds a tile either
+        const int4 d = q.desc[j];
+        const int r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
+        if (k1 - k0 > GBS_WT_NNZ) {
+            V sum = V(0), vd = V(0);
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const int c = gbs_ld_stream(colidx + k, pol_stream);
+                const V xv = gbs_ld(v + c, pol_keep);
+                if (c == r0) vd = xv;
+                sum = gbs_mac(gbs_ld_stream(vals + k, pol_stream), xv, sum);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                sum += __shfl_xor_sync(0xffffffffu, sum, off);
+                vd += __shfl_xor_sync(0xffffffffu, vd, off);
+            }
+            if (lane == 0) epi((int64_t)r0, sum, vd);
+        } else {
+            if (!gbs_mbar_wait(&q.bar[j], (parity >> j) & 1u, timeout_ns)) {
+                ok = false;
+                break;
+            }
+            parity ^= 1u << j;
+            const unsigned char *st = wsm + (size_t)j * cfg.sbytes;
+            const V *sval = reinterpret_cast<const V *>(st);
+            const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
+            const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
+            const int nrows = r1 - r0;
+            if (lane < nrows) {
+                const int row = r0 + lane;
+                const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+                const int beg = srp[row - rb], end = srp[row - rb + 1];
+                V sum = V(0), vd = V(0);
+#pragma unroll 8
+                for (int k = beg; k < end; ++k) {
+                    const int c = scol[k - cb];
+                    const V xv = gbs_ld(v + c, pol_keep);
+                    if (c == row) vd = xv;
+                    sum = gbs_mac(sval[k - vb], xv, sum);
+                }
+                epi((int64_t)row, sum, vd);
+            }
+        }
+        __syncwarp();
+    }
+    if (!ok) {
+        // wait (with a limit) for every copy still in flight, oldest first
+        for (int dd = 0; dd < NS; ++dd) {
+            const int jj = (m + dd) % NS;
+            if (q.tile[jj] >= 0 && q.desc[jj].w - q.desc[jj].y <= GBS_WT_NNZ &&
+                gbs_mbar_wait(&q.bar[jj], (parity >> jj) & 1u, timeout_ns))
+                parity ^= 1u << jj;
+        }
+    }
+    __syncwarp();
+    return ok;
 }
 
 #endif  // __CUDACC__

@@ -37,7 +37,7 @@
 namespace {
 
 constexpr int kSlots = 8;   // partial-sum slots per CTA
-constexpr size_t kPersistSmem = sizeof(GbsWarpTile<double>) * GBS_PWARPS;
+constexpr size_t kPersistSmem = (size_t)GBS_WARP_STAGE_BYTES * GBS_PWARPS;
 
 template <typename T>
 struct PcgSmall {
@@ -60,6 +60,7 @@ struct PcgArgs {
     int64_t n;
     int64_t ntiles;
     const int32_t *tiles;
+    const int32_t *tdesc;
     const int32_t *rowptr;
     const int32_t *colidx;
     const double *vals;
@@ -74,6 +75,7 @@ struct PcgArgs {
     float *b32, *x32, *r32, *z32, *p32, *q32;
     double *part64;   // kSlots * G
     float *part32;    // kSlots * G
+    GbsPipeCfg pipe64, pipe32;
     gbs_grid_barrier *bar;
     gbs_result_dev *res;
     double rtol;
@@ -111,7 +113,8 @@ template <typename T>
 __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T *bT, T *xT, T *rT,
                         T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
                         int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no,
-                        GbsWarpTile<T> &wt, PcgSmall<T> &sm, PcgCtl<T> &ctl, int *s_flag)
+                        unsigned char *wsm, GbsWarpQ &wq, uint32_t &parity, int *s_next,
+                        const GbsPipeCfg &cfg, PcgSmall<T> &sm, PcgCtl<T> &ctl, int *s_flag)
 {
     const int G = gridDim.x, c = blockIdx.x, warp = threadIdx.x >> 5;
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
@@ -126,7 +129,7 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
     // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b
     T acc[3] = {T(0), T(0), T(0)};
     if (!x0_zero) {
-        auto epi = [&](int64_t i, T s) {
+        auto epi = [&](int64_t i, T s, T) {
             const T bi = gbs_ld(bT + i, pk);
             const T ri = bi - s;
             const T zi = gbs_ld(dinv + i, pk) * ri;
@@ -137,9 +140,10 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
             acc[1] += ri * ri;
             acc[2] += bi * bi;
         };
-        for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
-            gbs_spmv_warp<T>(a.rowptr, a.colidx, vals, xT, __ldg(a.tiles + t),
-                             __ldg(a.tiles + t + 1), wt, ps, pk, epi);
+        if (!gbs_spmv_pipe<T>(a.tdesc, t0, t1, s_next, a.rowptr, a.colidx, vals, xT, wsm, wq,
+                              parity, cfg, ps, pk, a.timeout_ns, epi) &&
+            (threadIdx.x & 31) == 0)
+            atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
     } else {
         for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK) {
             const T bi = gbs_ld(bT + i, pk);
@@ -155,6 +159,7 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
     }
     gbs_block_sum_staged<T, 3, GBS_PBLOCK>(acc, sm.buf, sm.out);
     if (threadIdx.x == 0) {
+        *s_next = 0;
         part[0 * G + c] = sm.out[0];
         part[1 * G + c] = sm.out[1];
         part[2 * G + c] = sm.out[2];
@@ -180,15 +185,21 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
     for (int k_all = 0; ctl.go && k_all <= maxit; ++k_all) {
         // ---- S: q = A p, partial p.q
         T pq[1] = {T(0)};
-        auto epi = [&](int64_t i, T s) {
+        // p_i is the operand the row's diagonal entry gathered (every row
+        // has one: the Jacobi set-up checked it)
+        auto epi = [&](int64_t i, T s, T p_i) {
             gbs_st(qT + i, s, pk);
-            pq[0] += gbs_ld(pT + i, pk) * s;
+            pq[0] += p_i * s;
         };
-        for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
-            gbs_spmv_warp<T>(a.rowptr, a.colidx, vals, pT, __ldg(a.tiles + t),
-                             __ldg(a.tiles + t + 1), wt, ps, pk, epi);
+        if (!gbs_spmv_pipe<T>(a.tdesc, t0, t1, s_next, a.rowptr, a.colidx, vals, pT, wsm, wq,
+                              parity, cfg, ps, pk, a.timeout_ns, epi) &&
+            (threadIdx.x & 31) == 0)
+            atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         gbs_block_sum_staged<T, 1, GBS_PBLOCK>(pq, sm.buf, sm.out);
-        if (threadIdx.x == 0) part[3 * G + c] = sm.out[0];
+        if (threadIdx.x == 0) {
+            *s_next = 0;
+            part[3 * G + c] = sm.out[0];
+        }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
         if (warp == 0) {
@@ -206,33 +217,33 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
         const T alpha = ctl.alpha;
 
         // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
+        // (four rows per thread per trip: all 20 loads are issued before the
+        // first use)
         T u[2] = {T(0), T(0)};
-        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 2 * GBS_PBLOCK) {
-            const int64_t i1 = i0 + GBS_PBLOCK;
-            const bool h1 = i1 < re;
-            const T p0 = gbs_ld(pT + i0, pk), x0 = gbs_ld(xT + i0, pk), r0 = gbs_ld(rT + i0, pk);
-            const T q0 = gbs_ld(qT + i0, pk), d0 = gbs_ld(dinv + i0, pk);
-            T p1 = T(0), x1 = T(0), r1 = T(0), q1 = T(0), d1 = T(0);
-            if (h1) {
-                p1 = gbs_ld(pT + i1, pk);
-                x1 = gbs_ld(xT + i1, pk);
-                r1 = gbs_ld(rT + i1, pk);
-                q1 = gbs_ld(qT + i1, pk);
-                d1 = gbs_ld(dinv + i1, pk);
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 4 * GBS_PBLOCK) {
+            T pv[4], xv[4], rv[4], qv[4], dv[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t i = i0 + h * GBS_PBLOCK;
+                if (i < re) {
+                    pv[h] = gbs_ld(pT + i, pk);
+                    xv[h] = gbs_ld(xT + i, pk);
+                    rv[h] = gbs_ld(rT + i, pk);
+                    qv[h] = gbs_ld(qT + i, pk);
+                    dv[h] = gbs_ld(dinv + i, pk);
+                }
             }
-            const T rn0 = r0 - alpha * q0, zn0 = d0 * rn0;
-            gbs_st(xT + i0, x0 + alpha * p0, pk);
-            gbs_st(rT + i0, rn0, pk);
-            gbs_st(zT + i0, zn0, pk);
-            u[0] += rn0 * zn0;
-            u[1] += rn0 * rn0;
-            if (h1) {
-                const T rn1 = r1 - alpha * q1, zn1 = d1 * rn1;
-                gbs_st(xT + i1, x1 + alpha * p1, pk);
-                gbs_st(rT + i1, rn1, pk);
-                gbs_st(zT + i1, zn1, pk);
-                u[0] += rn1 * zn1;
-                u[1] += rn1 * rn1;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t i = i0 + h * GBS_PBLOCK;
+                if (i < re) {
+                    const T rn_ = rv[h] - alpha * qv[h], zn_ = dv[h] * rn_;
+                    gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
+                    gbs_st(rT + i, rn_, pk);
+                    gbs_st(zT + i, zn_, pk);
+                    u[0] += rn_ * zn_;
+                    u[1] += rn_ * rn_;
+                }
             }
         }
         gbs_block_sum_staged<T, 2, GBS_PBLOCK>(u, sm.buf, sm.out);
@@ -266,14 +277,21 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
         const T beta = ctl.beta;
 
         // ---- P: p = z + beta p
-        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 2 * GBS_PBLOCK) {
-            const int64_t i1 = i0 + GBS_PBLOCK;
-            const T z0 = gbs_ld(zT + i0, pk), p0 = gbs_ld(pT + i0, pk);
-            if (i1 < re) {
-                const T z1 = gbs_ld(zT + i1, pk), p1 = gbs_ld(pT + i1, pk);
-                gbs_st(pT + i1, z1 + beta * p1, pk);
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 4 * GBS_PBLOCK) {
+            T zv[4], pv[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t i = i0 + h * GBS_PBLOCK;
+                if (i < re) {
+                    zv[h] = gbs_ld(zT + i, pk);
+                    pv[h] = gbs_ld(pT + i, pk);
+                }
             }
-            gbs_st(pT + i0, z0 + beta * p0, pk);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t i = i0 + h * GBS_PBLOCK;
+                if (i < re) gbs_st(pT + i, zv[h] + beta * pv[h], pk);
+            }
         }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
@@ -295,13 +313,20 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PcgSmall<double> sm;
     __shared__ PcgCtl<double> ctl;
+    __shared__ GbsWarpQ s_q[GBS_PWARPS];
+    __shared__ int s_next;
     __shared__ int s_flag;
-    GbsWarpTile<double> &wt = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
+    const int warp = threadIdx.x >> 5;
+    gbs_warpq_init(s_q[warp]);
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    uint32_t parity = 0;
     int iters = 0, barrier_no = 0;
     double rn = 0.0, bn = 0.0;
     int st = pcg_loop<double>(a, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol,
-                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, wt, sm, ctl,
-                              &s_flag);
+                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no,
+                              smem + (size_t)warp * GBS_WARP_STAGE_BYTES, s_q[warp], parity,
+                              &s_next, a.pipe64, sm, ctl, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.res->status = st;
         a.res->iters = iters;
@@ -319,14 +344,20 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PcgSmall<double> sm64;
     __shared__ PcgCtl<float> ctl32;
+    __shared__ GbsWarpQ s_q[GBS_PWARPS];
     __shared__ double s_scale;
     __shared__ int s_go;
+    __shared__ int s_next;
     __shared__ int s_flag;
-    GbsWarpTile<double> &wt64 = reinterpret_cast<GbsWarpTile<double> *>(smem)[threadIdx.x >> 5];
-    GbsWarpTile<float> &wt32 = reinterpret_cast<GbsWarpTile<float> *>(smem)[threadIdx.x >> 5];
-    PcgSmall<float> &sm32 = *reinterpret_cast<PcgSmall<float> *>(&sm64);
-    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     const int G = gridDim.x, c = blockIdx.x, warp = threadIdx.x >> 5;
+    // the FP64 and FP32 pipelines share this warp's stage memory and mbarriers
+    unsigned char *wsm = smem + (size_t)warp * GBS_WARP_STAGE_BYTES;
+    PcgSmall<float> &sm32 = *reinterpret_cast<PcgSmall<float> *>(&sm64);
+    gbs_warpq_init(s_q[warp]);
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    uint32_t parity = 0;
+    const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     int64_t t0, t1;
     cta_tiles(a, t0, t1);
     const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
@@ -346,20 +377,23 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
                 acc[1] += bi * bi;
             }
         } else {
-            auto epi = [&](int64_t i, double s) {
+            auto epi = [&](int64_t i, double s, double) {
                 const double bi = gbs_ld(a.b + i, pk);
                 const double ri = bi - s;
                 gbs_st(a.r + i, ri, pk);
                 acc[0] += ri * ri;
                 if (first) acc[1] += bi * bi;
             };
-            for (int64_t t = t0 + warp; t < t1; t += GBS_PWARPS)
-                gbs_spmv_warp<double>(a.rowptr, a.colidx, a.vals, a.x, __ldg(a.tiles + t),
-                                      __ldg(a.tiles + t + 1), wt64, ps, pk, epi);
+            if (!gbs_spmv_pipe<double>(a.tdesc, t0, t1, &s_next, a.rowptr, a.colidx, a.vals, a.x,
+                                       wsm, s_q[warp], parity, a.pipe64, ps, pk, a.timeout_ns,
+                                       epi) &&
+                (threadIdx.x & 31) == 0)
+                atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         }
         gbs_block_sum_staged<double, 2, GBS_PBLOCK>(acc, sm64.buf, sm64.out);
         double *part = a.part64 + (it & 1) * 2 * G;
         if (threadIdx.x == 0) {
+            s_next = 0;
             part[c] = sm64.out[0];
             part[G + c] = sm64.out[1];
         }
@@ -396,7 +430,8 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
         float rin = 0.f, bin = 0.f;
         const int sti = pcg_loop<float>(a, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
                                         a.q32, a.part32, (float)a.inner_rtol, a.maxit, true, &kin,
-                                        &rin, &bin, &barrier_no, wt32, sm32, ctl32, &s_flag);
+                                        &rin, &bin, &barrier_no, wsm, s_q[warp], parity, &s_next,
+                                        a.pipe32, sm32, ctl32, &s_flag);
         inner_total += kin;
         if (sti < 0) { st = sti; break; }
         // ---- FP64 update x += ||r|| d (own rows), then a barrier so the next
@@ -473,12 +508,15 @@ void fill_matrix_args(PcgArgs &a, gbs_mat A)
     a.n = A->n;
     a.ntiles = A->ntiles;
     a.tiles = A->tiles;
+    a.tdesc = A->tdesc;
     a.rowptr = A->rowptr;
     a.colidx = A->colidx;
     a.vals = A->vals;
     a.vals32 = A->vals32;
     a.dinv = A->dinv;
     a.dinv32 = A->dinv32;
+    a.pipe64 = A->pipe64;
+    a.pipe32 = A->pipe32;
 }
 
 }  // namespace
