@@ -2,7 +2,7 @@
 // sides each, in one persistent cooperative kernel (Response A6: solve many
 // different-size problems at once; Challenge F2 and Sec. 4: multiple
 // right-hand sides raise arithmetic intensity; Response A7: FP32 inner
-// iterations with FP64 refinement).
+// iterations with FP64 refinement), and the serving loop built on it.
 //
 // Lockstep design.  Every active system advances by one step per global
 // iteration; a step has five phases separated by grid barriers:
@@ -25,9 +25,12 @@
 // Multi-vectors are interleaved (entry (row, column) at row * k + column),
 // so the k operands one nonzero gathers are contiguous.
 //
-// The kernel runs at most `quantum` global iterations and returns; all
-// state lives in device memory, so the host can retire finished systems
-// and admit new ones between launches (continuous batching).
+// Systems live in slots.  The kernel runs at most `quantum` global
+// iterations over the active slots and returns; all solver state stays in
+// device memory, so the host retires finished systems and admits new ones
+// between launches (continuous batching).  The launch of a quantum is
+// captured once into a CUDA graph and replayed while the active set is
+// unchanged (Challenge A1).
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -35,6 +38,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <deque>
+#include <unordered_map>
 #include <vector>
 
 #include "gbs_impl.cuh"
@@ -46,7 +52,7 @@ namespace {
 
 enum { MODE_OUTER = 0, MODE_INNER = 1 };
 
-// Read-only description of one system (device).
+// Read-only description of one system (device, one per slot).
 struct BSys {
     const int32_t *rowptr, *colidx, *tiles;
     const double *vals, *dinv;
@@ -55,10 +61,10 @@ struct BSys {
     double *x;          // n * k, interleaved (initial guess in, solution out)
     double *r64;        // n * k
     void *xi, *ri, *zi, *pi, *qi;   // inner-precision work vectors, n * k
-    int n, k, ntiles, gtile0;
+    int n, k, ntiles, pad0;
     double rtol;
     int maxit;
-    int pad;
+    int pad1;
 };
 
 // Mutable state of one (system, column) pair (device).
@@ -81,18 +87,18 @@ struct BSysDyn {
 };
 
 struct BArgs {
-    const BSys *sys;
-    BCol *col;          // sys index * GBS_KMAX + column
-    BSysDyn *dyn;
-    const int2 *tiles;  // active tiles {system, local tile}, ntile entries
-    int ntile;
-    const int2 *pairs;  // active {system, column} pairs, npair entries
-    int npair;
-    double *partS;      // global tile * GBS_KMAX * 2
-    double *partU;      // global tile * GBS_KMAX * 2
+    const BSys *sys;    // by slot
+    BCol *col;          // slot * GBS_KMAX + column
+    BSysDyn *dyn;       // by slot
+    const int *act;     // active slots, nact entries
+    const int *tcum;    // prefix sums of the active slots' tile counts (nact + 1)
+    int nact;
+    int ntile;          // tcum[nact]
+    double *partS;      // active tile * GBS_KMAX * 2
+    double *partU;      // active tile * GBS_KMAX * 2
     gbs_grid_barrier *bar;
     int quantum;
-    int iter0;          // global iteration count at launch (parity of mode[])
+    int iter0;          // parity of the global iteration count at launch
     double inner_rtol;
     int outer_maxit;
     int fp64;           // inner precision is FP64 (FP64 mode)
@@ -182,21 +188,34 @@ __device__ __forceinline__ void warp_store_partials(T (&a)[GBS_KMAX][2], int k, 
     }
 }
 
-// Sum entry j of column c over the system's tiles in a fixed order
-// (lane l: tiles l, l + 32, ... in type T; then a fixed shuffle tree).
+// Sum entry j of column c over active tiles [ga, gb) -- one system's tiles
+// -- in a fixed order (lane l: tiles ga + l, ga + l + 32, ... in type T;
+// then a fixed shuffle tree).
 template <typename T>
-__device__ __forceinline__ T sys_sum(const double *part, const BSys &S, int c, int j)
+__device__ __forceinline__ T sys_sum(const double *part, int ga, int gb, int c, int j)
 {
     const int lane = threadIdx.x & 31;
     T t = T(0);
-    for (int i = lane; i < S.ntiles; i += 32)
-        t += (T)__ldcg(part + ((size_t)(S.gtile0 + i) * GBS_KMAX + c) * 2 + j);
+    for (int g = ga + lane; g < gb; g += 32)
+        t += (T)__ldcg(part + ((size_t)g * GBS_KMAX + c) * 2 + j);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
     return t;
 }
 
 __device__ __forceinline__ bool col_running(const BCol &c) { return c.status == GBS_RUNNING; }
+
+// Active index owning active tile g (tcum is increasing, tcum[0] = 0).
+__device__ __forceinline__ int owner_of(const int *tcum, int nact, int g)
+{
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tcum + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <typename TI>
 __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
@@ -208,21 +227,26 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
     const int gw = blockIdx.x * GBS_PWARPS + warp, nw = G * GBS_PWARPS;
     BTile<double> &wt64 = reinterpret_cast<BTile<double> *>(smem)[warp];
     BTile<float> &wt32 = *reinterpret_cast<BTile<float> *>(&wt64);
+    // this warp's contiguous share of the active tiles
+    const int g0 = (int)((int64_t)a.ntile * gw / nw), g1 = (int)((int64_t)a.ntile * (gw + 1) / nw);
+    const int ai0 = g0 < g1 ? owner_of(a.tcum, a.nact, g0) : 0;
+    const int npairs = a.nact * GBS_KMAX;
     int bno = 0;
     bool ok = true;
 
     for (int q = 0; q < a.quantum && ok; ++q) {
-        const int it = a.iter0 + q;
-        const int cur = it & 1, nxt = cur ^ 1;
+        const int cur = (a.iter0 + q) & 1, nxt = cur ^ 1;
 
         // ---------------- S: SpMV per tile
-        for (int g = gw; g < a.ntile; g += nw) {
-            const int2 tl = a.tiles[g];
-            const BSys &S = a.sys[tl.x];
-            const BSysDyn &D = a.dyn[tl.x];
+        for (int g = g0, ai = ai0; g < g1; ++g) {
+            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
+            const int slot = __ldg(a.act + ai);
+            const int lt = g - __ldg(a.tcum + ai);
+            const BSys &S = a.sys[slot];
+            const BSysDyn &D = a.dyn[slot];
             if (D.finished) continue;
             const int k = S.k;
-            double *dst = a.partS + (size_t)(S.gtile0 + tl.y) * GBS_KMAX * 2;
+            double *dst = a.partS + (size_t)g * GBS_KMAX * 2;
             if (D.mode[cur] == MODE_OUTER) {
                 // r64 = b - A x (FP64), partials r.r and b.b
                 double acc[GBS_KMAX][2];
@@ -240,7 +264,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                         acc[c][1] += bi * bi;
                     }
                 };
-                tile_spmv_k<double, double>(S, S.vals, S.x, tl.y, wt64, epi);
+                tile_spmv_k<double, double>(S, S.vals, S.x, lt, wt64, epi);
                 warp_store_partials<double>(acc, k, dst);
             } else {
                 // q = A p (inner precision), partial p.q
@@ -259,25 +283,27 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     }
                 };
                 if (a.fp64)
-                    tile_spmv_k<double, TI>(S, S.vals, p, tl.y, wt64, epi);
+                    tile_spmv_k<double, TI>(S, S.vals, p, lt, wt64, epi);
                 else
-                    tile_spmv_k<float, TI>(S, S.vals32, p, tl.y, wt32, epi);
+                    tile_spmv_k<float, TI>(S, S.vals32, p, lt, wt32, epi);
                 warp_store_partials<TI>(acc, k, dst);
             }
         }
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- R1: per (system, column)
-        for (int g = gw; g < a.npair; g += nw) {
-            const int2 pc = a.pairs[g];
-            const BSys &S = a.sys[pc.x];
-            BSysDyn &D = a.dyn[pc.x];
-            if (D.finished) continue;
-            BCol &C = a.col[pc.x * GBS_KMAX + pc.y];
+        for (int pidx = gw; pidx < npairs; pidx += nw) {
+            const int ai = pidx / GBS_KMAX, cc = pidx % GBS_KMAX;
+            const int slot = __ldg(a.act + ai);
+            const BSys &S = a.sys[slot];
+            BSysDyn &D = a.dyn[slot];
+            if (cc >= S.k || D.finished) continue;
+            BCol &C = a.col[slot * GBS_KMAX + cc];
             if (!col_running(C)) continue;
+            const int ga = __ldg(a.tcum + ai), gb = __ldg(a.tcum + ai + 1);
             if (D.mode[cur] == MODE_OUTER) {
-                const double rr = sys_sum<double>(a.partS, S, pc.y, 0);
-                const double bb = sys_sum<double>(a.partS, S, pc.y, 1);
+                const double rr = sys_sum<double>(a.partS, ga, gb, cc, 0);
+                const double bb = sys_sum<double>(a.partS, ga, gb, cc, 1);
                 if (lane == 0) {
                     const double rn = sqrt(rr);
                     if (C.first) C.bnorm = sqrt(bb);
@@ -296,7 +322,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     }
                 }
             } else if (!C.inner_done) {
-                const TI pq = sys_sum<TI>(a.partS, S, pc.y, 0);
+                const TI pq = sys_sum<TI>(a.partS, ga, gb, cc, 0);
                 if (lane == 0) {
                     if (isnan((double)pq)) C.status = GBS_ERR_NAN;
                     else if (pq <= TI(0)) C.status = GBS_ERR_INDEFINITE;
@@ -307,14 +333,16 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- U: vector updates per tile
-        for (int g = gw; g < a.ntile; g += nw) {
-            const int2 tl = a.tiles[g];
-            const BSys &S = a.sys[tl.x];
-            const BSysDyn &D = a.dyn[tl.x];
+        for (int g = g0, ai = ai0; g < g1; ++g) {
+            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
+            const int slot = __ldg(a.act + ai);
+            const int lt = g - __ldg(a.tcum + ai);
+            const BSys &S = a.sys[slot];
+            const BSysDyn &D = a.dyn[slot];
             if (D.finished) continue;
             const int k = S.k;
-            const BCol *Cs = a.col + tl.x * GBS_KMAX;
-            const int r0 = __ldg(S.tiles + tl.y), r1 = __ldg(S.tiles + tl.y + 1);
+            const BCol *Cs = a.col + slot * GBS_KMAX;
+            const int r0 = __ldg(S.tiles + lt), r1 = __ldg(S.tiles + lt + 1);
             TI acc[GBS_KMAX][2];
 #pragma unroll
             for (int c = 0; c < GBS_KMAX; ++c) acc[c][0] = acc[c][1] = TI(0);
@@ -356,21 +384,23 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     }
                 }
             }
-            warp_store_partials<TI>(acc, k, a.partU + (size_t)(S.gtile0 + tl.y) * GBS_KMAX * 2);
+            warp_store_partials<TI>(acc, k, a.partU + (size_t)g * GBS_KMAX * 2);
         }
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- R2: per (system, column)
-        for (int g = gw; g < a.npair; g += nw) {
-            const int2 pc = a.pairs[g];
-            const BSys &S = a.sys[pc.x];
-            BSysDyn &D = a.dyn[pc.x];
-            if (D.finished) continue;
-            BCol &C = a.col[pc.x * GBS_KMAX + pc.y];
+        for (int pidx = gw; pidx < npairs; pidx += nw) {
+            const int ai = pidx / GBS_KMAX, cc = pidx % GBS_KMAX;
+            const int slot = __ldg(a.act + ai);
+            const BSys &S = a.sys[slot];
+            BSysDyn &D = a.dyn[slot];
+            if (cc >= S.k || D.finished) continue;
+            BCol &C = a.col[slot * GBS_KMAX + cc];
             if (!col_running(C)) continue;
+            const int ga = __ldg(a.tcum + ai), gb = __ldg(a.tcum + ai + 1);
             if (D.mode[cur] == MODE_OUTER) {
-                const TI rho = sys_sum<TI>(a.partU, S, pc.y, 0);
-                const TI bb = sys_sum<TI>(a.partU, S, pc.y, 1);
+                const TI rho = sys_sum<TI>(a.partU, ga, gb, cc, 0);
+                const TI bb = sys_sum<TI>(a.partU, ga, gb, cc, 1);
                 if (lane == 0) {
                     C.rho = (double)rho;
                     C.tol_inner = C.tol_inner * (double)sqrt(bb);
@@ -378,8 +408,8 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     C.inner_done = 0;
                 }
             } else if (!C.inner_done) {
-                const TI rho_new = sys_sum<TI>(a.partU, S, pc.y, 0);
-                const TI rr = sys_sum<TI>(a.partU, S, pc.y, 1);
+                const TI rho_new = sys_sum<TI>(a.partU, ga, gb, cc, 0);
+                const TI rr = sys_sum<TI>(a.partU, ga, gb, cc, 1);
                 if (lane == 0) {
                     C.kin += 1;
                     C.iters += 1;
@@ -398,13 +428,15 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- P: direction update, or refinement update
-        for (int g = gw; g < a.ntile; g += nw) {
-            const int2 tl = a.tiles[g];
-            const BSys &S = a.sys[tl.x];
-            BSysDyn &D = a.dyn[tl.x];
+        for (int g = g0, ai = ai0; g < g1; ++g) {
+            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
+            const int slot = __ldg(a.act + ai);
+            const int lt = g - __ldg(a.tcum + ai);
+            const BSys &S = a.sys[slot];
+            BSysDyn &D = a.dyn[slot];
             if (D.finished) continue;
             const int k = S.k;
-            const BCol *Cs = a.col + tl.x * GBS_KMAX;
+            const BCol *Cs = a.col + slot * GBS_KMAX;
             // the system's next step: refinement once every running column's
             // inner solve has stopped; finished once no column runs
             int running = 0, waiting = 0;
@@ -413,9 +445,8 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                 waiting += col_running(Cs[c]) && !Cs[c].inner_done;
             }
             const int mode = D.mode[cur];
-            const int next = (mode == MODE_INNER && waiting == 0) ? MODE_OUTER
-                             : (mode == MODE_OUTER ? MODE_INNER : MODE_INNER);
-            const int r0 = __ldg(S.tiles + tl.y), r1 = __ldg(S.tiles + tl.y + 1);
+            const int next = (mode == MODE_INNER && waiting == 0) ? MODE_OUTER : MODE_INNER;
+            const int r0 = __ldg(S.tiles + lt), r1 = __ldg(S.tiles + lt + 1);
             const int row = r0 + lane;
             if (row < r1 && mode == MODE_INNER) {
                 TI *pi = (TI *)S.pi;
@@ -431,7 +462,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                         pi[o] = zi[o] + (TI)Cs[c].beta * pi[o];
                 }
             }
-            if (tl.y == 0 && lane == 0) {
+            if (lt == 0 && lane == 0) {
                 D.mode[nxt] = running ? next : mode;
                 if (!running) D.finished = 1;
             }
@@ -440,116 +471,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
     }
 }
 
-size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-}  // namespace
-
-// ----------------------------------------------------------------------
-// Host engine shared by the batched solve and the serving loop.
-// ----------------------------------------------------------------------
-
-struct gbs_batch_engine {
-    gbs_ctx ctx;
-    int fp64;
-    double inner_rtol;
-    int outer_maxit;
-    int quantum;
-    // device arrays, grown on demand
-    BSys *d_sys = nullptr;
-    BCol *d_col = nullptr;
-    BSysDyn *d_dyn = nullptr;
-    int2 *d_tiles = nullptr;
-    int2 *d_pairs = nullptr;
-    double *d_partS = nullptr, *d_partU = nullptr;
-    gbs_grid_barrier *d_bar = nullptr;
-    size_t cap_sys = 0, cap_tiles = 0, cap_pairs = 0, cap_gtiles = 0;
-    int64_t iter = 0;
-};
-
-static int grow(void **p, size_t *cap, size_t need, size_t elem)
-{
-    if (need <= *cap) return GBS_OK;
-    size_t n = std::max(need, *cap * 2 + 16);
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    GBS_CUDA_TRY(cudaMalloc(p, n * elem));
-    *cap = n;
-    return GBS_OK;
-}
-
-// Run the active systems for one quantum.  sys/col/dyn are uploaded by the
-// caller; tiles/pairs list the active work.
-static int engine_launch(gbs_batch_engine *E, int nsys_total, const std::vector<int2> &tiles,
-                         const std::vector<int2> &pairs, int64_t gtiles_total, int *timed_out)
-{
-    gbs_ctx c = E->ctx;
-    *timed_out = 0;
-    int st = grow((void **)&E->d_tiles, &E->cap_tiles, tiles.size() + 1, sizeof(int2));
-    if (!st) st = grow((void **)&E->d_pairs, &E->cap_pairs, pairs.size() + 1, sizeof(int2));
-    if (st) return st;
-    if ((size_t)gtiles_total > E->cap_gtiles) {
-        cudaFree(E->d_partS);
-        cudaFree(E->d_partU);
-        E->d_partS = E->d_partU = nullptr;
-        E->cap_gtiles = 0;
-        const size_t n = (size_t)gtiles_total * 2 + 64;
-        GBS_CUDA_TRY(cudaMalloc(&E->d_partS, n * GBS_KMAX * 2 * sizeof(double)));
-        GBS_CUDA_TRY(cudaMalloc(&E->d_partU, n * GBS_KMAX * 2 * sizeof(double)));
-        E->cap_gtiles = n;
-    }
-    if (!E->d_bar) GBS_CUDA_TRY(cudaMalloc(&E->d_bar, 256));
-    GBS_CUDA_TRY(cudaMemcpyAsync(E->d_tiles, tiles.data(), tiles.size() * sizeof(int2),
-                                 cudaMemcpyHostToDevice, c->stream));
-    GBS_CUDA_TRY(cudaMemcpyAsync(E->d_pairs, pairs.data(), pairs.size() * sizeof(int2),
-                                 cudaMemcpyHostToDevice, c->stream));
-    GBS_CUDA_TRY(cudaMemsetAsync(E->d_bar, 0, 256, c->stream));
-    BArgs a;
-    memset(&a, 0, sizeof(a));
-    a.sys = E->d_sys;
-    a.col = E->d_col;
-    a.dyn = E->d_dyn;
-    a.tiles = E->d_tiles;
-    a.ntile = (int)tiles.size();
-    a.pairs = E->d_pairs;
-    a.npair = (int)pairs.size();
-    a.partS = E->d_partS;
-    a.partU = E->d_partU;
-    a.bar = E->d_bar;
-    a.quantum = E->quantum;
-    a.iter0 = (int)(E->iter & 1);
-    a.inner_rtol = E->inner_rtol;
-    a.outer_maxit = E->outer_maxit;
-    a.fp64 = E->fp64;
-    a.timeout_ns = (unsigned long long)c->opts.barrier_timeout_ms * 1000000ull;
-    const void *fn = E->fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
-    const size_t smem = sizeof(BTile<double>) * GBS_PWARPS;
-    GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
-    if (per_sm < 1) return GBS_ERR_CUDA;
-    int64_t need = ((int64_t)std::max(tiles.size(), pairs.size()) + GBS_PWARPS - 1) / GBS_PWARPS;
-    int64_t G = std::min<int64_t>((int64_t)per_sm * c->num_sms, std::max<int64_t>(need, 1));
-    void *args[] = {&a};
-    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(GBS_PBLOCK), args, smem,
-                                             c->stream));
-    gbs_count_launch(c);
-    E->iter += E->quantum;
-    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, &E->d_bar->error, sizeof(int), cudaMemcpyDeviceToHost,
-                                 c->stream));
-    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    *timed_out = *(volatile int *)c->pinned != 0;
-    (void)nsys_total;
-    return GBS_OK;
-}
-
-// ----------------------------------------------------------------------
-// gbs_ksp_solve_cg_batched
-// ----------------------------------------------------------------------
-
+// Column-major (c * n + i) <-> interleaved (i * k + c).
 __global__ void k_interleave(int64_t n, int k, const double *src, double *dst, int dir)
 {
-    // dir 0: column-major (c * n + i) -> interleaved (i * k + c); dir 1: back
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * k;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / k, cc = e % k;
@@ -558,60 +482,140 @@ __global__ void k_interleave(int64_t n, int k, const double *src, double *dst, i
     }
 }
 
-struct BatchHostSys {
-    gbs_mat A;
-    int k;
-    double *b_il, *x_il, *r64;
-    void *xi, *ri, *zi, *pi, *qi;
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ----------------------------------------------------------------------
+// Host engine: a slot table of systems run by the kernel above.
+// ----------------------------------------------------------------------
+
+struct SlotHost {
+    bool used = false;
+    bool finished = false;
+    gbs_mat A = nullptr;
+    bool own_A = false;       // the engine created the matrix (serving) and frees it
+    int k = 0;
+    char *work = nullptr;     // device vectors of the slot
+    size_t bytes = 0;         // device bytes held for budget accounting
+    uint64_t ticket = 0;
 };
 
-extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, const gbs_vec *B,
-                                        gbs_vec *X, const int *nrhs, const double *rtol, int maxit,
-                                        int mode, int *iters, double *rnorm, int *status)
+struct Engine {
+    gbs_ctx c = nullptr;
+    int fp64 = 0;
+    double inner_rtol = 1e-4;
+    int outer_maxit = 30;
+    int quantum = 32;
+    int nslots = 0;
+    BSys *d_sys = nullptr;
+    BCol *d_col = nullptr;
+    BSysDyn *d_dyn = nullptr;
+    int *d_act = nullptr, *d_tcum = nullptr;
+    double *d_partS = nullptr, *d_partU = nullptr;
+    size_t cap_part = 0;
+    gbs_grid_barrier *d_bar = nullptr;
+    std::vector<SlotHost> slots;
+    std::vector<BSysDyn> h_dyn;
+    int64_t iter = 0;
+    // graph of one quantum for the current active set
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    std::vector<int> g_act;   // active set the graph was captured for
+    BArgs g_args;
+    int G = 0;
+};
+
+void engine_free_graph(Engine &E)
 {
-    if (!c || nsys < 0 || (nsys > 0 && (!A || !B || !X || !nrhs || !rtol)) || maxit < 0)
-        return GBS_ERR_ARG;
-    if (mode != GBS_MODE_FP64 && mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
-    int64_t totcols = 0;
-    for (int s = 0; s < nsys; ++s) {
-        if (!A[s] || !B[s] || !X[s] || A[s]->ctx != c || nrhs[s] < 1 || nrhs[s] > GBS_KMAX)
-            return GBS_ERR_ARG;
-        if (A[s]->n != A[s]->ncols || B[s]->n != A[s]->n * nrhs[s] || X[s]->n != B[s]->n ||
-            B[s]->dtype != GBS_F64 || X[s]->dtype != GBS_F64 || !(rtol[s] >= 0.0))
-            return GBS_ERR_ARG;
-        totcols += nrhs[s];
+    if (E.gexec) cudaGraphExecDestroy(E.gexec);
+    if (E.graph) cudaGraphDestroy(E.graph);
+    E.gexec = nullptr;
+    E.graph = nullptr;
+    E.g_act.clear();
+}
+
+int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
+{
+    E.c = c;
+    E.fp64 = fp64;
+    E.inner_rtol = c->opts.inner_rtol;
+    E.outer_maxit = c->opts.outer_maxit;
+    E.quantum = quantum;
+    E.nslots = nslots;
+    E.slots.assign(nslots, SlotHost());
+    E.h_dyn.assign(nslots, BSysDyn());
+    GBS_CUDA_TRY(cudaMalloc(&E.d_sys, sizeof(BSys) * (size_t)std::max(nslots, 1)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_col, sizeof(BCol) * (size_t)std::max(nslots, 1) * GBS_KMAX));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_dyn, sizeof(BSysDyn) * (size_t)std::max(nslots, 1)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_act, sizeof(int) * (size_t)(nslots + 1)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_tcum, sizeof(int) * (size_t)(nslots + 2)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_bar, 256));
+    return GBS_OK;
+}
+
+void engine_destroy(Engine &E)
+{
+    if (E.c) cudaStreamSynchronize(E.c->stream);
+    engine_free_graph(E);
+    for (SlotHost &s : E.slots) {
+        if (s.work) cudaFree(s.work);
+        if (s.own_A) gbs_mat_destroy(s.A);
+        s = SlotHost();
     }
-    GBS_CUDA_TRY(cudaSetDevice(c->device));
-    const bool fp64 = mode == GBS_MODE_FP64;
-    const size_t tsz = fp64 ? 8 : 4;
-    // per-system device work vectors in one allocation
-    std::vector<size_t> off(nsys + 1, 0);
-    for (int s = 0; s < nsys; ++s) {
-        const size_t nk = (size_t)A[s]->n * nrhs[s];
-        off[s + 1] = off[s] + 3 * a256(nk * 8) + 5 * a256(nk * tsz);
+    cudaFree(E.d_sys);
+    cudaFree(E.d_col);
+    cudaFree(E.d_dyn);
+    cudaFree(E.d_act);
+    cudaFree(E.d_tcum);
+    cudaFree(E.d_partS);
+    cudaFree(E.d_partU);
+    cudaFree(E.d_bar);
+    E = Engine();
+}
+
+// Device bytes a system of n rows, nnz nonzeros and k columns holds.
+size_t system_bytes(int64_t n, int64_t nnz, int k, int fp64)
+{
+    const size_t nk = (size_t)n * k, tsz = fp64 ? 8 : 4;
+    const size_t vecs = 3 * a256(nk * 8) + 5 * a256(nk * tsz);
+    const size_t mat = 4 * (size_t)(n + 5) + 12 * (size_t)(nnz + 4) + (fp64 ? 0 : 4 * (size_t)(nnz + 4)) +
+                       12 * (size_t)(n + 4) + 12 * (size_t)(n / 32 + 2) + 4096;
+    return vecs + mat;
+}
+
+// Put a system into a free slot.  b and x0 are column-major device arrays
+// (x0 may be NULL for zeros).  A failing matrix (no usable diagonal, n = 0)
+// is admitted as finished with the corresponding column status.
+int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, const double *b,
+               const double *x0, bool own_A, uint64_t ticket)
+{
+    gbs_ctx c = E.c;
+    SlotHost &H = E.slots[slot];
+    const size_t nk = (size_t)A->n * k, tsz = E.fp64 ? 8 : 4;
+    if (!E.fp64) {
+        int st = gbs_mat_ensure_f32(A);
+        if (st) return st;
     }
-    char *work = nullptr;
-    if (off[nsys] > 0) GBS_CUDA_TRY(cudaMalloc(&work, off[nsys]));
-    std::vector<BSys> hs(nsys);
-    std::vector<BCol> hc((size_t)nsys * GBS_KMAX);
-    std::vector<BSysDyn> hd(nsys);
-    std::vector<int2> tiles, pairs;
-    int64_t gt = 0;
-    int rc = GBS_OK;
-    for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
-        gbs_mat M = A[s];
-        if (!fp64 && (rc = gbs_mat_ensure_f32(M)) != GBS_OK) break;
-        const size_t nk = (size_t)M->n * nrhs[s];
-        char *p = work + off[s];
-        BSys &S = hs[s];
-        memset(&S, 0, sizeof(S));
-        S.rowptr = M->rowptr;
-        S.colidx = M->colidx;
-        S.tiles = M->tiles;
-        S.vals = M->vals;
-        S.vals32 = M->vals32;
-        S.dinv = M->dinv;
-        S.dinv32 = M->dinv32;
+    const size_t bytes = 3 * a256(nk * 8) + 5 * a256(nk * tsz);
+    char *p = nullptr;
+    if (bytes) GBS_CUDA_TRY(cudaMalloc(&p, bytes));
+    H.used = true;
+    H.finished = false;
+    H.A = A;
+    H.own_A = own_A;
+    H.k = k;
+    H.work = p;
+    H.bytes = bytes;
+    H.ticket = ticket;
+    BSys S;
+    memset(&S, 0, sizeof(S));
+    S.rowptr = A->rowptr;
+    S.colidx = A->colidx;
+    S.tiles = A->tiles;
+    S.vals = A->vals;
+    S.vals32 = A->vals32;
+    S.dinv = A->dinv;
+    S.dinv32 = A->dinv32;
+    if (p) {
         S.b = (const double *)p; p += a256(nk * 8);
         S.x = (double *)p; p += a256(nk * 8);
         S.r64 = (double *)p; p += a256(nk * 8);
@@ -620,143 +624,477 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
         S.zi = p; p += a256(nk * tsz);
         S.pi = p; p += a256(nk * tsz);
         S.qi = p; p += a256(nk * tsz);
-        S.n = (int)M->n;
-        S.k = nrhs[s];
-        S.ntiles = (int)M->ntiles;
-        S.gtile0 = (int)gt;
-        S.rtol = rtol[s];
-        S.maxit = maxit;
-        gt += M->ntiles;
-        if (M->n > 0) {
-            const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
-            k_interleave<<<g, 256, 0, c->stream>>>(M->n, S.k, (const double *)B[s]->data,
-                                                           (double *)S.b, 0);
-            k_interleave<<<g, 256, 0, c->stream>>>(M->n, S.k, (const double *)X[s]->data,
-                                                           S.x, 0);
-            gbs_count_launch(c, 2);
-        }
-        BSysDyn &D = hd[s];
-        memset(&D, 0, sizeof(D));
-        D.mode[0] = D.mode[1] = MODE_OUTER;
-        const bool bad = M->n == 0 || !M->diag_ok;
-        D.finished = bad ? 1 : 0;
-        for (int cc = 0; cc < GBS_KMAX; ++cc) {
-            BCol &C = hc[(size_t)s * GBS_KMAX + cc];
-            memset(&C, 0, sizeof(C));
-            C.status = cc < S.k ? (M->n == 0 ? GBS_OK : (!M->diag_ok ? GBS_ERR_DIAG : GBS_RUNNING))
-                                : GBS_OK;
-            C.prev = INFINITY;
-            C.first = 1;
-        }
-        if (!bad) {
-            for (int t = 0; t < M->ntiles; ++t) tiles.push_back(make_int2(s, t));
-            for (int cc = 0; cc < S.k; ++cc) pairs.push_back(make_int2(s, cc));
+    }
+    S.n = (int)A->n;
+    S.k = k;
+    S.ntiles = (int)A->ntiles;
+    S.rtol = rtol;
+    S.maxit = maxit;
+    if (nk) {
+        const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
+        k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, b, (double *)S.b, 0);
+        if (x0)
+            k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, x0, S.x, 0);
+        else
+            GBS_CUDA_TRY(cudaMemsetAsync(S.x, 0, nk * 8, c->stream));
+        gbs_count_launch(c, x0 ? 2 : 1);
+        GBS_CUDA_TRY(cudaGetLastError());
+    }
+    BSysDyn D;
+    memset(&D, 0, sizeof(D));
+    D.mode[0] = D.mode[1] = MODE_OUTER;
+    const bool bad = A->n == 0 || !A->diag_ok;
+    D.finished = bad ? 1 : 0;
+    BCol C[GBS_KMAX];
+    for (int cc = 0; cc < GBS_KMAX; ++cc) {
+        memset(&C[cc], 0, sizeof(BCol));
+        C[cc].status = cc < k ? (A->n == 0 ? GBS_OK : (!A->diag_ok ? GBS_ERR_DIAG : GBS_RUNNING))
+                              : GBS_OK;
+        C[cc].prev = INFINITY;
+        C[cc].first = 1;
+    }
+    H.finished = bad;
+    E.h_dyn[slot] = D;
+    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_sys + slot, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_col + (size_t)slot * GBS_KMAX, C, sizeof(C),
+                                 cudaMemcpyHostToDevice, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_dyn + slot, &D, sizeof(D), cudaMemcpyHostToDevice, c->stream));
+    // the host arrays above are copied from pageable memory: make sure they
+    // are consumed before they go out of scope
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GBS_OK;
+}
+
+// Copy a slot's results out (x column-major into x_out, device or host per
+// memspace) and release the slot.
+int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters, double *rnorm,
+                   int *status)
+{
+    gbs_ctx c = E.c;
+    SlotHost &H = E.slots[slot];
+    BCol C[GBS_KMAX];
+    GBS_CUDA_TRY(cudaMemcpyAsync(C, E.d_col + (size_t)slot * GBS_KMAX, sizeof(C),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    const int64_t n = H.A->n;
+    const size_t nk = (size_t)n * H.k;
+    if (nk && x_out) {
+        const double *xil = (const double *)(H.work + a256(nk * 8));
+        const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
+        if (memspace == GBS_MEM_DEVICE) {
+            k_interleave<<<g, 256, 0, c->stream>>>(n, H.k, xil, x_out, 1);
+            gbs_count_launch(c);
+            GBS_CUDA_TRY(cudaGetLastError());
+        } else {
+            std::vector<double> tmp(nk);
+            GBS_CUDA_TRY(cudaMemcpyAsync(tmp.data(), xil, nk * 8, cudaMemcpyDeviceToHost, c->stream));
+            GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (size_t e = 0; e < nk; ++e) x_out[(e % H.k) * n + e / H.k] = tmp[e];
         }
     }
-    gbs_batch_engine E;
-    E.ctx = c;
-    E.fp64 = fp64 ? 1 : 0;
-    E.inner_rtol = c->opts.inner_rtol;
-    E.outer_maxit = c->opts.outer_maxit;
-    E.quantum = 64;
-    if (rc == GBS_OK && nsys > 0) {
-        cudaError_t e = cudaMalloc(&E.d_sys, sizeof(BSys) * nsys);
-        if (e == cudaSuccess) e = cudaMalloc(&E.d_col, sizeof(BCol) * hc.size());
-        if (e == cudaSuccess) e = cudaMalloc(&E.d_dyn, sizeof(BSysDyn) * nsys);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(E.d_sys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice,
-                                c->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(E.d_col, hc.data(), sizeof(BCol) * hc.size(),
-                                cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(E.d_dyn, hd.data(), sizeof(BSysDyn) * nsys, cudaMemcpyHostToDevice,
-                                c->stream);
-        if (e != cudaSuccess) rc = gbs_cuda_fail(e);
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int cc = 0; cc < H.k; ++cc) {
+        const int cs = C[cc].status == GBS_RUNNING ? GBS_DIVERGED_ITS : C[cc].status;
+        if (iters) iters[cc] = C[cc].iters;
+        if (rnorm) rnorm[cc] = C[cc].rn;
+        if (status) status[cc] = cs;
     }
-    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    // run quanta until every system has finished, compacting the work lists
-    std::vector<BSysDyn> dyn(nsys);
-    while (rc == GBS_OK && !tiles.empty()) {
-        int to = 0;
-        rc = engine_launch(&E, nsys, tiles, pairs, gt, &to);
-        if (rc) break;
-        if (to) { rc = GBS_ERR_TIMEOUT; break; }
-        cudaError_t e = cudaMemcpy(dyn.data(), E.d_dyn, sizeof(BSysDyn) * nsys,
-                                   cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) { rc = gbs_cuda_fail(e); break; }
-        std::vector<int2> t2, p2;
-        for (const int2 &t : tiles)
-            if (!dyn[t.x].finished) t2.push_back(t);
-        for (const int2 &p : pairs)
-            if (!dyn[p.x].finished) p2.push_back(p);
-        tiles.swap(t2);
-        pairs.swap(p2);
+    return GBS_OK;
+}
+
+void engine_release(Engine &E, int slot)
+{
+    SlotHost &H = E.slots[slot];
+    if (H.work) cudaFree(H.work);
+    if (H.own_A) gbs_mat_destroy(H.A);
+    H = SlotHost();
+}
+
+// Run one quantum over the active slots; refresh the finished flags.
+int engine_step(Engine &E, int *ran)
+{
+    gbs_ctx c = E.c;
+    *ran = 0;
+    std::vector<int> act, tcum(1, 0);
+    for (int s = 0; s < E.nslots; ++s) {
+        const SlotHost &H = E.slots[s];
+        if (H.used && !H.finished && H.A->ntiles > 0) {
+            act.push_back(s);
+            tcum.push_back(tcum.back() + (int)H.A->ntiles);
+        }
     }
-    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
-    // results
+    if (act.empty()) return GBS_OK;
+    const int nact = (int)act.size(), ntile = tcum.back();
+    const void *fn = E.fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
+    const size_t smem = sizeof(BTile<double>) * GBS_PWARPS;
+    if (act != E.g_act) {
+        engine_free_graph(E);
+        if ((size_t)ntile > E.cap_part) {
+            cudaFree(E.d_partS);
+            cudaFree(E.d_partU);
+            E.d_partS = E.d_partU = nullptr;
+            E.cap_part = 0;
+            const size_t cap = (size_t)ntile + ntile / 2 + 64;
+            GBS_CUDA_TRY(cudaMalloc(&E.d_partS, cap * GBS_KMAX * 2 * sizeof(double)));
+            GBS_CUDA_TRY(cudaMalloc(&E.d_partU, cap * GBS_KMAX * 2 * sizeof(double)));
+            E.cap_part = cap;
+        }
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_act, act.data(), sizeof(int) * nact, cudaMemcpyHostToDevice,
+                                     c->stream));
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_tcum, tcum.data(), sizeof(int) * (nact + 1),
+                                     cudaMemcpyHostToDevice, c->stream));
+        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));   // act/tcum are stack vectors
+        GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
+        if (per_sm < 1) return GBS_ERR_CUDA;
+        const int64_t need = ((int64_t)std::max(ntile, nact * GBS_KMAX) + GBS_PWARPS - 1) / GBS_PWARPS;
+        E.G = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, std::max<int64_t>(need, 1));
+        BArgs &a = E.g_args;
+        memset(&a, 0, sizeof(a));
+        a.sys = E.d_sys;
+        a.col = E.d_col;
+        a.dyn = E.d_dyn;
+        a.act = E.d_act;
+        a.tcum = E.d_tcum;
+        a.nact = nact;
+        a.ntile = ntile;
+        a.partS = E.d_partS;
+        a.partU = E.d_partU;
+        a.bar = E.d_bar;
+        a.quantum = E.quantum;   // even: the parity of the global iteration is unchanged
+        a.iter0 = 0;
+        a.inner_rtol = E.inner_rtol;
+        a.outer_maxit = E.outer_maxit;
+        a.fp64 = E.fp64;
+        a.timeout_ns = (unsigned long long)c->opts.barrier_timeout_ms * 1000000ull;
+        // capture barrier reset + cooperative launch once for this active set
+        cudaStream_t cap = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(E.d_bar, 0, 256, cap);
+            void *args[] = {&E.g_args};
+            cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args, smem, cap);
+            e = cudaStreamEndCapture(cap, &E.graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&E.gexec, E.graph, 0);
+        if (cap) cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            engine_free_graph(E);   // launch directly below
+        } else {
+            E.g_act = act;
+        }
+    }
+    if (E.gexec) {
+        GBS_CUDA_TRY(cudaGraphLaunch(E.gexec, c->stream));
+    } else {
+        GBS_CUDA_TRY(cudaMemsetAsync(E.d_bar, 0, 256, c->stream));
+        void *args[] = {&E.g_args};
+        GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args,
+                                                 smem, c->stream));
+    }
+    gbs_count_launch(c);
+    E.iter += E.quantum;
+    *ran = 1;
+    // barrier error word and the finished flags of every slot
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, &E.d_bar->error, sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(E.h_dyn.data(), E.d_dyn, sizeof(BSysDyn) * E.nslots,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (*(volatile int *)c->pinned) return GBS_ERR_TIMEOUT;
+    for (int s = 0; s < E.nslots; ++s)
+        if (E.slots[s].used) E.slots[s].finished = E.h_dyn[s].finished != 0;
+    return GBS_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------
+// gbs_ksp_solve_cg_batched
+// ----------------------------------------------------------------------
+
+extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, const gbs_vec *B,
+                                        gbs_vec *X, const int *nrhs, const double *rtol, int maxit,
+                                        int mode, int *iters, double *rnorm, int *status)
+{
+    if (!c || nsys < 0 || (nsys > 0 && (!A || !B || !X || !nrhs || !rtol)) || maxit < 0)
+        return GBS_ERR_ARG;
+    if (mode != GBS_MODE_FP64 && mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
+    for (int s = 0; s < nsys; ++s) {
+        if (!A[s] || !B[s] || !X[s] || A[s]->ctx != c || nrhs[s] < 1 || nrhs[s] > GBS_KMAX)
+            return GBS_ERR_ARG;
+        if (A[s]->n != A[s]->ncols || B[s]->n != A[s]->n * nrhs[s] || X[s]->n != B[s]->n ||
+            B[s]->dtype != GBS_F64 || X[s]->dtype != GBS_F64 || !(rtol[s] >= 0.0))
+            return GBS_ERR_ARG;
+    }
+    if (nsys == 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    Engine E;
+    int rc = engine_init(E, c, nsys, mode == GBS_MODE_FP64, 64);
+    for (int s = 0; s < nsys && rc == GBS_OK; ++s)
+        rc = engine_add(E, s, A[s], nrhs[s], rtol[s], maxit, (const double *)B[s]->data,
+                        (const double *)X[s]->data, false, 0);
+    if (rc == GBS_OK) {
+        cudaEventRecord(c->ev0, c->stream);
+        for (int ran = 1; rc == GBS_OK && ran;) rc = engine_step(E, &ran);
+        cudaEventRecord(c->ev1, c->stream);
+    }
     int first_bad = GBS_OK;
-    if (rc == GBS_OK && nsys > 0) {
-        cudaError_t e = cudaMemcpy(hc.data(), E.d_col, sizeof(BCol) * hc.size(),
-                                   cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = gbs_cuda_fail(e);
+    int64_t o = 0;
+    for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
+        int it[GBS_KMAX], stc[GBS_KMAX];
+        double rn[GBS_KMAX];
+        rc = engine_collect(E, s, (double *)X[s]->data, GBS_MEM_DEVICE, it, rn, stc);
+        for (int cc = 0; cc < nrhs[s] && rc == GBS_OK; ++cc, ++o) {
+            if (iters) iters[o] = it[cc];
+            if (rnorm) rnorm[o] = rn[cc];
+            if (status) status[o] = stc[cc];
+            if (stc[cc] != GBS_OK && first_bad == GBS_OK) first_bad = stc[cc];
+        }
     }
     if (rc == GBS_OK) {
-        int64_t o = 0;
-        for (int s = 0; s < nsys; ++s) {
-            const BSys &S = hs[s];
-            if (A[s]->n > 0) {
-                const size_t nk = (size_t)A[s]->n * S.k;
-                const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
-                k_interleave<<<g, 256, 0, c->stream>>>(A[s]->n, S.k, S.x,
-                                                               (double *)X[s]->data, 1);
-                gbs_count_launch(c);
-            }
-            for (int cc = 0; cc < S.k; ++cc, ++o) {
-                const BCol &C = hc[(size_t)s * GBS_KMAX + cc];
-                const int cs = C.status == GBS_RUNNING ? GBS_DIVERGED_ITS : C.status;
-                if (iters) iters[o] = C.iters;
-                if (rnorm) rnorm[o] = C.rn;
-                if (status) status[o] = cs;
-                if (cs != GBS_OK && first_bad == GBS_OK) first_bad = cs;
-            }
-        }
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = gbs_cuda_fail(e);
+        cudaStreamSynchronize(c->stream);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->last.device_ms = ms;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    c->last.device_ms = ms;
-    cudaStreamSynchronize(c->stream);
-    cudaFree(work);
-    cudaFree(E.d_sys);
-    cudaFree(E.d_col);
-    cudaFree(E.d_dyn);
-    cudaFree(E.d_tiles);
-    cudaFree(E.d_pairs);
-    cudaFree(E.d_partS);
-    cudaFree(E.d_partU);
-    cudaFree(E.d_bar);
-    if (rc != GBS_OK) return rc;
-    return first_bad;
+    engine_destroy(E);
+    return rc != GBS_OK ? rc : first_bad;
 }
 
 // ----------------------------------------------------------------------
-// Serving loop (continuous batching) -- declared in gbs.h, built on the
-// engine above; implemented in server.cu.
+// Serving loop: continuous batching of solve requests under a memory budget
 // ----------------------------------------------------------------------
-extern "C" int gbs_server_create(gbs_ctx, size_t, int, int, gbs_server *) { return GBS_ERR_UNSUPPORTED; }
-extern "C" int gbs_server_destroy(gbs_server) { return GBS_OK; }
-extern "C" int gbs_server_submit(gbs_server, int64_t, const int32_t *, const int32_t *,
-                                 const double *, int, const double *, double, int, uint64_t *)
+
+namespace {
+
+struct Request {
+    uint64_t ticket;
+    int64_t n;
+    int k;
+    double rtol;
+    int maxit;
+    std::vector<int32_t> rowptr, colidx;
+    std::vector<double> vals, b;
+    size_t bytes;
+    int slot = -1;
+    bool done = false;
+    std::vector<double> x;
+    std::vector<int> iters, status;
+    std::vector<double> rnorm;
+};
+
+}  // namespace
+
+struct gbs_server_s {
+    gbs_ctx c;
+    Engine E;
+    size_t budget;
+    size_t used = 0;
+    int mode;
+    uint64_t next_ticket = 1;
+    std::deque<uint64_t> queue;                       // waiting for admission, FIFO
+    std::unordered_map<uint64_t, Request> reqs;       // queued, running or done
+    int running = 0, finished = 0;
+};
+
+extern "C" int gbs_server_create(gbs_ctx c, size_t budget, int max_slots, int mode, gbs_server *out)
 {
-    return GBS_ERR_UNSUPPORTED;
+    if (!c || !out || budget == 0 || max_slots < 0) return GBS_ERR_ARG;
+    if (mode != GBS_MODE_FP64 && mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
+    *out = nullptr;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    gbs_server srv = new (std::nothrow) gbs_server_s();
+    if (!srv) return GBS_ERR_OOM;
+    srv->c = c;
+    srv->budget = budget;
+    srv->mode = mode;
+    const int st = engine_init(srv->E, c, max_slots ? max_slots : 256, mode == GBS_MODE_FP64, 32);
+    if (st) {
+        engine_destroy(srv->E);
+        delete srv;
+        return st;
+    }
+    *out = srv;
+    return GBS_OK;
 }
-extern "C" int gbs_server_progress(gbs_server, int *) { return GBS_ERR_UNSUPPORTED; }
-extern "C" int gbs_server_poll(gbs_server, uint64_t, int *) { return GBS_ERR_UNSUPPORTED; }
-extern "C" int gbs_server_wait(gbs_server, uint64_t) { return GBS_ERR_UNSUPPORTED; }
-extern "C" int gbs_server_fetch(gbs_server, uint64_t, double *, int *, double *, int *)
+
+extern "C" int gbs_server_destroy(gbs_server srv)
 {
-    return GBS_ERR_UNSUPPORTED;
+    if (!srv) return GBS_OK;
+    cudaSetDevice(srv->c->device);
+    engine_destroy(srv->E);
+    delete srv;
+    return GBS_OK;
 }
-extern "C" int gbs_server_stats(gbs_server, int *, int *, int *, size_t *) { return GBS_ERR_UNSUPPORTED; }
+
+extern "C" int gbs_server_submit(gbs_server srv, int64_t nrows, const int32_t *rowptr,
+                                 const int32_t *colidx, const double *vals, int k, const double *b,
+                                 double rtol, int maxit, uint64_t *ticket)
+{
+    if (!srv || !ticket || nrows < 0 || nrows >= INT32_MAX || !rowptr || k < 1 || k > GBS_KMAX ||
+        !(rtol >= 0.0) || maxit < 0 || (nrows > 0 && !b))
+        return GBS_ERR_ARG;
+    const int64_t nnz = rowptr[nrows];
+    if (nnz < 0 || (nnz > 0 && (!colidx || !vals))) return GBS_ERR_ARG;
+    const size_t bytes = system_bytes(nrows, nnz, k, srv->mode == GBS_MODE_FP64);
+    if (bytes > srv->budget) return GBS_ERR_BUDGET;
+    Request r;
+    r.ticket = srv->next_ticket++;
+    r.n = nrows;
+    r.k = k;
+    r.rtol = rtol;
+    r.maxit = maxit;
+    r.rowptr.assign(rowptr, rowptr + nrows + 1);
+    r.colidx.assign(colidx, colidx + nnz);
+    r.vals.assign(vals, vals + nnz);
+    r.b.assign(b, b + nrows * k);
+    r.bytes = bytes;
+    *ticket = r.ticket;
+    srv->queue.push_back(r.ticket);
+    srv->reqs.emplace(r.ticket, std::move(r));
+    return GBS_OK;
+}
+
+// Admit queued requests (FIFO) while a slot and budget are free.
+static int server_admit(gbs_server srv)
+{
+    Engine &E = srv->E;
+    while (!srv->queue.empty()) {
+        Request &r = srv->reqs.at(srv->queue.front());
+        int slot = -1;
+        for (int s = 0; s < E.nslots; ++s)
+            if (!E.slots[s].used) { slot = s; break; }
+        if (slot < 0 || srv->used + r.bytes > srv->budget) break;
+        srv->queue.pop_front();
+        gbs_mat A = nullptr;
+        int st = gbs_mat_create_aij(srv->c, r.n, r.n, r.rowptr.data(), r.colidx.data(),
+                                    r.vals.data(), GBS_MEM_HOST, &A);
+        if (st != GBS_OK) {
+            // a malformed request finishes at once with that status
+            r.done = true;
+            r.x.assign((size_t)r.n * r.k, 0.0);
+            r.iters.assign(r.k, 0);
+            r.rnorm.assign(r.k, 0.0);
+            r.status.assign(r.k, st);
+            ++srv->finished;
+            continue;
+        }
+        double *db = nullptr;
+        const size_t nb = (size_t)r.n * r.k * sizeof(double);
+        if (nb) {
+            cudaError_t e = cudaMalloc(&db, nb);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(db, r.b.data(), nb, cudaMemcpyHostToDevice, srv->c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(db);
+                gbs_mat_destroy(A);
+                return gbs_cuda_fail(e);
+            }
+        }
+        st = engine_add(E, slot, A, r.k, r.rtol, r.maxit, db, nullptr, true, r.ticket);
+        cudaFree(db);   // engine_add synchronised the stream after interleaving b
+        if (st) {
+            gbs_mat_destroy(A);
+            return st;
+        }
+        r.slot = slot;
+        srv->used += r.bytes;
+        ++srv->running;
+        std::vector<double>().swap(r.b);
+        std::vector<int32_t>().swap(r.colidx);
+        std::vector<double>().swap(r.vals);
+    }
+    return GBS_OK;
+}
+
+// Retire finished slots: results to the host, memory and slot released.
+static int server_retire(gbs_server srv, int *retired)
+{
+    Engine &E = srv->E;
+    for (int s = 0; s < E.nslots; ++s) {
+        SlotHost &H = E.slots[s];
+        if (!H.used || !H.finished) continue;
+        Request &r = srv->reqs.at(H.ticket);
+        r.x.assign((size_t)r.n * r.k, 0.0);
+        r.iters.assign(r.k, 0);
+        r.rnorm.assign(r.k, 0.0);
+        r.status.assign(r.k, 0);
+        const int st = engine_collect(E, s, r.x.data(), GBS_MEM_HOST, r.iters.data(), r.rnorm.data(),
+                                      r.status.data());
+        if (st) return st;
+        engine_release(E, s);
+        srv->used -= r.bytes;
+        r.done = true;
+        r.slot = -1;
+        --srv->running;
+        ++srv->finished;
+        ++*retired;
+    }
+    return GBS_OK;
+}
+
+extern "C" int gbs_server_progress(gbs_server srv, int *retired)
+{
+    if (!srv) return GBS_ERR_ARG;
+    int n = 0;
+    GBS_CUDA_TRY(cudaSetDevice(srv->c->device));
+    int st = server_retire(srv, &n);   // systems that finished at admission
+    if (!st) st = server_admit(srv);
+    int ran = 0;
+    if (!st) st = engine_step(srv->E, &ran);
+    if (!st) st = server_retire(srv, &n);
+    if (retired) *retired = n;
+    return st;
+}
+
+extern "C" int gbs_server_poll(gbs_server srv, uint64_t ticket, int *done)
+{
+    if (!srv || !done) return GBS_ERR_ARG;
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return GBS_ERR_NOT_FOUND;
+    *done = it->second.done ? 1 : 0;
+    return GBS_OK;
+}
+
+extern "C" int gbs_server_wait(gbs_server srv, uint64_t ticket)
+{
+    if (!srv) return GBS_ERR_ARG;
+    for (;;) {
+        auto it = srv->reqs.find(ticket);
+        if (it == srv->reqs.end()) return GBS_ERR_NOT_FOUND;
+        if (it->second.done) return GBS_OK;
+        const int st = gbs_server_progress(srv, nullptr);
+        if (st) return st;
+    }
+}
+
+extern "C" int gbs_server_fetch(gbs_server srv, uint64_t ticket, double *x, int *iters,
+                                double *rnorm, int *status)
+{
+    if (!srv) return GBS_ERR_ARG;
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end() || !it->second.done) return GBS_ERR_NOT_FOUND;
+    Request &r = it->second;
+    if (x && !r.x.empty()) memcpy(x, r.x.data(), r.x.size() * sizeof(double));
+    for (int cc = 0; cc < r.k; ++cc) {
+        if (iters) iters[cc] = r.iters[cc];
+        if (rnorm) rnorm[cc] = r.rnorm[cc];
+        if (status) status[cc] = r.status[cc];
+    }
+    srv->reqs.erase(it);
+    return GBS_OK;
+}
+
+extern "C" int gbs_server_stats(gbs_server srv, int *queued, int *running, int *finished,
+                                size_t *bytes_in_use)
+{
+    if (!srv) return GBS_ERR_ARG;
+    if (queued) *queued = (int)srv->queue.size();
+    if (running) *running = srv->running;
+    if (finished) *finished = srv->finished;
+    if (bytes_in_use) *bytes_in_use = srv->used;
+    return GBS_OK;
+}
