@@ -54,6 +54,10 @@ def parse_args():
                    help="device-resident headline solve only (no e2e, extras or CPU baseline)")
     p.add_argument("--maxit", type=int, default=20000,
                    help="iteration cap of the headline solve (profiling runs use a small cap)")
+    p.add_argument("--c4-systems", type=int, default=512, help="systems in the batched workload")
+    p.add_argument("--c5-requests", type=int, default=300, help="requests in the serving workload")
+    p.add_argument("--c5-pool", type=int, default=12,
+                   help="distinct operators the serving requests draw from")
     return p.parse_args()
 
 
@@ -485,6 +489,226 @@ def extras(g, args, A, Ah, xsv):
     for v in (xs3v, b3v, x3v, r3v):
         gbs.gbs_vec_destroy(v)
     gbs.gbs_mat_destroy(h)
+    out["c4_batched"] = c4_batched(g, args)
+    out["c5_serving"] = c5_serving(g, args)
+    return out
+
+
+def c4_batched(g, args):
+    """512 systems (2D 5-point / 3D 7-point, lognormal(0, 0.5) face links, n
+    log-uniform in [1e3, 2e5]) x 8 right-hand sides in one batched solve,
+    mixed precision and FP64, rtol 1e-10."""
+    import numpy as np
+    import torch
+    from paper_2011_00715_gb300 import inputs as I
+    gbs = g.gbs
+    nsys = args.c4_systems
+    specs = I.c4_batch_specs(nsys=nsys)
+    t_gen = time.perf_counter()
+    mats, bvs, bts, xvs, xts = [], [], [], [], []
+    nnz_tot = n_tot = 0
+    for s in specs:
+        A = I.family_matrix(s["family"], s["dims"], s["seed"], s["sigma"])
+        k = s["nrhs"]
+        h = g.mat(A)
+        xs = np.concatenate([I.xstar(A.n, 44, column=c, system=s["system"]) for c in range(k)])
+        xst = torch.from_numpy(xs).cuda()
+        bt = torch.empty_like(xst)
+        for c in range(k):          # b = A x* column by column, on the device
+            xv = gbs.gbs_vec_wrap(g.ctx, xst[c * A.n:(c + 1) * A.n])
+            bv = gbs.gbs_vec_wrap(g.ctx, bt[c * A.n:(c + 1) * A.n])
+            gbs.gbs_mat_mult(h, xv, bv)
+            gbs.gbs_vec_destroy(xv)
+            gbs.gbs_vec_destroy(bv)
+        xt = torch.zeros_like(bt)
+        mats.append((h, A, k))
+        bts.append(bt)
+        xts.append(xt)
+        bvs.append(gbs.gbs_vec_wrap(g.ctx, bt))
+        xvs.append(gbs.gbs_vec_wrap(g.ctx, xt))
+        nnz_tot += A.nnz
+        n_tot += A.n
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    res = {"systems": nsys, "rhs_per_system": 8, "rows_total": n_tot, "nnz_total": nnz_tot,
+           "setup_s": t_gen}
+    sols = {}
+    for name, mode in (("mixed", gbs.GBS_MODE_MIXED), ("fp64", gbs.GBS_MODE_FP64)):
+        times = []
+        for rep in range(2):
+            for xt in xts:
+                xt.zero_()
+            torch.cuda.synchronize()
+            l0 = g.launches()
+            t = time.perf_counter()
+            st, its, rns, sts = gbs.gbs_ksp_solve_cg_batched(
+                g.ctx, [m[0] for m in mats], bvs, xvs, [m[2] for m in mats], [1e-10] * nsys,
+                20000, mode)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+            launches = g.launches() - l0
+        ncols = int(sum(m[2] for m in mats))
+        # true FP64 residual of every column on the device
+        worst = 0.0
+        for (h, A, k), bt, xt in zip(mats, bts, xts):
+            rt = torch.empty_like(bt)
+            for c in range(k):
+                xv = gbs.gbs_vec_wrap(g.ctx, xt[c * A.n:(c + 1) * A.n])
+                rv = gbs.gbs_vec_wrap(g.ctx, rt[c * A.n:(c + 1) * A.n])
+                gbs.gbs_mat_mult(h, xv, rv)
+                gbs.gbs_vec_destroy(xv)
+                gbs.gbs_vec_destroy(rv)
+            for c in range(k):
+                sl = slice(c * A.n, (c + 1) * A.n)
+                worst = max(worst, float(torch.linalg.norm(bt[sl] - rt[sl]) / torch.linalg.norm(bt[sl])))
+        sols[name] = [xt.clone() for xt in xts]
+        res[name] = {"seconds": min(times), "solves_per_s": ncols / min(times),
+                     "status_ok": int((sts == 0).sum()), "columns": ncols,
+                     "inner_iters_mean": float(np.mean(its)), "inner_iters_max": int(its.max()),
+                     "max_true_rel_residual": worst, "kernel_launches": int(launches)}
+    diff = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+               for a, b in zip(sols["mixed"], sols["fp64"]))
+    res["max_rel_diff_mixed_vs_fp64_per_system"] = diff
+    res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+    for (h, _, _), bv, xv in zip(mats, bvs, xvs):
+        gbs.gbs_vec_destroy(bv)
+        gbs.gbs_vec_destroy(xv)
+        gbs.gbs_mat_destroy(h)
+    return res
+
+
+def c5_serving(g, args):
+    """Poisson-arriving solve requests on 27-point lognormal(0,1) operators
+    (n log-uniform in [1e3, 1e6], 1-4 right-hand sides, rtol 1e-10), served
+    by the continuous-batching engine (mixed precision, 150 GB budget) and,
+    on the same stream, by plain FP64 per-solve launches."""
+    import numpy as np
+    import torch
+    from paper_2011_00715_gb300 import inputs as I
+    gbs = g.gbs
+    nreq = args.c5_requests
+    pool = args.c5_pool
+    specs = I.c5_request_specs(count=nreq, pool=pool)
+    t_gen = time.perf_counter()
+    mats = {}
+    for s in specs:
+        key = s["matrix_key"]
+        if key not in mats:
+            mats[key] = I.var27(*s["dims"], seed=s["seed"], sigma=1.0)
+    # right-hand sides b = A x* on the device, then to the host (requests carry host data)
+    bs = []
+    dev = {}
+    for s in specs:
+        A = mats[s["matrix_key"]]
+        if s["matrix_key"] not in dev:
+            dev[s["matrix_key"]] = g.mat(A)
+        h = dev[s["matrix_key"]]
+        k = s["nrhs"]
+        xs = torch.from_numpy(np.concatenate(
+            [I.xstar(A.n, 55, column=c, system=s["request"]) for c in range(k)])).cuda()
+        bt = torch.empty_like(xs)
+        for c in range(k):
+            xv = gbs.gbs_vec_wrap(g.ctx, xs[c * A.n:(c + 1) * A.n])
+            bv = gbs.gbs_vec_wrap(g.ctx, bt[c * A.n:(c + 1) * A.n])
+            gbs.gbs_mat_mult(h, xv, bv)
+            gbs.gbs_vec_destroy(xv)
+            gbs.gbs_vec_destroy(bv)
+        bs.append(bt.cpu().numpy())
+    for h in dev.values():
+        gbs.gbs_mat_destroy(h)
+    t_gen = time.perf_counter() - t_gen
+    ncols = sum(s["nrhs"] for s in specs)
+    out = {"requests": nreq, "matrix_pool": pool, "columns": ncols, "setup_s": t_gen,
+           "rows_mean": float(np.mean([mats[s["matrix_key"]].n for s in specs]))}
+
+    def serve_batched(arrivals):
+        srv = gbs.gbs_server_create(g.ctx, 150 << 30, 0, gbs.GBS_MODE_MIXED)
+        lat = [None] * nreq
+        tickets = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        done = 0
+        worst = 0.0
+        while done < nreq:
+            now = time.perf_counter() - t0
+            while nxt < nreq and arrivals[nxt] <= now:
+                s = specs[nxt]
+                A = mats[s["matrix_key"]]
+                tickets[nxt] = gbs.gbs_server_submit(srv, A.n, A.rowptr, A.colidx, A.vals,
+                                                     s["nrhs"], bs[nxt], 1e-10, 20000)
+                nxt += 1
+            q, running, fin, used = gbs.gbs_server_stats(srv)
+            if running == 0 and q == 0 and nxt < nreq:
+                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+                continue
+            gbs.gbs_server_progress(srv)
+            tnow = time.perf_counter() - t0
+            for i, t in list(tickets.items()):
+                if gbs.gbs_server_poll(srv, t):
+                    s = specs[i]
+                    A = mats[s["matrix_key"]]
+                    x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, s["nrhs"])
+                    lat[i] = tnow - arrivals[i]
+                    worst = max(worst, float(np.max(rns / np.maximum(
+                        [np.linalg.norm(bs[i][c * A.n:(c + 1) * A.n]) for c in range(s["nrhs"])],
+                        1e-300))))
+                    if not np.all(sts == 0):
+                        worst = float("inf")
+                    del tickets[i]
+                    done += 1
+        total = time.perf_counter() - t0
+        gbs.gbs_server_destroy(srv)
+        return total, np.array(lat), worst
+
+    def serve_perop(arrivals):
+        lat = [None] * nreq
+        t0 = time.perf_counter()
+        o = gbs.gbs_opts_default(mode=gbs.GBS_MODE_FP64, algorithm=gbs.GBS_ALG_PERSISTENT)
+        worst = 0.0
+        for i, s in enumerate(specs):
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            A = mats[s["matrix_key"]]
+            h = gbs.gbs_mat_create_aij(g.ctx, A.n, A.n, A.rowptr, A.colidx, A.vals)
+            bt = torch.from_numpy(bs[i]).cuda()
+            xt = torch.zeros_like(bt)
+            for c in range(s["nrhs"]):
+                bv = gbs.gbs_vec_wrap(g.ctx, bt[c * A.n:(c + 1) * A.n])
+                xv = gbs.gbs_vec_wrap(g.ctx, xt[c * A.n:(c + 1) * A.n])
+                info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, 1e-10, 20000, o)
+                worst = max(worst, info.rnorm / info.bnorm if info.status == 0 else float("inf"))
+                gbs.gbs_vec_destroy(bv)
+                gbs.gbs_vec_destroy(xv)
+            xt.cpu()
+            gbs.gbs_mat_destroy(h)
+            lat[i] = time.perf_counter() - t0 - arrivals[i]
+        total = time.perf_counter() - t0
+        return total, np.array(lat), worst
+
+    # saturation (every request present at t = 0), then a Poisson stream at
+    # half the batched engine's saturated request rate
+    zero = np.zeros(nreq)
+    tb, lb, wb = serve_batched(zero)
+    rate = 0.5 * nreq / tb
+    arr = I.poisson_arrivals(5, rate, nreq)
+    runs = {"saturation": zero, f"poisson_{rate:.1f}_req_per_s": arr}
+    for name, arrivals in runs.items():
+        if name == "saturation":
+            t_b, l_b, w_b = tb, lb, wb
+        else:
+            t_b, l_b, w_b = serve_batched(arrivals)
+        t_p, l_p, w_p = serve_perop(arrivals)
+        out[name] = {
+            "batched_mixed": {"solves_per_s": ncols / t_b, "requests_per_s": nreq / t_b,
+                              "p50_ms": float(np.percentile(l_b, 50) * 1e3),
+                              "p99_ms": float(np.percentile(l_b, 99) * 1e3),
+                              "max_rel_residual": w_b},
+            "perop_fp64": {"solves_per_s": ncols / t_p, "requests_per_s": nreq / t_p,
+                           "p50_ms": float(np.percentile(l_p, 50) * 1e3),
+                           "p99_ms": float(np.percentile(l_p, 99) * 1e3),
+                           "max_rel_residual": w_p},
+            "speedup_solves_per_s": t_p / t_b}
     return out
 
 

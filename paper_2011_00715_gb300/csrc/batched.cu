@@ -94,8 +94,12 @@ struct BArgs {
     const int *tcum;    // prefix sums of the active slots' tile counts (nact + 1)
     int nact;
     int ntile;          // tcum[nact]
+    int nchunk;         // ccum[nact]
     double *partS;      // active tile * GBS_KMAX * 2
     double *partU;      // active tile * GBS_KMAX * 2
+    const int *ccum;    // prefix sums of the active slots' reduction chunks (nact + 1)
+    double *cpart;      // chunk * GBS_KMAX * 2: chunk partial sums
+    int *ccount;        // active slot * GBS_KMAX: chunks arrived (zero between phases)
     gbs_grid_barrier *bar;
     int quantum;
     int iter0;          // parity of the global iteration count at launch
@@ -205,6 +209,39 @@ __device__ __forceinline__ T sys_sum(const double *part, int ga, int gb, int c, 
 
 __device__ __forceinline__ bool col_running(const BCol &c) { return c.status == GBS_RUNNING; }
 
+// Tiles per reduction chunk: a system's per-tile partials are summed chunk
+// by chunk (one warp each), then the chunk sums are added by the warp that
+// completes the last chunk.  Both levels use a fixed order that depends
+// only on the system, so results stay independent of the batch.
+#define GBS_RCHUNK 128
+
+// Two-level reduction of entries 0 and 1 of column c over one system's
+// tiles, for the chunk [ga, gb) handled by this warp (chunk gc of the
+// active chunk range [ca, cb), system active index ai).  Returns true in
+// the warp whose chunk arrived last; that warp gets the totals in out[].
+template <typename T>
+__device__ __forceinline__ bool chunk_reduce(const BArgs &a, const double *part, int ga, int gb,
+                                             int gc, int ca, int cb, int ai, int c, T (&out)[2])
+{
+    const int lane = threadIdx.x & 31;
+    T s0 = sys_sum<T>(part, ga, gb, c, 0);
+    T s1 = sys_sum<T>(part, ga, gb, c, 1);
+    int last = 0;
+    if (lane == 0) {
+        a.cpart[((size_t)gc * GBS_KMAX + c) * 2 + 0] = (double)s0;
+        a.cpart[((size_t)gc * GBS_KMAX + c) * 2 + 1] = (double)s1;
+        __threadfence();
+        last = atomicAdd(&a.ccount[ai * GBS_KMAX + c], 1) == cb - ca - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return false;
+    __threadfence();
+    out[0] = sys_sum<T>(a.cpart, ca, cb, c, 0);
+    out[1] = sys_sum<T>(a.cpart, ca, cb, c, 1);
+    if (lane == 0) a.ccount[ai * GBS_KMAX + c] = 0;
+    return true;
+}
+
 // Active index owning active tile g (tcum is increasing, tcum[0] = 0).
 __device__ __forceinline__ int owner_of(const int *tcum, int nact, int g)
 {
@@ -230,7 +267,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
     // this warp's contiguous share of the active tiles
     const int g0 = (int)((int64_t)a.ntile * gw / nw), g1 = (int)((int64_t)a.ntile * (gw + 1) / nw);
     const int ai0 = g0 < g1 ? owner_of(a.tcum, a.nact, g0) : 0;
-    const int npairs = a.nact * GBS_KMAX;
+    const int nunits = a.nchunk * GBS_KMAX;   // reduction work units: (chunk, column)
     int bno = 0;
     bool ok = true;
 
@@ -292,18 +329,22 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- R1: per (system, column)
-        for (int pidx = gw; pidx < npairs; pidx += nw) {
-            const int ai = pidx / GBS_KMAX, cc = pidx % GBS_KMAX;
+        for (int u = gw; u < nunits; u += nw) {
+            const int gc = u / GBS_KMAX, cc = u % GBS_KMAX;
+            const int ai = owner_of(a.ccum, a.nact, gc);
             const int slot = __ldg(a.act + ai);
             const BSys &S = a.sys[slot];
             BSysDyn &D = a.dyn[slot];
             if (cc >= S.k || D.finished) continue;
             BCol &C = a.col[slot * GBS_KMAX + cc];
             if (!col_running(C)) continue;
-            const int ga = __ldg(a.tcum + ai), gb = __ldg(a.tcum + ai + 1);
+            const int ca = __ldg(a.ccum + ai), cb = __ldg(a.ccum + ai + 1);
+            const int ga = __ldg(a.tcum + ai) + (gc - ca) * GBS_RCHUNK;
+            const int gb = min(ga + GBS_RCHUNK, __ldg(a.tcum + ai + 1));
             if (D.mode[cur] == MODE_OUTER) {
-                const double rr = sys_sum<double>(a.partS, ga, gb, cc, 0);
-                const double bb = sys_sum<double>(a.partS, ga, gb, cc, 1);
+                double tot[2];
+                if (!chunk_reduce<double>(a, a.partS, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
+                const double rr = tot[0], bb = tot[1];
                 if (lane == 0) {
                     const double rn = sqrt(rr);
                     if (C.first) C.bnorm = sqrt(bb);
@@ -322,7 +363,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     }
                 }
             } else if (!C.inner_done) {
-                const TI pq = sys_sum<TI>(a.partS, ga, gb, cc, 0);
+                TI tot[2];
+                if (!chunk_reduce<TI>(a, a.partS, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
+                const TI pq = tot[0];
                 if (lane == 0) {
                     if (isnan((double)pq)) C.status = GBS_ERR_NAN;
                     else if (pq <= TI(0)) C.status = GBS_ERR_INDEFINITE;
@@ -389,18 +432,22 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
         if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
 
         // ---------------- R2: per (system, column)
-        for (int pidx = gw; pidx < npairs; pidx += nw) {
-            const int ai = pidx / GBS_KMAX, cc = pidx % GBS_KMAX;
+        for (int u = gw; u < nunits; u += nw) {
+            const int gc = u / GBS_KMAX, cc = u % GBS_KMAX;
+            const int ai = owner_of(a.ccum, a.nact, gc);
             const int slot = __ldg(a.act + ai);
             const BSys &S = a.sys[slot];
             BSysDyn &D = a.dyn[slot];
             if (cc >= S.k || D.finished) continue;
             BCol &C = a.col[slot * GBS_KMAX + cc];
             if (!col_running(C)) continue;
-            const int ga = __ldg(a.tcum + ai), gb = __ldg(a.tcum + ai + 1);
+            const int ca = __ldg(a.ccum + ai), cb = __ldg(a.ccum + ai + 1);
+            const int ga = __ldg(a.tcum + ai) + (gc - ca) * GBS_RCHUNK;
+            const int gb = min(ga + GBS_RCHUNK, __ldg(a.tcum + ai + 1));
             if (D.mode[cur] == MODE_OUTER) {
-                const TI rho = sys_sum<TI>(a.partU, ga, gb, cc, 0);
-                const TI bb = sys_sum<TI>(a.partU, ga, gb, cc, 1);
+                TI tot[2];
+                if (!chunk_reduce<TI>(a, a.partU, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
+                const TI rho = tot[0], bb = tot[1];
                 if (lane == 0) {
                     C.rho = (double)rho;
                     C.tol_inner = C.tol_inner * (double)sqrt(bb);
@@ -408,8 +455,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
                     C.inner_done = 0;
                 }
             } else if (!C.inner_done) {
-                const TI rho_new = sys_sum<TI>(a.partU, ga, gb, cc, 0);
-                const TI rr = sys_sum<TI>(a.partU, ga, gb, cc, 1);
+                TI tot[2];
+                if (!chunk_reduce<TI>(a, a.partU, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
+                const TI rho_new = tot[0], rr = tot[1];
                 if (lane == 0) {
                     C.kin += 1;
                     C.iters += 1;
@@ -509,7 +557,9 @@ struct Engine {
     BSys *d_sys = nullptr;
     BCol *d_col = nullptr;
     BSysDyn *d_dyn = nullptr;
-    int *d_act = nullptr, *d_tcum = nullptr;
+    int *d_act = nullptr, *d_tcum = nullptr, *d_ccum = nullptr, *d_ccount = nullptr;
+    double *d_cpart = nullptr;
+    size_t cap_cpart = 0;
     double *d_partS = nullptr, *d_partU = nullptr;
     size_t cap_part = 0;
     gbs_grid_barrier *d_bar = nullptr;
@@ -520,6 +570,8 @@ struct Engine {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     std::vector<int> g_act;   // active set the graph was captured for
+    std::vector<int> g_tcum;  // and its tile prefix sums
+    bool dirty = true;        // a slot was filled or released since the capture
     BArgs g_args;
     int G = 0;
 };
@@ -531,6 +583,7 @@ void engine_free_graph(Engine &E)
     E.gexec = nullptr;
     E.graph = nullptr;
     E.g_act.clear();
+    E.g_tcum.clear();
 }
 
 int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
@@ -548,6 +601,9 @@ int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
     GBS_CUDA_TRY(cudaMalloc(&E.d_dyn, sizeof(BSysDyn) * (size_t)std::max(nslots, 1)));
     GBS_CUDA_TRY(cudaMalloc(&E.d_act, sizeof(int) * (size_t)(nslots + 1)));
     GBS_CUDA_TRY(cudaMalloc(&E.d_tcum, sizeof(int) * (size_t)(nslots + 2)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_ccum, sizeof(int) * (size_t)(nslots + 2)));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_ccount, sizeof(int) * (size_t)(nslots + 1) * GBS_KMAX));
+    GBS_CUDA_TRY(cudaMemset(E.d_ccount, 0, sizeof(int) * (size_t)(nslots + 1) * GBS_KMAX));
     GBS_CUDA_TRY(cudaMalloc(&E.d_bar, 256));
     return GBS_OK;
 }
@@ -566,6 +622,9 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_dyn);
     cudaFree(E.d_act);
     cudaFree(E.d_tcum);
+    cudaFree(E.d_ccum);
+    cudaFree(E.d_ccount);
+    cudaFree(E.d_cpart);
     cudaFree(E.d_partS);
     cudaFree(E.d_partU);
     cudaFree(E.d_bar);
@@ -598,6 +657,9 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     const size_t bytes = 3 * a256(nk * 8) + 5 * a256(nk * tsz);
     char *p = nullptr;
     if (bytes) GBS_CUDA_TRY(cudaMalloc(&p, bytes));
+    // a reused slot may hold a system of another size: the active lists and
+    // the captured launch must be rebuilt before the next quantum
+    E.dirty = true;
     H.used = true;
     H.finished = false;
     H.A = A;
@@ -703,6 +765,7 @@ int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters,
 
 void engine_release(Engine &E, int slot)
 {
+    E.dirty = true;
     SlotHost &H = E.slots[slot];
     if (H.work) cudaFree(H.work);
     if (H.own_A) gbs_mat_destroy(H.A);
@@ -714,20 +777,22 @@ int engine_step(Engine &E, int *ran)
 {
     gbs_ctx c = E.c;
     *ran = 0;
-    std::vector<int> act, tcum(1, 0);
+    std::vector<int> act, tcum(1, 0), ccum(1, 0);
     for (int s = 0; s < E.nslots; ++s) {
         const SlotHost &H = E.slots[s];
         if (H.used && !H.finished && H.A->ntiles > 0) {
             act.push_back(s);
             tcum.push_back(tcum.back() + (int)H.A->ntiles);
+            ccum.push_back(ccum.back() + (int)((H.A->ntiles + GBS_RCHUNK - 1) / GBS_RCHUNK));
         }
     }
     if (act.empty()) return GBS_OK;
-    const int nact = (int)act.size(), ntile = tcum.back();
+    const int nact = (int)act.size(), ntile = tcum.back(), nchunk = ccum.back();
     const void *fn = E.fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
     const size_t smem = sizeof(BTile<double>) * GBS_PWARPS;
-    if (act != E.g_act) {
+    if (E.dirty || act != E.g_act || tcum != E.g_tcum) {
         engine_free_graph(E);
+        E.dirty = false;
         if ((size_t)ntile > E.cap_part) {
             cudaFree(E.d_partS);
             cudaFree(E.d_partU);
@@ -738,6 +803,16 @@ int engine_step(Engine &E, int *ran)
             GBS_CUDA_TRY(cudaMalloc(&E.d_partU, cap * GBS_KMAX * 2 * sizeof(double)));
             E.cap_part = cap;
         }
+        if ((size_t)nchunk > E.cap_cpart) {
+            cudaFree(E.d_cpart);
+            E.d_cpart = nullptr;
+            E.cap_cpart = 0;
+            const size_t cap = (size_t)nchunk + nchunk / 2 + 64;
+            GBS_CUDA_TRY(cudaMalloc(&E.d_cpart, cap * GBS_KMAX * 2 * sizeof(double)));
+            E.cap_cpart = cap;
+        }
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_ccum, ccum.data(), sizeof(int) * (nact + 1),
+                                     cudaMemcpyHostToDevice, c->stream));
         GBS_CUDA_TRY(cudaMemcpyAsync(E.d_act, act.data(), sizeof(int) * nact, cudaMemcpyHostToDevice,
                                      c->stream));
         GBS_CUDA_TRY(cudaMemcpyAsync(E.d_tcum, tcum.data(), sizeof(int) * (nact + 1),
@@ -747,7 +822,7 @@ int engine_step(Engine &E, int *ran)
         int per_sm = 0;
         GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
-        const int64_t need = ((int64_t)std::max(ntile, nact * GBS_KMAX) + GBS_PWARPS - 1) / GBS_PWARPS;
+        const int64_t need = ((int64_t)std::max(ntile, nchunk * GBS_KMAX) + GBS_PWARPS - 1) / GBS_PWARPS;
         E.G = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, std::max<int64_t>(need, 1));
         BArgs &a = E.g_args;
         memset(&a, 0, sizeof(a));
@@ -758,6 +833,10 @@ int engine_step(Engine &E, int *ran)
         a.tcum = E.d_tcum;
         a.nact = nact;
         a.ntile = ntile;
+        a.nchunk = nchunk;
+        a.ccum = E.d_ccum;
+        a.cpart = E.d_cpart;
+        a.ccount = E.d_ccount;
         a.partS = E.d_partS;
         a.partU = E.d_partU;
         a.bar = E.d_bar;
@@ -784,6 +863,7 @@ int engine_step(Engine &E, int *ran)
             engine_free_graph(E);   // launch directly below
         } else {
             E.g_act = act;
+            E.g_tcum = tcum;
         }
     }
     if (E.gexec) {

@@ -32,7 +32,8 @@ def lambda_min(A):
 def make_batch():
     specs = [("var5", (12, 9), 1), ("var7", (10, 9, 8), 8), ("var5", (40, 37), 3),
              ("var7", (17, 16, 15), 2), ("var5", (70, 65), 5), ("var7", (6, 5, 4), 4),
-             ("var5", (3, 2), 2), ("var7", (25, 24, 23), 1)]
+             ("var5", (3, 2), 2), ("var7", (25, 24, 23), 1),
+             ("var5", (150, 130), 2)]          # 610 tiles: several reduction chunks
     mats = []
     for i, (fam, dims, k) in enumerate(specs):
         A = I.family_matrix(fam, dims, seed=500 + i, sigma=0.5)

@@ -148,3 +148,19 @@ def test_server_malformed_and_degenerate_requests(S, orc):
     q, running, fin, used = gbs.gbs_server_stats(srv)
     assert q == 0 and running == 0 and used == 0
     gbs.gbs_server_destroy(srv)
+
+
+def test_server_slot_reuse_with_different_sizes(S, orc):
+    """One slot: every request lands in the same slot in turn, each with a
+    different size, so the engine must rebuild its active lists per request."""
+    srv = gbs.gbs_server_create(S.ctx, 1 << 30, 1, gbs.GBS_MODE_MIXED)
+    reqs = [request(orc, 40 + i, d, k) for i, (d, k) in
+            enumerate([((11, 10, 9), 1), ((5, 5, 4), 2), ((15, 14, 13), 1), ((8, 8, 8), 3)])]
+    ks = [1, 2, 1, 3]
+    ts = [submit(srv, A, b, k) for (A, b), k in zip(reqs, ks)]
+    for t in ts:
+        gbs.gbs_server_wait(srv, t)
+    for (A, b), k, t in zip(reqs, ks, ts):
+        x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, k)
+        check(orc, A, b, k, x, sts)
+    gbs.gbs_server_destroy(srv)
