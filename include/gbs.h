@@ -337,6 +337,14 @@ int gbs_server_submit(gbs_server srv, int64_t nrows, const int32_t *rowptr, cons
                       const double *vals, int k, const double *b, double rtol, int maxit,
                       uint64_t *ticket);
 
+/* As gbs_server_submit, but the arrays are borrowed instead of copied: the
+ * caller keeps rowptr, colidx, vals and b valid and unchanged until
+ * gbs_server_poll reports the request done (they are read when the request
+ * is admitted).  Saves a host copy of every request. */
+int gbs_server_submit_borrowed(gbs_server srv, int64_t nrows, const int32_t *rowptr,
+                               const int32_t *colidx, const double *vals, int k, const double *b,
+                               double rtol, int maxit, uint64_t *ticket);
+
 /* Advance the engine without blocking for long: admit queued requests,
  * launch or continue device work, retire finished requests.  Returns the
  * number of requests retired by this call in *retired (may be NULL). */
@@ -358,6 +366,13 @@ int gbs_server_fetch(gbs_server srv, uint64_t ticket, double *x, int *iters, dou
  * use (outputs may be NULL). */
 int gbs_server_stats(gbs_server srv, int *queued, int *running, int *finished,
                      size_t *bytes_in_use);
+
+/* Host wall time the engine has spent since creation, in seconds: admitting
+ * requests (matrix upload and set-up), running quanta (launch to
+ * completion), retiring requests (results to the host); and the number of
+ * quanta run (outputs may be NULL). */
+int gbs_server_times(gbs_server srv, double *admit_s, double *quanta_s, double *retire_s,
+                     int64_t *quanta);
 
 #ifdef __cplusplus
 }

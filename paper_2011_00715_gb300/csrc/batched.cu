@@ -5,26 +5,31 @@
 // iterations with FP64 refinement), and the serving loop built on it.
 //
 // Lockstep design.  Every active system advances by one step per global
-// iteration; a step has five phases separated by grid barriers:
+// iteration; a step has three phases separated by grid barriers:
 //   S   SpMV over every warp tile of every active system (all k columns
-//       of a system share one pass over its matrix), per-tile partials
-//   R1  per-(system, column) reductions of the S partials, in a fixed
-//       order over the system's tiles
-//   U   vector updates per tile, per-tile partials
-//   R2  per-(system, column) reductions of the U partials
+//       of a system share one pass over its matrix; INNER tiles are staged
+//       through a per-warp TMA ring), per-unit partials of p.q (or of
+//       r.r and b.b for the refinement residual)
+//   U   vector updates, per-unit partials of r.z and r.r
 //   P   direction update, or the FP64 solution update before a refinement
+// The reductions need no phase of their own: each unit of work stores its
+// partial sums and counts itself in; the warp that completes a chunk of
+// units adds the chunk up, and the warp that completes a system's last
+// chunk adds the chunks up and computes the system's scalars for the next
+// phase.  Both orders are fixed by the system alone.
 // A system is either in an INNER step (one PCG iteration in the inner
 // precision TI on all its unfinished columns) or an OUTER step (FP64
 // residual r = b - A x, stopping test, r / ||r|| becomes the inner
 // right-hand side).  Its columns advance together; a column whose inner
 // solve has converged waits for the others, then all refine together.
-// Because every per-system quantity depends only on the system's own tiles
+// Because every per-system quantity depends only on the system's own data
 // and a fixed reduction order, each column's result is bitwise the same
 // alone or in any batch.
 //
-// Multi-vectors are interleaved (entry (row, column) at row * k + column),
-// so the k operands one nonzero gathers are contiguous.
-//
+// Multi-vectors are interleaved with the column count padded to a power of
+// two, so the operands of one nonzero are one aligned vector load and the
+// update phases stream contiguous, coalesced entries.
+
 // Systems live in slots.  The kernel runs at most `quantum` global
 // iterations over the active slots and returns; all solver state stays in
 // device memory, so the host retires finished systems and admits new ones
@@ -38,6 +43,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <deque>
 #include <unordered_map>
@@ -47,29 +53,38 @@
 
 #define GBS_KMAX 8
 #define GBS_RUNNING (-100)
+#define GBS_RCHUNK 128          // reduction units per chunk
+#define GBS_SUB 256             // vector entries per update sub-block (8 per lane)
+#define GBS_BWARP_BYTES 13312   // bytes of one warp's stage ring
 
 namespace {
 
 enum { MODE_OUTER = 0, MODE_INNER = 1 };
 
-// Read-only description of one system (device, one per slot).
+// Read-only description of one system (device, one per slot).  Its
+// multi-vectors are interleaved with a padded stride kp (entry (row, c) at
+// row * kp + c, kp = k rounded up to 1, 2, 4 or 8; the padding columns
+// hold zeros), so the kp operands one nonzero gathers are one aligned
+// vector load.
 struct BSys {
-    const int32_t *rowptr, *colidx, *tiles;
+    const int32_t *rowptr, *colidx, *tdesc;   // tdesc: {row start, nonzero start} per warp tile
     const double *vals, *dinv;
     const float *vals32, *dinv32;
-    const double *b;    // n * k, interleaved
-    double *x;          // n * k, interleaved (initial guess in, solution out)
-    double *r64;        // n * k
-    void *xi, *ri, *zi, *pi, *qi;   // inner-precision work vectors, n * k
-    int n, k, ntiles, pad0;
+    const double *b;    // n x kp
+    double *x;          // n x kp (initial guess in, solution out)
+    double *r64;        // n x kp
+    void *xi, *ri, *pi, *qi;   // inner-precision work vectors, n x kp
+    int n, k, kp, ntiles;
+    int tg;             // warp tiles per S-phase reduction unit
+    int usub;           // update sub-blocks per U/P-phase unit
+    int maxit, pad0;
     double rtol;
-    int maxit;
-    int pad1;
 };
 
-// Mutable state of one (system, column) pair (device).
+// Mutable state of one (system, column) pair, touched only by the warp that
+// completes the system's reduction of a phase (device).
 struct BCol {
-    double rho, rr, alpha, beta, rn, bnorm, prev, scale, tol_inner;
+    double rho, alpha, beta, rn, bnorm, prev, scale, tol_inner;
     int status;       // GBS_RUNNING until final
     int iters;        // inner iterations, all refinement steps together
     int outer;        // refinement steps
@@ -77,6 +92,18 @@ struct BCol {
     int inner_done;   // the current inner solve has stopped
     int first;        // no residual computed yet
     int pad[2];
+};
+
+// Per-system scalars a phase hands to the next (device; written by the
+// warp that completes a reduction, read by every unit of the next phase).
+struct BPh {
+    double alpha64[GBS_KMAX], beta64[GBS_KMAX];   // inner step scalars (FP64 inner)
+    double scale[GBS_KMAX];                       // 1 / ||r|| of the refinement residual
+    double rn[GBS_KMAX];                          // ||r|| (the solution update x += ||r|| d)
+    float alpha32[GBS_KMAX], beta32[GBS_KMAX];    // inner step scalars (FP32 inner)
+    unsigned run;   // columns still running
+    unsigned upd;   // columns whose inner solve advances
+    int pad[14];
 };
 
 // Mutable per-system state (device).
@@ -89,18 +116,20 @@ struct BSysDyn {
 struct BArgs {
     const BSys *sys;    // by slot
     BCol *col;          // slot * GBS_KMAX + column
+    BPh *ph;            // by slot
     BSysDyn *dyn;       // by slot
     const int *act;     // active slots, nact entries
-    const int *tcum;    // prefix sums of the active slots' tile counts (nact + 1)
-    int nact;
-    int ntile;          // tcum[nact]
-    int nchunk;         // ccum[nact]
-    double *partS;      // active tile * GBS_KMAX * 2
-    double *partU;      // active tile * GBS_KMAX * 2
-    const int *ccum;    // prefix sums of the active slots' reduction chunks (nact + 1)
-    double *cpart;      // chunk * GBS_KMAX * 2: chunk partial sums
-    int *ccount;        // active slot * GBS_KMAX: chunks arrived (zero between phases)
+    const int *scum;    // prefix sums of the active systems' S units (nact + 1)
+    const int *ucum;    // prefix sums of the active systems' U/P units (nact + 1)
+    const int *ccs;     // prefix sums of their S reduction chunks (nact + 1)
+    const int *ccu;     // prefix sums of their U reduction chunks (nact + 1)
+    int nact, nsu, nuu; // active systems; S units; U/P units
+    double *partS, *partU;     // unit * 16: per-unit partial sums
+    double *cpartS, *cpartU;   // chunk * 16: per-chunk sums
+    int *cntS, *cntU;          // per chunk: units arrived (zero between phases)
+    int *sysS, *sysU;          // per active system: chunks arrived
     gbs_grid_barrier *bar;
+    GbsPipeCfg cfg;     // stage geometry covering every active system's tiles
     int quantum;
     int iter0;          // parity of the global iteration count at launch
     double inner_rtol;
@@ -109,428 +138,941 @@ struct BArgs {
     unsigned long long timeout_ns;
 };
 
-// Staging of one warp tile's colidx/vals in shared memory.
-template <typename V>
-struct BTile {
-    int32_t col[GBS_WT_NNZ];
-    V val[GBS_WT_NNZ];
+// Per-warp ring bookkeeping in shared memory.
+struct BWarpQ {
+    uint64_t bar[GBS_MAX_STAGES];
+    int4 desc[GBS_MAX_STAGES];    // {r0, k0, r1, k1}
+    int unit[GBS_MAX_STAGES];     // S unit of the tile in the stage (-1: none)
+    int ai[GBS_MAX_STAGES];       // its system's active index
+    int flags[GBS_MAX_STAGES];    // 1: copied into the stage; 2: first tile of the unit;
+                                  // 4: last tile of the unit; 8: INNER step
 };
 
-__device__ __forceinline__ double bmac(double a, double x, double s) { return fma(a, x, s); }
-__device__ __forceinline__ float bmac(float a, float x, float s) { return fmaf(a, x, s); }
+template <typename TI> __device__ __forceinline__ const TI *bvals(const BSys &S);
+template <> __device__ __forceinline__ const float *bvals<float>(const BSys &S) { return S.vals32; }
+template <> __device__ __forceinline__ const double *bvals<double>(const BSys &S) { return S.vals; }
+template <typename TI> __device__ __forceinline__ const TI *bdinv(const BSys &S);
+template <> __device__ __forceinline__ const float *bdinv<float>(const BSys &S) { return S.dinv32; }
+template <> __device__ __forceinline__ const double *bdinv<double>(const BSys &S) { return S.dinv; }
 
-// y_c = (A v_c)(row) for the rows of one warp tile and all k columns;
-// epi(row, sums[]) runs in the lane that owns the row.
-template <typename V, typename X, typename Epi>
-__device__ __forceinline__ void tile_spmv_k(const BSys &S, const V *vals, const X *v, int lt,
-                                            BTile<V> &wt, Epi &epi)
+__device__ __forceinline__ float ph_alpha(const BPh &P, int c, float) { return P.alpha32[c]; }
+__device__ __forceinline__ double ph_alpha(const BPh &P, int c, double) { return P.alpha64[c]; }
+__device__ __forceinline__ float ph_beta(const BPh &P, int c, float) { return P.beta32[c]; }
+__device__ __forceinline__ double ph_beta(const BPh &P, int c, double) { return P.beta64[c]; }
+__device__ __forceinline__ void ph_set(BPh &P, int c, float al, float be, bool a)
 {
-    const int lane = threadIdx.x & 31;
-    const int k = S.k;
-    const int r0 = __ldg(S.tiles + lt), r1 = __ldg(S.tiles + lt + 1);
-    const int nrows = r1 - r0;
-    int beg = 0, end = 0;
-    if (lane < nrows) {
-        beg = __ldg(S.rowptr + r0 + lane);
-        end = __ldg(S.rowptr + r0 + lane + 1);
-    }
-    const int k0 = __shfl_sync(0xffffffffu, beg, 0);
-    const int k1 = __shfl_sync(0xffffffffu, end, nrows - 1);
-    X sum[GBS_KMAX];
+    if (a) P.alpha32[c] = al;
+    else P.beta32[c] = be;
+}
+__device__ __forceinline__ void ph_set(BPh &P, int c, double al, double be, bool a)
+{
+    if (a) P.alpha64[c] = al;
+    else P.beta64[c] = be;
+}
+
+// Rounded product (kept out of any fused multiply-add).
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+// KP consecutive entries of type T at p, KP * sizeof(T) aligned.
+template <typename T, int KP>
+__device__ __forceinline__ void vload(const T *p, T (&v)[KP])
+{
+    constexpr int B = KP * (int)sizeof(T);
+    if constexpr (B >= 16) {
+        constexpr int W = 16 / (int)sizeof(T);
 #pragma unroll
-    for (int c = 0; c < GBS_KMAX; ++c) sum[c] = X(0);
-    if (k1 - k0 <= GBS_WT_NNZ) {
-        for (int e = k0 + lane; e < k1; e += 32) {
-            wt.col[e - k0] = __ldg(S.colidx + e);
-            wt.val[e - k0] = __ldg(vals + e);
-        }
-        __syncwarp();
-        if (lane < nrows) {
-            for (int e = beg; e < end; ++e) {
-                const X a = (X)wt.val[e - k0];
-                const X *vp = v + (size_t)wt.col[e - k0] * k;
+        for (int i = 0; i < B / 16; ++i) {
+            const float4 w = reinterpret_cast<const float4 *>(p)[i];
+            T t[W];
+            memcpy(t, &w, 16);
 #pragma unroll
-                for (int c = 0; c < GBS_KMAX; ++c)
-                    if (c < k) sum[c] = bmac(a, vp[c], sum[c]);
-            }
-            epi(r0 + lane, sum);
+            for (int l = 0; l < W; ++l) v[i * W + l] = t[l];
         }
-        __syncwarp();
+    } else if constexpr (B == 8) {
+        const float2 w = *reinterpret_cast<const float2 *>(p);
+        memcpy(v, &w, 8);
     } else {
-        // one long row: strided partial sums per column, fixed shuffle tree
-        for (int e = k0 + lane; e < k1; e += 32) {
-            const X a = (X)__ldg(vals + e);
-            const X *vp = v + (size_t)__ldg(S.colidx + e) * k;
-#pragma unroll
-            for (int c = 0; c < GBS_KMAX; ++c)
-                if (c < k) sum[c] = bmac(a, vp[c], sum[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < GBS_KMAX; ++c)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], off);
-        if (lane == 0) epi(r0, sum);
-        __syncwarp();
+        v[0] = *p;
     }
 }
 
-// Warp-wide fixed-tree sum of per-lane values; lane 0 stores them.
-template <typename T>
-__device__ __forceinline__ void warp_store_partials(T (&a)[GBS_KMAX][2], int k, double *dst)
+template <typename T, int KP>
+__device__ __forceinline__ void vstore(T *p, const T (&v)[KP])
+{
+    constexpr int B = KP * (int)sizeof(T);
+    if constexpr (B >= 16) {
+        constexpr int W = 16 / (int)sizeof(T);
+#pragma unroll
+        for (int i = 0; i < B / 16; ++i) {
+            T t[W];
+#pragma unroll
+            for (int l = 0; l < W; ++l) t[l] = v[i * W + l];
+            float4 w;
+            memcpy(&w, t, 16);
+            reinterpret_cast<float4 *>(p)[i] = w;
+        }
+    } else if constexpr (B == 8) {
+        float2 w;
+        memcpy(&w, v, 8);
+        *reinterpret_cast<float2 *>(p) = w;
+    } else {
+        *p = v[0];
+    }
+}
+
+// ---------------------------------------------------------------------
+// S phase: one warp tile
+// ---------------------------------------------------------------------
+
+// INNER step, tile staged in shared memory: q = A p on its rows, lane l
+// owning row r0 + l (left to right over the row, all KP columns at once);
+// acc[c][0] += p_row,c q_row,c (p_row from the diagonal entry's gather).
+template <typename TI, int KP>
+__device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char *st,
+                                             const GbsPipeCfg &cfg, int4 d, TI (&acc)[KP][2])
+{
+    constexpr int E = 16 / (int)sizeof(TI);
+    const int lane = threadIdx.x & 31;
+    const int r0 = d.x, k0 = d.y, r1 = d.z;
+    if (lane >= r1 - r0) return;
+    const TI *sval = reinterpret_cast<const TI *>(st);
+    const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
+    const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
+    const int row = r0 + lane;
+    const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+    const int beg = srp[row - rb], end = srp[row - rb + 1];
+    const TI *p = static_cast<const TI *>(S.pi);
+    TI sum[KP], pd[KP];
+#pragma unroll
+    for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
+#pragma unroll 4
+    for (int e = beg; e < end; ++e) {
+        const int c = scol[e - cb];
+        const TI a = sval[e - vb];
+        TI v[KP];
+        vload<TI, KP>(p + (size_t)c * KP, v);
+        const bool dg = c == row;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            pd[i] = dg ? v[i] : pd[i];
+            sum[i] = fma(a, v[i], sum[i]);
+        }
+    }
+    vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
+}
+
+// INNER step, a tile holding one row longer than GBS_WT_NNZ (read directly;
+// lane-strided sums, fixed shuffle tree; lane 0 accumulates).
+template <typename TI, int KP>
+__device__ __forceinline__ void s_long_inner(const BSys &S, int4 d, TI (&acc)[KP][2], uint64_t ps)
 {
     const int lane = threadIdx.x & 31;
+    const int row = d.x, k0 = d.y, k1 = d.w;
+    const TI *vals = bvals<TI>(S);
+    const TI *p = static_cast<const TI *>(S.pi);
+    TI sum[KP], pd[KP];
+#pragma unroll
+    for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
+    for (int e = k0 + lane; e < k1; e += 32) {
+        const int c = gbs_ld_stream(S.colidx + e, ps);
+        const TI a = gbs_ld_stream(vals + e, ps);
+        TI v[KP];
+        vload<TI, KP>(p + (size_t)c * KP, v);
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            if (c == row) pd[i] = v[i];
+            sum[i] = fma(a, v[i], sum[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < KP; ++i)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
+            pd[i] += __shfl_xor_sync(0xffffffffu, pd[i], off);
+        }
+    if (lane == 0) {
+        vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
+#pragma unroll
+        for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
+    }
+}
+
+// OUTER step (FP64, read directly): r64 = b - A x on the tile's rows;
+// acc[c][0] += r.r, acc[c][1] += b.b.
+template <int KP>
+__device__ __forceinline__ void s_tile_outer(const BSys &S, int4 d, double (&acc)[KP][2], uint64_t ps)
+{
+    const int lane = threadIdx.x & 31;
+    const int r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
+    double sum[KP];
+#pragma unroll
+    for (int i = 0; i < KP; ++i) sum[i] = 0.0;
+    int row = r0 + lane;
+    bool own = false;
+    if (k1 - k0 > GBS_WT_NNZ) {
+        for (int e = k0 + lane; e < k1; e += 32) {
+            const int c = gbs_ld_stream(S.colidx + e, ps);
+            const double a = gbs_ld_stream(S.vals + e, ps);
+            double v[KP];
+            vload<double, KP>(S.x + (size_t)c * KP, v);
+#pragma unroll
+            for (int i = 0; i < KP; ++i) sum[i] = fma(a, v[i], sum[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
+        row = r0;
+        own = lane == 0;
+    } else if (lane < r1 - r0) {
+        const int beg = __ldg(S.rowptr + row), end = __ldg(S.rowptr + row + 1);
+#pragma unroll 4
+        for (int e = beg; e < end; ++e) {
+            const int c = gbs_ld_stream(S.colidx + e, ps);
+            const double a = gbs_ld_stream(S.vals + e, ps);
+            double v[KP];
+            vload<double, KP>(S.x + (size_t)c * KP, v);
+#pragma unroll
+            for (int i = 0; i < KP; ++i) sum[i] = fma(a, v[i], sum[i]);
+        }
+        own = true;
+    }
+    if (own) {
+        double bv[KP], rv[KP];
+        vload<double, KP>(S.b + (size_t)row * KP, bv);
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            rv[i] = bv[i] - sum[i];
+            acc[i][0] += rv[i] * rv[i];
+            acc[i][1] += bv[i] * bv[i];
+        }
+        vstore<double, KP>(S.r64 + (size_t)row * KP, rv);
+    }
+}
+
+// ---------------------------------------------------------------------
+// Reductions: per-unit partials, summed by the warp that completes them
+// ---------------------------------------------------------------------
+
+// Fixed-tree warp sums of entries [c][j], c < k, j < NJ; every lane gets them.
+template <typename T, int NJ>
+__device__ __forceinline__ void warp_tree(T (&acc)[GBS_KMAX][2], int k)
+{
 #pragma unroll
     for (int c = 0; c < GBS_KMAX; ++c) {
         if (c >= k) break;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            T t = a[c][j];
+        for (int j = 0; j < NJ; ++j)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-            if (lane == 0) dst[c * 2 + j] = (double)t;
+            for (int off = 16; off > 0; off >>= 1)
+                acc[c][j] += __shfl_xor_sync(0xffffffffu, acc[c][j], off);
+    }
+}
+
+// Sum entries [c][j] of the 16-value records [ua, ub) of src in type T, in
+// a fixed order (lane l: records ua + l, ua + l + 32, ...; then a fixed
+// shuffle tree); every lane gets the totals.
+template <typename T, int NJ>
+__device__ __forceinline__ void sum_records(const double *src, int ua, int ub, int k,
+                                            T (&tot)[GBS_KMAX][2])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < GBS_KMAX; ++c) tot[c][0] = tot[c][1] = T(0);
+    for (int u = ua + lane; u < ub; u += 32) {
+        const double2 *s = reinterpret_cast<const double2 *>(src + (size_t)u * 2 * GBS_KMAX);
+#pragma unroll
+        for (int c = 0; c < GBS_KMAX; ++c) {
+            if (c >= k) break;
+            const double2 w = __ldcg(s + c);
+            tot[c][0] += (T)w.x;
+            if (NJ > 1) tot[c][1] += (T)w.y;
         }
     }
+    warp_tree<T, NJ>(tot, k);
 }
 
-// Sum entry j of column c over active tiles [ga, gb) -- one system's tiles
-// -- in a fixed order (lane l: tiles ga + l, ga + l + 32, ... in type T;
-// then a fixed shuffle tree).
-template <typename T>
-__device__ __forceinline__ T sys_sum(const double *part, int ga, int gb, int c, int j)
+// Unit u of one system (units [u0, u0 + nu), chunks from c0) has stored its
+// partials.  The warp that completes a chunk of GBS_RCHUNK units adds the
+// chunk up; the warp that completes the system's last chunk adds the chunk
+// sums up and returns true with the totals in every lane.  Both orders
+// depend on the system alone, so the totals are the same in any batch.
+template <typename T, int NJ>
+__device__ __forceinline__ bool reduce_last(const double *part, double *cpart, int *ccnt,
+                                            int *scnt, int u, int u0, int nu, int c0, int k,
+                                            T (&tot)[GBS_KMAX][2])
 {
     const int lane = threadIdx.x & 31;
-    T t = T(0);
-    for (int g = ga + lane; g < gb; g += 32)
-        t += (T)__ldcg(part + ((size_t)g * GBS_KMAX + c) * 2 + j);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    return t;
-}
-
-__device__ __forceinline__ bool col_running(const BCol &c) { return c.status == GBS_RUNNING; }
-
-// Tiles per reduction chunk: a system's per-tile partials are summed chunk
-// by chunk (one warp each), then the chunk sums are added by the warp that
-// completes the last chunk.  Both levels use a fixed order that depends
-// only on the system, so results stay independent of the batch.
-#define GBS_RCHUNK 128
-
-// Two-level reduction of entries 0 and 1 of column c over one system's
-// tiles, for the chunk [ga, gb) handled by this warp (chunk gc of the
-// active chunk range [ca, cb), system active index ai).  Returns true in
-// the warp whose chunk arrived last; that warp gets the totals in out[].
-template <typename T>
-__device__ __forceinline__ bool chunk_reduce(const BArgs &a, const double *part, int ga, int gb,
-                                             int gc, int ca, int cb, int ai, int c, T (&out)[2])
-{
-    const int lane = threadIdx.x & 31;
-    T s0 = sys_sum<T>(part, ga, gb, c, 0);
-    T s1 = sys_sum<T>(part, ga, gb, c, 1);
+    const int ch = (u - u0) / GBS_RCHUNK;
+    const int ua = u0 + ch * GBS_RCHUNK, ub = min(ua + GBS_RCHUNK, u0 + nu);
+    const int nch = (nu + GBS_RCHUNK - 1) / GBS_RCHUNK;
     int last = 0;
     if (lane == 0) {
-        a.cpart[((size_t)gc * GBS_KMAX + c) * 2 + 0] = (double)s0;
-        a.cpart[((size_t)gc * GBS_KMAX + c) * 2 + 1] = (double)s1;
         __threadfence();
-        last = atomicAdd(&a.ccount[ai * GBS_KMAX + c], 1) == cb - ca - 1;
+        last = atomicAdd(&ccnt[c0 + ch], 1) == ub - ua - 1;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return false;
+    if (!__shfl_sync(0xffffffffu, last, 0)) return false;
     __threadfence();
-    out[0] = sys_sum<T>(a.cpart, ca, cb, c, 0);
-    out[1] = sys_sum<T>(a.cpart, ca, cb, c, 1);
-    if (lane == 0) a.ccount[ai * GBS_KMAX + c] = 0;
+    sum_records<T, NJ>(part, ua, ub, k, tot);
+    if (lane == 0) {
+        double *dst = cpart + (size_t)(c0 + ch) * 2 * GBS_KMAX;
+#pragma unroll
+        for (int c = 0; c < GBS_KMAX; ++c) {
+            if (c >= k) break;
+            dst[2 * c] = (double)tot[c][0];
+            dst[2 * c + 1] = NJ > 1 ? (double)tot[c][1] : 0.0;
+        }
+        ccnt[c0 + ch] = 0;
+        __threadfence();
+        last = atomicAdd(scnt, 1) == nch - 1;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+    __threadfence();
+    sum_records<T, NJ>(cpart, c0, c0 + nch, k, tot);
+    if (lane == 0) *scnt = 0;
     return true;
 }
 
-// Active index owning active tile g (tcum is increasing, tcum[0] = 0).
-__device__ __forceinline__ int owner_of(const int *tcum, int nact, int g)
+// Lane 0 stores the warp-summed entries [c][j] as the unit's record.
+template <typename T, int NJ>
+__device__ __forceinline__ void store_record(double *part, int u, int k, const T (&acc)[GBS_KMAX][2])
 {
-    int lo = 0, hi = nact - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(tcum + mid) <= g) lo = mid;
-        else hi = mid - 1;
+    if ((threadIdx.x & 31) != 0) return;
+    double *dst = part + (size_t)u * 2 * GBS_KMAX;
+#pragma unroll
+    for (int c = 0; c < GBS_KMAX; ++c) {
+        if (c >= k) break;
+        dst[2 * c] = (double)acc[c][0];
+        dst[2 * c + 1] = NJ > 1 ? (double)acc[c][1] : 0.0;
     }
-    return lo;
 }
 
-template <typename TI>
-__global__ void __launch_bounds__(GBS_PBLOCK) k_batched(BArgs a)
+// The value of column `lane` (lanes < k) out of a register array.
+template <typename T>
+__device__ __forceinline__ T mine(const T (&tot)[GBS_KMAX][2], int j)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    T v = T(0);
+#pragma unroll
+    for (int c = 0; c < GBS_KMAX; ++c) v = c == lane ? tot[c][j] : v;
+    return v;
+}
+
+// ---------------------------------------------------------------------
+// Scalar steps, run by the warp that completes a system's reduction
+// (lane c handles column c)
+// ---------------------------------------------------------------------
+
+// OUTER residual r = b - A x is complete: stopping test, refinement scale.
+__device__ __noinline__ void s_finish_outer(const BArgs &a, int slot, double rr, double bb)
+{
+    const int lane = threadIdx.x & 31;
+    const BSys &S = a.sys[slot];
+    BPh &P = a.ph[slot];
+    bool run = false;
+    if (lane < S.k) {
+        BCol &C = a.col[slot * GBS_KMAX + lane];
+        if (C.status == GBS_RUNNING) {
+            const double rn = sqrt(rr);
+            if (C.first) C.bnorm = sqrt(bb);
+            C.first = 0;
+            C.rn = rn;
+            if (isnan(rn)) C.status = GBS_ERR_NAN;
+            else if (rn <= S.rtol * C.bnorm) C.status = GBS_OK;
+            else if (rn > 0.5 * C.prev) C.status = GBS_ERR_STAGNATION;
+            else if (C.outer >= a.outer_maxit || C.iters >= S.maxit) C.status = GBS_DIVERGED_ITS;
+            else {
+                C.prev = rn;
+                C.scale = 1.0 / rn;
+                C.outer += 1;
+                // FP64 inner solves aim below rtol ||b|| at once
+                C.tol_inner = a.fp64 ? 0.5 * S.rtol * C.bnorm / rn : a.inner_rtol;
+                P.scale[lane] = C.scale;
+                P.rn[lane] = rn;
+                run = true;
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, run);
+    if (lane == 0) {
+        P.run = m;
+        P.upd = m;
+        if (!m) a.dyn[slot].finished = 1;
+    }
+}
+
+// INNER p.q is complete: step length alpha, or breakdown.
+template <typename TI>
+__device__ __noinline__ void s_finish_inner(const BArgs &a, int slot, TI pq)
+{
+    const int lane = threadIdx.x & 31;
+    const BSys &S = a.sys[slot];
+    BPh &P = a.ph[slot];
+    const unsigned upd = P.upd;
+    bool bad = false;
+    if (lane < S.k && ((upd >> lane) & 1u)) {
+        BCol &C = a.col[slot * GBS_KMAX + lane];
+        if (isnan(pq)) C.status = GBS_ERR_NAN;
+        else if (pq <= TI(0)) C.status = GBS_ERR_INDEFINITE;
+        else {
+            const TI al = (TI)C.rho / pq;
+            C.alpha = (double)al;
+            ph_set(P, lane, al, al, true);
+        }
+        bad = C.status != GBS_RUNNING;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (lane == 0 && m) {
+        P.upd = upd & ~m;
+        P.run &= ~m;
+        if (!P.run) a.dyn[slot].finished = 1;
+    }
+}
+
+// OUTER start of an inner solve is complete: rho = r.z, inner tolerance.
+template <typename TI>
+__device__ __noinline__ void u_finish_outer(const BArgs &a, int slot, int nxt, TI rho, TI rr)
+{
+    const int lane = threadIdx.x & 31;
+    const BSys &S = a.sys[slot];
+    BPh &P = a.ph[slot];
+    if (lane < S.k && ((P.run >> lane) & 1u)) {
+        BCol &C = a.col[slot * GBS_KMAX + lane];
+        C.rho = (double)rho;
+        C.tol_inner = C.tol_inner * (double)sqrt(rr);
+        C.kin = 0;
+        C.inner_done = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        P.upd = P.run;
+        a.dyn[slot].mode[nxt] = MODE_INNER;
+    }
+}
+
+// INNER r.z and r.r are complete: beta, inner stopping test, next step.
+template <typename TI>
+__device__ __noinline__ void u_finish_inner(const BArgs &a, int slot, int nxt, TI rho_new, TI rr)
+{
+    const int lane = threadIdx.x & 31;
+    const BSys &S = a.sys[slot];
+    BPh &P = a.ph[slot];
+    const unsigned upd = P.upd;
+    bool fail = false, waiting = false;
+    if (lane < S.k && ((upd >> lane) & 1u)) {
+        BCol &C = a.col[slot * GBS_KMAX + lane];
+        C.kin += 1;
+        C.iters += 1;
+        if (rho_new < TI(0)) {
+            C.status = GBS_ERR_INDEFINITE;
+        } else if (isnan(rr)) {
+            C.status = GBS_ERR_NAN;
+        } else {
+            const TI be = rho_new / (TI)C.rho;
+            C.beta = (double)be;
+            C.rho = (double)rho_new;
+            ph_set(P, lane, be, be, false);
+            if ((double)sqrt(rr) <= C.tol_inner || C.iters >= S.maxit) C.inner_done = 1;
+        }
+        fail = C.status != GBS_RUNNING;
+        waiting = !fail && !C.inner_done;
+    }
+    const unsigned mf = __ballot_sync(0xffffffffu, fail);
+    const unsigned mw = __ballot_sync(0xffffffffu, waiting);
+    if (lane == 0) {
+        const unsigned run = P.run & ~mf;
+        P.run = run;
+        P.upd = mw;
+        // refinement once every running column's inner solve has stopped
+        if (!run) a.dyn[slot].finished = 1;
+        else a.dyn[slot].mode[nxt] = mw ? MODE_INNER : MODE_OUTER;
+    }
+}
+
+// ---------------------------------------------------------------------
+// S phase: the warp's stage ring over the CTA's S units
+// ---------------------------------------------------------------------
+
+// Run the S unit whose first tile sits in stage m % NS (issued and
+// checked): consume its tiles, which follow one another in the warp's ring,
+// then store the unit's partials and take part in the system's reduction.
+// Returns false if a copy did not complete in time (m then names the stage
+// that failed).
+template <typename TI, int KP, bool INNER, typename Issue>
+__device__ __forceinline__ bool s_unit(const BArgs &a, BWarpQ &q, unsigned char *wsm,
+                                       const GbsPipeCfg &cfg, int &m, uint32_t &parity, uint64_t ps,
+                                       Issue &issue)
+{
+    using T = typename std::conditional<INNER, TI, double>::type;
+    constexpr int NJ = INNER ? 1 : 2;
+    const int lane = threadIdx.x & 31;
+    const int NS = cfg.stages;
+    const int unit = q.unit[m % NS], ai = q.ai[m % NS];
+    const int slot = __ldg(a.act + ai);
+    const BSys &S = a.sys[slot];
+    T acc[KP][2];
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[i][0] = acc[i][1] = T(0);
+    for (;;) {
+        const int j = m % NS;
+        const int4 d = q.desc[j];
+        const int flags = q.flags[j];
+        if (flags & 1) {
+            if (!gbs_mbar_wait(&q.bar[j], (parity >> j) & 1u, a.timeout_ns)) return false;
+            parity ^= 1u << j;
+        }
+        if constexpr (INNER) {
+            if (flags & 1) s_tile_inner<TI, KP>(S, wsm + (size_t)j * cfg.sbytes, cfg, d, acc);
+            else s_long_inner<TI, KP>(S, d, acc, ps);
+        } else {
+            s_tile_outer<KP>(S, d, acc, ps);
+        }
+        __syncwarp();
+        ++m;
+        if (flags & 4) break;   // the unit's last tile
+        if (lane == 0) issue((m + NS - 1) % NS);
+        __syncwarp();
+    }
+    const int k = S.k;
+#pragma unroll
+    for (int i = 0; i < KP; ++i)
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                acc[i][jj] += __shfl_xor_sync(0xffffffffu, acc[i][jj], off);
+    if (lane == 0) {
+        double *dst = a.partS + (size_t)unit * 2 * GBS_KMAX;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            if (i >= k) break;
+            dst[2 * i] = (double)acc[i][0];
+            dst[2 * i + 1] = NJ > 1 ? (double)acc[i][1] : 0.0;
+        }
+    }
+    const int u0 = __ldg(a.scum + ai), nu = __ldg(a.scum + ai + 1) - u0;
+    T tot[GBS_KMAX][2];
+    if (reduce_last<T, NJ>(a.partS, a.cpartS, a.cntS, a.sysS + ai, unit, u0, nu, __ldg(a.ccs + ai), k,
+                           tot)) {
+        if constexpr (INNER) s_finish_inner<TI>(a, slot, mine(tot, 0));
+        else s_finish_outer(a, slot, mine(tot, 0), mine(tot, 1));
+    }
+    return true;
+}
+
+// A unit is `tg` consecutive warp tiles of one system.  Lane 0 of each warp
+// claims the next unit of the CTA's range from *s_next, keeps the next tile
+// and its descriptor one step ahead, and copies the CSR slice of each INNER
+// tile into the next free stage of the warp's ring (cfg.stages stages,
+// cfg.stages - 1 in flight).  OUTER tiles (FP64, once per refinement step)
+// and single rows longer than GBS_WT_NNZ are read directly.  After a unit's
+// last tile the warp stores the unit's partials and takes part in the
+// system's reduction.  Returns false if a copy did not complete within the
+// time limit (the copies in flight are then waited for, again with a limit).
+template <typename TI>
+__device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *s_next, unsigned char *wsm,
+                        BWarpQ &q, uint32_t &parity, uint64_t ps)
+{
+    constexpr int E = 16 / (int)sizeof(TI);
+    const int lane = threadIdx.x & 31;
+    const GbsPipeCfg cfg = a.cfg;
+    const int NS = cfg.stages;
+    // lane 0: the pending tile (next to issue) with its descriptor
+    int p_unit = -1, p_ai = 0, p_slot = 0, p_lt = 0, p_le = 0, p_mode = 0, p_first = 0;
+    int2 d_lo = make_int2(0, 0), d_hi = make_int2(0, 0);
+    int cai = 0;
+    if (lane == 0 && gb < ge) {
+        int lo = 0, hi = a.nact - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.scum + mid) <= gb) lo = mid;
+            else hi = mid - 1;
+        }
+        cai = lo;
+    }
+    auto load_desc = [&]() {
+        const int2 *td = reinterpret_cast<const int2 *>(a.sys[p_slot].tdesc);
+        d_lo = __ldg(td + p_lt);
+        d_hi = __ldg(td + p_lt + 1);
+    };
+    auto claim = [&]() {
+        for (;;) {
+            const int u = gb + atomicAdd(s_next, 1);
+            if (u >= ge) {
+                p_unit = -1;
+                return;
+            }
+            while (__ldg(a.scum + cai + 1) <= u) ++cai;
+            const int slot = __ldg(a.act + cai);
+            const BSysDyn &D = a.dyn[slot];
+            if (D.finished) {   // skip the rest of a finished system
+                atomicMax(s_next, __ldg(a.scum + cai + 1) - gb);
+                continue;
+            }
+            const BSys &S = a.sys[slot];
+            p_unit = u;
+            p_ai = cai;
+            p_slot = slot;
+            p_mode = D.mode[cur];
+            p_lt = (u - __ldg(a.scum + cai)) * S.tg;
+            p_le = min(p_lt + S.tg, S.ntiles);
+            p_first = 1;
+            load_desc();
+            return;
+        }
+    };
+    auto issue = [&](int j) {
+        if (p_unit < 0) {
+            q.unit[j] = -1;
+            return;
+        }
+        const int r0 = d_lo.x, k0 = d_lo.y, r1 = d_hi.x, k1 = d_hi.y;
+        const int staged = p_mode == MODE_INNER && k1 - k0 <= GBS_WT_NNZ;
+        const BSys &S = a.sys[p_slot];
+        q.unit[j] = p_unit;
+        q.ai[j] = p_ai;
+        q.desc[j] = make_int4(r0, k0, r1, k1);
+        q.flags[j] = staged | (p_first << 1) | ((p_lt + 1 == p_le) << 2) |
+                     ((p_mode == MODE_INNER) << 3);
+        const TI *vals = bvals<TI>(S);
+        const int32_t *colidx = S.colidx, *rowptr = S.rowptr;
+        // the next tile: of this unit, or of the next claimed one
+        if (p_lt + 1 < p_le) {
+            ++p_lt;
+            p_first = 0;
+            load_desc();
+        } else {
+            claim();
+        }
+        if (!staged) return;
+        const int vb = k0 & ~(E - 1), ve = (k1 + E - 1) & ~(E - 1);
+        const int cb = k0 & ~3, ce = (k1 + 3) & ~3;
+        const int rb = r0 & ~3, re = (r1 + 4) & ~3;
+        const uint32_t bv = (uint32_t)(sizeof(TI) * (ve - vb)), bc = 4u * (uint32_t)(ce - cb),
+                       br = 4u * (uint32_t)(re - rb);
+        unsigned char *st = wsm + (size_t)j * cfg.sbytes;
+        gbs_mbar_expect_tx(&q.bar[j], bv + bc + br);
+        gbs_bulk_g2s(st + cfg.rpoff, rowptr + rb, br, &q.bar[j], ps);
+        if (bv) gbs_bulk_g2s(st, vals + vb, bv, &q.bar[j], ps);
+        if (bc) gbs_bulk_g2s(st + cfg.coloff, colidx + cb, bc, &q.bar[j], ps);
+    };
+    if (lane == 0) {
+        claim();
+        for (int j = 0; j < NS - 1; ++j) issue(j);
+    }
+    __syncwarp();
+    bool ok = true;
+    int m = 0;
+    for (;;) {
+        const int j = m % NS;
+        if (lane == 0) issue((m + NS - 1) % NS);   // that stage was consumed at m - 1
+        __syncwarp();
+        if (q.unit[j] < 0) break;   // claims are monotonic: no later stage holds a tile either
+        const int kp = a.sys[__ldg(a.act + q.ai[j])].kp;
+        if (q.flags[j] & 8) {
+            switch (kp) {
+            case 1: ok = s_unit<TI, 1, true>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            case 2: ok = s_unit<TI, 2, true>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            case 4: ok = s_unit<TI, 4, true>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            default: ok = s_unit<TI, 8, true>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            }
+        } else {
+            switch (kp) {
+            case 1: ok = s_unit<TI, 1, false>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            case 2: ok = s_unit<TI, 2, false>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            case 4: ok = s_unit<TI, 4, false>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            default: ok = s_unit<TI, 8, false>(a, q, wsm, cfg, m, parity, ps, issue); break;
+            }
+        }
+        if (!ok) break;
+    }
+    if (!ok) {
+        // wait (with a limit) for every copy still in flight, oldest first
+        for (int dd = 0; dd < NS; ++dd) {
+            const int jj = (m + dd) % NS;
+            if (q.unit[jj] >= 0 && (q.flags[jj] & 1) &&
+                gbs_mbar_wait(&q.bar[jj], (parity >> jj) & 1u, a.timeout_ns))
+                parity ^= 1u << jj;
+        }
+    }
+    __syncwarp();
+    return ok;
+}
+
+// ---------------------------------------------------------------------
+// U and P phases: flat passes over the interleaved vectors
+// ---------------------------------------------------------------------
+
+// A U/P unit is `usub` sub-blocks of GBS_SUB consecutive entries of the
+// n x kp vectors; lane l handles entries l, l + 32, ... of each sub-block,
+// all of one column c = l mod kp.
+
+// U: x += alpha p, r -= alpha q, z = D^-1 r (INNER) or the start of an
+// inner solve on r / ||r|| (OUTER); partials r.z and r.r per column.
+// A lane takes its entries four at a time (offsets 0, 32, 64, 96 from
+// the first); the row of the entry at offset 32 jj has its D^-1 at
+// offset 32 jj / kp.
+template <typename TI>
+__device__ __forceinline__ void u_unit(const BArgs &a, int cur, int nxt, int slot, int ai, int u)
+{
+    const BSys &S = a.sys[slot];
+    const BPh &P = a.ph[slot];
+    const int KP = S.kp, lk = __ffs(KP) - 1, R = 32 >> lk;
+    const int lane = threadIdx.x & 31, c = lane & (KP - 1), k = S.k;
+    const int u0 = __ldg(a.ucum + ai);
+    const int64_t nk = (int64_t)S.n * KP;
+    const int64_t base = (int64_t)(u - u0) * S.usub * GBS_SUB + lane;
+    const int mode = a.dyn[slot].mode[cur];
+    TI s0 = TI(0), s1 = TI(0);
+    if (mode == MODE_OUTER) {
+        if (c < k && ((P.run >> c) & 1u)) {
+            const double sc = P.scale[c];
+            for (int sb = 0; sb < 2 * S.usub; ++sb) {
+                const int64_t e0 = base + (int64_t)sb * (GBS_SUB / 2);
+                const int64_t rem = nk - e0;
+                if (rem <= 0) break;
+                const double *rp = S.r64 + e0;
+                const TI *dp = bdinv<TI>(S) + (e0 >> lk);
+                TI *xp = static_cast<TI *>(S.xi) + e0, *r_ = static_cast<TI *>(S.ri) + e0,
+                   *pp = static_cast<TI *>(S.pi) + e0;
+                double rv[4];
+                TI dg[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (32 * jj < rem) {
+                        rv[jj] = rp[32 * jj];
+                        dg[jj] = dp[R * jj];
+                    }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (32 * jj < rem) {
+                        const TI bi = (TI)(rv[jj] * sc);
+                        const TI zi = rmul(dg[jj], bi);
+                        xp[32 * jj] = TI(0);
+                        r_[32 * jj] = bi;
+                        pp[32 * jj] = zi;
+                        s0 += bi * zi;
+                        s1 += bi * bi;
+                    }
+            }
+        }
+    } else {
+        if (c < k && ((P.upd >> c) & 1u)) {
+            const TI al = ph_alpha(P, c, TI(0));
+            for (int sb = 0; sb < 2 * S.usub; ++sb) {
+                const int64_t e0 = base + (int64_t)sb * (GBS_SUB / 2);
+                const int64_t rem = nk - e0;
+                if (rem <= 0) break;
+                const TI *dp = bdinv<TI>(S) + (e0 >> lk);
+                TI *xp = static_cast<TI *>(S.xi) + e0, *r_ = static_cast<TI *>(S.ri) + e0;
+                const TI *pp = static_cast<const TI *>(S.pi) + e0, *qp = static_cast<const TI *>(S.qi) + e0;
+                TI xv[4], pv[4], rv[4], qv[4], dg[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (32 * jj < rem) {
+                        xv[jj] = xp[32 * jj];
+                        pv[jj] = pp[32 * jj];
+                        rv[jj] = r_[32 * jj];
+                        qv[jj] = qp[32 * jj];
+                        dg[jj] = dp[R * jj];
+                    }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (32 * jj < rem) {
+                        xp[32 * jj] = xv[jj] + al * pv[jj];
+                        const TI rn = rv[jj] - al * qv[jj];
+                        const TI zn = rmul(dg[jj], rn);
+                        r_[32 * jj] = rn;
+                        s0 += rn * zn;
+                        s1 += rn * rn;
+                    }
+            }
+        }
+    }
+    // fixed tree over the lanes of one column; lane c then holds column c
+    for (int off = 16; off >= KP; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    }
+    // lane 0 gathers the column sums and stores the unit's record
+    for (int cc = 0; cc < KP; ++cc) {
+        const TI v0 = __shfl_sync(0xffffffffu, s0, cc), v1 = __shfl_sync(0xffffffffu, s1, cc);
+        if (lane == 0 && cc < k) {
+            double *dst = a.partU + (size_t)u * 2 * GBS_KMAX;
+            dst[2 * cc] = (double)v0;
+            dst[2 * cc + 1] = (double)v1;
+        }
+    }
+    TI tot[GBS_KMAX][2];
+    if (reduce_last<TI, 2>(a.partU, a.cpartU, a.cntU, a.sysU + ai, u, u0, __ldg(a.ucum + ai + 1) - u0,
+                           __ldg(a.ccu + ai), k, tot)) {
+        const TI t0 = mine(tot, 0), t1 = mine(tot, 1);
+        if (mode == MODE_OUTER) u_finish_outer<TI>(a, slot, nxt, t0, t1);
+        else u_finish_inner<TI>(a, slot, nxt, t0, t1);
+    }
+}
+
+// P: p = D^-1 r + beta p, or x += ||r|| d once the inner solve has stopped.
+template <typename TI>
+__device__ __forceinline__ void p_unit(const BArgs &a, int nxt, int slot, int ai, int u)
+{
+    const BSys &S = a.sys[slot];
+    const BPh &P = a.ph[slot];
+    const int KP = S.kp, lk = __ffs(KP) - 1, R = 32 >> lk;
+    const int lane = threadIdx.x & 31, c = lane & (KP - 1), k = S.k;
+    const int64_t nk = (int64_t)S.n * KP;
+    const int64_t base = (int64_t)(u - __ldg(a.ucum + ai)) * S.usub * GBS_SUB + lane;
+    if (a.dyn[slot].mode[nxt] == MODE_OUTER) {
+        if (!(c < k && ((P.run >> c) & 1u))) return;
+        const double rn = P.rn[c];
+        for (int sb = 0; sb < 2 * S.usub; ++sb) {
+            const int64_t e0 = base + (int64_t)sb * (GBS_SUB / 2);
+            const int64_t rem = nk - e0;
+            if (rem <= 0) break;
+            const TI *dp_ = static_cast<const TI *>(S.xi) + e0;
+            double *xp = S.x + e0;
+            TI dv[4];
+            double xv[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (32 * jj < rem) {
+                    dv[jj] = dp_[32 * jj];
+                    xv[jj] = xp[32 * jj];
+                }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (32 * jj < rem) xp[32 * jj] = fma(rn, (double)dv[jj], xv[jj]);
+        }
+    } else {
+        if (!(c < k && ((P.upd >> c) & 1u))) return;
+        const TI be = ph_beta(P, c, TI(0));
+        for (int sb = 0; sb < 2 * S.usub; ++sb) {
+            const int64_t e0 = base + (int64_t)sb * (GBS_SUB / 2);
+            const int64_t rem = nk - e0;
+            if (rem <= 0) break;
+            const TI *dp = bdinv<TI>(S) + (e0 >> lk);
+            const TI *r_ = static_cast<const TI *>(S.ri) + e0;
+            TI *pp = static_cast<TI *>(S.pi) + e0;
+            TI rv[4], pv[4], dg[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (32 * jj < rem) {
+                    rv[jj] = r_[32 * jj];
+                    pv[jj] = pp[32 * jj];
+                    dg[jj] = dp[R * jj];
+                }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (32 * jj < rem) pp[32 * jj] = fma(be, pv[jj], rmul(dg[jj], rv[jj]));
+        }
+    }
+}
+
+// The warp's units of a U or P pass over the CTA's range [gb, ge).
+template <typename TI, bool U>
+__device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int gb, int ge, int *s_next)
+{
+    const int lane = threadIdx.x & 31;
+    int cai = 0;
+    if (gb < ge) {
+        int lo = 0, hi = a.nact - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.ucum + mid) <= gb) lo = mid;
+            else hi = mid - 1;
+        }
+        cai = lo;
+    }
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = gb + atomicAdd(s_next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= ge) break;
+        while (__ldg(a.ucum + cai + 1) <= u) ++cai;
+        const int slot = __ldg(a.act + cai);
+        const BSysDyn &D = a.dyn[slot];
+        // nothing to do for a finished system, nor in P after an OUTER step
+        if (D.finished || (!U && D.mode[cur] != MODE_INNER)) {
+            if (lane == 0) atomicMax(s_next, __ldg(a.ucum + cai + 1) - gb);
+            continue;
+        }
+        if (U) u_unit<TI>(a, cur, nxt, slot, cai, u);
+        else p_unit<TI>(a, nxt, slot, cai, u);
+    }
+}
+
+// One quantum of lockstep global iterations over the active systems:
+// S (SpMV, p.q or the refinement residual), U (vector updates, r.z, r.r),
+// P (direction update or solution update), a grid barrier after each.
+// The warp completing a system's reduction in S or U computes the
+// system's scalars for the next phase, so the barriers are the only
+// global synchronisation.  CTA b owns a contiguous share of each phase's
+// units; its warps claim them dynamically.
+template <typename TI>
+__global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ BWarpQ s_q[GBS_PWARPS];
+    __shared__ int s_next[3];
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = gridDim.x;
-    const int gw = blockIdx.x * GBS_PWARPS + warp, nw = G * GBS_PWARPS;
-    BTile<double> &wt64 = reinterpret_cast<BTile<double> *>(smem)[warp];
-    BTile<float> &wt32 = *reinterpret_cast<BTile<float> *>(&wt64);
-    // this warp's contiguous share of the active tiles
-    const int g0 = (int)((int64_t)a.ntile * gw / nw), g1 = (int)((int64_t)a.ntile * (gw + 1) / nw);
-    const int ai0 = g0 < g1 ? owner_of(a.tcum, a.nact, g0) : 0;
-    const int nunits = a.nchunk * GBS_KMAX;   // reduction work units: (chunk, column)
+    unsigned char *wsm = smem + (size_t)warp * GBS_BWARP_BYTES;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < GBS_MAX_STAGES; ++j) gbs_mbar_init(&s_q[warp].bar[j], 1);
+        gbs_fence_mbar_init();
+    }
+    if (threadIdx.x < 3) s_next[threadIdx.x] = 0;
+    __syncthreads();
+    const int b = blockIdx.x, G = gridDim.x;
+    const int sb = (int)((int64_t)a.nsu * b / G), se = (int)((int64_t)a.nsu * (b + 1) / G);
+    const int ub = (int)((int64_t)a.nuu * b / G), ue = (int)((int64_t)a.nuu * (b + 1) / G);
+    const uint64_t ps = gbs_policy_stream();
+    uint32_t parity = 0;
     int bno = 0;
-    bool ok = true;
-
-    for (int q = 0; q < a.quantum && ok; ++q) {
+    for (int q = 0; q < a.quantum; ++q) {
         const int cur = (a.iter0 + q) & 1, nxt = cur ^ 1;
-
-        // ---------------- S: SpMV per tile
-        for (int g = g0, ai = ai0; g < g1; ++g) {
-            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
-            const int slot = __ldg(a.act + ai);
-            const int lt = g - __ldg(a.tcum + ai);
-            const BSys &S = a.sys[slot];
-            const BSysDyn &D = a.dyn[slot];
-            if (D.finished) continue;
-            const int k = S.k;
-            double *dst = a.partS + (size_t)g * GBS_KMAX * 2;
-            if (D.mode[cur] == MODE_OUTER) {
-                // r64 = b - A x (FP64), partials r.r and b.b
-                double acc[GBS_KMAX][2];
-#pragma unroll
-                for (int c = 0; c < GBS_KMAX; ++c) acc[c][0] = acc[c][1] = 0.0;
-                auto epi = [&](int row, double(&s)[GBS_KMAX]) {
-#pragma unroll
-                    for (int c = 0; c < GBS_KMAX; ++c) {
-                        if (c >= k) break;
-                        const size_t o = (size_t)row * k + c;
-                        const double bi = S.b[o];
-                        const double ri = bi - s[c];
-                        S.r64[o] = ri;
-                        acc[c][0] += ri * ri;
-                        acc[c][1] += bi * bi;
-                    }
-                };
-                tile_spmv_k<double, double>(S, S.vals, S.x, lt, wt64, epi);
-                warp_store_partials<double>(acc, k, dst);
-            } else {
-                // q = A p (inner precision), partial p.q
-                TI acc[GBS_KMAX][2];
-#pragma unroll
-                for (int c = 0; c < GBS_KMAX; ++c) acc[c][0] = acc[c][1] = TI(0);
-                const TI *p = (const TI *)S.pi;
-                TI *qv = (TI *)S.qi;
-                auto epi = [&](int row, TI(&s)[GBS_KMAX]) {
-#pragma unroll
-                    for (int c = 0; c < GBS_KMAX; ++c) {
-                        if (c >= k) break;
-                        const size_t o = (size_t)row * k + c;
-                        qv[o] = s[c];
-                        acc[c][0] += p[o] * s[c];
-                    }
-                };
-                if (a.fp64)
-                    tile_spmv_k<double, TI>(S, S.vals, p, lt, wt64, epi);
-                else
-                    tile_spmv_k<float, TI>(S, S.vals32, p, lt, wt32, epi);
-                warp_store_partials<TI>(acc, k, dst);
-            }
-        }
-        if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
-
-        // ---------------- R1: per (system, column)
-        for (int u = gw; u < nunits; u += nw) {
-            const int gc = u / GBS_KMAX, cc = u % GBS_KMAX;
-            const int ai = owner_of(a.ccum, a.nact, gc);
-            const int slot = __ldg(a.act + ai);
-            const BSys &S = a.sys[slot];
-            BSysDyn &D = a.dyn[slot];
-            if (cc >= S.k || D.finished) continue;
-            BCol &C = a.col[slot * GBS_KMAX + cc];
-            if (!col_running(C)) continue;
-            const int ca = __ldg(a.ccum + ai), cb = __ldg(a.ccum + ai + 1);
-            const int ga = __ldg(a.tcum + ai) + (gc - ca) * GBS_RCHUNK;
-            const int gb = min(ga + GBS_RCHUNK, __ldg(a.tcum + ai + 1));
-            if (D.mode[cur] == MODE_OUTER) {
-                double tot[2];
-                if (!chunk_reduce<double>(a, a.partS, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
-                const double rr = tot[0], bb = tot[1];
-                if (lane == 0) {
-                    const double rn = sqrt(rr);
-                    if (C.first) C.bnorm = sqrt(bb);
-                    C.first = 0;
-                    C.rn = rn;
-                    if (isnan(rn)) C.status = GBS_ERR_NAN;
-                    else if (rn <= S.rtol * C.bnorm) C.status = GBS_OK;
-                    else if (rn > 0.5 * C.prev) C.status = GBS_ERR_STAGNATION;
-                    else if (C.outer >= a.outer_maxit || C.iters >= S.maxit) C.status = GBS_DIVERGED_ITS;
-                    else {
-                        C.prev = rn;
-                        C.scale = 1.0 / rn;
-                        C.outer += 1;
-                        // FP64 inner solves aim below rtol ||b|| at once
-                        C.tol_inner = a.fp64 ? 0.5 * S.rtol * C.bnorm / rn : a.inner_rtol;
-                    }
-                }
-            } else if (!C.inner_done) {
-                TI tot[2];
-                if (!chunk_reduce<TI>(a, a.partS, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
-                const TI pq = tot[0];
-                if (lane == 0) {
-                    if (isnan((double)pq)) C.status = GBS_ERR_NAN;
-                    else if (pq <= TI(0)) C.status = GBS_ERR_INDEFINITE;
-                    else C.alpha = (double)((TI)C.rho / pq);
-                }
-            }
-        }
-        if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
-
-        // ---------------- U: vector updates per tile
-        for (int g = g0, ai = ai0; g < g1; ++g) {
-            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
-            const int slot = __ldg(a.act + ai);
-            const int lt = g - __ldg(a.tcum + ai);
-            const BSys &S = a.sys[slot];
-            const BSysDyn &D = a.dyn[slot];
-            if (D.finished) continue;
-            const int k = S.k;
-            const BCol *Cs = a.col + slot * GBS_KMAX;
-            const int r0 = __ldg(S.tiles + lt), r1 = __ldg(S.tiles + lt + 1);
-            TI acc[GBS_KMAX][2];
-#pragma unroll
-            for (int c = 0; c < GBS_KMAX; ++c) acc[c][0] = acc[c][1] = TI(0);
-            TI *xi = (TI *)S.xi, *ri = (TI *)S.ri, *zi = (TI *)S.zi, *pi = (TI *)S.pi;
-            const TI *qi = (const TI *)S.qi;
-            const int row = r0 + lane;
-            if (row < r1) {
-                const TI dg = a.fp64 ? (TI)S.dinv[row] : (TI)S.dinv32[row];
-                if (D.mode[cur] == MODE_OUTER) {
-                    // start an inner solve on r / ||r||: x_i = 0, r_i = b_i, z = D^-1 r_i, p = z
-#pragma unroll
-                    for (int c = 0; c < GBS_KMAX; ++c) {
-                        if (c >= k) break;
-                        if (!col_running(Cs[c])) continue;
-                        const size_t o = (size_t)row * k + c;
-                        const TI bi = (TI)(S.r64[o] * Cs[c].scale);
-                        const TI zi_ = dg * bi;
-                        xi[o] = TI(0);
-                        ri[o] = bi;
-                        zi[o] = zi_;
-                        pi[o] = zi_;
-                        acc[c][0] += bi * zi_;
-                        acc[c][1] += bi * bi;
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < GBS_KMAX; ++c) {
-                        if (c >= k) break;
-                        if (!col_running(Cs[c]) || Cs[c].inner_done) continue;
-                        const size_t o = (size_t)row * k + c;
-                        const TI al = (TI)Cs[c].alpha;
-                        xi[o] = xi[o] + al * pi[o];
-                        const TI rn_ = ri[o] - al * qi[o];
-                        const TI zn_ = dg * rn_;
-                        ri[o] = rn_;
-                        zi[o] = zn_;
-                        acc[c][0] += rn_ * zn_;
-                        acc[c][1] += rn_ * rn_;
-                    }
-                }
-            }
-            warp_store_partials<TI>(acc, k, a.partU + (size_t)g * GBS_KMAX * 2);
-        }
-        if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
-
-        // ---------------- R2: per (system, column)
-        for (int u = gw; u < nunits; u += nw) {
-            const int gc = u / GBS_KMAX, cc = u % GBS_KMAX;
-            const int ai = owner_of(a.ccum, a.nact, gc);
-            const int slot = __ldg(a.act + ai);
-            const BSys &S = a.sys[slot];
-            BSysDyn &D = a.dyn[slot];
-            if (cc >= S.k || D.finished) continue;
-            BCol &C = a.col[slot * GBS_KMAX + cc];
-            if (!col_running(C)) continue;
-            const int ca = __ldg(a.ccum + ai), cb = __ldg(a.ccum + ai + 1);
-            const int ga = __ldg(a.tcum + ai) + (gc - ca) * GBS_RCHUNK;
-            const int gb = min(ga + GBS_RCHUNK, __ldg(a.tcum + ai + 1));
-            if (D.mode[cur] == MODE_OUTER) {
-                TI tot[2];
-                if (!chunk_reduce<TI>(a, a.partU, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
-                const TI rho = tot[0], bb = tot[1];
-                if (lane == 0) {
-                    C.rho = (double)rho;
-                    C.tol_inner = C.tol_inner * (double)sqrt(bb);
-                    C.kin = 0;
-                    C.inner_done = 0;
-                }
-            } else if (!C.inner_done) {
-                TI tot[2];
-                if (!chunk_reduce<TI>(a, a.partU, ga, gb, gc, ca, cb, ai, cc, tot)) continue;
-                const TI rho_new = tot[0], rr = tot[1];
-                if (lane == 0) {
-                    C.kin += 1;
-                    C.iters += 1;
-                    if (rho_new < TI(0)) {
-                        C.status = GBS_ERR_INDEFINITE;
-                    } else if (isnan((double)rr)) {
-                        C.status = GBS_ERR_NAN;
-                    } else {
-                        C.beta = (double)(rho_new / (TI)C.rho);
-                        C.rho = (double)rho_new;
-                        if ((double)sqrt(rr) <= C.tol_inner || C.iters >= S.maxit) C.inner_done = 1;
-                    }
-                }
-            }
-        }
-        if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
-
-        // ---------------- P: direction update, or refinement update
-        for (int g = g0, ai = ai0; g < g1; ++g) {
-            while (__ldg(a.tcum + ai + 1) <= g) ++ai;
-            const int slot = __ldg(a.act + ai);
-            const int lt = g - __ldg(a.tcum + ai);
-            const BSys &S = a.sys[slot];
-            BSysDyn &D = a.dyn[slot];
-            if (D.finished) continue;
-            const int k = S.k;
-            const BCol *Cs = a.col + slot * GBS_KMAX;
-            // the system's next step: refinement once every running column's
-            // inner solve has stopped; finished once no column runs
-            int running = 0, waiting = 0;
-            for (int c = 0; c < k; ++c) {
-                running += col_running(Cs[c]);
-                waiting += col_running(Cs[c]) && !Cs[c].inner_done;
-            }
-            const int mode = D.mode[cur];
-            const int next = (mode == MODE_INNER && waiting == 0) ? MODE_OUTER : MODE_INNER;
-            const int r0 = __ldg(S.tiles + lt), r1 = __ldg(S.tiles + lt + 1);
-            const int row = r0 + lane;
-            if (row < r1 && mode == MODE_INNER) {
-                TI *pi = (TI *)S.pi;
-                const TI *zi = (const TI *)S.zi, *xi = (const TI *)S.xi;
-#pragma unroll
-                for (int c = 0; c < GBS_KMAX; ++c) {
-                    if (c >= k) break;
-                    if (!col_running(Cs[c])) continue;
-                    const size_t o = (size_t)row * k + c;
-                    if (next == MODE_OUTER)
-                        S.x[o] += Cs[c].rn * (double)xi[o];   // x += ||r|| d
-                    else if (!Cs[c].inner_done)
-                        pi[o] = zi[o] + (TI)Cs[c].beta * pi[o];
-                }
-            }
-            if (lt == 0 && lane == 0) {
-                D.mode[nxt] = running ? next : mode;
-                if (!running) D.finished = 1;
-            }
-        }
-        if (!(ok = gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag))) break;
+        // each claim counter is reset one phase after its last use (a grid
+        // barrier lies between the reset and both uses)
+        if (threadIdx.x == 0) s_next[2] = 0;
+        if (!phase_s<TI>(a, cur, sb, se, &s_next[0], wsm, s_q[warp], parity, ps) && lane == 0)
+            atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
+        if (threadIdx.x == 0) s_next[0] = 0;
+        phase_up<TI, true>(a, cur, nxt, ub, ue, &s_next[1]);
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
+        if (threadIdx.x == 0) s_next[1] = 0;
+        phase_up<TI, false>(a, cur, nxt, ub, ue, &s_next[2]);
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
     }
 }
 
-// Column-major (c * n + i) <-> interleaved (i * k + c).
-__global__ void k_interleave(int64_t n, int k, const double *src, double *dst, int dir)
+// Column-major (c * n + i) <-> interleaved with padded stride kp
+// (i * kp + c; padding entries are written as zeros).
+__global__ void k_interleave(int64_t n, int k, int kp, const double *src, double *dst, int dir)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * kp;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / k, cc = e % k;
-        if (dir == 0) dst[e] = src[cc * n + i];
-        else dst[cc * n + i] = src[e];
+        const int64_t i = e / kp, cc = e % kp;
+        if (dir == 0) dst[e] = cc < k ? src[cc * n + i] : 0.0;
+        else if (cc < k) dst[cc * n + i] = src[e];
     }
 }
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Column stride of a system with k right-hand sides: k rounded up to a power of two.
+int padded_k(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
+
+// Reduction units of a system.  Large systems group more work per unit, so
+// the per-unit completion count costs little; the grouping depends on the
+// system alone (results do not depend on the batch).
+int tiles_per_unit(int64_t ntiles) { return (int)std::min<int64_t>(8, std::max<int64_t>(1, ntiles / 1024)); }
+int subs_per_unit(int64_t nsub) { return (int)std::min<int64_t>(4, std::max<int64_t>(1, nsub / 1024)); }
 
 // ----------------------------------------------------------------------
 // Host engine: a slot table of systems run by the kernel above.
@@ -541,7 +1083,8 @@ struct SlotHost {
     bool finished = false;
     gbs_mat A = nullptr;
     bool own_A = false;       // the engine created the matrix (serving) and frees it
-    int k = 0;
+    int k = 0, kp = 1;
+    int nsu = 0, nuu = 0;     // S units and U/P units
     char *work = nullptr;     // device vectors of the slot
     size_t bytes = 0;         // device bytes held for budget accounting
     uint64_t ticket = 0;
@@ -556,12 +1099,13 @@ struct Engine {
     int nslots = 0;
     BSys *d_sys = nullptr;
     BCol *d_col = nullptr;
+    BPh *d_ph = nullptr;
     BSysDyn *d_dyn = nullptr;
-    int *d_act = nullptr, *d_tcum = nullptr, *d_ccum = nullptr, *d_ccount = nullptr;
-    double *d_cpart = nullptr;
-    size_t cap_cpart = 0;
-    double *d_partS = nullptr, *d_partU = nullptr;
-    size_t cap_part = 0;
+    int *d_idx = nullptr;     // act | scum | ucum | ccs | ccu
+    int *d_cnt = nullptr;     // cntS | cntU | sysS | sysU
+    size_t cap_cnt = 0;
+    double *d_partS = nullptr, *d_partU = nullptr, *d_cpartS = nullptr, *d_cpartU = nullptr;
+    size_t cap_partS = 0, cap_partU = 0, cap_cpartS = 0, cap_cpartU = 0;
     gbs_grid_barrier *d_bar = nullptr;
     std::vector<SlotHost> slots;
     std::vector<BSysDyn> h_dyn;
@@ -570,8 +1114,8 @@ struct Engine {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     std::vector<int> g_act;   // active set the graph was captured for
-    std::vector<int> g_tcum;  // and its tile prefix sums
     bool dirty = true;        // a slot was filled or released since the capture
+    size_t cnt_bytes = 0;
     BArgs g_args;
     int G = 0;
 };
@@ -583,7 +1127,6 @@ void engine_free_graph(Engine &E)
     E.gexec = nullptr;
     E.graph = nullptr;
     E.g_act.clear();
-    E.g_tcum.clear();
 }
 
 int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
@@ -596,14 +1139,12 @@ int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
     E.nslots = nslots;
     E.slots.assign(nslots, SlotHost());
     E.h_dyn.assign(nslots, BSysDyn());
-    GBS_CUDA_TRY(cudaMalloc(&E.d_sys, sizeof(BSys) * (size_t)std::max(nslots, 1)));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_col, sizeof(BCol) * (size_t)std::max(nslots, 1) * GBS_KMAX));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_dyn, sizeof(BSysDyn) * (size_t)std::max(nslots, 1)));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_act, sizeof(int) * (size_t)(nslots + 1)));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_tcum, sizeof(int) * (size_t)(nslots + 2)));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_ccum, sizeof(int) * (size_t)(nslots + 2)));
-    GBS_CUDA_TRY(cudaMalloc(&E.d_ccount, sizeof(int) * (size_t)(nslots + 1) * GBS_KMAX));
-    GBS_CUDA_TRY(cudaMemset(E.d_ccount, 0, sizeof(int) * (size_t)(nslots + 1) * GBS_KMAX));
+    const size_t ns = (size_t)std::max(nslots, 1);
+    GBS_CUDA_TRY(cudaMalloc(&E.d_sys, sizeof(BSys) * ns));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_col, sizeof(BCol) * ns * GBS_KMAX));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_ph, sizeof(BPh) * ns));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_dyn, sizeof(BSysDyn) * ns));
+    GBS_CUDA_TRY(cudaMalloc(&E.d_idx, sizeof(int) * 5 * (ns + 2)));
     GBS_CUDA_TRY(cudaMalloc(&E.d_bar, 256));
     return GBS_OK;
 }
@@ -619,14 +1160,14 @@ void engine_destroy(Engine &E)
     }
     cudaFree(E.d_sys);
     cudaFree(E.d_col);
+    cudaFree(E.d_ph);
     cudaFree(E.d_dyn);
-    cudaFree(E.d_act);
-    cudaFree(E.d_tcum);
-    cudaFree(E.d_ccum);
-    cudaFree(E.d_ccount);
-    cudaFree(E.d_cpart);
+    cudaFree(E.d_idx);
+    cudaFree(E.d_cnt);
     cudaFree(E.d_partS);
     cudaFree(E.d_partU);
+    cudaFree(E.d_cpartS);
+    cudaFree(E.d_cpartU);
     cudaFree(E.d_bar);
     E = Engine();
 }
@@ -634,11 +1175,25 @@ void engine_destroy(Engine &E)
 // Device bytes a system of n rows, nnz nonzeros and k columns holds.
 size_t system_bytes(int64_t n, int64_t nnz, int k, int fp64)
 {
-    const size_t nk = (size_t)n * k, tsz = fp64 ? 8 : 4;
-    const size_t vecs = 3 * a256(nk * 8) + 5 * a256(nk * tsz);
+    const size_t nk = (size_t)n * padded_k(k), tsz = fp64 ? 8 : 4;
+    const size_t vecs = 3 * a256(nk * 8) + 4 * a256(nk * tsz);
     const size_t mat = 4 * (size_t)(n + 5) + 12 * (size_t)(nnz + 4) + (fp64 ? 0 : 4 * (size_t)(nnz + 4)) +
                        12 * (size_t)(n + 4) + 12 * (size_t)(n / 32 + 2) + 4096;
     return vecs + mat;
+}
+
+// Grow a device buffer to hold at least `need` elements (contents dropped).
+template <typename T>
+int ensure_cap(T *&p, size_t &cap, size_t need)
+{
+    if (need <= cap && p) return GBS_OK;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t n = need + need / 2 + 64;
+    GBS_CUDA_TRY(cudaMalloc(&p, n * sizeof(T)));
+    cap = n;
+    return GBS_OK;
 }
 
 // Put a system into a free slot.  b and x0 are column-major device arrays
@@ -649,22 +1204,32 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
 {
     gbs_ctx c = E.c;
     SlotHost &H = E.slots[slot];
-    const size_t nk = (size_t)A->n * k, tsz = E.fp64 ? 8 : 4;
+    const int kp = padded_k(k);
+    const size_t nk = (size_t)A->n * kp, tsz = E.fp64 ? 8 : 4;
     if (!E.fp64) {
         int st = gbs_mat_ensure_f32(A);
         if (st) return st;
     }
-    const size_t bytes = 3 * a256(nk * 8) + 5 * a256(nk * tsz);
+    const size_t bytes = 3 * a256(nk * 8) + 4 * a256(nk * tsz);
     char *p = nullptr;
-    if (bytes) GBS_CUDA_TRY(cudaMalloc(&p, bytes));
+    if (bytes) {
+        GBS_CUDA_TRY(cudaMalloc(&p, bytes));
+        // padding columns and unused entries hold zeros
+        GBS_CUDA_TRY(cudaMemsetAsync(p, 0, bytes, c->stream));
+    }
     // a reused slot may hold a system of another size: the active lists and
     // the captured launch must be rebuilt before the next quantum
     E.dirty = true;
+    const int64_t nsub = ((int64_t)nk + GBS_SUB - 1) / GBS_SUB;
+    const int tg = tiles_per_unit(A->ntiles), usub = subs_per_unit(nsub);
     H.used = true;
     H.finished = false;
     H.A = A;
     H.own_A = own_A;
     H.k = k;
+    H.kp = kp;
+    H.nsu = (int)((A->ntiles + tg - 1) / tg);
+    H.nuu = (int)((nsub + usub - 1) / usub);
     H.work = p;
     H.bytes = bytes;
     H.ticket = ticket;
@@ -672,7 +1237,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     memset(&S, 0, sizeof(S));
     S.rowptr = A->rowptr;
     S.colidx = A->colidx;
-    S.tiles = A->tiles;
+    S.tdesc = A->tdesc;
     S.vals = A->vals;
     S.vals32 = A->vals32;
     S.dinv = A->dinv;
@@ -683,22 +1248,21 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
         S.r64 = (double *)p; p += a256(nk * 8);
         S.xi = p; p += a256(nk * tsz);
         S.ri = p; p += a256(nk * tsz);
-        S.zi = p; p += a256(nk * tsz);
         S.pi = p; p += a256(nk * tsz);
         S.qi = p; p += a256(nk * tsz);
     }
     S.n = (int)A->n;
     S.k = k;
+    S.kp = kp;
     S.ntiles = (int)A->ntiles;
+    S.tg = tg;
+    S.usub = usub;
     S.rtol = rtol;
     S.maxit = maxit;
     if (nk) {
         const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
-        k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, b, (double *)S.b, 0);
-        if (x0)
-            k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, x0, S.x, 0);
-        else
-            GBS_CUDA_TRY(cudaMemsetAsync(S.x, 0, nk * 8, c->stream));
+        k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, kp, b, (double *)S.b, 0);
+        if (x0) k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, kp, x0, S.x, 0);
         gbs_count_launch(c, x0 ? 2 : 1);
         GBS_CUDA_TRY(cudaGetLastError());
     }
@@ -720,6 +1284,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     GBS_CUDA_TRY(cudaMemcpyAsync(E.d_sys + slot, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
     GBS_CUDA_TRY(cudaMemcpyAsync(E.d_col + (size_t)slot * GBS_KMAX, C, sizeof(C),
                                  cudaMemcpyHostToDevice, c->stream));
+    GBS_CUDA_TRY(cudaMemsetAsync(E.d_ph + slot, 0, sizeof(BPh), c->stream));
     GBS_CUDA_TRY(cudaMemcpyAsync(E.d_dyn + slot, &D, sizeof(D), cudaMemcpyHostToDevice, c->stream));
     // the host arrays above are copied from pageable memory: make sure they
     // are consumed before they go out of scope
@@ -728,7 +1293,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
 }
 
 // Copy a slot's results out (x column-major into x_out, device or host per
-// memspace) and release the slot.
+// memspace).
 int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters, double *rnorm,
                    int *status)
 {
@@ -738,19 +1303,21 @@ int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters,
     GBS_CUDA_TRY(cudaMemcpyAsync(C, E.d_col + (size_t)slot * GBS_KMAX, sizeof(C),
                                  cudaMemcpyDeviceToHost, c->stream));
     const int64_t n = H.A->n;
-    const size_t nk = (size_t)n * H.k;
+    const int kp = H.kp;
+    const size_t nk = (size_t)n * kp;
     if (nk && x_out) {
         const double *xil = (const double *)(H.work + a256(nk * 8));
         const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
         if (memspace == GBS_MEM_DEVICE) {
-            k_interleave<<<g, 256, 0, c->stream>>>(n, H.k, xil, x_out, 1);
+            k_interleave<<<g, 256, 0, c->stream>>>(n, H.k, kp, xil, x_out, 1);
             gbs_count_launch(c);
             GBS_CUDA_TRY(cudaGetLastError());
         } else {
             std::vector<double> tmp(nk);
             GBS_CUDA_TRY(cudaMemcpyAsync(tmp.data(), xil, nk * 8, cudaMemcpyDeviceToHost, c->stream));
             GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-            for (size_t e = 0; e < nk; ++e) x_out[(e % H.k) * n + e / H.k] = tmp[e];
+            for (size_t e = 0; e < nk; ++e)
+                if ((int)(e % kp) < H.k) x_out[(e % kp) * n + e / kp] = tmp[e];
         }
     }
     GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -772,85 +1339,109 @@ void engine_release(Engine &E, int slot)
     H = SlotHost();
 }
 
+// Stage geometry covering the tiles of every active system.
+GbsPipeCfg engine_pipe_cfg(const Engine &E, const std::vector<int> &act)
+{
+    int v = 16, cl = 16, r = 16;
+    for (int s : act) {
+        const GbsPipeCfg &p = E.fp64 ? E.slots[s].A->pipe64 : E.slots[s].A->pipe32;
+        v = std::max(v, p.coloff);
+        cl = std::max(cl, p.rpoff - p.coloff);
+        r = std::max(r, p.sbytes - p.rpoff);
+    }
+    GbsPipeCfg cfg;
+    cfg.coloff = v;
+    cfg.rpoff = v + cl;
+    cfg.sbytes = v + cl + r;
+    cfg.stages = std::min(GBS_MAX_STAGES, std::max(1, GBS_BWARP_BYTES / cfg.sbytes));
+    return cfg;
+}
+
 // Run one quantum over the active slots; refresh the finished flags.
 int engine_step(Engine &E, int *ran)
 {
     gbs_ctx c = E.c;
     *ran = 0;
-    std::vector<int> act, tcum(1, 0), ccum(1, 0);
+    std::vector<int> act;
     for (int s = 0; s < E.nslots; ++s) {
         const SlotHost &H = E.slots[s];
-        if (H.used && !H.finished && H.A->ntiles > 0) {
-            act.push_back(s);
-            tcum.push_back(tcum.back() + (int)H.A->ntiles);
-            ccum.push_back(ccum.back() + (int)((H.A->ntiles + GBS_RCHUNK - 1) / GBS_RCHUNK));
-        }
+        if (H.used && !H.finished && H.A->ntiles > 0) act.push_back(s);
     }
     if (act.empty()) return GBS_OK;
-    const int nact = (int)act.size(), ntile = tcum.back(), nchunk = ccum.back();
+    const int nact = (int)act.size();
     const void *fn = E.fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
-    const size_t smem = sizeof(BTile<double>) * GBS_PWARPS;
-    if (E.dirty || act != E.g_act || tcum != E.g_tcum) {
+    const size_t smem = (size_t)GBS_BWARP_BYTES * GBS_PWARPS;
+    if (E.dirty || act != E.g_act) {
         engine_free_graph(E);
         E.dirty = false;
-        if ((size_t)ntile > E.cap_part) {
-            cudaFree(E.d_partS);
-            cudaFree(E.d_partU);
-            E.d_partS = E.d_partU = nullptr;
-            E.cap_part = 0;
-            const size_t cap = (size_t)ntile + ntile / 2 + 64;
-            GBS_CUDA_TRY(cudaMalloc(&E.d_partS, cap * GBS_KMAX * 2 * sizeof(double)));
-            GBS_CUDA_TRY(cudaMalloc(&E.d_partU, cap * GBS_KMAX * 2 * sizeof(double)));
-            E.cap_part = cap;
+        // act | scum | ucum | ccs | ccu
+        std::vector<int> idx(5 * (size_t)(nact + 1), 0);
+        int *h_act = idx.data(), *scum = h_act + (nact + 1), *ucum = scum + (nact + 1),
+            *ccs = ucum + (nact + 1), *ccu = ccs + (nact + 1);
+        for (int i = 0; i < nact; ++i) {
+            const SlotHost &H = E.slots[act[i]];
+            h_act[i] = act[i];
+            scum[i + 1] = scum[i] + H.nsu;
+            ucum[i + 1] = ucum[i] + H.nuu;
+            ccs[i + 1] = ccs[i] + (H.nsu + GBS_RCHUNK - 1) / GBS_RCHUNK;
+            ccu[i + 1] = ccu[i] + (H.nuu + GBS_RCHUNK - 1) / GBS_RCHUNK;
         }
-        if ((size_t)nchunk > E.cap_cpart) {
-            cudaFree(E.d_cpart);
-            E.d_cpart = nullptr;
-            E.cap_cpart = 0;
-            const size_t cap = (size_t)nchunk + nchunk / 2 + 64;
-            GBS_CUDA_TRY(cudaMalloc(&E.d_cpart, cap * GBS_KMAX * 2 * sizeof(double)));
-            E.cap_cpart = cap;
-        }
-        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_ccum, ccum.data(), sizeof(int) * (nact + 1),
+        const int nsu = scum[nact], nuu = ucum[nact], nchs = ccs[nact], nchu = ccu[nact];
+        int st = ensure_cap(E.d_partS, E.cap_partS, (size_t)nsu * 2 * GBS_KMAX);
+        if (!st) st = ensure_cap(E.d_partU, E.cap_partU, (size_t)nuu * 2 * GBS_KMAX);
+        if (!st) st = ensure_cap(E.d_cpartS, E.cap_cpartS, (size_t)nchs * 2 * GBS_KMAX);
+        if (!st) st = ensure_cap(E.d_cpartU, E.cap_cpartU, (size_t)nchu * 2 * GBS_KMAX);
+        const size_t ncnt = (size_t)nchs + nchu + 2 * (size_t)nact;
+        if (!st) st = ensure_cap(E.d_cnt, E.cap_cnt, ncnt);
+        if (st) return st;
+        E.cnt_bytes = ncnt * sizeof(int);
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_idx, idx.data(), sizeof(int) * idx.size(),
                                      cudaMemcpyHostToDevice, c->stream));
-        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_act, act.data(), sizeof(int) * nact, cudaMemcpyHostToDevice,
-                                     c->stream));
-        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_tcum, tcum.data(), sizeof(int) * (nact + 1),
-                                     cudaMemcpyHostToDevice, c->stream));
-        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));   // act/tcum are stack vectors
+        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));   // idx is a stack vector
         GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
-        const int64_t need = ((int64_t)std::max(ntile, nchunk * GBS_KMAX) + GBS_PWARPS - 1) / GBS_PWARPS;
+        // at most one CTA per GBS_PWARPS units of the larger pass
+        const int64_t need = ((int64_t)std::max(nsu, nuu) + GBS_PWARPS - 1) / GBS_PWARPS;
         E.G = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, std::max<int64_t>(need, 1));
         BArgs &a = E.g_args;
         memset(&a, 0, sizeof(a));
         a.sys = E.d_sys;
         a.col = E.d_col;
+        a.ph = E.d_ph;
         a.dyn = E.d_dyn;
-        a.act = E.d_act;
-        a.tcum = E.d_tcum;
+        a.act = E.d_idx;
+        a.scum = E.d_idx + (nact + 1);
+        a.ucum = E.d_idx + 2 * (nact + 1);
+        a.ccs = E.d_idx + 3 * (nact + 1);
+        a.ccu = E.d_idx + 4 * (nact + 1);
         a.nact = nact;
-        a.ntile = ntile;
-        a.nchunk = nchunk;
-        a.ccum = E.d_ccum;
-        a.cpart = E.d_cpart;
-        a.ccount = E.d_ccount;
+        a.nsu = nsu;
+        a.nuu = nuu;
         a.partS = E.d_partS;
         a.partU = E.d_partU;
+        a.cpartS = E.d_cpartS;
+        a.cpartU = E.d_cpartU;
+        a.cntS = E.d_cnt;
+        a.cntU = E.d_cnt + nchs;
+        a.sysS = E.d_cnt + nchs + nchu;
+        a.sysU = E.d_cnt + nchs + nchu + nact;
         a.bar = E.d_bar;
+        a.cfg = engine_pipe_cfg(E, act);
         a.quantum = E.quantum;   // even: the parity of the global iteration is unchanged
         a.iter0 = 0;
         a.inner_rtol = E.inner_rtol;
         a.outer_maxit = E.outer_maxit;
         a.fp64 = E.fp64;
         a.timeout_ns = (unsigned long long)c->opts.barrier_timeout_ms * 1000000ull;
-        // capture barrier reset + cooperative launch once for this active set
+        // capture the counter and barrier reset and the cooperative launch
+        // once for this active set
         cudaStream_t cap = nullptr;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            cudaMemsetAsync(E.d_cnt, 0, E.cnt_bytes, cap);
             cudaMemsetAsync(E.d_bar, 0, 256, cap);
             void *args[] = {&E.g_args};
             cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args, smem, cap);
@@ -863,12 +1454,12 @@ int engine_step(Engine &E, int *ran)
             engine_free_graph(E);   // launch directly below
         } else {
             E.g_act = act;
-            E.g_tcum = tcum;
         }
     }
     if (E.gexec) {
         GBS_CUDA_TRY(cudaGraphLaunch(E.gexec, c->stream));
     } else {
+        GBS_CUDA_TRY(cudaMemsetAsync(E.d_cnt, 0, E.cnt_bytes, c->stream));
         GBS_CUDA_TRY(cudaMemsetAsync(E.d_bar, 0, 256, c->stream));
         void *args[] = {&E.g_args};
         GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args,
@@ -958,6 +1549,9 @@ struct Request {
     int maxit;
     std::vector<int32_t> rowptr, colidx;
     std::vector<double> vals, b;
+    // the arrays in use: the copies above, or the caller's (borrowed)
+    const int32_t *p_rowptr = nullptr, *p_colidx = nullptr;
+    const double *p_vals = nullptr, *p_b = nullptr;
     size_t bytes;
     int slot = -1;
     bool done = false;
@@ -978,7 +1572,64 @@ struct gbs_server_s {
     std::deque<uint64_t> queue;                       // waiting for admission, FIFO
     std::unordered_map<uint64_t, Request> reqs;       // queued, running or done
     int running = 0, finished = 0;
+    double t_admit = 0.0, t_quanta = 0.0, t_retire = 0.0;   // seconds spent in each step
+    int64_t quanta = 0;
 };
+
+namespace {
+
+double seconds_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int server_submit(gbs_server srv, int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
+                  const double *vals, int k, const double *b, double rtol, int maxit, bool copy,
+                  uint64_t *ticket)
+{
+    if (!srv || !ticket || nrows < 0 || nrows >= INT32_MAX || !rowptr || k < 1 || k > GBS_KMAX ||
+        !(rtol >= 0.0) || maxit < 0 || (nrows > 0 && !b))
+        return GBS_ERR_ARG;
+    const int64_t nnz = rowptr[nrows];
+    if (nnz < 0 || (nnz > 0 && (!colidx || !vals))) return GBS_ERR_ARG;
+    const size_t bytes = system_bytes(nrows, nnz, k, srv->mode == GBS_MODE_FP64);
+    if (bytes > srv->budget) return GBS_ERR_BUDGET;
+    Request r;
+    r.ticket = srv->next_ticket++;
+    r.n = nrows;
+    r.k = k;
+    r.rtol = rtol;
+    r.maxit = maxit;
+    if (copy) {
+        r.rowptr.assign(rowptr, rowptr + nrows + 1);
+        r.colidx.assign(colidx, colidx + nnz);
+        r.vals.assign(vals, vals + nnz);
+        r.b.assign(b, b + nrows * k);
+        r.p_rowptr = r.rowptr.data();
+        r.p_colidx = r.colidx.data();
+        r.p_vals = r.vals.data();
+        r.p_b = r.b.data();
+    } else {
+        r.p_rowptr = rowptr;
+        r.p_colidx = colidx;
+        r.p_vals = vals;
+        r.p_b = b;
+    }
+    r.bytes = bytes;
+    *ticket = r.ticket;
+    srv->queue.push_back(r.ticket);
+    auto it = srv->reqs.emplace(r.ticket, std::move(r)).first;
+    if (copy) {   // the vectors moved: point at their new storage
+        Request &q = it->second;
+        q.p_rowptr = q.rowptr.data();
+        q.p_colidx = q.colidx.data();
+        q.p_vals = q.vals.data();
+        q.p_b = q.b.data();
+    }
+    return GBS_OK;
+}
+
+}  // namespace
 
 extern "C" int gbs_server_create(gbs_ctx c, size_t budget, int max_slots, int mode, gbs_server *out)
 {
@@ -1014,28 +1665,14 @@ extern "C" int gbs_server_submit(gbs_server srv, int64_t nrows, const int32_t *r
                                  const int32_t *colidx, const double *vals, int k, const double *b,
                                  double rtol, int maxit, uint64_t *ticket)
 {
-    if (!srv || !ticket || nrows < 0 || nrows >= INT32_MAX || !rowptr || k < 1 || k > GBS_KMAX ||
-        !(rtol >= 0.0) || maxit < 0 || (nrows > 0 && !b))
-        return GBS_ERR_ARG;
-    const int64_t nnz = rowptr[nrows];
-    if (nnz < 0 || (nnz > 0 && (!colidx || !vals))) return GBS_ERR_ARG;
-    const size_t bytes = system_bytes(nrows, nnz, k, srv->mode == GBS_MODE_FP64);
-    if (bytes > srv->budget) return GBS_ERR_BUDGET;
-    Request r;
-    r.ticket = srv->next_ticket++;
-    r.n = nrows;
-    r.k = k;
-    r.rtol = rtol;
-    r.maxit = maxit;
-    r.rowptr.assign(rowptr, rowptr + nrows + 1);
-    r.colidx.assign(colidx, colidx + nnz);
-    r.vals.assign(vals, vals + nnz);
-    r.b.assign(b, b + nrows * k);
-    r.bytes = bytes;
-    *ticket = r.ticket;
-    srv->queue.push_back(r.ticket);
-    srv->reqs.emplace(r.ticket, std::move(r));
-    return GBS_OK;
+    return server_submit(srv, nrows, rowptr, colidx, vals, k, b, rtol, maxit, true, ticket);
+}
+
+extern "C" int gbs_server_submit_borrowed(gbs_server srv, int64_t nrows, const int32_t *rowptr,
+                                          const int32_t *colidx, const double *vals, int k,
+                                          const double *b, double rtol, int maxit, uint64_t *ticket)
+{
+    return server_submit(srv, nrows, rowptr, colidx, vals, k, b, rtol, maxit, false, ticket);
 }
 
 // Admit queued requests (FIFO) while a slot and budget are free.
@@ -1050,8 +1687,8 @@ static int server_admit(gbs_server srv)
         if (slot < 0 || srv->used + r.bytes > srv->budget) break;
         srv->queue.pop_front();
         gbs_mat A = nullptr;
-        int st = gbs_mat_create_aij(srv->c, r.n, r.n, r.rowptr.data(), r.colidx.data(),
-                                    r.vals.data(), GBS_MEM_HOST, &A);
+        int st = gbs_mat_create_aij(srv->c, r.n, r.n, r.p_rowptr, r.p_colidx, r.p_vals,
+                                    GBS_MEM_HOST, &A);
         if (st != GBS_OK) {
             // a malformed request finishes at once with that status
             r.done = true;
@@ -1067,7 +1704,7 @@ static int server_admit(gbs_server srv)
         if (nb) {
             cudaError_t e = cudaMalloc(&db, nb);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(db, r.b.data(), nb, cudaMemcpyHostToDevice, srv->c->stream);
+                e = cudaMemcpyAsync(db, r.p_b, nb, cudaMemcpyHostToDevice, srv->c->stream);
             if (e != cudaSuccess) {
                 cudaFree(db);
                 gbs_mat_destroy(A);
@@ -1086,6 +1723,9 @@ static int server_admit(gbs_server srv)
         std::vector<double>().swap(r.b);
         std::vector<int32_t>().swap(r.colidx);
         std::vector<double>().swap(r.vals);
+        r.p_colidx = nullptr;
+        r.p_vals = nullptr;
+        r.p_b = nullptr;
     }
     return GBS_OK;
 }
@@ -1121,11 +1761,20 @@ extern "C" int gbs_server_progress(gbs_server srv, int *retired)
     if (!srv) return GBS_ERR_ARG;
     int n = 0;
     GBS_CUDA_TRY(cudaSetDevice(srv->c->device));
+    auto t0 = std::chrono::steady_clock::now();
     int st = server_retire(srv, &n);   // systems that finished at admission
+    srv->t_retire += seconds_since(t0);
+    t0 = std::chrono::steady_clock::now();
     if (!st) st = server_admit(srv);
+    srv->t_admit += seconds_since(t0);
     int ran = 0;
+    t0 = std::chrono::steady_clock::now();
     if (!st) st = engine_step(srv->E, &ran);
+    srv->t_quanta += seconds_since(t0);
+    srv->quanta += ran;
+    t0 = std::chrono::steady_clock::now();
     if (!st) st = server_retire(srv, &n);
+    srv->t_retire += seconds_since(t0);
     if (retired) *retired = n;
     return st;
 }
@@ -1176,5 +1825,16 @@ extern "C" int gbs_server_stats(gbs_server srv, int *queued, int *running, int *
     if (running) *running = srv->running;
     if (finished) *finished = srv->finished;
     if (bytes_in_use) *bytes_in_use = srv->used;
+    return GBS_OK;
+}
+
+extern "C" int gbs_server_times(gbs_server srv, double *admit_s, double *quanta_s, double *retire_s,
+                                int64_t *quanta)
+{
+    if (!srv) return GBS_ERR_ARG;
+    if (admit_s) *admit_s = srv->t_admit;
+    if (quanta_s) *quanta_s = srv->t_quanta;
+    if (retire_s) *retire_s = srv->t_retire;
+    if (quanta) *quanta = srv->quanta;
     return GBS_OK;
 }

@@ -125,11 +125,15 @@ _SIGS = {
     "gbs_server_destroy": ([_VP], ctypes.c_int),
     "gbs_server_submit": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int,
                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gbs_server_submit_borrowed": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_double,
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "gbs_server_progress": ([_VP, _I32P], ctypes.c_int),
     "gbs_server_poll": ([_VP, ctypes.c_uint64, _I32P], ctypes.c_int),
     "gbs_server_wait": ([_VP, ctypes.c_uint64], ctypes.c_int),
     "gbs_server_fetch": ([_VP, ctypes.c_uint64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gbs_server_stats": ([_VP, _I32P, _I32P, _I32P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gbs_server_times": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
 
 
@@ -458,6 +462,20 @@ def gbs_server_submit(srv, nrows: int, rowptr, colidx, vals, k: int, b, rtol: fl
     return t.value
 
 
+def gbs_server_submit_borrowed(srv, nrows: int, rowptr, colidx, vals, k: int, b, rtol: float,
+                               maxit: int) -> int:
+    """As gbs_server_submit without the copy: the caller keeps the four
+    arrays alive and unchanged until the request is done."""
+    for a in (rowptr, colidx, vals, b):
+        if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("server inputs are contiguous host numpy arrays")
+    t = ctypes.c_uint64()
+    _check(lib().gbs_server_submit_borrowed(srv, int(nrows), rowptr.ctypes.data, colidx.ctypes.data,
+                                            vals.ctypes.data, int(k), b.ctypes.data, float(rtol),
+                                            int(maxit), ctypes.byref(t)), "gbs_server_submit_borrowed")
+    return t.value
+
+
 def gbs_server_progress(srv) -> int:
     r = ctypes.c_int()
     _check(lib().gbs_server_progress(srv, ctypes.byref(r)), "gbs_server_progress")
@@ -491,3 +509,12 @@ def gbs_server_stats(srv):
     _check(lib().gbs_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f),
                                   ctypes.byref(b)), "gbs_server_stats")
     return q.value, r.value, f.value, b.value
+
+
+def gbs_server_times(srv):
+    """(admit_s, quanta_s, retire_s, quanta) since the server was created."""
+    a, q, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().gbs_server_times(srv, ctypes.byref(a), ctypes.byref(q), ctypes.byref(r),
+                                  ctypes.byref(n)), "gbs_server_times")
+    return a.value, q.value, r.value, n.value

@@ -164,3 +164,21 @@ def test_server_slot_reuse_with_different_sizes(S, orc):
         x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, k)
         check(orc, A, b, k, x, sts)
     gbs.gbs_server_destroy(srv)
+
+
+def test_server_borrowed_submit_matches_copy(S, orc):
+    """A borrowed-array request gives bitwise the result of a copied one;
+    the engine's time counters add up."""
+    A, b = request(orc, 7, (15, 14, 13), 3)
+    out = []
+    for borrowed in (False, True):
+        srv = gbs.gbs_server_create(S.ctx, 8 << 30, 0, gbs.GBS_MODE_MIXED)
+        f = gbs.gbs_server_submit_borrowed if borrowed else gbs.gbs_server_submit
+        t = f(srv, A.n, A.rowptr, A.colidx, A.vals, 3, b, 1e-10, 20000)
+        gbs.gbs_server_wait(srv, t)
+        ta, tq, tr, nq = gbs.gbs_server_times(srv)
+        assert nq >= 1 and tq > 0.0 and ta > 0.0 and tr >= 0.0
+        out.append(gbs.gbs_server_fetch(srv, t, A.n, 3))
+        gbs.gbs_server_destroy(srv)
+    check(orc, A, b, 3, out[1][0], out[1][3])
+    assert np.array_equal(out[0][0], out[1][0])
