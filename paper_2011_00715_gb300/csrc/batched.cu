@@ -128,6 +128,7 @@ struct BArgs {
     double *cpartS, *cpartU;   // chunk * 16: per-chunk sums
     int *cntS, *cntU;          // per chunk: units arrived (zero between phases)
     int *sysS, *sysU;          // per active system: chunks arrived
+    int *claim;                // 3 per global iteration of the quantum: next unclaimed unit of S, U, P
     gbs_grid_barrier *bar;
     GbsPipeCfg cfg;     // stage geometry covering every active system's tiles
     int quantum;
@@ -246,7 +247,8 @@ __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char 
     TI sum[KP], pd[KP];
 #pragma unroll
     for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
-#pragma unroll 4
+    // gathers in flight per lane: as many as the registers allow
+#pragma unroll(KP * sizeof(TI) >= 32 ? 4 : 8)
     for (int e = beg; e < end; ++e) {
         const int c = scol[e - cb];
         const TI a = sval[e - vb];
@@ -665,7 +667,8 @@ __device__ __forceinline__ bool s_unit(const BArgs &a, BWarpQ &q, unsigned char 
 }
 
 // A unit is `tg` consecutive warp tiles of one system.  Lane 0 of each warp
-// claims the next unit of the CTA's range from *s_next, keeps the next tile
+// claims the next unit of [gb, ge) from the counter *next (shared by the
+// whole grid, so the work balances across SMs), keeps the next tile
 // and its descriptor one step ahead, and copies the CSR slice of each INNER
 // tile into the next free stage of the warp's ring (cfg.stages stages,
 // cfg.stages - 1 in flight).  OUTER tiles (FP64, once per refinement step)
@@ -674,7 +677,7 @@ __device__ __forceinline__ bool s_unit(const BArgs &a, BWarpQ &q, unsigned char 
 // system's reduction.  Returns false if a copy did not complete within the
 // time limit (the copies in flight are then waited for, again with a limit).
 template <typename TI>
-__device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *s_next, unsigned char *wsm,
+__device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *next, unsigned char *wsm,
                         BWarpQ &q, uint32_t &parity, uint64_t ps)
 {
     constexpr int E = 16 / (int)sizeof(TI);
@@ -701,7 +704,7 @@ __device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *s_next, un
     };
     auto claim = [&]() {
         for (;;) {
-            const int u = gb + atomicAdd(s_next, 1);
+            const int u = gb + atomicAdd(next, 1);
             if (u >= ge) {
                 p_unit = -1;
                 return;
@@ -710,7 +713,7 @@ __device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *s_next, un
             const int slot = __ldg(a.act + cai);
             const BSysDyn &D = a.dyn[slot];
             if (D.finished) {   // skip the rest of a finished system
-                atomicMax(s_next, __ldg(a.scum + cai + 1) - gb);
+                atomicMax(next, __ldg(a.scum + cai + 1) - gb);
                 continue;
             }
             const BSys &S = a.sys[slot];
@@ -972,32 +975,25 @@ __device__ __forceinline__ void p_unit(const BArgs &a, int nxt, int slot, int ai
     }
 }
 
-// The warp's units of a U or P pass over the CTA's range [gb, ge).
+// The warp's units of a U or P pass over [gb, ge), claimed from the grid-wide
+// counter *next one unit ahead (the claim's latency overlaps a unit's work).
 template <typename TI, bool U>
-__device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int gb, int ge, int *s_next)
+__device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int gb, int ge, int *next)
 {
     const int lane = threadIdx.x & 31;
     int cai = 0;
-    if (gb < ge) {
-        int lo = 0, hi = a.nact - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(a.ucum + mid) <= gb) lo = mid;
-            else hi = mid - 1;
-        }
-        cai = lo;
-    }
+    int pend = 0;
+    if (lane == 0) pend = gb + atomicAdd(next, 1);
     for (;;) {
-        int u = 0;
-        if (lane == 0) u = gb + atomicAdd(s_next, 1);
-        u = __shfl_sync(0xffffffffu, u, 0);
+        const int u = __shfl_sync(0xffffffffu, pend, 0);
         if (u >= ge) break;
+        if (lane == 0) pend = gb + atomicAdd(next, 1);
         while (__ldg(a.ucum + cai + 1) <= u) ++cai;
         const int slot = __ldg(a.act + cai);
         const BSysDyn &D = a.dyn[slot];
         // nothing to do for a finished system, nor in P after an OUTER step
         if (D.finished || (!U && D.mode[cur] != MODE_INNER)) {
-            if (lane == 0) atomicMax(s_next, __ldg(a.ucum + cai + 1) - gb);
+            if (lane == 0) atomicMax(next, __ldg(a.ucum + cai + 1) - gb);
             continue;
         }
         if (U) u_unit<TI>(a, cur, nxt, slot, cai, u);
@@ -1010,14 +1006,14 @@ __device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int g
 // P (direction update or solution update), a grid barrier after each.
 // The warp completing a system's reduction in S or U computes the
 // system's scalars for the next phase, so the barriers are the only
-// global synchronisation.  CTA b owns a contiguous share of each phase's
-// units; its warps claim them dynamically.
+// global synchronisation.  Warps claim the units of each phase from
+// grid-wide counters (one per phase and global iteration, zeroed before
+// the launch), so SMs share the work evenly whatever the units cost.
 template <typename TI>
 __global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ BWarpQ s_q[GBS_PWARPS];
-    __shared__ int s_next[3];
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wsm = smem + (size_t)warp * GBS_BWARP_BYTES;
@@ -1026,27 +1022,19 @@ __global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
         for (int j = 0; j < GBS_MAX_STAGES; ++j) gbs_mbar_init(&s_q[warp].bar[j], 1);
         gbs_fence_mbar_init();
     }
-    if (threadIdx.x < 3) s_next[threadIdx.x] = 0;
     __syncthreads();
-    const int b = blockIdx.x, G = gridDim.x;
-    const int sb = (int)((int64_t)a.nsu * b / G), se = (int)((int64_t)a.nsu * (b + 1) / G);
-    const int ub = (int)((int64_t)a.nuu * b / G), ue = (int)((int64_t)a.nuu * (b + 1) / G);
     const uint64_t ps = gbs_policy_stream();
     uint32_t parity = 0;
     int bno = 0;
     for (int q = 0; q < a.quantum; ++q) {
         const int cur = (a.iter0 + q) & 1, nxt = cur ^ 1;
-        // each claim counter is reset one phase after its last use (a grid
-        // barrier lies between the reset and both uses)
-        if (threadIdx.x == 0) s_next[2] = 0;
-        if (!phase_s<TI>(a, cur, sb, se, &s_next[0], wsm, s_q[warp], parity, ps) && lane == 0)
+        int *ctr = a.claim + 3 * q;
+        if (!phase_s<TI>(a, cur, 0, a.nsu, ctr, wsm, s_q[warp], parity, ps) && lane == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
-        if (threadIdx.x == 0) s_next[0] = 0;
-        phase_up<TI, true>(a, cur, nxt, ub, ue, &s_next[1]);
+        phase_up<TI, true>(a, cur, nxt, 0, a.nuu, ctr + 1);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
-        if (threadIdx.x == 0) s_next[1] = 0;
-        phase_up<TI, false>(a, cur, nxt, ub, ue, &s_next[2]);
+        phase_up<TI, false>(a, cur, nxt, 0, a.nuu, ctr + 2);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
     }
 }
@@ -1071,8 +1059,8 @@ int padded_k(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
 // Reduction units of a system.  Large systems group more work per unit, so
 // the per-unit completion count costs little; the grouping depends on the
 // system alone (results do not depend on the batch).
-int tiles_per_unit(int64_t ntiles) { return (int)std::min<int64_t>(8, std::max<int64_t>(1, ntiles / 1024)); }
-int subs_per_unit(int64_t nsub) { return (int)std::min<int64_t>(4, std::max<int64_t>(1, nsub / 1024)); }
+int tiles_per_unit(int64_t ntiles) { return (int)std::min<int64_t>(8, std::max<int64_t>(1, ntiles / 256)); }
+int subs_per_unit(int64_t nsub) { return (int)std::min<int64_t>(4, std::max<int64_t>(1, nsub / 256)); }
 
 // ----------------------------------------------------------------------
 // Host engine: a slot table of systems run by the kernel above.
@@ -1102,7 +1090,7 @@ struct Engine {
     BPh *d_ph = nullptr;
     BSysDyn *d_dyn = nullptr;
     int *d_idx = nullptr;     // act | scum | ucum | ccs | ccu
-    int *d_cnt = nullptr;     // cntS | cntU | sysS | sysU
+    int *d_cnt = nullptr;     // cntS | cntU | sysS | sysU | claim
     size_t cap_cnt = 0;
     double *d_partS = nullptr, *d_partU = nullptr, *d_cpartS = nullptr, *d_cpartU = nullptr;
     size_t cap_partS = 0, cap_partU = 0, cap_cpartS = 0, cap_cpartU = 0;
@@ -1391,7 +1379,7 @@ int engine_step(Engine &E, int *ran)
         if (!st) st = ensure_cap(E.d_partU, E.cap_partU, (size_t)nuu * 2 * GBS_KMAX);
         if (!st) st = ensure_cap(E.d_cpartS, E.cap_cpartS, (size_t)nchs * 2 * GBS_KMAX);
         if (!st) st = ensure_cap(E.d_cpartU, E.cap_cpartU, (size_t)nchu * 2 * GBS_KMAX);
-        const size_t ncnt = (size_t)nchs + nchu + 2 * (size_t)nact;
+        const size_t ncnt = (size_t)nchs + nchu + 2 * (size_t)nact + 3 * (size_t)E.quantum;
         if (!st) st = ensure_cap(E.d_cnt, E.cap_cnt, ncnt);
         if (st) return st;
         E.cnt_bytes = ncnt * sizeof(int);
@@ -1427,6 +1415,7 @@ int engine_step(Engine &E, int *ran)
         a.cntU = E.d_cnt + nchs;
         a.sysS = E.d_cnt + nchs + nchu;
         a.sysU = E.d_cnt + nchs + nchu + nact;
+        a.claim = E.d_cnt + nchs + nchu + 2 * nact;
         a.bar = E.d_bar;
         a.cfg = engine_pipe_cfg(E, act);
         a.quantum = E.quantum;   // even: the parity of the global iteration is unchanged
