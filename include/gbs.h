@@ -104,7 +104,13 @@ typedef struct {
     int fault_skip_arrival;  /* testing only: if >= 0, that CTA of the next
                                 persistent solve does not arrive at its first
                                 grid barrier, so the barrier times out (default -1) */
-    int reserved[8];
+    int batched_lanes;       /* batched and serving engines: lanes per matrix row
+                                in the SpMV (1, 2 or 4), or 0 (default) to let the
+                                autotuner pick per class of systems (row length,
+                                right-hand-side count, precision), timing the
+                                candidates once per context on the first system
+                                of the class */
+    int reserved[7];
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -117,6 +123,8 @@ typedef struct {
                             true FP64 residual ||b - A x||_2 in MIXED mode */
     double bnorm;        /* ||b||_2 */
     double device_ms;    /* device time of the solve (CUDA events) */
+    double model_bytes;  /* algorithmic bytes the solve moved by the library's
+                            byte model (batched solves; 0 where not computed) */
 } gbs_solve_info;
 
 /* Library version string (static storage). */
@@ -314,6 +322,16 @@ int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, double rtol,
 int gbs_ksp_solve_cg_batched(gbs_ctx ctx, int nsys, const gbs_mat *A, const gbs_vec *B,
                              gbs_vec *X, const int *nrhs, const double *rtol, int maxit,
                              int mode, int *iters, double *rnorm, int *status);
+
+/* Autotune the batched engines for systems like A with k right-hand sides
+ * in `mode` (GBS_MODE_FP64 or GBS_MODE_MIXED): the lanes per matrix row of
+ * the SpMV (1, 2 or 4) for A's class (row length, column stride,
+ * precision) is chosen by timing the candidates on copies of A, once per
+ * context; later batched solves and servers on ctx use the decision.  The
+ * chosen lanes go to *lanes (may be NULL).  With gbs_opts.batched_lanes set
+ * (non-zero), nothing is timed and that value is reported.  Lets a caller
+ * pay the tuning before its first timed solve. */
+int gbs_batched_tune(gbs_ctx ctx, gbs_mat A, int k, int mode, int *lanes);
 
 /* ----------------------------------------------------------- serving --- */
 

@@ -77,7 +77,8 @@ struct BSys {
     int n, k, kp, ntiles;
     int tg;             // warp tiles per S-phase reduction unit
     int usub;           // update sub-blocks per U/P-phase unit
-    int maxit, pad0;
+    int maxit;
+    int lanes_log;      // log2 of the lanes sharing a row in the INNER SpMV
     double rtol;
 };
 
@@ -110,7 +111,9 @@ struct BPh {
 struct BSysDyn {
     int mode[2];      // indexed by global iteration parity
     int finished;
-    int pad;
+    int isteps;       // INNER steps taken
+    int osteps;       // OUTER steps taken
+    int pad[3];
 };
 
 struct BArgs {
@@ -226,44 +229,58 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[KP])
 // S phase: one warp tile
 // ---------------------------------------------------------------------
 
-// INNER step, tile staged in shared memory: q = A p on its rows, lane l
-// owning row r0 + l (left to right over the row, all KP columns at once);
-// acc[c][0] += p_row,c q_row,c (p_row from the diagonal entry's gather).
+// INNER step, tile staged in shared memory: q = A p on its rows.  L = 2^li
+// lanes share a row: lane l takes row r0 + l / L and every L-th nonzero of
+// it from l mod L on (all KP columns at once); the L partial sums are added
+// by a fixed shuffle tree.  acc[c][0] += p_row,c q_row,c (p_row from the
+// diagonal entry's gather).
 template <typename TI, int KP>
 __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char *st,
                                              const GbsPipeCfg &cfg, int4 d, TI (&acc)[KP][2])
 {
     constexpr int E = 16 / (int)sizeof(TI);
     const int lane = threadIdx.x & 31;
+    const int li = S.lanes_log, L = 1 << li;
     const int r0 = d.x, k0 = d.y, r1 = d.z;
-    if (lane >= r1 - r0) return;
-    const TI *sval = reinterpret_cast<const TI *>(st);
-    const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
-    const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
-    const int row = r0 + lane;
-    const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
-    const int beg = srp[row - rb], end = srp[row - rb + 1];
-    const TI *p = static_cast<const TI *>(S.pi);
+    const int rl = lane >> li, h = lane & (L - 1);
+    const bool act = rl < r1 - r0;
+    const int row = r0 + rl;
     TI sum[KP], pd[KP];
 #pragma unroll
     for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
-    // gathers in flight per lane: as many as the registers allow
+    if (act) {
+        const TI *sval = reinterpret_cast<const TI *>(st);
+        const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
+        const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
+        const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+        const int beg = srp[row - rb], end = srp[row - rb + 1];
+        const TI *p = static_cast<const TI *>(S.pi);
+        // gathers in flight per lane: as many as the registers allow
 #pragma unroll(KP * sizeof(TI) >= 32 ? 4 : 8)
-    for (int e = beg; e < end; ++e) {
-        const int c = scol[e - cb];
-        const TI a = sval[e - vb];
-        TI v[KP];
-        vload<TI, KP>(p + (size_t)c * KP, v);
-        const bool dg = c == row;
+        for (int e = beg + h; e < end; e += L) {
+            const int c = scol[e - cb];
+            const TI a = sval[e - vb];
+            TI v[KP];
+            vload<TI, KP>(p + (size_t)c * KP, v);
+            const bool dg = c == row;
 #pragma unroll
-        for (int i = 0; i < KP; ++i) {
-            pd[i] = dg ? v[i] : pd[i];
-            sum[i] = fma(a, v[i], sum[i]);
+            for (int i = 0; i < KP; ++i) {
+                pd[i] = dg ? v[i] : pd[i];
+                sum[i] = fma(a, v[i], sum[i]);
+            }
         }
     }
-    vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
+    for (int off = 1; off < L; off <<= 1)
 #pragma unroll
-    for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
+        for (int i = 0; i < KP; ++i) {
+            sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
+            pd[i] += __shfl_xor_sync(0xffffffffu, pd[i], off);
+        }
+    if (act && h == 0) {
+        vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
+#pragma unroll
+        for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
+    }
 }
 
 // INNER step, a tile holding one row longer than GBS_WT_NNZ (read directly;
@@ -503,6 +520,7 @@ __device__ __noinline__ void s_finish_outer(const BArgs &a, int slot, double rr,
     if (lane == 0) {
         P.run = m;
         P.upd = m;
+        a.dyn[slot].osteps += 1;
         if (!m) a.dyn[slot].finished = 1;
     }
 }
@@ -589,6 +607,7 @@ __device__ __noinline__ void u_finish_inner(const BArgs &a, int slot, int nxt, T
         const unsigned run = P.run & ~mf;
         P.run = run;
         P.upd = mw;
+        a.dyn[slot].isteps += 1;
         // refinement once every running column's inner solve has stopped
         if (!run) a.dyn[slot].finished = 1;
         else a.dyn[slot].mode[nxt] = mw ? MODE_INNER : MODE_OUTER;
@@ -1072,6 +1091,7 @@ struct SlotHost {
     gbs_mat A = nullptr;
     bool own_A = false;       // the engine created the matrix (serving) and frees it
     int k = 0, kp = 1;
+    int li = 0;               // log2 of the lanes per row of its SpMV tiling
     int nsu = 0, nuu = 0;     // S units and U/P units
     char *work = nullptr;     // device vectors of the slot
     size_t bytes = 0;         // device bytes held for budget accounting
@@ -1170,6 +1190,23 @@ size_t system_bytes(int64_t n, int64_t nnz, int k, int fp64)
     return vecs + mat;
 }
 
+// Algorithmic bytes of the steps a slot's system has taken: an INNER step
+// streams the inner-precision values and colidx, rowptr, the p gather and q
+// (S), x, p, r, q read and x, r written plus D^-1 (U), r, p read and p
+// written plus D^-1 (P); an OUTER step streams the FP64 values and colidx,
+// rowptr, the x gather, b and r64 (S), r64 read, D^-1 and x_i, r_i, p_i
+// written (U).  Vector entries count kp per row.
+double slot_model_bytes(const Engine &E, int slot)
+{
+    const SlotHost &H = E.slots[slot];
+    if (!H.used || !H.A) return 0.0;
+    const BSysDyn &D = E.h_dyn[slot];
+    const double n = (double)H.A->n, nnz = (double)H.A->nnz, kp = H.kp, tsz = E.fp64 ? 8 : 4;
+    const double inner = (tsz + 4) * nnz + 4 * (n + 1) + tsz * n * (8 * kp + 2);
+    const double outer = 12 * nnz + 4 * (n + 1) + 32 * n * kp + tsz * n * (3 * kp + 1);
+    return D.isteps * inner + D.osteps * outer;
+}
+
 // Grow a device buffer to hold at least `need` elements (contents dropped).
 template <typename T>
 int ensure_cap(T *&p, size_t &cap, size_t need)
@@ -1188,11 +1225,16 @@ int ensure_cap(T *&p, size_t &cap, size_t need)
 // (x0 may be NULL for zeros).  A failing matrix (no usable diagonal, n = 0)
 // is admitted as finished with the corresponding column status.
 int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, const double *b,
-               const double *x0, bool own_A, uint64_t ticket)
+               const double *x0, bool own_A, uint64_t ticket, int li)
 {
     gbs_ctx c = E.c;
     SlotHost &H = E.slots[slot];
     const int kp = padded_k(k);
+    {
+        const int st = gbs_mat_ensure_lane_tiling(A, li);
+        if (st) return st;
+    }
+    const int64_t ntiles = A->ntiles_lanes[li];
     const size_t nk = (size_t)A->n * kp, tsz = E.fp64 ? 8 : 4;
     if (!E.fp64) {
         int st = gbs_mat_ensure_f32(A);
@@ -1209,14 +1251,15 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     // the captured launch must be rebuilt before the next quantum
     E.dirty = true;
     const int64_t nsub = ((int64_t)nk + GBS_SUB - 1) / GBS_SUB;
-    const int tg = tiles_per_unit(A->ntiles), usub = subs_per_unit(nsub);
+    const int tg = tiles_per_unit(ntiles), usub = subs_per_unit(nsub);
     H.used = true;
     H.finished = false;
     H.A = A;
     H.own_A = own_A;
     H.k = k;
     H.kp = kp;
-    H.nsu = (int)((A->ntiles + tg - 1) / tg);
+    H.li = li;
+    H.nsu = (int)((ntiles + tg - 1) / tg);
     H.nuu = (int)((nsub + usub - 1) / usub);
     H.work = p;
     H.bytes = bytes;
@@ -1225,7 +1268,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     memset(&S, 0, sizeof(S));
     S.rowptr = A->rowptr;
     S.colidx = A->colidx;
-    S.tdesc = A->tdesc;
+    S.tdesc = A->tdesc_lanes[li];
     S.vals = A->vals;
     S.vals32 = A->vals32;
     S.dinv = A->dinv;
@@ -1242,7 +1285,8 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     S.n = (int)A->n;
     S.k = k;
     S.kp = kp;
-    S.ntiles = (int)A->ntiles;
+    S.ntiles = (int)ntiles;
+    S.lanes_log = li;
     S.tg = tg;
     S.usub = usub;
     S.rtol = rtol;
@@ -1332,7 +1376,8 @@ GbsPipeCfg engine_pipe_cfg(const Engine &E, const std::vector<int> &act)
 {
     int v = 16, cl = 16, r = 16;
     for (int s : act) {
-        const GbsPipeCfg &p = E.fp64 ? E.slots[s].A->pipe64 : E.slots[s].A->pipe32;
+        const SlotHost &H = E.slots[s];
+        const GbsPipeCfg &p = E.fp64 ? H.A->pipe64_lanes[H.li] : H.A->pipe32_lanes[H.li];
         v = std::max(v, p.coloff);
         cl = std::max(cl, p.rpoff - p.coloff);
         r = std::max(r, p.sbytes - p.rpoff);
@@ -1353,7 +1398,7 @@ int engine_step(Engine &E, int *ran)
     std::vector<int> act;
     for (int s = 0; s < E.nslots; ++s) {
         const SlotHost &H = E.slots[s];
-        if (H.used && !H.finished && H.A->ntiles > 0) act.push_back(s);
+        if (H.used && !H.finished && H.nsu > 0) act.push_back(s);
     }
     if (act.empty()) return GBS_OK;
     const int nact = (int)act.size();
@@ -1469,7 +1514,112 @@ int engine_step(Engine &E, int *ran)
     return GBS_OK;
 }
 
+
+// ----------------------------------------------------------------------
+// Lanes-per-row autotuner
+// ----------------------------------------------------------------------
+
+__global__ void k_fill(int64_t n, double v, double *x)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+int ilog2(int64_t v)
+{
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+// Time one quantum of 16 global iterations of `rep` copies of the system
+// (its own matrix, right-hand sides of ones, rtol 0 so nothing stops) with
+// the tiling for 2^li lanes per row; the copies emulate a loaded engine.
+int time_lanes(gbs_ctx c, gbs_mat A, int k, int fp64, int li, int rep, const double *b, float *ms)
+{
+    Engine T;
+    int st = engine_init(T, c, rep, fp64, 16);
+    for (int r = 0; r < rep && st == GBS_OK; ++r)
+        st = engine_add(T, r, A, k, 0.0, 1 << 30, b, nullptr, false, 0, li);
+    int ran = 0;
+    if (st == GBS_OK) st = engine_step(T, &ran);   // capture, first refinement residual
+    if (st == GBS_OK) {
+        cudaEventRecord(c->ev0, c->stream);
+        st = engine_step(T, &ran);
+        cudaEventRecord(c->ev1, c->stream);
+        cudaEventSynchronize(c->ev1);
+        cudaEventElapsedTime(ms, c->ev0, c->ev1);
+    }
+    engine_destroy(T);
+    return st;
+}
+
+// Lanes per row (as log2) for a system in a batched engine: the option's
+// fixed value, else the context's decision for the system's class (row
+// length, column stride, precision), made on first use by timing 1, 2 and
+// 4 lanes per row on copies of the system that fill about 4 M rows (a
+// loaded engine); more lanes are taken only when at least 10 % faster.
+// The decision depends only on the class, so a system gets the same tiling
+// alone and in any batch of the same context.
+int choose_lanes(gbs_ctx c, gbs_mat A, int k, int fp64, int *li)
+{
+    *li = 0;
+    if (c->opts.batched_lanes > 0) {
+        *li = ilog2(c->opts.batched_lanes);
+        return GBS_OK;
+    }
+    if (A->n == 0 || A->ntiles == 0 || !A->diag_ok) return GBS_OK;
+    const int kp = padded_k(k);
+    const int rb = std::min(7, ilog2(std::max<int64_t>(1, A->nnz / A->n)));
+    signed char &slot = c->lane_choice[fp64 ? 1 : 0][ilog2(kp)][rb];
+    if (slot > 0) {
+        *li = slot - 1;
+        return GBS_OK;
+    }
+    if (!fp64) {
+        const int st = gbs_mat_ensure_f32(A);
+        if (st) return st;
+    }
+    const int64_t nk = A->n * (int64_t)k;
+    const int rep = (int)std::min<int64_t>(256, std::max<int64_t>(1, 4000000 / A->n));
+    double *b = nullptr;
+    GBS_CUDA_TRY(cudaMalloc(&b, sizeof(double) * (size_t)nk));
+    const int g = (int)std::min<int64_t>((nk + 255) / 256, (int64_t)c->num_sms * 8);
+    k_fill<<<g, 256, 0, c->stream>>>(nk, 1.0, b);
+    gbs_count_launch(c);
+    float t[3] = {INFINITY, INFINITY, INFINITY};
+    int st = GBS_OK;
+    for (int l = 0; l < 3 && st == GBS_OK; ++l) st = time_lanes(c, A, k, fp64, l, rep, b, &t[l]);
+    cudaFree(b);
+    if (st) return st;
+    int pick = 0;
+    for (int l = 1; l < 3; ++l)
+        if (t[l] < 0.9f * t[pick]) pick = l;
+    slot = (signed char)(pick + 1);
+    *li = pick;
+    return GBS_OK;
+}
+
 }  // namespace
+
+// ----------------------------------------------------------------------
+// gbs_batched_tune
+// ----------------------------------------------------------------------
+
+extern "C" int gbs_batched_tune(gbs_ctx c, gbs_mat A, int k, int mode, int *lanes)
+{
+    if (!c || !A || A->ctx != c || k < 1 || k > GBS_KMAX || A->n != A->ncols) return GBS_ERR_ARG;
+    if (mode != GBS_MODE_FP64 && mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    int li = 0;
+    const int st = choose_lanes(c, A, k, mode == GBS_MODE_FP64, &li);
+    if (st == GBS_OK && lanes) *lanes = 1 << li;
+    return st;
+}
 
 // ----------------------------------------------------------------------
 // gbs_ksp_solve_cg_batched
@@ -1493,9 +1643,13 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
     GBS_CUDA_TRY(cudaSetDevice(c->device));
     Engine E;
     int rc = engine_init(E, c, nsys, mode == GBS_MODE_FP64, 64);
-    for (int s = 0; s < nsys && rc == GBS_OK; ++s)
-        rc = engine_add(E, s, A[s], nrhs[s], rtol[s], maxit, (const double *)B[s]->data,
-                        (const double *)X[s]->data, false, 0);
+    for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
+        int li = 0;
+        rc = choose_lanes(c, A[s], nrhs[s], mode == GBS_MODE_FP64, &li);
+        if (rc == GBS_OK)
+            rc = engine_add(E, s, A[s], nrhs[s], rtol[s], maxit, (const double *)B[s]->data,
+                            (const double *)X[s]->data, false, 0, li);
+    }
     if (rc == GBS_OK) {
         cudaEventRecord(c->ev0, c->stream);
         for (int ran = 1; rc == GBS_OK && ran;) rc = engine_step(E, &ran);
@@ -1503,6 +1657,8 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
     }
     int first_bad = GBS_OK;
     int64_t o = 0;
+    double model = 0.0;
+    for (int s = 0; s < nsys; ++s) model += slot_model_bytes(E, s);
     for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
         int it[GBS_KMAX], stc[GBS_KMAX];
         double rn[GBS_KMAX];
@@ -1514,11 +1670,14 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
             if (stc[cc] != GBS_OK && first_bad == GBS_OK) first_bad = stc[cc];
         }
     }
+    memset(&c->last, 0, sizeof(c->last));
+    c->last.status = rc != GBS_OK ? rc : first_bad;
     if (rc == GBS_OK) {
         cudaStreamSynchronize(c->stream);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
         c->last.device_ms = ms;
+        c->last.model_bytes = model;
     }
     engine_destroy(E);
     return rc != GBS_OK ? rc : first_bad;
@@ -1700,7 +1859,9 @@ static int server_admit(gbs_server srv)
                 return gbs_cuda_fail(e);
             }
         }
-        st = engine_add(E, slot, A, r.k, r.rtol, r.maxit, db, nullptr, true, r.ticket);
+        int li = 0;
+        st = choose_lanes(srv->c, A, r.k, srv->mode == GBS_MODE_FP64, &li);
+        if (st == GBS_OK) st = engine_add(E, slot, A, r.k, r.rtol, r.maxit, db, nullptr, true, r.ticket, li);
         cudaFree(db);   // engine_add synchronised the stream after interleaving b
         if (st) {
             gbs_mat_destroy(A);

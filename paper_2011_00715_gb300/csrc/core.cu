@@ -67,6 +67,9 @@ static int opts_valid(const gbs_opts *o)
     if (o->algorithm < GBS_ALG_AUTO || o->algorithm > GBS_ALG_GRAPH) return 0;
     if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)) return 0;
     if (o->outer_maxit < 0 || o->barrier_timeout_ms <= 0 || o->graph_iters <= 0) return 0;
+    if (o->batched_lanes != 0 && o->batched_lanes != 1 && o->batched_lanes != 2 &&
+        o->batched_lanes != 4)
+        return 0;
     return 1;
 }
 
@@ -251,7 +254,8 @@ static int grid_for(gbs_ctx c, int64_t n, int per_sm = 4)
 
 // Split rows into warp tiles: at most GBS_WT_ROWS rows and GBS_WT_NNZ
 // nonzeros each; a longer row is a tile of its own.
-static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &tiles, int *maxrow)
+static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &tiles, int *maxrow,
+                       int rows_cap = GBS_WT_ROWS)
 {
     tiles.clear();
     tiles.push_back(0);
@@ -259,7 +263,7 @@ static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &t
     int mr = 0;
     while (start < n) {
         int64_t end = start;
-        while (end < n && end - start < GBS_WT_ROWS) {
+        while (end < n && end - start < rows_cap) {
             const int64_t rn = rowptr[end + 1] - rowptr[end];
             if (rn > mr) mr = (int)rn;
             if (end > start && rowptr[end + 1] - rowptr[start] > GBS_WT_NNZ) break;
@@ -311,7 +315,48 @@ static void mat_free(gbs_mat A)
     cudaFree(A->dinv32);
     cudaFree(A->tiles);
     cudaFree(A->tdesc);
+    cudaFree(A->tdesc_lanes[1]);
+    cudaFree(A->tdesc_lanes[2]);
     free(A);
+}
+
+int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
+{
+    if (li < 0 || li > 2) return GBS_ERR_ARG;
+    if (li == 0) {
+        A->tdesc_lanes[0] = A->tdesc;
+        A->ntiles_lanes[0] = A->ntiles;
+        A->pipe64_lanes[0] = A->pipe64;
+        A->pipe32_lanes[0] = A->pipe32;
+        return GBS_OK;
+    }
+    if (A->tdesc_lanes[li]) return GBS_OK;
+    gbs_ctx c = A->ctx;
+    std::vector<int32_t> hrp((size_t)A->n + 1), tiles;
+    GBS_CUDA_TRY(cudaMemcpyAsync(hrp.data(), A->rowptr, sizeof(int32_t) * hrp.size(),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int mr = 0;
+    make_tiles(hrp.data(), A->n, tiles, &mr, GBS_WT_ROWS >> li);
+    std::vector<int32_t> tdesc(2 * tiles.size());
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        tdesc[2 * t] = tiles[t];
+        tdesc[2 * t + 1] = hrp[tiles[t]];
+    }
+    int32_t *d = nullptr;
+    GBS_CUDA_TRY(cudaMalloc(&d, sizeof(int32_t) * tdesc.size()));
+    cudaError_t e = cudaMemcpyAsync(d, tdesc.data(), sizeof(int32_t) * tdesc.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // tdesc is a stack vector
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return gbs_cuda_fail(e);
+    }
+    A->tdesc_lanes[li] = d;
+    A->ntiles_lanes[li] = (int64_t)tiles.size() - 1;
+    A->pipe64_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 8);
+    A->pipe32_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 4);
+    return GBS_OK;
 }
 
 extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const int32_t *rowptr,

@@ -34,6 +34,9 @@ struct gbs_ctx_s {
     gbs_solve_info last;
     int64_t launches;           // kernel launches issued by this library
     cudaEvent_t ev0, ev1;
+    // batched engines' lanes-per-row decisions, per precision, column stride
+    // and row-length class: 0 = not tuned yet, else 1 + log2(lanes)
+    signed char lane_choice[2][4][8];
 };
 
 // Geometry of the bulk-copy pipeline of one matrix for one value type,
@@ -63,6 +66,11 @@ struct gbs_mat_s {
     GbsPipeCfg pipe64, pipe32;  // pipeline geometry for FP64 and FP32 values
     int64_t ntiles;
     int max_row_nnz;
+    // tilings for 1, 2 and 4 lanes per row (warp tiles of at most 32, 16 and
+    // 8 rows; made on first use; entry 0 is the tiling above)
+    int32_t *tdesc_lanes[3];
+    int64_t ntiles_lanes[3];
+    GbsPipeCfg pipe64_lanes[3], pipe32_lanes[3];
 };
 
 struct gbs_vec_s {
@@ -105,6 +113,8 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
 int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
                     const gbs_opts *o, gbs_solve_info *info, int use_graph);
 int gbs_mat_ensure_f32(gbs_mat A);
+// Make the tiling for 2^li lanes per row (li = 0, 1, 2) if it does not exist.
+int gbs_mat_ensure_lane_tiling(gbs_mat A, int li);
 
 // ------------------------------------------------------------------------
 // Device helpers

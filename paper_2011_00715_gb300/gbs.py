@@ -57,13 +57,14 @@ class gbs_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("algorithm", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
-                ("fault_skip_arrival", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class gbs_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("device_ms", ctypes.c_double)]
+                ("device_ms", ctypes.c_double), ("model_bytes", ctypes.c_double)]
 
 
 @dataclass
@@ -74,6 +75,7 @@ class SolveInfo:
     rnorm: float
     bnorm: float
     device_ms: float
+    model_bytes: float = 0.0
 
 
 _lib = None
@@ -127,6 +129,7 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "gbs_server_submit_borrowed": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gbs_batched_tune": ([_VP, _VP, ctypes.c_int, ctypes.c_int, _I32P], ctypes.c_int),
     "gbs_server_progress": ([_VP, _I32P], ctypes.c_int),
     "gbs_server_poll": ([_VP, ctypes.c_uint64, _I32P], ctypes.c_int),
     "gbs_server_wait": ([_VP, ctypes.c_uint64], ctypes.c_int),
@@ -370,7 +373,7 @@ def gbs_pc_destroy(pc):
 # ----------------------------------------------------------------- solver --
 
 def _info(i: gbs_solve_info) -> SolveInfo:
-    return SolveInfo(i.status, i.iters, i.outer_iters, i.rnorm, i.bnorm, i.device_ms)
+    return SolveInfo(i.status, i.iters, i.outer_iters, i.rnorm, i.bnorm, i.device_ms, i.model_bytes)
 
 
 _RESULT_STATUSES = (GBS_OK, GBS_DIVERGED_ITS, GBS_ERR_DIAG, GBS_ERR_INDEFINITE, GBS_ERR_NAN,
@@ -439,6 +442,15 @@ def gbs_ksp_solve_cg_batched(ctx, mats, Bs, Xs, nrhs, rtols, maxit: int, mode: i
 
 
 # ---------------------------------------------------------------- serving --
+
+def gbs_batched_tune(ctx, A, k: int, mode: int = GBS_MODE_MIXED) -> int:
+    """Lanes per row the batched engines use for systems like A (tuned once
+    per class and context)."""
+    lanes = ctypes.c_int()
+    _check(lib().gbs_batched_tune(ctx, A, int(k), int(mode), ctypes.byref(lanes)),
+           "gbs_batched_tune")
+    return lanes.value
+
 
 def gbs_server_create(ctx, hbm_budget_bytes: int, max_slots: int = 0, mode: int = GBS_MODE_MIXED):
     h = _VP()

@@ -6,11 +6,11 @@ from paper_2011_00715_gb300 import gbs
 
 
 class Session:
-    def __init__(self):
+    def __init__(self, opts=None):
         import torch
         self.torch = torch
         gbs.lib()
-        self.ctx = gbs.gbs_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+        self.ctx = gbs.gbs_ctx_create(0, torch.cuda.current_stream().cuda_stream, opts)
         self._keep = []
 
     def mat(self, A, device=False):

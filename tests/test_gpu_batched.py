@@ -87,6 +87,30 @@ def test_batched_against_oracle(S, orc, mode):
             o += 1
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_batched_lanes_per_row(orc, lanes):
+    """Every lanes-per-row tiling of the SpMV (the autotuner's candidates)
+    meets the same bar against the oracle, in both precisions."""
+    from gpu_util import Session
+    S = Session(gbs.gbs_opts_default(batched_lanes=lanes))
+    mats = make_batch()[:8]
+    rhs = [rhs_for(orc, A, k, i) for i, (A, k) in enumerate(mats)]
+    for mode in (gbs.GBS_MODE_MIXED, gbs.GBS_MODE_FP64):
+        st, its, rns, sts, xs = run_batch(S, mats, rhs, mode)
+        assert st == gbs.GBS_OK and np.all(sts == gbs.GBS_OK)
+        for (A, k), b, x in zip(mats, rhs, xs):
+            lmin = lambda_min(A)
+            for c in range(k):
+                bc, xc = b[c * A.n:(c + 1) * A.n], x[c * A.n:(c + 1) * A.n]
+                ref = orc.pcg(A, bc, 1e-10, 20000)
+                tr = np.linalg.norm(bc - orc.spmv(A, xc))
+                assert tr <= 1e-10 * np.linalg.norm(bc)
+                trr = np.linalg.norm(bc - orc.spmv(A, ref["x"]))
+                tol = max(1e-8, (tr + trr) / (lmin * np.linalg.norm(ref["x"])))
+                assert np.linalg.norm(xc - ref["x"]) <= tol * np.linalg.norm(ref["x"])
+    gbs.gbs_ctx_destroy(S.ctx)
+
+
 def test_batched_isolation_bitwise(S, orc):
     """A system's columns come out bitwise identical alone and in the mix."""
     mats = make_batch()
@@ -146,3 +170,24 @@ def test_batched_matches_single_solves(S, orc):
     assert abs(info.outer_iters - 3) <= 1
     assert np.linalg.norm(xs[0] - x1) <= 1e-8 * np.linalg.norm(x1)
     gbs.gbs_mat_destroy(h)
+
+
+def test_batched_tune_decision_is_cached(S, orc):
+    """The autotuner reports one of its candidates, keeps the decision for
+    the class (a second system of the class gets it without timing), and a
+    fixed option short-cuts it."""
+    from gpu_util import Session
+    A = I.var5(60, 55, seed=3)
+    h = S.mat(A)
+    lanes = gbs.gbs_batched_tune(S.ctx, h, 3, gbs.GBS_MODE_MIXED)
+    assert lanes in (1, 2, 4)
+    B = I.var5(70, 40, seed=4)          # same class: 5-point rows, stride 4, FP32 inner
+    hb = S.mat(B)
+    assert gbs.gbs_batched_tune(S.ctx, hb, 4, gbs.GBS_MODE_MIXED) == lanes
+    gbs.gbs_mat_destroy(h)
+    gbs.gbs_mat_destroy(hb)
+    F = Session(gbs.gbs_opts_default(batched_lanes=2))
+    hf = F.mat(A)
+    assert gbs.gbs_batched_tune(F.ctx, hf, 3, gbs.GBS_MODE_FP64) == 2
+    gbs.gbs_mat_destroy(hf)
+    gbs.gbs_ctx_destroy(F.ctx)
