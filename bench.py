@@ -60,6 +60,8 @@ def parse_args():
                    help="run only the batched workload (profiling of the batched kernel)")
     p.add_argument("--c5-only", action="store_true",
                    help="run only the serving workload")
+    p.add_argument("--sweep-only", action="store_true",
+                   help="run only the vector-operation / MatMult size sweep")
     p.add_argument("--c5-pool", type=int, default=12,
                    help="distinct operators the serving requests draw from")
     return p.parse_args()
@@ -519,9 +521,76 @@ def extras(g, args, A, Ah, xsv):
     for v in (xs3v, b3v, x3v, r3v):
         gbs.gbs_vec_destroy(v)
     gbs.gbs_mat_destroy(h)
+    out["c2_sweep"] = c2_sweep(g, args)
     out["c4_batched"] = c4_batched(g, args)
     out["c5_serving"] = c5_serving(g, args)
     return out
+
+
+# Memory accesses per vector entry of the vector operations (Sec. 5.1:
+# VecAXPY 3, VecCopy 2; VecDot reads two vectors).
+SWEEP_ACCESSES = {"VecAXPY": 3, "VecCopy": 2, "VecDot": 2}
+
+
+def c2_sweep(g, args):
+    """Work-time spectrum (Sec. 5.1) of the vector operations over lengths
+    10^3 .. 10^8 and of MatMult on 7-point cubes: time per call as the
+    caller sees it (a loop of calls on the stream, CUDA events around it;
+    VecDot returns its scalar to the host every call), bytes per call by the
+    accesses-per-entry model, hence latency (small sizes) and asymptotic
+    bandwidth (large sizes)."""
+    import numpy as np
+    import torch
+    from paper_2011_00715_gb300 import inputs as I
+    gbs = g.gbs
+    hbm, _ = peaks()
+    rows = []
+    for e10 in range(6, 17):          # lengths 10^3, 10^3.5, ..., 10^8
+        n = int(round(10 ** (e10 / 2)))
+        xt = torch.rand(n, dtype=torch.float64, device="cuda")
+        yt = torch.rand(n, dtype=torch.float64, device="cuda")
+        xv, yv = gbs.gbs_vec_wrap(g.ctx, xt), gbs.gbs_vec_wrap(g.ctx, yt)
+        ops = {"VecAXPY": lambda: gbs.gbs_vec_axpy(yv, 1e-3, xv),
+               "VecCopy": lambda: gbs.gbs_vec_copy(xv, yv),
+               "VecDot": lambda: gbs.gbs_vec_dot(xv, yv)}
+        for name, f in ops.items():
+            nbytes = SWEEP_ACCESSES[name] * 8 * n
+            reps = int(min(2000, max(10, 4e9 // nbytes)))
+            for _ in range(3):
+                f()
+            el = event_time(torch, f, reps) / reps
+            rows.append({"op": name, "n": n, "us": el * 1e6, "GBps": nbytes / el / 1e9})
+        gbs.gbs_vec_destroy(xv)
+        gbs.gbs_vec_destroy(yv)
+        del xt, yt
+    # MatMult on N^3 7-point Laplacians, n = 10^3 .. ~10^7 (host generation
+    # of larger operators would dominate the run)
+    for N in (10, 22, 46, 100, 215):
+        A = I.lap3d7(N)
+        h = g.mat(A)
+        xt = torch.rand(A.n, dtype=torch.float64, device="cuda")
+        yt = torch.empty_like(xt)
+        xv, yv = gbs.gbs_vec_wrap(g.ctx, xt), gbs.gbs_vec_wrap(g.ctx, yt)
+        f = lambda: gbs.gbs_mat_mult(h, xv, yv)
+        nbytes = bytes_spmv_fp64(A.n, A.nnz)
+        reps = int(min(2000, max(10, 4e9 // nbytes)))
+        for _ in range(3):
+            f()
+        el = event_time(torch, f, reps) / reps
+        rows.append({"op": "MatMult", "n": A.n, "nnz": A.nnz, "us": el * 1e6, "GBps": nbytes / el / 1e9})
+        gbs.gbs_vec_destroy(xv)
+        gbs.gbs_vec_destroy(yv)
+        gbs.gbs_mat_destroy(h)
+        del A, xt, yt
+    summary = {}
+    for op in ("VecAXPY", "VecCopy", "VecDot", "MatMult"):
+        rs = [r for r in rows if r["op"] == op]
+        best = max(r["GBps"] for r in rs)
+        summary[op] = {"latency_us": min(r["us"] for r in rs), "asymptotic_GBps": best,
+                       "asymptotic_frac_of_measured_hbm": best / hbm}
+    return {"points": rows, "summary": summary,
+            "bytes_model": "VecAXPY 3, VecCopy 2, VecDot 2 accesses x 8 B per entry (Sec. 5.1); "
+                           "MatMult 12 nnz + 4(n+1) + 8n + 8n"}
 
 
 def c4_batched(g, args):
@@ -779,6 +848,12 @@ def main():
         B.build()
         g = Gpu(local)
         print(json.dumps({"c4_batched": c4_batched(g, args)}), flush=True)
+        return
+    if args.sweep_only:
+        from paper_2011_00715_gb300 import build as B
+        B.build()
+        g = Gpu(local)
+        print(json.dumps({"c2_sweep": c2_sweep(g, args)}), flush=True)
         return
     if args.c5_only:
         from paper_2011_00715_gb300 import build as B

@@ -77,6 +77,25 @@ def test_c1_lap2d5_64(S, orc, alg):
     assert abs(info.bnorm - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
 
 
+def test_c1_matches_stored_golden(S, orc):
+    """The stored C1 fixture (tests/golden, written from the oracle): same
+    iteration count within 2, recurrence residual at the stopping test."""
+    import os
+    g = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "c1_lap2d5_64_pcg.txt")) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = (t.strip() for t in line.split("=", 1))
+                g[k] = v
+    A = I.lap2d5(64)
+    b = orc.spmv(A, I.xstar(A.n, 1))
+    info, x = solve(S, A, b, 1e-8, 10000, algorithm=ALGS["persistent"])
+    assert info.status == gbs.GBS_OK
+    assert abs(info.iters - int(g["iters"])) <= 2
+    assert info.rnorm <= 1e-8 * float.fromhex(g["bnorm"]) * (1 + 1e-12)
+
+
 @pytest.mark.parametrize("alg", sorted(ALGS))
 @pytest.mark.parametrize("maker", [lambda: I.lap3d7(40), lambda: I.var7(33, 27, 21, seed=7),
                                    lambda: I.var27(22, seed=3)])
