@@ -262,8 +262,8 @@ def event_time(torch, fn, reps):
 # the hash of the kernel sources it was taken on; the roofline reports the
 # traffic scaled to the full launch only while the sources are unchanged.
 TRAFFIC_SOURCES = ("paper_2011_00715_gb300/csrc/solve.cu", "paper_2011_00715_gb300/csrc/gbs_impl.cuh")
-TRAFFIC_PER_ITER = {"sha256": "2da970c1391d03e8dacc6b1fa606b9a44d4fd0b6f3c41f12e90896775b119d74",
-                    "bytes": 278839476}
+TRAFFIC_PER_ITER = {"sha256": "d6e0d09bd60a03915c8d7a394a9fc7516b817fdf94022c7b992ada811b04650a",
+                    "bytes": 282315381}
 
 
 def kernel_source_hash():
@@ -582,12 +582,16 @@ def c2_sweep(g, args):
         gbs.gbs_vec_destroy(yv)
         gbs.gbs_mat_destroy(h)
         del A, xt, yt
+    # latency: the shortest call; asymptotic bandwidth: the largest size,
+    # whose working set is many times the 126 MB L2
     summary = {}
     for op in ("VecAXPY", "VecCopy", "VecDot", "MatMult"):
         rs = [r for r in rows if r["op"] == op]
-        best = max(r["GBps"] for r in rs)
-        summary[op] = {"latency_us": min(r["us"] for r in rs), "asymptotic_GBps": best,
-                       "asymptotic_frac_of_measured_hbm": best / hbm}
+        big = max(rs, key=lambda r: r["n"])
+        summary[op] = {"latency_us": min(r["us"] for r in rs), "asymptotic_GBps": big["GBps"],
+                       "asymptotic_n": big["n"],
+                       "asymptotic_frac_of_measured_hbm": big["GBps"] / hbm,
+                       "peak_GBps_any_size": max(r["GBps"] for r in rs)}
     return {"points": rows, "summary": summary,
             "bytes_model": "VecAXPY 3, VecCopy 2, VecDot 2 accesses x 8 B per entry (Sec. 5.1); "
                            "MatMult 12 nnz + 4(n+1) + 8n + 8n"}

@@ -69,6 +69,8 @@ def _load():
         lib.orc_norm2.restype = ctypes.c_double
         lib.orc_axpy.argtypes = [i64, ctypes.c_double, f64p, f64p]
         lib.orc_aypx.argtypes = [i64, ctypes.c_double, f64p, f64p]
+        lib.orc_axpy_fused.argtypes = [i64, ctypes.c_double, f64p, f64p]
+        lib.orc_aypx_fused.argtypes = [i64, ctypes.c_double, f64p, f64p]
         lib.orc_jacobi_dinv.argtypes = [i64, i32p, i32p, f64p, f64p]
         lib.orc_jacobi_dinv.restype = ctypes.c_int
         lib.orc_pcg.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double, i64,
@@ -148,6 +150,20 @@ def aypx(beta, x, y) -> np.ndarray:
     """Returns x + beta y (y is copied, not modified)."""
     xx, yy = _f64(x), _f64(y).copy()
     _load().orc_aypx(len(xx), beta, _p(xx), _p(yy))
+    return yy
+
+
+def axpy_fused(alpha, x, y) -> np.ndarray:
+    """Returns alpha x + y with one rounding per entry (fused multiply-add)."""
+    xx, yy = _f64(x), _f64(y).copy()
+    _load().orc_axpy_fused(len(xx), alpha, _p(xx), _p(yy))
+    return yy
+
+
+def aypx_fused(beta, x, y) -> np.ndarray:
+    """Returns x + beta y with one rounding per entry (fused multiply-add)."""
+    xx, yy = _f64(x), _f64(y).copy()
+    _load().orc_aypx_fused(len(xx), beta, _p(xx), _p(yy))
     return yy
 
 

@@ -135,6 +135,19 @@ void orc_aypx(int64_t n, double beta, const double *x, double *y)
     for (int64_t i = 0; i < n; ++i) y[i] = x[i] + beta * y[i];
 }
 
+/* The same two operations with one rounding per entry (the IEEE fused
+ * multiply-add of C99 fma: the exact alpha x_i + y_i, rounded once), the
+ * way the library's standalone VecAXPY and VecAYPX compute them. */
+void orc_axpy_fused(int64_t n, double alpha, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = fma(alpha, x[i], y[i]);
+}
+
+void orc_aypx_fused(int64_t n, double beta, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = fma(beta, y[i], x[i]);
+}
+
 /* Pairwise (cascade) sum of v[0..n) in binary32: split in halves down to
  * blocks of at most 8, which are summed left to right. */
 static float pairwise_f32(const float *v, int64_t n)

@@ -682,16 +682,15 @@ extern "C" int gbs_vec_get_values(gbs_vec v, void *dst, int memspace)
     return GBS_OK;
 }
 
-// Separately rounded multiply and add (no fused multiply-add), so each
-// standalone vector operation is the correctly rounded sequence of its
-// definition.
+// Rounded product (never fused into an add).
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
 
 // Elementwise kernels.  op: 0 set, 1 copy(y=x), 2 axpy(y=a x+y), 3 aypx(y=x+a y),
-// 4 pointwise (y = x * w), 5 jacobi (y = dinv * x).
+// 4 pointwise (y = x * w), 5 jacobi (y = dinv * x).  AXPY and AYPX round the
+// exact a x + y once (one fused multiply-add per entry): on this GPU FP64
+// operations are scarce enough that a separate multiply and add would make
+// an FP64 AXPY ALU-bound instead of bandwidth-bound.
 template <typename TX, typename TY>
 __global__ void k_elementwise(int op, int64_t n, double a, const TX *__restrict__ x,
                               const TY *__restrict__ w, TY *__restrict__ y)
@@ -701,8 +700,8 @@ __global__ void k_elementwise(int op, int64_t n, double a, const TX *__restrict_
         switch (op) {
         case 0: y[i] = (TY)a; break;
         case 1: y[i] = (TY)x[i]; break;
-        case 2: y[i] = rn_add(rn_mul((TY)a, (TY)x[i]), y[i]); break;
-        case 3: y[i] = rn_add((TY)x[i], rn_mul((TY)a, y[i])); break;
+        case 2: y[i] = fma((TY)a, (TY)x[i], y[i]); break;
+        case 3: y[i] = fma((TY)a, y[i], (TY)x[i]); break;
         case 4: y[i] = rn_mul((TY)x[i], w[i]); break;
         }
     }

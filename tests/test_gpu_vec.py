@@ -34,11 +34,12 @@ def test_axpy_aypx_pointwise_copy_set(S, orc, n):
     y = I.uniform_pm1(1, 1, n)
     xv, xt = S.vec(x)
     yv, yt = S.vec(y)
+    # one fused multiply-add per entry: bitwise the oracle's fused form
     gbs.gbs_vec_axpy(yv, -0.37, xv)
-    assert np.array_equal(S.host(yt), orc.axpy(-0.37, x, y))
+    assert np.array_equal(S.host(yt), orc.axpy_fused(-0.37, x, y))
     y2 = S.host(yt).copy()
     gbs.gbs_vec_aypx(yv, 1.9, xv)
-    assert np.array_equal(S.host(yt), orc.aypx(1.9, x, y2))
+    assert np.array_equal(S.host(yt), orc.aypx_fused(1.9, x, y2))
     wv, wt = S.zeros(n)
     gbs.gbs_vec_pointwise_mult(wv, xv, yv)
     assert np.array_equal(S.host(wt), x * S.host(yt))

@@ -133,6 +133,25 @@ def test_axpy_aypx_roles(orc):
     assert np.array_equal(orc.aypx(2.0, x, y), [21.0, 42.0, 57.0])      # x + 2y
 
 
+def test_fused_axpy_aypx_round_the_exact_value_once(orc):
+    """alpha x + y computed exactly in rationals and rounded once (Python's
+    float(Fraction) rounds to nearest even) equals the fused oracle entry by
+    entry, including cancelling and tiny/huge operands; the separately
+    rounded form differs somewhere, so the pin tells the two apart."""
+    rng = np.random.default_rng(5)
+    n = 400
+    x = rng.standard_normal(n) * 10.0 ** rng.integers(-8, 9, n)
+    y = rng.standard_normal(n) * 10.0 ** rng.integers(-8, 9, n)
+    x[:50] = 1.0 + rng.random(50) * 2.0 ** -30      # alpha x close to -y: cancellation
+    y[:50] = -0.37 * x[:50] + rng.standard_normal(50) * 2.0 ** -40
+    for alpha in (-0.37, 1.9, 3.0 ** 0.5):
+        exact = np.array([float(Fraction(alpha) * Fraction(xi) + Fraction(yi)) for xi, yi in zip(x, y)])
+        assert np.array_equal(orc.axpy_fused(alpha, x, y), exact)
+        exact_aypx = np.array([float(Fraction(xi) + Fraction(alpha) * Fraction(yi)) for xi, yi in zip(x, y)])
+        assert np.array_equal(orc.aypx_fused(alpha, x, y), exact_aypx)
+    assert not np.array_equal(orc.axpy(-0.37, x, y), orc.axpy_fused(-0.37, x, y))
+
+
 def test_jacobi_dinv(orc):
     A = I.var5(5, 4, seed=2)
     st, dinv = orc.jacobi_dinv(A)
