@@ -76,6 +76,11 @@ def _load():
         lib.orc_pcg.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double, i64,
                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double), f64p]
         lib.orc_pcg.restype = ctypes.c_int
+        lib.orc_chebyshev.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, i64,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                      f64p]
+        lib.orc_chebyshev.restype = ctypes.c_int
         lib.orc_pcg_f32.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, f64p, ctypes.c_float, i64,
                                     ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_float)]
         lib.orc_pcg_f32.restype = ctypes.c_int
@@ -184,6 +189,23 @@ def pcg(A, b, rtol, maxit, x0=None, history=False):
     rh = np.full(maxit + 1, np.nan) if history else None
     st = _load().orc_pcg(A.n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), float(rtol), int(maxit),
                          ctypes.byref(it), ctypes.byref(rn), _p(rh) if history else None)
+    out = {"x": x, "status": st, "iters": it.value, "rnorm": rn.value}
+    if history:
+        out["rhist"] = rh[: it.value + 1]
+    return out
+
+
+def chebyshev(A, b, emin, emax, rtol, maxit, x0=None, history=False):
+    """Jacobi-preconditioned Chebyshev iteration for a spectrum of D^-1 A in
+    [emin, emax], in FP64.  Returns dict(x, status, iters, rnorm[, rhist])."""
+    rp, ci, v, bb = _i32(A.rowptr), _i32(A.colidx), _f64(A.vals), _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    it = ctypes.c_int64(0)
+    rn = ctypes.c_double(0.0)
+    rh = np.full(maxit + 1, np.nan) if history else None
+    st = _load().orc_chebyshev(A.n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), float(emin), float(emax),
+                               float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rn),
+                               _p(rh) if history else None)
     out = {"x": x, "status": st, "iters": it.value, "rnorm": rn.value}
     if history:
         out["rhist"] = rh[: it.value + 1]

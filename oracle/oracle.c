@@ -362,3 +362,69 @@ int orc_pcg_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, const
     free(dinv); free(vals32); free(dinv32); free(r32); free(d32); free(r);
     return status;
 }
+
+/*
+ * Jacobi-preconditioned Chebyshev iteration (KSPCHEBYSHEV with PCJACOBI,
+ * the paper's multigrid smoother of Sec. 5.3): Chebyshev acceleration of
+ * the preconditioned Richardson iteration for a spectrum of D^-1 A inside
+ * [emin, emax] (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed.,
+ * Algorithm 12.1, Chebyshev acceleration, with the preconditioned residual
+ * z = D^-1 r in place of r where the direction is formed).
+ *
+ *   theta = (emax + emin) / 2,  delta = (emax - emin) / 2,  sigma = theta / delta
+ *   r = b - A x,  d = z / theta,  rho = 1 / sigma
+ *   repeat:  x += d;  r -= A d;  rho' = 1 / (2 sigma - rho);
+ *            d = rho' rho d + (2 rho' / delta) z;  rho = rho'
+ *
+ * The recurrence is carried as rho = delta / (2 theta - rho delta), so
+ * that d = (rho delta / c) d + (2 / c) z with c = 2 theta - rho delta:
+ * algebraically the same, and delta = 0 (a single eigenvalue) needs no
+ * division by zero.  Stopping test as in orc_pcg, before each iteration.
+ * There are no inner products in the iteration itself.
+ */
+int orc_chebyshev(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                  const double *b, double *x, double emin, double emax, double rtol,
+                  int64_t maxit, int64_t *iters, double *rnorm, double *rhist)
+{
+    *iters = 0;
+    *rnorm = 0.0;
+    if (n < 0 || maxit < 0 || !(rtol >= 0.0) || !(emin > 0.0) || !(emax >= emin) ||
+        isinf(emax))
+        return ORC_ERR_ARG;
+    if (n == 0) return ORC_CONVERGED;
+    double *dinv = malloc(sizeof(double) * n);
+    double *r = malloc(sizeof(double) * n);
+    double *d = malloc(sizeof(double) * n);
+    double *q = malloc(sizeof(double) * n);
+    int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
+    if (status == 0) {
+        const double theta = 0.5 * (emax + emin), delta = 0.5 * (emax - emin);
+        orc_spmv(n, rowptr, colidx, vals, x, q);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        for (int64_t i = 0; i < n; ++i) d[i] = (dinv[i] * r[i]) / theta;
+        double rho = delta / theta;
+        const double bnorm = orc_norm2(n, b);
+        int64_t k = 0;
+        status = ORC_DIVERGED_ITS;
+        for (;;) {
+            const double rn = orc_norm2(n, r);
+            *rnorm = rn;
+            if (rhist) rhist[k] = rn;
+            if (isnan(rn)) { status = ORC_ERR_NAN; break; }
+            if (rn <= rtol * bnorm) { status = ORC_CONVERGED; break; }
+            if (k >= maxit) break;
+            orc_spmv(n, rowptr, colidx, vals, d, q);
+            for (int64_t i = 0; i < n; ++i) x[i] = x[i] + d[i];
+            for (int64_t i = 0; i < n; ++i) r[i] = r[i] - q[i];
+            const double c = 2.0 * theta - rho * delta;
+            const double a1 = (rho * delta) / c, a2 = 2.0 / c;
+            for (int64_t i = 0; i < n; ++i) d[i] = a1 * d[i] + a2 * (dinv[i] * r[i]);
+            rho = delta / c;
+            ++k;
+        }
+        *iters = k;
+    }
+    free(dinv); free(r); free(d); free(q);
+    return status;
+}
+

@@ -35,6 +35,14 @@ MUTANTS = {
     "f32_residual_sign": ("r[i] = -alpha * q[i] + r[i];", "r[i] = alpha * q[i] + r[i];"),
     "mixed_update_unscaled": ("x[i] += rn * (double)d32[i];", "x[i] += (double)d32[i];"),
     "csr_check_allows_duplicates": ("colidx[k] <= colidx[k - 1]", "colidx[k] < colidx[k - 1]"),
+    "cheb_direction_unpreconditioned": ("d[i] = a1 * d[i] + a2 * (dinv[i] * r[i]);",
+                                        "d[i] = a1 * d[i] + a2 * r[i];"),
+    "cheb_rho_frozen": ("rho = delta / c;", "rho = delta / theta;"),
+    "cheb_first_direction_unscaled": ("d[i] = (dinv[i] * r[i]) / theta;", "d[i] = dinv[i] * r[i];"),
+    "cheb_residual_sign": ("r[i] = r[i] - q[i];", "r[i] = r[i] + q[i];"),
+    "cheb_interval_centre_and_radius_swapped": (
+        "const double theta = 0.5 * (emax + emin), delta = 0.5 * (emax - emin);",
+        "const double theta = 0.5 * (emax - emin), delta = 0.5 * (emax + emin);"),
 }
 
 PINS = [
@@ -52,6 +60,9 @@ PINS = [
     lambda o: P.test_pcg_diagonal_matrix_one_step(o),
     lambda o: P.test_pcg_f32_close_to_fp64(o),
     lambda o: P.test_mixed_refinement_reaches_fp64_accuracy(o),
+    lambda o: P.test_chebyshev_error_is_the_scaled_chebyshev_polynomial(o, 5),
+    lambda o: P.test_chebyshev_rate_with_exact_bounds(o),
+    lambda o: P.test_chebyshev_single_eigenvalue_and_arguments(o),
 ]
 
 

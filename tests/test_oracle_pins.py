@@ -353,3 +353,83 @@ def test_mixed_zero_rhs_and_bad_diag(orc):
     assert m["status"] == orc.CONVERGED and m["outer"] == 0
     C = I.CSR(2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 0.0]))
     assert orc.pcg_mixed(C, np.ones(2), 1e-10)["status"] == orc.ERR_DIAG
+
+
+# ------------------------------------------------------------- Chebyshev --
+
+def _cheb_T(k, t):
+    """Chebyshev polynomial of the first kind by its three-term recurrence."""
+    a, b = np.ones_like(t), t
+    if k == 0:
+        return a
+    for _ in range(k - 1):
+        a, b = b, 2 * t * b - a
+    return b
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_chebyshev_error_is_the_scaled_chebyshev_polynomial(orc, k):
+    """After k steps from x0, e_k = p_k(D^-1 A) e_0 with
+    p_k(l) = T_k((theta - l) / delta) / T_k(theta / delta) — for any interval
+    [emin, emax], here one strictly wider than the spectrum; computed from
+    the eigen-decomposition of the symmetric D^-1/2 A D^-1/2."""
+    A = I.var7(5, 4, 3, seed=11, sigma=0.7)
+    n = A.n
+    d = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    d[rows, A.colidx] = A.vals
+    dg = np.diag(d).copy()
+    B = d / np.sqrt(np.outer(dg, dg))
+    lam, Q = np.linalg.eigh(B)
+    emin, emax = 0.9 * lam[0], 1.05 * lam[-1]
+    theta, delta = (emax + emin) / 2, (emax - emin) / 2
+    xs = I.uniform_pm1(3, 0, n)
+    b = d @ xs
+    x0 = I.uniform_pm1(3, 1, n)
+    r = orc.chebyshev(A, b, emin, emax, 0.0, k, x0=x0)
+    assert r["iters"] == k
+    p = _cheb_T(k, (theta - lam) / delta) / _cheb_T(k, np.array([theta / delta]))[0]
+    S, Si = np.diag(np.sqrt(dg)), np.diag(1 / np.sqrt(dg))
+    ek = Si @ Q @ np.diag(p) @ Q.T @ S @ (x0 - xs)
+    assert np.linalg.norm(r["x"] - (xs + ek)) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_chebyshev_rate_with_exact_bounds(orc):
+    """With the exact extreme eigenvalues of D^-1 A (closed form for the 2D
+    Laplacian, D = 4I), ||e_k||_A <= ||e_0||_A / T_k(sigma), and the
+    iteration count meets the bound that implies (x0 = 0, as for CG)."""
+    N = 24
+    A = I.lap2d5(N)
+    c1 = math.cos(math.pi / (N + 1))
+    emin, emax = (4 - 4 * c1) / 4, (4 + 4 * c1) / 4
+    sigma = (emax + emin) / (emax - emin)
+    xs = I.xstar(A.n, 5)
+    b = orc.spmv(A, xs)
+    e0 = math.sqrt(float(xs @ orc.spmv(A, xs)))
+    for k in (5, 20, 60):
+        r = orc.chebyshev(A, b, emin, emax, 0.0, k)
+        e = r["x"] - xs
+        ek = math.sqrt(float(e @ orc.spmv(A, e)))
+        assert ek <= e0 / math.cosh(k * math.acosh(sigma)) * (1 + 1e-9)
+    kappa = emax / emin
+    r = orc.chebyshev(A, b, emin, emax, 1e-8, 100000)
+    # ||r_k|| / ||b|| <= sqrt(kappa) ||e_k||_A / ||e_0||_A <= sqrt(kappa) / T_k(sigma)
+    bound = math.ceil(math.acosh(math.sqrt(kappa) / 1e-8) / math.acosh(sigma))
+    assert r["status"] == 0 and r["iters"] <= bound
+
+
+def test_chebyshev_single_eigenvalue_and_arguments(orc):
+    """D^-1 A = I (a diagonal matrix) with emin = emax = 1: exact after one
+    step; bad intervals are refused; b = 0 stops at once."""
+    n = 7
+    A = I.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32),
+              np.linspace(1.0, 3.0, n))
+    xs = I.uniform_pm1(2, 0, n)
+    b = A.vals * xs
+    r = orc.chebyshev(A, b, 1.0, 1.0, 1e-14, 10)
+    assert r["status"] == 0 and r["iters"] == 1
+    assert np.allclose(r["x"], xs, rtol=1e-15, atol=0)
+    for lo, hi in ((0.0, 1.0), (2.0, 1.0), (-1.0, 1.0), (1.0, math.inf)):
+        assert orc.chebyshev(A, b, lo, hi, 1e-8, 10)["status"] == orc.ERR_ARG
+    r = orc.chebyshev(A, np.zeros(n), 0.5, 2.0, 1e-8, 10)
+    assert r["status"] == 0 and r["iters"] == 0 and not r["x"].any()
