@@ -273,6 +273,23 @@ int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
 /* Result of the last solve issued on the context. */
 int gbs_ksp_last_info(gbs_ctx ctx, gbs_solve_info *info);
 
+/* Jacobi-preconditioned Chebyshev iteration (KSPCHEBYSHEV with PCJACOBI,
+ * the paper's multigrid smoother, Sec. 5.3; Chebyshev acceleration as in
+ * Saad, Iterative Methods for Sparse Linear Systems, Algorithm 12.1, with
+ * D^-1 r where the direction is formed) for A x = b in FP64, given an
+ * interval [emin, emax] that holds the spectrum of D^-1 A (0 < emin <=
+ * emax < inf; for a Dirichlet Laplacian it is known in closed form, and a
+ * wider interval still converges, more slowly).  x holds the initial guess
+ * on entry and the solution on return.  Same stopping test and statuses as
+ * gbs_ksp_solve_cg (no inner products inside the iteration, so no
+ * GBS_ERR_INDEFINITE); info (may be NULL) gets iterations, the final
+ * ||r||_2 (recurrence residual), ||b||_2, device time and the algorithmic
+ * bytes moved.  GBS_ERR_ARG for a bad interval or arguments, GBS_ERR_DIAG
+ * for a missing or non-positive diagonal.  One persistent launch, one grid
+ * barrier per iteration. */
+int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double emax,
+                            double rtol, int maxit, gbs_solve_info *info);
+
 /* Largest system gbs_ksp_solve_cg_noalloc accepts (rows). */
 #define GBS_NOALLOC_MAX_ROWS 262144
 

@@ -521,16 +521,20 @@ __device__ __forceinline__ void gbs_warpq_init(GbsWarpQ &q)
 // across calls.  Returns false if a copy did not complete within
 // timeout_ns; the copies still in flight are then waited for (again with a
 // limit) before returning.
-template <typename V, typename Epi>
-__device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc, int64_t t_begin,
-                                              int64_t t_end, int *s_next,
-                                              const int32_t *__restrict__ rowptr,
-                                              const int32_t *__restrict__ colidx,
-                                              const V *__restrict__ vals, const V *v,
-                                              unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
-                                              const GbsPipeCfg &cfg, uint64_t pol_stream,
-                                              uint64_t pol_keep, unsigned long long timeout_ns,
-                                              Epi &epi)
+//
+// gbs_spmv_pipe_pre is the same with a per-row prefetch: pre(row) runs before
+// the row's nonzeros are gathered (so the loads it issues are in flight with
+// the gathers) and its value is handed to epi(row, sum, vdiag, pre_value).
+template <typename V, typename Pre, typename Epi>
+__device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ tdesc, int64_t t_begin,
+                                                  int64_t t_end, int *s_next,
+                                                  const int32_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ colidx,
+                                                  const V *__restrict__ vals, const V *v,
+                                                  unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
+                                                  const GbsPipeCfg &cfg, uint64_t pol_stream,
+                                                  uint64_t pol_keep, unsigned long long timeout_ns,
+                                                  Pre &pre, Epi &epi)
 {
     constexpr int E = 16 / (int)sizeof(V);   // values per 16 bytes
     const int lane = threadIdx.x & 31;
@@ -582,6 +586,7 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
         const int4 d = q.desc[j];
         const int r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
         if (k1 - k0 > GBS_WT_NNZ) {
+            const auto pv = pre((int64_t)r0);
             V sum = V(0), vd = V(0);
             for (int k = k0 + lane; k < k1; k += 32) {
                 const int c = gbs_ld_stream(colidx + k, pol_stream);
@@ -594,7 +599,7 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
                 sum += __shfl_xor_sync(0xffffffffu, sum, off);
                 vd += __shfl_xor_sync(0xffffffffu, vd, off);
             }
-            if (lane == 0) epi((int64_t)r0, sum, vd);
+            if (lane == 0) epi((int64_t)r0, sum, vd, pv);
         } else {
             if (!gbs_mbar_wait(&q.bar[j], (parity >> j) & 1u, timeout_ns)) {
                 ok = false;
@@ -609,6 +614,7 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
             if (lane < nrows) {
                 const int row = r0 + lane;
                 const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+                const auto pv = pre((int64_t)row);
                 const int beg = srp[row - rb], end = srp[row - rb + 1];
                 V sum = V(0), vd = V(0);
 #pragma unroll 8
@@ -618,7 +624,7 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
                     if (c == row) vd = xv;
                     sum = gbs_mac(sval[k - vb], xv, sum);
                 }
-                epi((int64_t)row, sum, vd);
+                epi((int64_t)row, sum, vd, pv);
             }
         }
         __syncwarp();
@@ -634,6 +640,28 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
     }
     __syncwarp();
     return ok;
+}
+
+// No per-row prefetch.
+struct GbsNoPre {
+    __device__ __forceinline__ int operator()(int64_t) const { return 0; }
+};
+
+template <typename V, typename Epi>
+__device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc, int64_t t_begin,
+                                              int64_t t_end, int *s_next,
+                                              const int32_t *__restrict__ rowptr,
+                                              const int32_t *__restrict__ colidx,
+                                              const V *__restrict__ vals, const V *v,
+                                              unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
+                                              const GbsPipeCfg &cfg, uint64_t pol_stream,
+                                              uint64_t pol_keep, unsigned long long timeout_ns,
+                                              Epi &epi)
+{
+    GbsNoPre pre;
+    auto e = [&](int64_t row, V sum, V vd, int) { epi(row, sum, vd); };
+    return gbs_spmv_pipe_pre<V>(tdesc, t_begin, t_end, s_next, rowptr, colidx, vals, v, wsm, q,
+                                parity, cfg, pol_stream, pol_keep, timeout_ns, pre, e);
 }
 
 #endif  // __CUDACC__

@@ -119,6 +119,8 @@ _SIGS = {
     "gbs_ksp_solve_cg_ex": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.POINTER(gbs_opts),
                              ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
     "gbs_ksp_last_info": ([_VP, ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
+    "gbs_ksp_solve_chebyshev": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
     "gbs_ksp_solve_cg_noalloc": ([_VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(gbs_solve_info)], ctypes.c_int),
     "gbs_ksp_solve_cg_batched": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_int,
@@ -396,6 +398,17 @@ def gbs_ksp_solve_cg_ex(A, b, x, rtol: float, maxit: int, opts: gbs_opts | None 
                                    ctypes.byref(opts) if opts else None, ctypes.byref(info))
     if st not in _RESULT_STATUSES:
         _check(st, "gbs_ksp_solve_cg_ex")
+    return _info(info)
+
+
+def gbs_ksp_solve_chebyshev(A, b, x, emin: float, emax: float, rtol: float, maxit: int) -> SolveInfo:
+    """Jacobi-preconditioned Chebyshev iteration for a spectrum of D^-1 A in
+    [emin, emax].  Result statuses are returned in the SolveInfo."""
+    info = gbs_solve_info()
+    st = lib().gbs_ksp_solve_chebyshev(A, b, x, float(emin), float(emax), float(rtol), int(maxit),
+                                       ctypes.byref(info))
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_chebyshev")
     return _info(info)
 
 
