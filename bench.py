@@ -337,7 +337,11 @@ def run_gbs(args, rank, world, local):
     statuses = {i.status for i in infos}
     iters = [i.iters for i in infos]
     dev_ms = statistics.mean(i.device_ms for i in infos)
-    value = world * args.steps / el_max
+    # every rank ran args.steps solves; the job's rate is all ranks' solves
+    # over the slowest rank's time
+    from paper_2011_00715_gb300 import shard
+    value = shard.job_throughput(args.steps, el, device="cuda") if dist is not None \
+        else args.steps / el
     n, nnz = A.n, A.nnz
     hbm, peak_kind = peaks()
     bpl = iters[0] * bytes_per_iter_fp64(n, nnz)
