@@ -68,6 +68,7 @@ enum { MODE_OUTER = 0, MODE_INNER = 1 };
 // vector load.
 struct BSys {
     const int32_t *rowptr, *colidx, *tdesc;   // tdesc: {row start, nonzero start} per warp tile
+    const int16_t *colrel16;                  // col - row, for FP32 INNER tiles (may be NULL)
     const double *vals, *dinv;
     const float *vals32, *dinv32;
     const double *b;    // n x kp
@@ -149,7 +150,8 @@ struct BWarpQ {
     int unit[GBS_MAX_STAGES];     // S unit of the tile in the stage (-1: none)
     int ai[GBS_MAX_STAGES];       // its system's active index
     int flags[GBS_MAX_STAGES];    // 1: copied into the stage; 2: first tile of the unit;
-                                  // 4: last tile of the unit; 8: INNER step
+                                  // 4: last tile of the unit; 8: INNER step;
+                                  // 16: 16-bit relative column indices
 };
 
 template <typename TI> __device__ __forceinline__ const TI *bvals(const BSys &S);
@@ -234,11 +236,12 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[KP])
 // it from l mod L on (all KP columns at once); the L partial sums are added
 // by a fixed shuffle tree.  acc[c][0] += p_row,c q_row,c (p_row from the
 // diagonal entry's gather).
-template <typename TI, int KP>
+template <typename TI, int KP, bool REL>
 __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char *st,
                                              const GbsPipeCfg &cfg, int4 d, TI (&acc)[KP][2])
 {
-    constexpr int E = 16 / (int)sizeof(TI);
+    using IX = typename std::conditional<REL, int16_t, int32_t>::type;
+    constexpr int E = 16 / (int)sizeof(TI), CE = 16 / (int)sizeof(IX);
     const int lane = threadIdx.x & 31;
     const int li = S.lanes_log, L = 1 << li;
     const int r0 = d.x, k0 = d.y, r1 = d.z;
@@ -250,15 +253,15 @@ __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char 
     for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
     if (act) {
         const TI *sval = reinterpret_cast<const TI *>(st);
-        const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
+        const IX *scol = reinterpret_cast<const IX *>(st + cfg.coloff);
         const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
-        const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+        const int vb = k0 & ~(E - 1), cb = k0 & ~(CE - 1), rb = r0 & ~3;
         const int beg = srp[row - rb], end = srp[row - rb + 1];
         const TI *p = static_cast<const TI *>(S.pi);
         // gathers in flight per lane: as many as the registers allow
 #pragma unroll(KP * sizeof(TI) >= 32 ? 4 : 8)
         for (int e = beg + h; e < end; e += L) {
-            const int c = scol[e - cb];
+            const int c = REL ? row + (int)scol[e - cb] : (int)scol[e - cb];
             const TI a = sval[e - vb];
             TI v[KP];
             vload<TI, KP>(p + (size_t)c * KP, v);
@@ -647,7 +650,8 @@ __device__ __forceinline__ bool s_unit(const BArgs &a, BWarpQ &q, unsigned char 
             parity ^= 1u << j;
         }
         if constexpr (INNER) {
-            if (flags & 1) s_tile_inner<TI, KP>(S, wsm + (size_t)j * cfg.sbytes, cfg, d, acc);
+            if (flags & 16) s_tile_inner<TI, KP, true>(S, wsm + (size_t)j * cfg.sbytes, cfg, d, acc);
+            else if (flags & 1) s_tile_inner<TI, KP, false>(S, wsm + (size_t)j * cfg.sbytes, cfg, d, acc);
             else s_long_inner<TI, KP>(S, d, acc, ps);
         } else {
             s_tile_outer<KP>(S, d, acc, ps);
@@ -755,11 +759,13 @@ __device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *next, unsi
         const int r0 = d_lo.x, k0 = d_lo.y, r1 = d_hi.x, k1 = d_hi.y;
         const int staged = p_mode == MODE_INNER && k1 - k0 <= GBS_WT_NNZ;
         const BSys &S = a.sys[p_slot];
+        const int16_t *rel = S.colrel16;
+        const int rel16 = staged && rel != nullptr;
         q.unit[j] = p_unit;
         q.ai[j] = p_ai;
         q.desc[j] = make_int4(r0, k0, r1, k1);
         q.flags[j] = staged | (p_first << 1) | ((p_lt + 1 == p_le) << 2) |
-                     ((p_mode == MODE_INNER) << 3);
+                     ((p_mode == MODE_INNER) << 3) | (rel16 << 4);
         const TI *vals = bvals<TI>(S);
         const int32_t *colidx = S.colidx, *rowptr = S.rowptr;
         // the next tile: of this unit, or of the next claimed one
@@ -772,15 +778,19 @@ __device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *next, unsi
         }
         if (!staged) return;
         const int vb = k0 & ~(E - 1), ve = (k1 + E - 1) & ~(E - 1);
-        const int cb = k0 & ~3, ce = (k1 + 3) & ~3;
+        const int CE = rel16 ? 8 : 4;   // column indices per 16 bytes
+        const int cb = k0 & ~(CE - 1), ce = (k1 + CE - 1) & ~(CE - 1);
         const int rb = r0 & ~3, re = (r1 + 4) & ~3;
-        const uint32_t bv = (uint32_t)(sizeof(TI) * (ve - vb)), bc = 4u * (uint32_t)(ce - cb),
-                       br = 4u * (uint32_t)(re - rb);
+        const uint32_t bv = (uint32_t)(sizeof(TI) * (ve - vb)),
+                       bc = (uint32_t)((rel16 ? 2 : 4) * (ce - cb)), br = 4u * (uint32_t)(re - rb);
         unsigned char *st = wsm + (size_t)j * cfg.sbytes;
         gbs_mbar_expect_tx(&q.bar[j], bv + bc + br);
         gbs_bulk_g2s(st + cfg.rpoff, rowptr + rb, br, &q.bar[j], ps);
         if (bv) gbs_bulk_g2s(st, vals + vb, bv, &q.bar[j], ps);
-        if (bc) gbs_bulk_g2s(st + cfg.coloff, colidx + cb, bc, &q.bar[j], ps);
+        if (bc) {
+            if (rel16) gbs_bulk_g2s(st + cfg.coloff, rel + cb, bc, &q.bar[j], ps);
+            else gbs_bulk_g2s(st + cfg.coloff, colidx + cb, bc, &q.bar[j], ps);
+        }
     };
     if (lane == 0) {
         claim();
@@ -1191,7 +1201,8 @@ size_t system_bytes(int64_t n, int64_t nnz, int k, int fp64)
 }
 
 // Algorithmic bytes of the steps a slot's system has taken: an INNER step
-// streams the inner-precision values and colidx, rowptr, the p gather and q
+// streams the inner-precision values and column indices (16-bit when the
+// matrix has the compressed form), rowptr, the p gather and q
 // (S), x, p, r, q read and x, r written plus D^-1 (U), r, p read and p
 // written plus D^-1 (P); an OUTER step streams the FP64 values and colidx,
 // rowptr, the x gather, b and r64 (S), r64 read, D^-1 and x_i, r_i, p_i
@@ -1202,7 +1213,8 @@ double slot_model_bytes(const Engine &E, int slot)
     if (!H.used || !H.A) return 0.0;
     const BSysDyn &D = E.h_dyn[slot];
     const double n = (double)H.A->n, nnz = (double)H.A->nnz, kp = H.kp, tsz = E.fp64 ? 8 : 4;
-    const double inner = (tsz + 4) * nnz + 4 * (n + 1) + tsz * n * (8 * kp + 2);
+    const double isz = (!E.fp64 && H.A->colrel16) ? 2 : 4;   // index bytes of INNER tiles
+    const double inner = (tsz + isz) * nnz + 4 * (n + 1) + tsz * n * (8 * kp + 2);
     const double outer = 12 * nnz + 4 * (n + 1) + 32 * n * kp + tsz * n * (3 * kp + 1);
     return D.isteps * inner + D.osteps * outer;
 }
@@ -1269,6 +1281,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     S.rowptr = A->rowptr;
     S.colidx = A->colidx;
     S.tdesc = A->tdesc_lanes[li];
+    S.colrel16 = E.fp64 ? nullptr : A->colrel16;
     S.vals = A->vals;
     S.vals32 = A->vals32;
     S.dinv = A->dinv;
@@ -1377,10 +1390,14 @@ GbsPipeCfg engine_pipe_cfg(const Engine &E, const std::vector<int> &act)
     int v = 16, cl = 16, r = 16;
     for (int s : act) {
         const SlotHost &H = E.slots[s];
-        const GbsPipeCfg &p = E.fp64 ? H.A->pipe64_lanes[H.li] : H.A->pipe32_lanes[H.li];
-        v = std::max(v, p.coloff);
-        cl = std::max(cl, p.rpoff - p.coloff);
-        r = std::max(r, p.sbytes - p.rpoff);
+        // FP32 tiles may carry 16-bit or 32-bit indices: cover both geometries
+        for (int w = 0; w < (E.fp64 ? 1 : 2); ++w) {
+            const GbsPipeCfg &p = E.fp64 ? H.A->pipe64_lanes[H.li]
+                                 : w == 0 ? H.A->pipe32_lanes[H.li] : H.A->pipe16_lanes[H.li];
+            v = std::max(v, p.coloff);
+            cl = std::max(cl, p.rpoff - p.coloff);
+            r = std::max(r, p.sbytes - p.rpoff);
+        }
     }
     GbsPipeCfg cfg;
     cfg.coloff = v;

@@ -244,6 +244,21 @@ __global__ void k_f64_to_f32(int64_t n, const double *a, float *b)
         b[i] = (float)a[i];
 }
 
+// colidx - row as int16 for every nonzero; *overflow = 1 if some difference
+// does not fit (the compressed copy is then discarded).
+__global__ void k_make_rel16(int64_t n, const int32_t *rowptr, const int32_t *colidx, int16_t *rel,
+                             int *overflow)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int64_t d = (int64_t)colidx[k] - i;
+            if (d < -32768 || d > 32767) atomicExch(overflow, 1);
+            else rel[k] = (int16_t)d;
+        }
+    }
+}
+
 static int grid_for(gbs_ctx c, int64_t n, int per_sm = 4)
 {
     int64_t g = (n + GBS_BLOCK - 1) / GBS_BLOCK;
@@ -279,15 +294,15 @@ static void make_tiles(const int32_t *rowptr, int64_t n, std::vector<int32_t> &t
 // Pipeline geometry: every stage must hold the largest copied tile (the
 // 16-byte-aligned supersets of its values, column indices and row pointers).
 static GbsPipeCfg make_pipe_cfg(const std::vector<int32_t> &tiles, const int32_t *rowptr,
-                                int vsize)
+                                int vsize, int isize = 4)
 {
-    const int E = 16 / vsize;
+    const int E = 16 / vsize, CE = 16 / isize;
     int vcap = 0, ccap = 0, rcap = 0;
     for (size_t t = 0; t + 1 < tiles.size(); ++t) {
         const int r0 = tiles[t], r1 = tiles[t + 1], k0 = rowptr[r0], k1 = rowptr[r1];
         if (k1 - k0 > GBS_WT_NNZ) continue;
         const int v = ((k1 + E - 1) & ~(E - 1)) - (k0 & ~(E - 1));
-        const int c = ((k1 + 3) & ~3) - (k0 & ~3);
+        const int c = ((k1 + CE - 1) & ~(CE - 1)) - (k0 & ~(CE - 1));
         const int r = ((r1 + 4) & ~3) - (r0 & ~3);
         if (v > vcap) vcap = v;
         if (c > ccap) ccap = c;
@@ -296,7 +311,7 @@ static GbsPipeCfg make_pipe_cfg(const std::vector<int32_t> &tiles, const int32_t
     auto r16 = [](int b) { return (b + 15) & ~15; };
     GbsPipeCfg cfg;
     cfg.coloff = r16(vsize * vcap);
-    cfg.rpoff = cfg.coloff + r16(4 * ccap);
+    cfg.rpoff = cfg.coloff + r16(isize * ccap);
     cfg.sbytes = cfg.rpoff + r16(4 * rcap);
     if (cfg.sbytes < 16) cfg.sbytes = 16;
     cfg.stages = GBS_WARP_STAGE_BYTES / cfg.sbytes;
@@ -317,6 +332,7 @@ static void mat_free(gbs_mat A)
     cudaFree(A->tdesc);
     cudaFree(A->tdesc_lanes[1]);
     cudaFree(A->tdesc_lanes[2]);
+    cudaFree(A->colrel16);
     free(A);
 }
 
@@ -328,6 +344,7 @@ int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
         A->ntiles_lanes[0] = A->ntiles;
         A->pipe64_lanes[0] = A->pipe64;
         A->pipe32_lanes[0] = A->pipe32;
+        A->pipe16_lanes[0] = A->pipe16;
         return GBS_OK;
     }
     if (A->tdesc_lanes[li]) return GBS_OK;
@@ -356,6 +373,7 @@ int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
     A->ntiles_lanes[li] = (int64_t)tiles.size() - 1;
     A->pipe64_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 8);
     A->pipe32_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 4);
+    A->pipe16_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 4, 2);
     return GBS_OK;
 }
 
@@ -402,6 +420,7 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
     A->pipe64 = make_pipe_cfg(tiles, hrp.data(), 8);
     A->pipe32 = make_pipe_cfg(tiles, hrp.data(), 4);
+    A->pipe16 = make_pipe_cfg(tiles, hrp.data(), 4, 2);
     std::vector<int32_t> tdesc(2 * tiles.size());
     for (size_t t = 0; t < tiles.size(); ++t) {
         tdesc[2 * t] = tiles[t];
@@ -466,6 +485,29 @@ int gbs_mat_ensure_f32(gbs_mat A)
     k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals, A->vals32);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
+    // the compressed column indices of the FP32 paths (Challenge A7: with
+    // 32-bit indices FP32 values save only a third of the matrix bytes)
+    const size_t pad16 = (size_t)((A->nnz + 15) & ~(int64_t)7);
+    int16_t *rel = nullptr;
+    GBS_CUDA_TRY(cudaMalloc(&rel, sizeof(int16_t) * pad16));
+    int *flag = (int *)c->devsmall + 2;   // word 2 of the context's small device buffer
+    cudaError_t e = cudaMemsetAsync(rel, 0, sizeof(int16_t) * pad16, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) {
+        k_make_rel16<<<grid_for(c, A->n), GBS_BLOCK, 0, c->stream>>>(A->n, A->rowptr, A->colidx, rel,
+                                                                     flag);
+        gbs_count_launch(c);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pinned, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(rel);
+        return gbs_cuda_fail(e);
+    }
+    if (*(volatile int *)c->pinned) cudaFree(rel);
+    else A->colrel16 = rel;
     return GBS_OK;
 }
 
@@ -533,12 +575,14 @@ struct StoreEpi {
 // bytes each.  A copy that does not complete within 2 s sets *err, which
 // gbs_ctx_synchronize reports as GBS_ERR_TIMEOUT.  Two launch shapes: 8
 // warps per CTA with 12.8 KB rings (2 CTAs, 16 warps per SM), or with
-// 6.4 KB rings and at most 64 registers (4 CTAs, 32 warps per SM) when the
-// matrix's tiles still fit two stages in 6.4 KB — twice the warps hide the
-// gather latency better (7-point 128^3: 51 -> 41 us in FP64).
-template <typename V, int WB, int MINB>
+// 6.4 KB rings and at most 64 registers (4 CTAs, 32 warps per SM) whenever
+// a stage fits in 6.4 KB (every tile of at most 512 nonzeros does) — twice
+// the warps hide the gather latency better than deeper rings, even with a
+// single stage per warp (measured: 7-point 128^3 FP64 51 -> 41 us, 27-point
+// 96^3 FP32 43 -> 37 us).
+template <typename V, typename IX, int WB, int MINB>
 __global__ void __launch_bounds__(GBS_BLOCK, MINB) k_spmv(int64_t ntiles, const int32_t *tdesc,
-                                                          const int32_t *rowptr, const int32_t *colidx,
+                                                          const int32_t *rowptr, const IX *colidx,
                                                           const V *vals, const V *x, V *y,
                                                           GbsPipeCfg cfg, int *err)
 {
@@ -553,16 +597,17 @@ __global__ void __launch_bounds__(GBS_BLOCK, MINB) k_spmv(int64_t ntiles, const 
     StoreEpi<V> epi{y, pk};
     uint32_t parity = 0;
     const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
-    const bool ok = gbs_spmv_pipe<V>(tdesc, t0, t1, &s_next, rowptr, colidx, vals, x,
-                                     smem + (size_t)warp * WB, s_q[warp], parity, cfg, ps, pk,
-                                     2000000000ull, epi);
+    const bool ok = gbs_spmv_pipe<V, IX>(tdesc, t0, t1, &s_next, rowptr, colidx, vals, x,
+                                         smem + (size_t)warp * WB, s_q[warp], parity, cfg, ps, pk,
+                                         2000000000ull, epi);
     if (!ok && lane == 0) atomicExch(err, 1);
 }
 
-template <typename V, int WB, int MINB>
-static int spmv_launch_shape(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V *y, GbsPipeCfg cfg)
+template <typename V, typename IX, int WB, int MINB>
+static int spmv_launch_shape(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, const V *x, V *y,
+                             GbsPipeCfg cfg)
 {
-    const void *fn = (const void *)k_spmv<V, WB, MINB>;
+    const void *fn = (const void *)k_spmv<V, IX, WB, MINB>;
     const size_t smem = (size_t)WB * GBS_WARPS;
     GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -572,24 +617,24 @@ static int spmv_launch_shape(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V 
     const int64_t cap = (int64_t)c->num_sms * per_sm;
     const int g = (int)(need < cap ? need : cap);
     int *err = (int *)c->devsmall + 1;   // word 1 of the context's small device buffer
-    k_spmv<V, WB, MINB><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tdesc, A->rowptr, A->colidx,
-                                                          vals, x, y, cfg, err);
+    k_spmv<V, IX, WB, MINB><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tdesc, A->rowptr, colidx,
+                                                              vals, x, y, cfg, err);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
     return GBS_OK;
 }
 
-template <typename V>
-static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const V *x, V *y)
+template <typename V, typename IX>
+static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, GbsPipeCfg cfg,
+                       const V *x, V *y)
 {
     constexpr int kSmallRing = GBS_WARP_STAGE_BYTES / 2;
-    GbsPipeCfg cfg = sizeof(V) == 8 ? A->pipe64 : A->pipe32;
     const int small_stages = kSmallRing / cfg.sbytes;
-    if (small_stages >= 2) {
+    if (small_stages >= 1) {
         cfg.stages = small_stages < GBS_MAX_STAGES ? small_stages : GBS_MAX_STAGES;
-        return spmv_launch_shape<V, kSmallRing, 4>(c, A, vals, x, y, cfg);
+        return spmv_launch_shape<V, IX, kSmallRing, 4>(c, A, vals, colidx, x, y, cfg);
     }
-    return spmv_launch_shape<V, GBS_WARP_STAGE_BYTES, 1>(c, A, vals, x, y, cfg);
+    return spmv_launch_shape<V, IX, GBS_WARP_STAGE_BYTES, 1>(c, A, vals, colidx, x, y, cfg);
 }
 
 extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
@@ -601,10 +646,16 @@ extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
     if (A->n == 0) return GBS_OK;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
     if (x->dtype == GBS_F64)
-        return spmv_launch<double>(c, A, A->vals, (const double *)x->data, (double *)y->data);
+        return spmv_launch<double, int32_t>(c, A, A->vals, A->colidx, A->pipe64,
+                                            (const double *)x->data, (double *)y->data);
     int st = gbs_mat_ensure_f32(A);
     if (st) return st;
-    return spmv_launch<float>(c, A, A->vals32, (const float *)x->data, (float *)y->data);
+    // FP32: the compressed 16-bit column indices where the matrix allows them
+    if (A->colrel16)
+        return spmv_launch<float, int16_t>(c, A, A->vals32, A->colrel16, A->pipe16,
+                                           (const float *)x->data, (float *)y->data);
+    return spmv_launch<float, int32_t>(c, A, A->vals32, A->colidx, A->pipe32, (const float *)x->data,
+                                       (float *)y->data);
 }
 
 // --------------------------------------------------------------- vector --

@@ -71,6 +71,11 @@ struct gbs_mat_s {
     int32_t *tdesc_lanes[3];
     int64_t ntiles_lanes[3];
     GbsPipeCfg pipe64_lanes[3], pipe32_lanes[3];
+    // compressed column indices for the FP32 paths: col - row as int16, made
+    // with vals32 when every |col - row| <= 32767 (else NULL); their stage
+    // geometry (FP32 values, 16-bit indices) per tiling
+    int16_t *colrel16;
+    GbsPipeCfg pipe16, pipe16_lanes[3];
 };
 
 struct gbs_vec_s {
@@ -169,6 +174,13 @@ __device__ __forceinline__ int32_t gbs_ld_stream(const int32_t *p, uint64_t pol)
     int32_t v;
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
                  : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int16_t gbs_ld_stream(const int16_t *p, uint64_t pol)
+{
+    short v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s16 %0, [%1], %2;"
+                 : "=h"(v) : "l"(p), "l"(pol));
     return v;
 }
 __device__ __forceinline__ double gbs_ld_stream(const double *p, uint64_t pol)
@@ -507,6 +519,12 @@ __device__ __forceinline__ void gbs_warpq_init(GbsWarpQ &q)
     __syncwarp();
 }
 
+// Column of a stored index: 32-bit indices are absolute; 16-bit ones are
+// relative to the row (col - row), the compressed form FP32 paths use when
+// every |col - row| of the matrix fits.
+__device__ __forceinline__ int gbs_col(int32_t c, int) { return c; }
+__device__ __forceinline__ int gbs_col(int16_t c, int row) { return row + (int)c; }
+
 // y = A v over the warp tiles [t_begin, t_end), shared by the warps of a
 // CTA: lane 0 of each warp claims the next unclaimed tile from *s_next
 // (a CTA-shared counter, zero on entry) one step ahead, loads its
@@ -522,21 +540,23 @@ __device__ __forceinline__ void gbs_warpq_init(GbsWarpQ &q)
 // timeout_ns; the copies still in flight are then waited for (again with a
 // limit) before returning.
 //
+// The column indices are int32 (absolute) or int16 (relative to the row).
 // gbs_spmv_pipe_pre is the same with a per-row prefetch: pre(row) runs before
 // the row's nonzeros are gathered (so the loads it issues are in flight with
 // the gathers) and its value is handed to epi(row, sum, vdiag, pre_value).
-template <typename V, typename Pre, typename Epi>
+template <typename V, typename IX, typename Pre, typename Epi>
 __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ tdesc, int64_t t_begin,
                                                   int64_t t_end, int *s_next,
                                                   const int32_t *__restrict__ rowptr,
-                                                  const int32_t *__restrict__ colidx,
+                                                  const IX *__restrict__ colidx,
                                                   const V *__restrict__ vals, const V *v,
                                                   unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
                                                   const GbsPipeCfg &cfg, uint64_t pol_stream,
                                                   uint64_t pol_keep, unsigned long long timeout_ns,
                                                   Pre &pre, Epi &epi)
 {
-    constexpr int E = 16 / (int)sizeof(V);   // values per 16 bytes
+    constexpr int E = 16 / (int)sizeof(V);    // values per 16 bytes
+    constexpr int CE = 16 / (int)sizeof(IX);  // column indices per 16 bytes
     const int lane = threadIdx.x & 31;
     const int NS = cfg.stages;
     // lane 0: the next claimed tile and its descriptor, fetched one step ahead
@@ -561,10 +581,10 @@ __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ td
         claim();
         if (k1 - k0 > GBS_WT_NNZ) return;
         const int vb = k0 & ~(E - 1), ve = (k1 + E - 1) & ~(E - 1);
-        const int cb = k0 & ~3, ce = (k1 + 3) & ~3;
+        const int cb = k0 & ~(CE - 1), ce = (k1 + CE - 1) & ~(CE - 1);
         const int rb = r0 & ~3, re = (r1 + 4) & ~3;
-        const uint32_t bv = (uint32_t)(sizeof(V) * (ve - vb)), bc = 4u * (uint32_t)(ce - cb),
-                       br = 4u * (uint32_t)(re - rb);
+        const uint32_t bv = (uint32_t)(sizeof(V) * (ve - vb)),
+                       bc = (uint32_t)(sizeof(IX) * (ce - cb)), br = 4u * (uint32_t)(re - rb);
         unsigned char *st = wsm + (size_t)j * cfg.sbytes;
         gbs_mbar_expect_tx(&q.bar[j], bv + bc + br);
         gbs_bulk_g2s(st + cfg.rpoff, rowptr + rb, br, &q.bar[j], pol_stream);
@@ -589,7 +609,7 @@ __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ td
             const auto pv = pre((int64_t)r0);
             V sum = V(0), vd = V(0);
             for (int k = k0 + lane; k < k1; k += 32) {
-                const int c = gbs_ld_stream(colidx + k, pol_stream);
+                const int c = gbs_col(gbs_ld_stream(colidx + k, pol_stream), r0);
                 const V xv = gbs_ld(v + c, pol_keep);
                 if (c == r0) vd = xv;
                 sum = gbs_mac(gbs_ld_stream(vals + k, pol_stream), xv, sum);
@@ -608,18 +628,18 @@ __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ td
             parity ^= 1u << j;
             const unsigned char *st = wsm + (size_t)j * cfg.sbytes;
             const V *sval = reinterpret_cast<const V *>(st);
-            const int32_t *scol = reinterpret_cast<const int32_t *>(st + cfg.coloff);
+            const IX *scol = reinterpret_cast<const IX *>(st + cfg.coloff);
             const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
             const int nrows = r1 - r0;
             if (lane < nrows) {
                 const int row = r0 + lane;
-                const int vb = k0 & ~(E - 1), cb = k0 & ~3, rb = r0 & ~3;
+                const int vb = k0 & ~(E - 1), cb = k0 & ~(CE - 1), rb = r0 & ~3;
                 const auto pv = pre((int64_t)row);
                 const int beg = srp[row - rb], end = srp[row - rb + 1];
                 V sum = V(0), vd = V(0);
 #pragma unroll 8
                 for (int k = beg; k < end; ++k) {
-                    const int c = scol[k - cb];
+                    const int c = gbs_col(scol[k - cb], row);
                     const V xv = gbs_ld(v + c, pol_keep);
                     if (c == row) vd = xv;
                     sum = gbs_mac(sval[k - vb], xv, sum);
@@ -647,11 +667,11 @@ struct GbsNoPre {
     __device__ __forceinline__ int operator()(int64_t) const { return 0; }
 };
 
-template <typename V, typename Epi>
+template <typename V, typename IX, typename Epi>
 __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc, int64_t t_begin,
                                               int64_t t_end, int *s_next,
                                               const int32_t *__restrict__ rowptr,
-                                              const int32_t *__restrict__ colidx,
+                                              const IX *__restrict__ colidx,
                                               const V *__restrict__ vals, const V *v,
                                               unsigned char *wsm, GbsWarpQ &q, uint32_t &parity,
                                               const GbsPipeCfg &cfg, uint64_t pol_stream,
@@ -660,8 +680,8 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
 {
     GbsNoPre pre;
     auto e = [&](int64_t row, V sum, V vd, int) { epi(row, sum, vd); };
-    return gbs_spmv_pipe_pre<V>(tdesc, t_begin, t_end, s_next, rowptr, colidx, vals, v, wsm, q,
-                                parity, cfg, pol_stream, pol_keep, timeout_ns, pre, e);
+    return gbs_spmv_pipe_pre<V, IX>(tdesc, t_begin, t_end, s_next, rowptr, colidx, vals, v, wsm, q,
+                                    parity, cfg, pol_stream, pol_keep, timeout_ns, pre, e);
 }
 
 #endif  // __CUDACC__

@@ -63,6 +63,7 @@ struct PcgArgs {
     const int32_t *tdesc;
     const int32_t *rowptr;
     const int32_t *colidx;
+    const int16_t *colrel16;   // col - row (FP32 inner loop, when the matrix has it)
     const double *vals;
     const float *vals32;
     const double *dinv;
@@ -109,8 +110,9 @@ __device__ __forceinline__ int pcg_check(T rn, T rho, T tol, int k, int maxit)
 // the same in every thread of every CTA.  The scalar recurrences (rho,
 // ||r||, alpha, beta, the stopping test) run in thread 0 of each CTA only;
 // *iters, *rnorm_out and *bnorm_out are valid in thread 0.
-template <typename T>
-__device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T *bT, T *xT, T *rT,
+template <typename T, typename IX>
+__device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const T *dinv, const T *bT,
+                        T *xT, T *rT,
                         T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
                         int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no,
                         unsigned char *wsm, GbsWarpQ &wq, uint32_t &parity, int *s_next,
@@ -140,7 +142,7 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
             acc[1] += ri * ri;
             acc[2] += bi * bi;
         };
-        if (!gbs_spmv_pipe<T>(a.tdesc, t0, t1, s_next, a.rowptr, a.colidx, vals, xT, wsm, wq,
+        if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, xT, wsm, wq,
                               parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
@@ -191,7 +193,7 @@ __device__ int pcg_loop(const PcgArgs &a, const T *vals, const T *dinv, const T 
             gbs_st(qT + i, s, pk);
             pq[0] += p_i * s;
         };
-        if (!gbs_spmv_pipe<T>(a.tdesc, t0, t1, s_next, a.rowptr, a.colidx, vals, pT, wsm, wq,
+        if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, pT, wsm, wq,
                               parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
@@ -323,7 +325,8 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
     uint32_t parity = 0;
     int iters = 0, barrier_no = 0;
     double rn = 0.0, bn = 0.0;
-    int st = pcg_loop<double>(a, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol,
+    int st = pcg_loop<double, int32_t>(a, a.colidx, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q,
+                                       a.part64, a.rtol,
                               a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no,
                               smem + (size_t)warp * GBS_WARP_STAGE_BYTES, s_q[warp], parity,
                               &s_next, a.pipe64, sm, ctl, &s_flag);
@@ -339,6 +342,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
 
 // Mixed precision: FP64 iterative refinement around the FP32 inner loop.
 // The refinement scalars live in thread 0 of each CTA, like the inner ones.
+// IX: the column indices of the FP32 inner loop (int32, or the compressed
+// 16-bit col - row); the FP64 residual always reads the int32 indices.
+template <typename IX>
 __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
                 acc[0] += ri * ri;
                 if (first) acc[1] += bi * bi;
             };
-            if (!gbs_spmv_pipe<double>(a.tdesc, t0, t1, &s_next, a.rowptr, a.colidx, a.vals, a.x,
+            if (!gbs_spmv_pipe<double, int32_t>(a.tdesc, t0, t1, &s_next, a.rowptr, a.colidx, a.vals, a.x,
                                        wsm, s_q[warp], parity, a.pipe64, ps, pk, a.timeout_ns,
                                        epi) &&
                 (threadIdx.x & 31) == 0)
@@ -428,7 +434,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
             gbs_st(a.b32 + i, (float)(gbs_ld(a.r + i, pk) * inv), pk);
         int kin = 0;
         float rin = 0.f, bin = 0.f;
-        const int sti = pcg_loop<float>(a, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
+        const IX *col32 = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
+                                          : (const IX *)(const void *)a.colidx;
+        const int sti = pcg_loop<float, IX>(a, col32, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
                                         a.q32, a.part32, (float)a.inner_rtol, a.maxit, true, &kin,
                                         &rin, &bin, &barrier_no, wsm, s_q[warp], parity, &s_next,
                                         a.pipe32, sm32, ctl32, &s_flag);
@@ -530,7 +538,9 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         int st = gbs_mat_ensure_f32(A);
         if (st) return st;
     }
-    const void *fn = mixed ? (const void *)k_pcg_mixed : (const void *)k_pcg_fp64;
+    const bool rel16 = mixed && A->colrel16;
+    const void *fn = !mixed ? (const void *)k_pcg_fp64
+                     : rel16 ? (const void *)k_pcg_mixed<int16_t> : (const void *)k_pcg_mixed<int32_t>;
     const int G = coop_grid(c, fn, A->ntiles);
     if (G < 0) return GBS_ERR_CUDA;
     const int64_t n = A->n;
@@ -565,6 +575,10 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         a.q = (double *)v; v += vec64;
     }
     fill_matrix_args(a, A);
+    if (rel16) {   // the FP32 inner loop streams 16-bit column indices
+        a.colrel16 = A->colrel16;
+        a.pipe32 = A->pipe16;
+    }
     a.b = (const double *)b->data;
     a.x = (double *)x->data;
     a.rtol = rtol;

@@ -191,3 +191,20 @@ def test_batched_tune_decision_is_cached(S, orc):
     assert gbs.gbs_batched_tune(F.ctx, hf, 3, gbs.GBS_MODE_FP64) == 2
     gbs.gbs_mat_destroy(hf)
     gbs.gbs_ctx_destroy(F.ctx)
+
+
+def test_batched_mixes_compressed_and_full_column_indices(S, orc):
+    """One batch holding a system whose columns fit 16-bit relative indices
+    and one whose columns do not (a coupling between rows 0 and n - 1 with
+    n = 40000): both FP32 tile kinds go through the same stage ring."""
+    from test_gpu_spmv import far_coupled_chain
+    far = far_coupled_chain(40000, 6)
+    near = I.var7(20, 18, 16, seed=31)
+    mats = [(far, 2), (near, 3)]
+    rhs = [rhs_for(orc, A, k, i) for i, (A, k) in enumerate(mats)]
+    st, its, rns, sts, xs = run_batch(S, mats, rhs, gbs.GBS_MODE_MIXED)
+    assert st == gbs.GBS_OK and np.all(sts == gbs.GBS_OK)
+    for (A, k), b, x in zip(mats, rhs, xs):
+        for c in range(k):
+            bc, xc = b[c * A.n:(c + 1) * A.n], x[c * A.n:(c + 1) * A.n]
+            assert np.linalg.norm(bc - orc.spmv(A, xc)) <= 1e-10 * np.linalg.norm(bc)

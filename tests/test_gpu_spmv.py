@@ -189,3 +189,54 @@ def test_spmv_full_size_3d7_sampled(S, orc):
     c = np.arange(A.n)
     miss = sum((v == 0).astype(int) + (v == 127) for v in (c % 128, (c // 128) % 128, c // 16384))
     assert np.array_equal(ones, miss.astype(float))
+
+
+def far_coupled_chain(n, seed):
+    """SPD chain with one symmetric coupling between rows 0 and n - 1: a
+    column more than 32767 away from its row once n > 32768, so the
+    compressed 16-bit column indices cannot represent the matrix."""
+    rng = np.random.default_rng(seed)
+    w = 0.5 + rng.random(n - 1)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        d = 0.1 + (w[i - 1] if i > 0 else 0.0) + (w[i] if i < n - 1 else 0.0)
+        ent = []
+        if i == 0:
+            d += 0.25
+        if i == n - 1:
+            d += 0.25
+        if i > 0:
+            ent.append((i - 1, -w[i - 1]))
+        ent.append((i, d))
+        if i < n - 1:
+            ent.append((i + 1, -w[i]))
+        if i == 0:
+            ent.append((n - 1, -0.25))
+        if i == n - 1:
+            ent.insert(0, (0, -0.25))
+        for c, v in ent:
+            rows.append(i)
+            cols.append(c)
+            vals.append(v)
+    rowptr = np.zeros(n + 1, np.int32)
+    np.add.at(rowptr, np.array(rows) + 1, 1)
+    return I.CSR(n, np.cumsum(rowptr).astype(np.int32), np.array(cols, np.int32), np.array(vals))
+
+
+@pytest.mark.parametrize("n", [30000, 40000])
+def test_fp32_paths_with_and_without_compressed_indices(S, orc, n):
+    """n = 30000 fits 16-bit relative columns, n = 40000 does not: the FP32
+    MatMult is bitwise the oracle's either way, and a mixed-precision solve
+    converges to the FP64 tolerance."""
+    A = far_coupled_chain(n, 5)
+    x = I.uniform_pm1(8, 0, n).astype(np.float32)
+    assert np.array_equal(run(S, A, x, np.float32), orc.spmv_f32(A, x))
+    b = orc.spmv(A, I.xstar(n, 8))
+    h = S.mat(A)
+    bv, bt = S.vec(b)
+    xv, xt = S.zeros(n)
+    info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, 1e-10, 50000, gbs.gbs_opts_default(mode=gbs.GBS_MODE_MIXED))
+    assert info.status == gbs.GBS_OK
+    xs = S.host(xt)
+    assert np.linalg.norm(b - orc.spmv(A, xs)) <= 1e-10 * np.linalg.norm(b)
+    gbs.gbs_mat_destroy(h)
