@@ -81,6 +81,9 @@ def _load():
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                       f64p]
         lib.orc_chebyshev.restype = ctypes.c_int
+        lib.orc_coo_to_csr.argtypes = [i64, i64, i64, i32p, i32p, f64p, i32p, i32p, f64p,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_coo_to_csr.restype = ctypes.c_int
         lib.orc_pcg_f32.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, f64p, ctypes.c_float, i64,
                                     ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_float)]
         lib.orc_pcg_f32.restype = ctypes.c_int
@@ -210,6 +213,20 @@ def chebyshev(A, b, emin, emax, rtol, maxit, x0=None, history=False):
     if history:
         out["rhist"] = rh[: it.value + 1]
     return out
+
+
+def coo_to_csr(nrows, ncols, ti, tj, v):
+    """Returns (status, rowptr, colidx, vals): triplets (ti, tj, v) assembled
+    into CSR, duplicates summed in triplet order."""
+    ti, tj, v = _i32(ti), _i32(tj), _f64(v)
+    m = len(ti)
+    rowptr = np.zeros(nrows + 1, dtype=np.int32)
+    colidx = np.zeros(max(m, 1), dtype=np.int32)
+    vals = np.zeros(max(m, 1))
+    nout = ctypes.c_int64(0)
+    st = _load().orc_coo_to_csr(int(nrows), int(ncols), m, _p(ti), _p(tj), _p(v), _p(rowptr),
+                                _p(colidx), _p(vals), ctypes.byref(nout))
+    return st, rowptr, colidx[: nout.value].copy(), vals[: nout.value].copy()
 
 
 def pcg_f32(A, b, rtol, maxit):

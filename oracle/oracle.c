@@ -428,3 +428,61 @@ int orc_chebyshev(int64_t n, const int32_t *rowptr, const int32_t *colidx, const
     return status;
 }
 
+/*
+ * Assembly from coordinate triplets (MatSetPreallocationCOO followed by
+ * MatSetValuesCOO, Sec. 4): triplet k adds v[k] at (ti[k], tj[k]).  The
+ * result is CSR with rows in order and columns strictly increasing;
+ * duplicates of one (row, column) are summed in the order the triplets
+ * come (k increasing), left to right.  rowptr has nrows + 1 entries; colidx
+ * and vals hold at most nnz_in entries; *nnz_out gets the count.  An index
+ * out of range gives ORC_ERR_CSR.  Plain counting sort by row (stable),
+ * then insertion sort by column within each row (stable), then a merge.
+ */
+int orc_coo_to_csr(int64_t nrows, int64_t ncols, int64_t nnz_in, const int32_t *ti,
+                   const int32_t *tj, const double *v, int32_t *rowptr, int32_t *colidx,
+                   double *vals, int64_t *nnz_out)
+{
+    *nnz_out = 0;
+    if (nrows < 0 || ncols < 0 || nnz_in < 0) return ORC_ERR_ARG;
+    for (int64_t k = 0; k < nnz_in; ++k)
+        if (ti[k] < 0 || ti[k] >= nrows || tj[k] < 0 || tj[k] >= ncols) return ORC_ERR_CSR;
+    int64_t *start = calloc((size_t)nrows + 1, sizeof(int64_t));
+    int64_t *order = malloc(sizeof(int64_t) * (size_t)(nnz_in > 0 ? nnz_in : 1));
+    for (int64_t k = 0; k < nnz_in; ++k) start[ti[k] + 1] += 1;
+    for (int64_t r = 0; r < nrows; ++r) start[r + 1] += start[r];
+    int64_t *fill = calloc((size_t)nrows + 1, sizeof(int64_t));
+    for (int64_t k = 0; k < nnz_in; ++k) order[start[ti[k]] + fill[ti[k]]++] = k;
+    int64_t out = 0;
+    rowptr[0] = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t a = start[r], b = start[r + 1];
+        for (int64_t p = a + 1; p < b; ++p) {        /* stable insertion sort by column */
+            const int64_t key = order[p];
+            int64_t q = p - 1;
+            while (q >= a && tj[order[q]] > tj[key]) {
+                order[q + 1] = order[q];
+                --q;
+            }
+            order[q + 1] = key;
+        }
+        for (int64_t p = a; p < b;) {
+            const int32_t c = tj[order[p]];
+            double s = v[order[p]];
+            ++p;
+            while (p < b && tj[order[p]] == c) {
+                s = s + v[order[p]];
+                ++p;
+            }
+            colidx[out] = c;
+            vals[out] = s;
+            ++out;
+        }
+        rowptr[r + 1] = (int32_t)out;
+    }
+    *nnz_out = out;
+    free(start);
+    free(order);
+    free(fill);
+    return ORC_CONVERGED;
+}
+

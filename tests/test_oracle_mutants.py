@@ -43,6 +43,10 @@ MUTANTS = {
     "cheb_interval_centre_and_radius_swapped": (
         "const double theta = 0.5 * (emax + emin), delta = 0.5 * (emax - emin);",
         "const double theta = 0.5 * (emax - emin), delta = 0.5 * (emax + emin);"),
+    "coo_unstable_column_sort": ("while (q >= a && tj[order[q]] > tj[key]) {",
+                                 "while (q >= a && tj[order[q]] >= tj[key]) {"),
+    "coo_duplicates_not_merged": ("while (p < b && tj[order[p]] == c) {", "while (0) {"),
+    "coo_last_duplicate_wins": ("s = s + v[order[p]];", "s = v[order[p]];"),
 }
 
 PINS = [
@@ -63,6 +67,9 @@ PINS = [
     lambda o: P.test_chebyshev_error_is_the_scaled_chebyshev_polynomial(o, 5),
     lambda o: P.test_chebyshev_rate_with_exact_bounds(o),
     lambda o: P.test_chebyshev_single_eigenvalue_and_arguments(o),
+    lambda o: P.test_coo_assembly_equals_dense_accumulation_and_scipy(o),
+    lambda o: P.test_coo_duplicates_are_summed_in_triplet_order(o),
+    lambda o: P.test_coo_degenerate_and_invalid(o),
 ]
 
 

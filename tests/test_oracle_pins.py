@@ -433,3 +433,73 @@ def test_chebyshev_single_eigenvalue_and_arguments(orc):
         assert orc.chebyshev(A, b, lo, hi, 1e-8, 10)["status"] == orc.ERR_ARG
     r = orc.chebyshev(A, np.zeros(n), 0.5, 2.0, 1e-8, 10)
     assert r["status"] == 0 and r["iters"] == 0 and not r["x"].any()
+
+
+# ------------------------------------------------------------- COO -> CSR --
+
+def _random_triplets(seed, nrows, ncols, m, dup_rows=True):
+    rng = np.random.default_rng(seed)
+    ti = rng.integers(0, nrows, m).astype(np.int32)
+    tj = rng.integers(0, ncols, m).astype(np.int32)
+    if dup_rows:                      # force many duplicates
+        ti[m // 2:] = ti[: m - m // 2]
+        tj[m // 2:] = tj[: m - m // 2]
+    return ti, tj, rng
+
+
+def test_coo_assembly_equals_dense_accumulation_and_scipy(orc):
+    """Integer values (exact in FP64): the assembled CSR is the dense sum of
+    the triplets, with exactly the structural pattern of the triplets, rows
+    in order and columns strictly increasing; scipy's coo -> csr agrees."""
+    sp = pytest.importorskip("scipy.sparse")
+    for seed, (nr, nc, m) in enumerate([(40, 50, 600), (7, 3, 100), (200, 200, 50)]):
+        ti, tj, rng = _random_triplets(seed, nr, nc, m)
+        v = rng.integers(-1000, 1000, m).astype(np.float64)
+        st, rp, ci, vals = orc.coo_to_csr(nr, nc, ti, tj, v)
+        assert st == 0
+        assert orc.csr_check(nr, nc, rp, ci) == 0
+        dense = np.zeros((nr, nc))
+        np.add.at(dense, (ti, tj), v)
+        got = np.zeros((nr, nc))
+        rows = np.repeat(np.arange(nr), np.diff(rp))
+        got[rows, ci] = vals
+        assert np.array_equal(got, dense)
+        assert set(zip(rows.tolist(), ci.tolist())) == set(zip(ti.tolist(), tj.tolist()))
+        S = sp.coo_matrix((v, (ti, tj)), shape=(nr, nc)).tocsr()
+        S.sort_indices()
+        assert np.array_equal(S.indptr, rp) and np.array_equal(S.indices, ci)
+        assert np.array_equal(S.data, vals)
+
+
+def test_coo_duplicates_are_summed_in_triplet_order(orc):
+    """Magnitudes chosen so that the order of a duplicate sum changes the
+    result: the assembled value is the left-to-right sum in triplet order
+    (a plain Python loop over the few triplets)."""
+    ti = np.array([0, 1, 0, 0, 1, 1, 0], np.int32)
+    tj = np.array([0, 2, 0, 0, 2, 2, 1], np.int32)
+    v = np.array([1e16, 3.0, 1.0, -1e16, -3e16, 3e16, 7.0])
+    st, rp, ci, vals = orc.coo_to_csr(2, 3, ti, tj, v)
+    assert st == 0 and list(rp) == [0, 2, 3] and list(ci) == [0, 1, 2]
+    expect = {}
+    for a, b, x in zip(ti.tolist(), tj.tolist(), v.tolist()):
+        expect[(a, b)] = expect[(a, b)] + x if (a, b) in expect else x
+    assert vals[0] == expect[(0, 0)] == 0.0          # (1e16 + 1) - 1e16 rounds to 0
+    assert vals[1] == 7.0 and vals[2] == expect[(1, 2)]
+    rng = np.random.default_rng(9)
+    ti, tj, _ = _random_triplets(9, 30, 30, 400)
+    v = rng.standard_normal(400) * 10.0 ** rng.integers(-12, 13, 400)
+    st, rp, ci, vals = orc.coo_to_csr(30, 30, ti, tj, v)
+    expect = {}
+    for a, b, x in zip(ti.tolist(), tj.tolist(), v.tolist()):
+        expect[(a, b)] = expect[(a, b)] + x if (a, b) in expect else x
+    rows = np.repeat(np.arange(30), np.diff(rp))
+    assert all(vals[k] == expect[(int(rows[k]), int(ci[k]))] for k in range(len(ci)))
+
+
+def test_coo_degenerate_and_invalid(orc):
+    st, rp, ci, vals = orc.coo_to_csr(4, 4, [], [], [])
+    assert st == 0 and list(rp) == [0] * 5 and len(ci) == 0
+    assert orc.coo_to_csr(3, 3, [0, 3], [0, 0], [1.0, 1.0])[0] == orc.ERR_CSR
+    assert orc.coo_to_csr(3, 3, [0, 1], [0, -1], [1.0, 1.0])[0] == orc.ERR_CSR
+    st, rp, ci, vals = orc.coo_to_csr(0, 0, [], [], [])
+    assert st == 0 and list(rp) == [0]
