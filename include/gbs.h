@@ -192,6 +192,32 @@ int gbs_mat_destroy(gbs_mat A);
  * x (GBS_ERR_ARG).  Asynchronous. */
 int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y);
 
+/* Assemble a matrix on the device from nnz_in coordinate triplets
+ * (MatSetPreallocationCOO + MatSetValuesCOO, Sec. 4): triplet k adds v[k]
+ * at row i[k], column j[k] (int32 indices, FP64 values; any order, repeats
+ * allowed).  Repeated (row, column) pairs are summed in triplet order (k
+ * increasing, left to right), so the result does not depend on thread
+ * scheduling.  The arrays live in memspace (host or device) and are not
+ * kept.  The matrix is then set up as by gbs_mat_create_aij (validation,
+ * Jacobi diagonal, tiling) and remembers the triplet-to-entry map, so
+ * gbs_mat_set_values_coo can refill its values.  GBS_ERR_CSR if an index
+ * is out of range; GBS_ERR_ARG for bad arguments or more than 2^31 - 1
+ * distinct entries; GBS_ERR_OOM. */
+int gbs_mat_create_coo(gbs_ctx ctx, int64_t nrows, int64_t ncols, int64_t nnz_in, const int32_t *i,
+                       const int32_t *j, const double *v, int memspace, gbs_mat *out);
+
+/* New values for the triplets of a matrix made by gbs_mat_create_coo (the
+ * same count and order as at creation), summed the same way; the Jacobi
+ * diagonal and the FP32 copy follow.  GBS_ERR_ARG if A was not made from
+ * triplets. */
+int gbs_mat_set_values_coo(gbs_mat A, const double *v, int memspace);
+
+/* Copy the matrix's CSR out (MatGetRowIJ / MatSeqAIJGetArray, Sec. 4):
+ * rowptr (nrows + 1), colidx and vals (nnz entries each, see
+ * gbs_mat_get_info) into caller buffers in memspace; any pointer may be
+ * NULL to skip that array.  Blocks until the copies are done. */
+int gbs_mat_get_csr(gbs_mat A, int32_t *rowptr, int32_t *colidx, double *vals, int memspace);
+
 /* ------------------------------------------------------------ vector --- */
 
 /* VecCreate: a device vector of n entries of `dtype`, owned by the library,

@@ -333,6 +333,8 @@ static void mat_free(gbs_mat A)
     cudaFree(A->tdesc_lanes[1]);
     cudaFree(A->tdesc_lanes[2]);
     cudaFree(A->colrel16);
+    cudaFree(A->coo_seg);
+    cudaFree(A->coo_perm);
     free(A);
 }
 
@@ -508,6 +510,25 @@ int gbs_mat_ensure_f32(gbs_mat A)
     }
     if (*(volatile int *)c->pinned) cudaFree(rel);
     else A->colrel16 = rel;
+    return GBS_OK;
+}
+
+extern "C" int gbs_mat_get_csr(gbs_mat A, int32_t *rowptr, int32_t *colidx, double *vals,
+                               int memspace)
+{
+    if (!A) return GBS_ERR_ARG;
+    if (memspace != GBS_MEM_HOST && memspace != GBS_MEM_DEVICE) return GBS_ERR_ARG;
+    gbs_ctx c = A->ctx;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const cudaMemcpyKind kind =
+        memspace == GBS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (rowptr)
+        GBS_CUDA_TRY(cudaMemcpyAsync(rowptr, A->rowptr, sizeof(int32_t) * (A->n + 1), kind, c->stream));
+    if (colidx && A->nnz > 0)
+        GBS_CUDA_TRY(cudaMemcpyAsync(colidx, A->colidx, sizeof(int32_t) * A->nnz, kind, c->stream));
+    if (vals && A->nnz > 0)
+        GBS_CUDA_TRY(cudaMemcpyAsync(vals, A->vals, sizeof(double) * A->nnz, kind, c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GBS_OK;
 }
 

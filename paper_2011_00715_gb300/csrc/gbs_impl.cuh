@@ -76,6 +76,11 @@ struct gbs_mat_s {
     // geometry (FP32 values, 16-bit indices) per tiling
     int16_t *colrel16;
     GbsPipeCfg pipe16, pipe16_lanes[3];
+    // made from coordinate triplets: their count, the triplet indices in
+    // sorted (row, column, index) order and each entry's segment of them
+    int64_t coo_m;
+    int64_t *coo_seg;     // nnz + 1
+    uint32_t *coo_perm;   // coo_m
 };
 
 struct gbs_vec_s {

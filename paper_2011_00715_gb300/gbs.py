@@ -95,6 +95,10 @@ _SIGS = {
     "gbs_ctx_launch_count": ([_VP, ctypes.POINTER(_I64)], ctypes.c_int),
     "gbs_mat_create_aij": ([_VP, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "gbs_mat_set_values": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
+    "gbs_mat_create_coo": ([_VP, _I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)],
+                           ctypes.c_int),
+    "gbs_mat_set_values_coo": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
+    "gbs_mat_get_csr": ([_VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "gbs_mat_get_info": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "gbs_mat_destroy": ([_VP], ctypes.c_int),
     "gbs_mat_mult": ([_VP, _VP, _VP], ctypes.c_int),
@@ -265,6 +269,42 @@ def gbs_mat_create_aij(ctx, nrows: int, ncols: int, rowptr, colidx, vals):
 def gbs_mat_set_values(A, vals):
     p, s, _k = _ptr_space(vals)
     _check(lib().gbs_mat_set_values(A, _VP(p), s), "gbs_mat_set_values")
+
+
+def gbs_mat_create_coo(ctx, nrows: int, ncols: int, i, j, v):
+    """Device assembly from triplets (i, j int32, v float64; all numpy/host
+    or all CUDA tensors); repeated (row, column) pairs summed in order."""
+    p_i, s_i, _k1 = _ptr_space(i)
+    p_j, s_j, _k2 = _ptr_space(j)
+    p_v, s_v, _k3 = _ptr_space(v)
+    if not (s_i == s_j == s_v):
+        raise ValueError("i, j and v must live in the same memory space")
+    if str(i.dtype).split(".")[-1] != "int32" or str(j.dtype).split(".")[-1] != "int32":
+        raise TypeError("i and j must be int32")
+    if _dtype_code(v) != GBS_F64:
+        raise TypeError("v must be float64")
+    if not (len(i) == len(j) == len(v)):
+        raise ValueError("i, j and v must have the same length")
+    h = _VP()
+    _check(lib().gbs_mat_create_coo(ctx, int(nrows), int(ncols), len(i), _VP(p_i), _VP(p_j), _VP(p_v),
+                                    s_i, ctypes.byref(h)), "gbs_mat_create_coo")
+    return h
+
+
+def gbs_mat_set_values_coo(A, v):
+    p, s, _k = _ptr_space(v)
+    _check(lib().gbs_mat_set_values_coo(A, _VP(p), s), "gbs_mat_set_values_coo")
+
+
+def gbs_mat_get_csr(A):
+    """(rowptr, colidx, vals) as host numpy arrays."""
+    n, _m, nnz = gbs_mat_get_info(A)
+    rp = np.empty(n + 1, dtype=np.int32)
+    ci = np.empty(max(nnz, 1), dtype=np.int32)
+    v = np.empty(max(nnz, 1))
+    _check(lib().gbs_mat_get_csr(A, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, GBS_MEM_HOST),
+           "gbs_mat_get_csr")
+    return rp, ci[:nnz], v[:nnz]
 
 
 def gbs_mat_get_info(A):

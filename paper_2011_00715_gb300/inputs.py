@@ -40,7 +40,7 @@ __all__ = [
     "CSR", "counter_u64", "uniform01", "uniform_pm1", "normal", "lognormal",
     "lap2d5", "lap3d7", "var5", "var7", "var27", "random_csr",
     "exact_csr", "exact_vector", "c4_batch_specs", "c5_request_specs",
-    "poisson_arrivals", "grid_for_n", "family_matrix", "xstar",
+    "poisson_arrivals", "grid_for_n", "family_matrix", "xstar", "lap3d7_edge_triplets",
 ]
 
 _U64 = np.uint64
@@ -396,3 +396,36 @@ def poisson_arrivals(seed: int, rate: float, count: int) -> np.ndarray:
     """Arrival times (s) of a Poisson process: cumulative exponential gaps."""
     u = uniform01(seed, 220, np.arange(count))
     return np.cumsum(-np.log1p(-u) / rate)
+
+
+def lap3d7_edge_triplets(nx: int, ny: int | None = None, nz: int | None = None, seed: int = 0):
+    """Coordinate triplets (i, j, v) whose sum is the 3D 7-point Dirichlet
+    Laplacian, the way a finite-element or finite-volume code produces them:
+    every interior edge (p, q) of the grid adds +1 at (p, p) and (q, q) and
+    -1 at (p, q) and (q, p); every edge to an eliminated Dirichlet neighbour
+    adds +1 at (p, p).  The triplets come in a seeded random order (a
+    permutation), so assembly has to sort and sum repeated entries."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    n = nx * ny * nz
+    cell = np.arange(n, dtype=np.int64)
+    x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+    ii, jj, vv = [], [], []
+    for step, coord, size in ((1, x, nx), (nx, y, ny), (nx * ny, z, nz)):
+        inner = coord < size - 1
+        p, q = cell[inner], cell[inner] + step
+        ones = np.ones(len(p))
+        ii += [p, q, p, q]
+        jj += [p, q, q, p]
+        vv += [ones, ones, -ones, -ones]
+        # Dirichlet neighbours below and above
+        for bnd in (coord == 0, coord == size - 1):
+            ii.append(cell[bnd])
+            jj.append(cell[bnd])
+            vv.append(np.ones(int(bnd.sum())))
+    i = np.concatenate(ii).astype(np.int32)
+    j = np.concatenate(jj).astype(np.int32)
+    v = np.concatenate(vv)
+    # seeded shuffle: sort by counter-based random keys
+    order = np.argsort(counter_u64(seed, 91, np.arange(len(i))), kind="stable")
+    return i[order], j[order], v[order]

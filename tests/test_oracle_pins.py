@@ -503,3 +503,15 @@ def test_coo_degenerate_and_invalid(orc):
     assert orc.coo_to_csr(3, 3, [0, 1], [0, -1], [1.0, 1.0])[0] == orc.ERR_CSR
     st, rp, ci, vals = orc.coo_to_csr(0, 0, [], [], [])
     assert st == 0 and list(rp) == [0]
+
+
+def test_coo_assembly_of_edge_contributions_is_the_laplacian(orc):
+    """The seeded, shuffled edge contributions of the 3D grid sum to the
+    7-point Dirichlet Laplacian: assembly reproduces it exactly."""
+    for dims in ((6, 5, 4), (1, 1, 3), (9, 9, 9)):
+        i, j, v = I.lap3d7_edge_triplets(*dims, seed=4)
+        A = I.lap3d7(*dims)
+        st, rp, ci, vals = orc.coo_to_csr(A.n, A.n, i, j, v)
+        assert st == 0
+        assert np.array_equal(rp, A.rowptr) and np.array_equal(ci, A.colidx)
+        assert np.array_equal(vals, A.vals)
