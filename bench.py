@@ -145,6 +145,14 @@ def c2_problem():
     return A, xs
 
 
+METRIC = "Jacobi-PCG solves/s (128^3 7-point Laplacian, FP64 CSR, rtol 1e-10)"
+
+
+def config_for(world):
+    """The workload keys both arms report."""
+    return {"workload": WORKLOAD,
+            "l2": "inputs larger than L2 (matrix 175 MB + 5 vectors of 16.8 MB)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 WORKLOAD = (f"3D 7-point Dirichlet Laplacian {N_GRID}^3 (n=2,097,152, nnz=14,581,760), FP64 CSR, "
             "one Jacobi-PCG solve per step, rtol 1e-10 (unpreconditioned ||r||<=rtol||b||), x0=0, "
             "b=A x*, x* uniform[-1,1) seed 2")
@@ -213,11 +221,12 @@ def run_reference(args, rank, world):
     el = time.perf_counter() - t0
     sec_per_solve = statistics.mean(vals)
     value = 1.0 / sec_per_solve
-    line = {"impl": "reference", "metric": "Jacobi-PCG solves/s (128^3 7-point, FP64, rtol 1e-10)",
-            "value": value, "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
+    line = {"impl": "reference", "metric": METRIC,
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "data": "synthetic (seeded stencil matrix and manufactured solution)",
+            "config": dict(config_for(world), algorithm="CPU oracle: plain C, one thread"),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": samples[-1]["sample"] + f"; {args.steps} steps in {el:.1f} s"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -356,15 +365,13 @@ def run_gbs(args, rank, world, local):
     true_rel = float(torch.linalg.norm(bt - rt) / torch.linalg.norm(bt))
     err_xs = float(torch.linalg.norm(xt - xst) / torch.linalg.norm(xst))
 
-    line = {"metric": "Jacobi-PCG solves/s (128^3 7-point Laplacian, FP64 CSR, rtol 1e-10)",
+    line = {"metric": METRIC,
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded stencil matrix and manufactured solution)",
-            "config": {"workload": WORKLOAD,
-                       "l2": "inputs larger than L2 (matrix 175 MB + 5 vectors of 16.8 MB)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "algorithm": "persistent cooperative kernel, 3 grid barriers/iteration"},
+            "config": dict(config_for(world),
+                           algorithm="persistent cooperative kernel, 3 grid barriers/iteration"),
             "solve": {"status": sorted(statuses), "iters": iters[0],
                       "true_rel_residual": true_rel, "rel_err_vs_xstar": err_xs,
                       "kernel_ms": dev_ms, "us_per_iter": dev_ms * 1e3 / iters[0]},
