@@ -275,8 +275,8 @@ def event_time(torch, fn, reps):
 # the hash of the kernel sources it was taken on; the roofline reports the
 # traffic scaled to the full launch only while the sources are unchanged.
 TRAFFIC_SOURCES = ("paper_2011_00715_gb300/csrc/solve.cu", "paper_2011_00715_gb300/csrc/gbs_impl.cuh")
-TRAFFIC_PER_ITER = {"sha256": "9335ee16cb64c2cb1ed57d1528eaab59276c93aab9e58887e0793462bfc507ef",
-                    "bytes": 277974286}
+TRAFFIC_PER_ITER = {"sha256": "b3e49f0ce7d31b44f5dd423709baca00b9831386d0a76fcfdbb856a7651502d3",
+                    "bytes": 278443836}
 
 
 def kernel_source_hash():
@@ -476,8 +476,8 @@ def extras(g, args, A, Ah, xsv):
     x1 = torch.zeros(C1.n, dtype=torch.float64, device="cuda")
     x1v = gbs.gbs_vec_wrap(g.ctx, x1)
     res = {}
-    for name, alg in (("persistent", gbs.GBS_ALG_PERSISTENT), ("perop", gbs.GBS_ALG_PEROP),
-                      ("graph", gbs.GBS_ALG_GRAPH)):
+    for name, alg in (("cluster", gbs.GBS_ALG_CLUSTER), ("persistent", gbs.GBS_ALG_PERSISTENT),
+                      ("perop", gbs.GBS_ALG_PEROP), ("graph", gbs.GBS_ALG_GRAPH)):
         o = gbs.gbs_opts_default(algorithm=alg)
         info = None
 

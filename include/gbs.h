@@ -80,9 +80,18 @@ enum {
                                 kept on the device, convergence read by the
                                 host every iteration: the library-call-per-op
                                 pattern of PETSc's GPU back-end */
-    GBS_ALG_GRAPH = 3        /* GBS_ALG_PEROP's kernels captured once into a
+    GBS_ALG_GRAPH = 3,       /* GBS_ALG_PEROP's kernels captured once into a
                                 CUDA graph of several iterations and replayed
                                 (Challenge A1: CUDA graphs) */
+    GBS_ALG_CLUSTER = 4      /* FP64, n <= GBS_CLUSTER_MAX_ROWS: the whole solve
+                                in one thread-block cluster of up to 16 CTAs,
+                                the vectors in shared memory, hardware cluster
+                                barriers instead of grid barriers (Challenge A1:
+                                small problems are latency-bound).  GBS_ALG_AUTO
+                                takes it for small FP64 systems.
+                                GBS_ERR_UNSUPPORTED for a larger system, for
+                                GBS_MODE_MIXED, or where the device cannot
+                                keep such a cluster resident */
 };
 
 typedef struct gbs_ctx_s *gbs_ctx;
@@ -110,7 +119,9 @@ typedef struct {
                                 right-hand-side count, precision), timing the
                                 candidates once per context on the first system
                                 of the class */
-    int reserved[7];
+    int persistent_ctas;     /* persistent solves: CTAs of the launch (at most one per
+                                SM), or 0 (default) for the library's choice */
+    int reserved[6];
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -315,6 +326,10 @@ int gbs_ksp_last_info(gbs_ctx ctx, gbs_solve_info *info);
  * barrier per iteration. */
 int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double emax,
                             double rtol, int maxit, gbs_solve_info *info);
+
+/* Largest system GBS_ALG_CLUSTER takes (rows): 8 CTAs (the portable
+ * cluster size) of 4096 rows, x, r, p, A p and D^-1 in FP64 shared memory. */
+#define GBS_CLUSTER_MAX_ROWS 32768
 
 /* Largest system gbs_ksp_solve_cg_noalloc accepts (rows). */
 #define GBS_NOALLOC_MAX_ROWS 262144

@@ -1,0 +1,357 @@
+// FP64 Jacobi-PCG for small systems in one thread-block cluster
+// (Challenge A1: below a few tens of thousands of rows a solve is bound by
+// synchronisation latency, not by bandwidth).
+//
+// The grid-wide persistent kernel pays three software grid barriers per
+// iteration across all 152 SMs.  A small system instead runs in one cluster
+// of up to 16 CTAs: CTA k owns the rows [k R, (k+1) R) (R a power of two)
+// and keeps x, r, p, A p and D^-1 of those rows in its shared memory.  The
+// SpMV reads the direction vector p of other CTAs' rows through distributed
+// shared memory, and the CTAs synchronise with the hardware cluster
+// barrier.  One SM alone would not do: GB300 issues about two FP64 FMAs per
+// clock per SM, so the iteration's FP64 work is spread over the cluster.
+//
+// Same iteration, stopping test and statuses as the persistent kernel
+// (textbook PCG, Saad Alg. 9.1; ||r|| <= rtol ||b|| before each iteration).
+// z = D^-1 r is not stored: it is recomputed as one rounded product where
+// it is needed.
+//
+// Reductions are deterministic: each thread sums its rows in order, a fixed
+// shuffle tree per warp and over the warp partials gives the CTA's partial,
+// which every CTA writes into its slot of every CTA's shared memory; after
+// the cluster barrier every CTA adds the slots by the same fixed tree, so
+// all CTAs hold bitwise the same scalars and take the same branches (every
+// CTA meets every cluster barrier).  No wait in this kernel spins on memory: the only
+// waits are the CTA and cluster barriers, which all CTAs reach on the same
+// control path.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "gbs_impl.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kCT = 512;                 // threads per CTA
+constexpr int kCW = kCT / 32;            // warps per CTA
+constexpr int kMaxCluster = 16;          // the opt-in (non-portable) cluster size
+constexpr int kPortableCluster = 8;
+constexpr int kMinRows = 128;            // rows per CTA at least
+constexpr int kMaxRowsPerCta = GBS_CLUSTER_MAX_ROWS / kPortableCluster;
+constexpr size_t kMaxSmem = (size_t)5 * kMaxRowsPerCta * sizeof(double);
+static_assert(kMaxSmem <= 200 * 1024, "five FP64 vectors of R rows fit in shared memory");
+static_assert((kMaxRowsPerCta & (kMaxRowsPerCta - 1)) == 0, "rows per CTA is a power of two");
+
+struct ClArgs {
+    int n;
+    int rows, log_rows;      // rows per CTA (a power of two)
+    const int32_t *rowptr, *colidx;
+    const double *vals, *dinv, *b;
+    double *x;               // initial guess in, solution out (global)
+    double rtol;
+    int maxit;
+    gbs_result_dev *res;
+};
+
+struct ClShared {
+    double *pseg[kMaxCluster];           // each rank's p segment, as this CTA addresses it
+    double init[3 * kMaxCluster];        // set-up partials r.z, r.r, b.b; slot = writing rank
+    double pq[kMaxCluster];              // p.Ap partials
+    double u[2 * kMaxCluster];           // r.z, r.r partials after the update
+    double wpart[3][kCW];                // warp partials
+    double alpha, beta;
+    int go, status;
+};
+
+__device__ __forceinline__ int cl_check(double rn, double rho, double tol, int k, int maxit)
+{
+    if (isnan(rn) || isnan(rho)) return GBS_ERR_NAN;
+    if (rn <= tol) return GBS_OK;
+    if (k >= maxit) return GBS_DIVERGED_ITS;
+    return -100;
+}
+
+// The CTA's sum of v (fixed tree), written into slot `rank` of dst[k *
+// kMaxCluster] in the shared memory of every CTA of the cluster.  The
+// caller's next cluster barrier publishes the writes.
+template <int K>
+__device__ __forceinline__ void cta_publish(double (&v)[K], double *dst, ClShared &s,
+                                            cg::cluster_group &cl, int rank, int cs)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0) s.wpart[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < kCW ? s.wpart[k][lane] : 0.0;
+#pragma unroll
+            for (int off = kCW / 2; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (lane < cs) cl.map_shared_rank(dst + k * kMaxCluster, lane)[rank] = t;
+        }
+    }
+}
+
+// Sum of the cs published partials by a fixed tree over the slots (the
+// same in every CTA); called by all of warp 0, the total is in lane 0.  A
+// tree rather than a running sum: each dependent FP64 step costs a full
+// pass of the warp through the narrow FP64 pipe.
+__device__ __forceinline__ double cluster_total(const double *slots, int cs)
+{
+    const int lane = threadIdx.x & 31;
+    double t = lane < cs ? slots[lane] : 0.0;
+#pragma unroll
+    for (int off = kMaxCluster / 2; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    return t;
+}
+
+__global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    __shared__ ClShared s;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
+    const int R = a.rows, lo = rank * R;
+    const int nl = max(0, min(a.n - lo, R));   // rows this CTA owns
+    double *x = sm, *r = sm + R, *p = sm + 2 * R, *q = sm + 3 * R, *dinv = sm + 4 * R;
+    if (threadIdx.x < cs) s.pseg[threadIdx.x] = cl.map_shared_rank(p, (int)threadIdx.x);
+
+    // ---- set-up: r = b - A x0 (x0 read from global memory), p = z = D^-1 r
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nl; i += kCT) {
+        const int gi = lo + i;
+        double sum = 0.0;
+        const int e1 = __ldg(a.rowptr + gi + 1);
+        for (int e = __ldg(a.rowptr + gi); e < e1; ++e)
+            sum = fma(__ldg(a.vals + e), __ldg(a.x + __ldg(a.colidx + e)), sum);
+        const double bi = __ldg(a.b + gi), di = __ldg(a.dinv + gi);
+        const double ri = bi - sum, zi = __dmul_rn(di, ri);
+        x[i] = __ldg(a.x + gi);
+        dinv[i] = di;
+        r[i] = ri;
+        p[i] = zi;
+        acc[0] = fma(ri, zi, acc[0]);
+        acc[1] = fma(ri, ri, acc[1]);
+        acc[2] = fma(bi, bi, acc[2]);
+    }
+    // every CTA of the cluster is running before the first remote access
+    cl.sync();
+    cta_publish<3>(acc, s.init, s, cl, rank, cs);
+    cl.sync();
+    // scalar state, meaningful in thread 0 only
+    double rho = 0.0, rr = 0.0, bnorm = 0.0;
+    int k = 0, status = GBS_DIVERGED_ITS;
+    if (threadIdx.x < 32) {
+        rho = cluster_total(s.init, cs);
+        rr = cluster_total(s.init + kMaxCluster, cs);
+        bnorm = cluster_total(s.init + 2 * kMaxCluster, cs);
+    }
+    if (threadIdx.x == 0) {
+        bnorm = sqrt(bnorm);
+        const int st = cl_check(sqrt(rr), rho, a.rtol * bnorm, 0, a.maxit);
+        s.go = st == -100;
+        if (!s.go) status = st;
+    }
+    __syncthreads();
+
+    const int R1 = R - 1, lg = a.log_rows;
+    for (int kk = 0; s.go && kk <= a.maxit; ++kk) {
+        // ---- S: q = A p (p of other CTAs' rows through distributed shared
+        // memory), partial p.q
+        double pq[1] = {0.0};
+        for (int i = threadIdx.x; i < nl; i += kCT) {
+            const int gi = lo + i;
+            double sum = 0.0;
+            const int e1 = __ldg(a.rowptr + gi + 1);
+            for (int e = __ldg(a.rowptr + gi); e < e1; ++e) {
+                const int c = __ldg(a.colidx + e), owner = c >> lg, off = c & R1;
+                const double pc = owner == rank ? p[off] : s.pseg[owner][off];
+                sum = fma(__ldg(a.vals + e), pc, sum);
+            }
+            q[i] = sum;
+            pq[0] = fma(p[i], sum, pq[0]);
+        }
+        cta_publish<1>(pq, s.pq, s, cl, rank, cs);
+        cl.sync();
+        double pi = 0.0;
+        if (threadIdx.x < 32) pi = cluster_total(s.pq, cs);
+        if (threadIdx.x == 0) {
+            if (isnan(pi)) status = GBS_ERR_NAN;
+            else if (pi <= 0.0) status = GBS_ERR_INDEFINITE;
+            s.go = !(isnan(pi) || pi <= 0.0);
+            s.alpha = rho / pi;
+        }
+        __syncthreads();
+        if (!s.go) break;
+        const double alpha = s.alpha;
+
+        // ---- U: x += alpha p; r -= alpha q; partials r.z, r.r
+        double u[2] = {0.0, 0.0};
+        for (int i = threadIdx.x; i < nl; i += kCT) {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            const double zi = __dmul_rn(dinv[i], ri);
+            u[0] = fma(ri, zi, u[0]);
+            u[1] = fma(ri, ri, u[1]);
+        }
+        cta_publish<2>(u, s.u, s, cl, rank, cs);
+        cl.sync();
+        double rho_new = 0.0, rr_new = 0.0;
+        if (threadIdx.x < 32) {
+            rho_new = cluster_total(s.u, cs);
+            rr_new = cluster_total(s.u + kMaxCluster, cs);
+        }
+        if (threadIdx.x == 0) {
+            ++k;
+            rr = rr_new;
+            if (rho_new < 0.0) {
+                status = GBS_ERR_INDEFINITE;
+                s.go = 0;
+            } else {
+                s.beta = rho_new / rho;
+                rho = rho_new;
+                const int st = cl_check(sqrt(rr), rho, a.rtol * bnorm, k, a.maxit);
+                s.go = st == -100;
+                if (!s.go) status = st;
+            }
+        }
+        __syncthreads();
+        if (!s.go) break;
+        const double beta = s.beta;
+
+        // ---- P: p = z + beta p on this CTA's rows; the barrier publishes
+        // them to the next SpMV of every CTA
+        for (int i = threadIdx.x; i < nl; i += kCT) p[i] = fma(beta, p[i], __dmul_rn(dinv[i], r[i]));
+        cl.sync();
+    }
+    for (int i = threadIdx.x; i < nl; i += kCT) a.x[lo + i] = x[i];
+    if (rank == 0 && threadIdx.x == 0) {
+        a.res->status = status;
+        a.res->iters = k;
+        a.res->outer = 0;
+        a.res->rnorm = sqrt(rr);
+        a.res->bnorm = bnorm;
+        a.res->timeout_where = -1;
+    }
+    // no CTA leaves while another may still address its shared memory
+    cl.sync();
+}
+
+// Largest cluster a launch of k_pcg_cluster with the largest shared-memory
+// size can keep resident on the device: 16 where the opt-in size fits, 8
+// (portable) otherwise, 0 if not even that.  Cached per device.
+std::atomic<int> g_cluster_max[64];
+
+int cluster_max(int device)
+{
+    if (device < 0 || device >= 64) return 0;
+    int v = g_cluster_max[device].load();
+    if (v) return v > 0 ? v : 0;
+    const void *fn = (const void *)k_pcg_cluster;
+    int found = -1;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        for (int cs : {kMaxCluster, kPortableCluster}) {
+            cudaLaunchConfig_t cfg;
+            memset(&cfg, 0, sizeof(cfg));
+            cfg.gridDim = dim3(cs);
+            cfg.blockDim = dim3(kCT);
+            cfg.dynamicSmemBytes = kMaxSmem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cs;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0) {
+                found = cs;
+                break;
+            }
+        }
+    }
+    cudaGetLastError();   // a refused query leaves no sticky error behind
+    g_cluster_max[device].store(found);
+    return found > 0 ? found : 0;
+}
+
+}  // namespace
+
+int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, gbs_solve_info *info)
+{
+    gbs_ctx c = A->ctx;
+    const int64_t n = A->n;
+    if (n <= 0 || n > GBS_CLUSTER_MAX_ROWS) return GBS_ERR_UNSUPPORTED;
+    const int csmax = cluster_max(c->device);
+    if (csmax == 0) return GBS_ERR_UNSUPPORTED;
+    int rows = kMinRows, lg = 7;
+    while ((n + rows - 1) / rows > csmax) {
+        rows *= 2;
+        ++lg;
+    }
+    if (rows > kMaxRowsPerCta) return GBS_ERR_UNSUPPORTED;
+    const int cs = (int)((n + rows - 1) / rows);
+    void *scr = nullptr;
+    const int st = gbs_ctx_reserve(c, 256, &scr);
+    if (st) return st;
+    ClArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = (int)n;
+    a.rows = rows;
+    a.log_rows = lg;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.vals = A->vals;
+    a.dinv = A->dinv;
+    a.b = (const double *)b->data;
+    a.x = (double *)x->data;
+    a.rtol = rtol;
+    a.maxit = maxit;
+    a.res = (gbs_result_dev *)scr;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kCT);
+    cfg.dynamicSmemBytes = (size_t)5 * rows * sizeof(double);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    GBS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pcg_cluster, a));
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    gbs_result_dev r;
+    memcpy(&r, c->pinned, sizeof(r));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->status = r.status;
+    info->iters = r.iters;
+    info->outer_iters = 0;
+    info->rnorm = r.rnorm;
+    info->bnorm = r.bnorm;
+    info->device_ms = ms;
+    return r.status;
+}

@@ -64,12 +64,13 @@ extern "C" int gbs_opts_default(gbs_opts *o)
 static int opts_valid(const gbs_opts *o)
 {
     if (o->mode != GBS_MODE_FP64 && o->mode != GBS_MODE_MIXED) return 0;
-    if (o->algorithm < GBS_ALG_AUTO || o->algorithm > GBS_ALG_GRAPH) return 0;
+    if (o->algorithm < GBS_ALG_AUTO || o->algorithm > GBS_ALG_CLUSTER) return 0;
     if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)) return 0;
     if (o->outer_maxit < 0 || o->barrier_timeout_ms <= 0 || o->graph_iters <= 0) return 0;
     if (o->batched_lanes != 0 && o->batched_lanes != 1 && o->batched_lanes != 2 &&
         o->batched_lanes != 4)
         return 0;
+    if (o->persistent_ctas < 0) return 0;
     return 1;
 }
 

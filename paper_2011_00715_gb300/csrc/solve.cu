@@ -469,7 +469,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Cooperative grid for a persistent kernel: as many co-resident CTAs as
 // fit, but no more than one CTA per GBS_PWARPS warp tiles (small systems
 // run on few CTAs, so their barriers are cheap).
-int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles)
+int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0)
 {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmem) !=
         cudaSuccess)
@@ -480,6 +480,7 @@ int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles)
         return -1;
     if (per_sm < 1) return -1;
     int64_t g = (int64_t)per_sm * c->num_sms;
+    if (want > 0) return (int)(want < g ? want : g);   // the caller's choice, within residency
     const int64_t need = (ntiles + GBS_PWARPS - 1) / GBS_PWARPS;
     if (g > need) g = need;
     return g < 1 ? 1 : (int)g;
@@ -541,7 +542,7 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     const bool rel16 = mixed && A->colrel16;
     const void *fn = !mixed ? (const void *)k_pcg_fp64
                      : rel16 ? (const void *)k_pcg_mixed<int16_t> : (const void *)k_pcg_mixed<int32_t>;
-    const int G = coop_grid(c, fn, A->ntiles);
+    const int G = coop_grid(c, fn, A->ntiles, o->persistent_ctas);
     if (G < 0) return GBS_ERR_CUDA;
     const int64_t n = A->n;
     const size_t vec64 = align256(sizeof(double) * (size_t)n);
@@ -863,6 +864,10 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, con
 // Public solve entry points
 // ----------------------------------------------------------------------
 
+// Largest FP64 system GBS_ALG_AUTO gives to the one-cluster solve rather
+// than to the grid-wide persistent kernel (the crossover measured on GB300).
+constexpr int64_t kClusterAutoRows = GBS_CLUSTER_MAX_ROWS;
+
 extern "C" int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
                                    const gbs_opts *opts, gbs_solve_info *info)
 {
@@ -887,10 +892,21 @@ extern "C" int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol,
     } else {
         GBS_CUDA_TRY(cudaSetDevice(c->device));
         int alg = o->algorithm;
-        if (alg == GBS_ALG_AUTO) alg = GBS_ALG_PERSISTENT;
+        // AUTO: a small FP64 system runs in one thread-block cluster (no
+        // grid barriers); anything else, or a device that cannot keep the
+        // cluster resident, in the persistent grid kernel
+        const bool fits = o->mode == GBS_MODE_FP64 && A->n <= GBS_CLUSTER_MAX_ROWS;
+        const bool auto_cluster = alg == GBS_ALG_AUTO && fits && A->n <= kClusterAutoRows &&
+                                  o->persistent_ctas == 0 && o->fault_skip_arrival < 0;
+        if (alg == GBS_ALG_AUTO) alg = auto_cluster ? GBS_ALG_CLUSTER : GBS_ALG_PERSISTENT;
+        st = GBS_ERR_UNSUPPORTED;
+        if (alg == GBS_ALG_CLUSTER) {
+            if (fits) st = gbs_solve_cluster(A, b, x, rtol, maxit, &tmp);
+            if (st == GBS_ERR_UNSUPPORTED && auto_cluster) alg = GBS_ALG_PERSISTENT;
+        }
         if (alg == GBS_ALG_PERSISTENT)
             st = gbs_solve_persistent(A, b, x, rtol, maxit, o, &tmp);
-        else
+        else if (alg == GBS_ALG_PEROP || alg == GBS_ALG_GRAPH)
             st = gbs_solve_perop(A, b, x, rtol, maxit, o, &tmp, alg == GBS_ALG_GRAPH);
         if (st == GBS_ERR_CUDA || st == GBS_ERR_OOM || st == GBS_ERR_UNSUPPORTED ||
             st == GBS_ERR_ARG)

@@ -45,6 +45,9 @@ GBS_ALG_AUTO = 0
 GBS_ALG_PERSISTENT = 1
 GBS_ALG_PEROP = 2
 GBS_ALG_GRAPH = 3
+GBS_ALG_CLUSTER = 4
+GBS_CLUSTER_MAX_ROWS = 32768
+GBS_NOALLOC_MAX_ROWS = 262144
 
 
 class GbsError(RuntimeError):
@@ -58,7 +61,7 @@ class gbs_opts(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("persistent_ctas", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class gbs_solve_info(ctypes.Structure):
