@@ -49,7 +49,7 @@ struct RowVals {
 
 struct ChebShared {
     double buf[2 * GBS_PBLOCK];
-    double out[2];
+    double out[8];   // totals and part sums
     double rn, bn;
     int status;   // -100 while the iteration goes on
 };

@@ -17,7 +17,7 @@
 // it is needed.
 //
 // Reductions are deterministic: each thread sums its rows in order, a fixed
-// shuffle tree per warp and over the warp partials gives the CTA's partial,
+// staged tree over the threads' values gives the CTA's partial,
 // which every CTA writes into its slot of every CTA's shared memory; after
 // the cluster barrier every CTA adds the slots by the same fixed tree, so
 // all CTAs hold bitwise the same scalars and take the same branches (every
@@ -64,7 +64,8 @@ struct ClShared {
     double init[3 * kMaxCluster];        // set-up partials r.z, r.r, b.b; slot = writing rank
     double pq[kMaxCluster];              // p.Ap partials
     double u[2 * kMaxCluster];           // r.z, r.r partials after the update
-    double wpart[3][kCW];                // warp partials
+    double stage[3][kCT];                // per-thread values of a CTA sum
+    double part[3][4];                   // per-warp sums of a CTA sum
     double alpha, beta;
     int go, status;
 };
@@ -77,29 +78,48 @@ __device__ __forceinline__ int cl_check(double rn, double rho, double tol, int k
     return -100;
 }
 
-// The CTA's sum of v (fixed tree), written into slot `rank` of dst[k *
-// kMaxCluster] in the shared memory of every CTA of the cluster.  The
-// caller's next cluster barrier publishes the writes.
+// The CTA's sum of v, written into slot `rank` of dst[k * kMaxCluster] in
+// the shared memory of every CTA of the cluster; the caller's next cluster
+// barrier publishes the writes.  Staged so as to spend few FP64
+// instructions: an SM partition retires about one FP64 warp instruction
+// per 76 cycles, whether or not its lanes are all useful, so a shuffle
+// tree in every warp is costly.  Every thread stages its K values; W = 4/K
+// warps per value (one per SM partition where possible) each add their
+// share of the entries per lane and finish with a shuffle tree; one lane
+// per value adds the W part sums.  A fixed order throughout.
 template <int K>
-__device__ __forceinline__ void cta_publish(double (&v)[K], double *dst, ClShared &s,
+__device__ __forceinline__ void cta_publish(const double (&v)[K], double *dst, ClShared &s,
                                             cg::cluster_group &cl, int rank, int cs)
 {
+    constexpr int W = K >= 3 ? 1 : 4 / K;   // warps per value
+    constexpr int PER = kCT / 32 / W;       // entries per lane
+    static_assert(W * K <= kCW && W <= 4, "warps per value");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k) s.stage[k][threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp < W * K) {
+        const int k = warp / W, j = warp % W;
+        const double *src = s.stage[k] + j * (kCT / W) + lane;
+        double t = src[0];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-        if (lane == 0) s.wpart[k][warp] = v[k];
+        for (int m = 1; m < PER; ++m) t += src[32 * m];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) s.part[k][j] = t;
     }
     __syncthreads();
     if (warp == 0) {
+        double t[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double t = lane < kCW ? s.wpart[k][lane] : 0.0;
+            if (W == 4) t[k] = (s.part[k][0] + s.part[k][1]) + (s.part[k][2] + s.part[k][3]);
+            else if (W == 2) t[k] = s.part[k][0] + s.part[k][1];
+            else t[k] = s.part[k][0];
+        }
+        if (lane < cs) {
 #pragma unroll
-            for (int off = kCW / 2; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-            t = __shfl_sync(0xffffffffu, t, 0);
-            if (lane < cs) cl.map_shared_rank(dst + k * kMaxCluster, lane)[rank] = t;
+            for (int k = 0; k < K; ++k) cl.map_shared_rank(dst + k * kMaxCluster, lane)[rank] = t[k];
         }
     }
 }

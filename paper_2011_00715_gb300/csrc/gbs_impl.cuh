@@ -256,26 +256,43 @@ __device__ __forceinline__ void gbs_block_sum(T (&v)[K], T *s_red)
     __syncthreads();
 }
 
-// Sum v[0..K) over a CTA of NT threads with few FP64 operations: every
-// thread stages its values in s_buf (K * NT entries), then warp k adds value
-// k (lane l takes entries l, l+32, ... left to right) and finishes with a
-// fixed shuffle tree.  Deterministic.  Requires K <= NT / 32.  The totals
-// are returned in s_out[0..K) after a CTA barrier.
+// Sum v[0..K) over a CTA of NT threads with few FP64 instructions (an SM
+// partition retires about one FP64 warp instruction per 76 cycles, useful
+// lanes or not, so a shuffle tree in every warp is costly): every thread
+// stages its values in s_buf (K * NT entries); W = 4/K warps per value
+// (K = 3: one) each add their share of the entries per lane, left to
+// right, and finish with a fixed shuffle tree; one lane per value adds the
+// W part sums.  Deterministic.  s_out holds 8 entries: the totals are
+// returned in s_out[0..K) after a CTA barrier, s_out[4..8) is scratch.
 template <typename T, int K, int NT>
 __device__ __forceinline__ void gbs_block_sum_staged(const T (&v)[K], T *s_buf, T *s_out)
 {
-    static_assert(K <= NT / 32, "one warp per value");
+    constexpr int W = K >= 3 ? 1 : 4 / K;
+    constexpr int PER = NT / 32 / W;
+    static_assert(W * K <= NT / 32 && W * K <= 4 && PER >= 1, "warps per value");
 #pragma unroll
     for (int k = 0; k < K; ++k) s_buf[k * NT + threadIdx.x] = v[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < K) {
-        T t = T(0);
+    if (warp < W * K) {
+        const int k = warp / W, j = warp % W;
+        const T *src = s_buf + k * NT + j * (NT / W) + lane;
+        T t = src[0];
 #pragma unroll
-        for (int j = lane; j < NT; j += 32) t += s_buf[warp * NT + j];
+        for (int m = 1; m < PER; ++m) t += src[32 * m];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (lane == 0) s_out[warp] = t;
+        if (lane == 0) {
+            if (W == 1) s_out[k] = t;
+            else s_out[4 + k * W + j] = t;
+        }
+    }
+    if (W > 1) {
+        __syncthreads();
+        if (threadIdx.x < K) {
+            const T *q = s_out + 4 + threadIdx.x * W;
+            s_out[threadIdx.x] = W == 4 ? (q[0] + q[1]) + (q[2] + q[3]) : q[0] + q[1];
+        }
     }
     __syncthreads();
 }

@@ -42,7 +42,7 @@ constexpr size_t kPersistSmem = (size_t)GBS_WARP_STAGE_BYTES * GBS_PWARPS;
 template <typename T>
 struct PcgSmall {
     T buf[3 * GBS_PBLOCK];   // staged block sums
-    T out[4];
+    T out[8];                // totals and part sums
 };
 
 // Control block written by thread 0 of each CTA after a grid reduction and
