@@ -278,6 +278,17 @@ int gbs_vec_dot(gbs_vec x, gbs_vec y, double *out);
 /* VecNorm(NORM_2): *out = ||x||_2.  Synchronises the stream. */
 int gbs_vec_norm2(gbs_vec x, double *out);
 
+/* VecDot and VecNorm without a host synchronisation (Challenge A1: a
+ * scalar returned to the host stalls the kernel queue): the result is
+ * written, in stream order on the context's stream, to dev_out, a DEVICE
+ * pointer to one 8-byte-aligned double that the caller owns and keeps valid
+ * until the stream has passed the write.  Same bits as gbs_vec_dot /
+ * gbs_vec_norm2 (an FP32 vector's FP32 result is widened to double).
+ * GBS_ERR_ARG for NULL or misaligned pointers or mismatched vectors; the
+ * pointer's memory space is not checked. */
+int gbs_vec_dot_async(gbs_vec x, gbs_vec y, double *dev_out);
+int gbs_vec_norm2_async(gbs_vec x, double *dev_out);
+
 /* ---------------------------------------------------- preconditioner --- */
 
 /* PCJACOBI (Sec. 5.3): z = D^-1 r with D = diag(A).  GBS_ERR_DIAG if a

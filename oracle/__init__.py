@@ -76,6 +76,11 @@ def _load():
         lib.orc_pcg.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double, i64,
                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double), f64p]
         lib.orc_pcg.restype = ctypes.c_int
+        lib.orc_pcg_norm.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double, i64,
+                                     ctypes.c_int, ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), f64p]
+        lib.orc_pcg_norm.restype = ctypes.c_int
         lib.orc_chebyshev.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, i64,
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
@@ -183,16 +188,20 @@ def jacobi_dinv(A):
     return st, d
 
 
-def pcg(A, b, rtol, maxit, x0=None, history=False):
-    """Jacobi-PCG in FP64.  Returns dict(x, status, iters, rnorm[, rhist])."""
+def pcg(A, b, rtol, maxit, x0=None, history=False, norm=0):
+    """Jacobi-PCG in FP64 with the stopping test N(r) <= rtol N(b) in norm
+    0 (||v||_2), 1 (||D^-1 v||_2) or 2 (sqrt(v . D^-1 v)).  Returns
+    dict(x, status, iters, rnorm, bnorm[, rhist])."""
     rp, ci, v, bb = _i32(A.rowptr), _i32(A.colidx), _f64(A.vals), _f64(b)
     x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
     it = ctypes.c_int64(0)
     rn = ctypes.c_double(0.0)
+    bn = ctypes.c_double(0.0)
     rh = np.full(maxit + 1, np.nan) if history else None
-    st = _load().orc_pcg(A.n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), float(rtol), int(maxit),
-                         ctypes.byref(it), ctypes.byref(rn), _p(rh) if history else None)
-    out = {"x": x, "status": st, "iters": it.value, "rnorm": rn.value}
+    st = _load().orc_pcg_norm(A.n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), float(rtol), int(maxit),
+                              int(norm), ctypes.byref(it), ctypes.byref(rn), ctypes.byref(bn),
+                              _p(rh) if history else None)
+    out = {"x": x, "status": st, "iters": it.value, "rnorm": rn.value, "bnorm": bn.value}
     if history:
         out["rhist"] = rh[: it.value + 1]
     return out

@@ -189,34 +189,53 @@ int orc_jacobi_dinv(int64_t n, const int32_t *rowptr, const int32_t *colidx,
 /* ------------------------------------------------------------ KSPCG --- */
 
 /*
- * Jacobi-preconditioned CG, FP64.
- *   x (in/out) initial guess -> solution; rtol relative to ||b||_2;
- *   maxit iterations at most; rhist (optional, maxit+1 doubles) receives
- *   ||r_k||_2 for k = 0..iters.
- * Returns a status code; *iters = SpMVs done, *rnorm = last ||r||_2 of the
- * recurrence.
+ * Norm of the stopping test.  The paper names KSPCG (Sec. 5.5) but does
+ * not fix the norm its test uses; three are offered:
+ *   0  unpreconditioned  N(v) = ||v||_2
+ *   1  preconditioned    N(v) = ||D^-1 v||_2
+ *   2  natural           N(v) = sqrt(v . D^-1 v)
+ * w is scratch of n doubles.
+ */
+static double orc_test_norm(int norm, int64_t n, const double *v, const double *dinv, double *w)
+{
+    if (norm == 0) return orc_norm2(n, v);
+    for (int64_t i = 0; i < n; ++i) w[i] = dinv[i] * v[i];
+    return norm == 1 ? orc_norm2(n, w) : sqrt(orc_dot(n, v, w));
+}
+
+/*
+ * Jacobi-preconditioned CG, FP64 (Saad, Iterative Methods for Sparse
+ * Linear Systems, Alg. 9.1, the method behind KSPCG with PCJACOBI).
+ *   x (in/out) initial guess -> solution; the test before each iteration
+ *   is N(r) <= rtol N(b) in the chosen norm (above); maxit iterations at
+ *   most; rhist (optional, maxit+1 doubles) receives N(r_k) for
+ *   k = 0..iters.
+ * Returns a status code; *iters = SpMVs done, *rnorm = last N(r) of the
+ * recurrence, *bnorm = N(b).  The iterates do not depend on the norm.
  *
  *   r = b - A x;  z = D^-1 r;  p = z;  rho = r.z
  *   for k = 0, 1, ...:
- *       if ||r|| <= rtol ||b||: converged after k iterations
+ *       if N(r) <= rtol N(b): converged after k iterations
  *       q = A p;  pi = p.q;  (pi <= 0: indefinite)
  *       alpha = rho / pi;  x += alpha p;  r -= alpha q;  z = D^-1 r
  *       rho' = r.z;  (rho' < 0: indefinite preconditioner)
  *       beta = rho' / rho;  rho = rho';  p = z + beta p
  */
-int orc_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
-            const double *b, double *x, double rtol, int64_t maxit,
-            int64_t *iters, double *rnorm, double *rhist)
+int orc_pcg_norm(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                 const double *b, double *x, double rtol, int64_t maxit, int norm,
+                 int64_t *iters, double *rnorm, double *bnorm_out, double *rhist)
 {
     *iters = 0;
     *rnorm = 0.0;
-    if (n < 0 || maxit < 0 || !(rtol >= 0.0)) return ORC_ERR_ARG;
+    *bnorm_out = 0.0;
+    if (n < 0 || maxit < 0 || !(rtol >= 0.0) || norm < 0 || norm > 2) return ORC_ERR_ARG;
     if (n == 0) return ORC_CONVERGED;
     double *dinv = malloc(sizeof(double) * n);
     double *r = malloc(sizeof(double) * n);
     double *z = malloc(sizeof(double) * n);
     double *p = malloc(sizeof(double) * n);
     double *q = malloc(sizeof(double) * n);
+    double *w = malloc(sizeof(double) * n);
     int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
     if (status == 0) {
         orc_spmv(n, rowptr, colidx, vals, x, q);
@@ -224,11 +243,12 @@ int orc_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const doubl
         for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
         memcpy(p, z, sizeof(double) * n);
         double rho = orc_dot(n, r, z);
-        double bnorm = orc_norm2(n, b);
+        const double bnorm = orc_test_norm(norm, n, b, dinv, w);
+        *bnorm_out = bnorm;
         int64_t k = 0;
         status = ORC_DIVERGED_ITS;
         for (;;) {
-            double rn = orc_norm2(n, r);
+            double rn = orc_test_norm(norm, n, r, dinv, w);
             *rnorm = rn;
             if (rhist) rhist[k] = rn;
             if (isnan(rn) || isnan(rho)) { status = ORC_ERR_NAN; break; }
@@ -244,15 +264,29 @@ int orc_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const doubl
             for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
             double rho_new = orc_dot(n, r, z);
             ++k;
-            if (rho_new < 0.0) { *rnorm = orc_norm2(n, r); status = ORC_ERR_INDEFINITE; break; }
+            if (rho_new < 0.0) {
+                *rnorm = orc_test_norm(norm, n, r, dinv, w);
+                status = ORC_ERR_INDEFINITE;
+                break;
+            }
             double beta = rho_new / rho;
             rho = rho_new;
             orc_aypx(n, beta, z, p);
         }
         *iters = k;
     }
-    free(dinv); free(r); free(z); free(p); free(q);
+    free(dinv); free(r); free(z); free(p); free(q); free(w);
     return status;
+}
+
+/* orc_pcg_norm with the unpreconditioned norm. */
+int orc_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+            const double *b, double *x, double rtol, int64_t maxit,
+            int64_t *iters, double *rnorm, double *rhist)
+{
+    double bnorm = 0.0;
+    return orc_pcg_norm(n, rowptr, colidx, vals, b, x, rtol, maxit, 0, iters, rnorm, &bnorm,
+                        rhist);
 }
 
 /*

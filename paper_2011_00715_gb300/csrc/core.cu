@@ -859,11 +859,12 @@ extern "C" int gbs_vec_pointwise_mult(gbs_vec w, gbs_vec x, gbs_vec y)
 
 // Dot product in two fixed-order stages within one launch: each CTA sums a
 // grid-stride slice (thread partials, then a shuffle tree), the last CTA to
-// finish adds the CTA partials in index order.  Result in out[0] (T).
+// finish adds the CTA partials in index order.  out[0] (FP64) gets the
+// total, or its square root (VecNorm), taken in T and then widened.
 template <typename T>
 __global__ void __launch_bounds__(GBS_BLOCK) k_dot(int64_t n, const T *__restrict__ x,
                                                    const T *__restrict__ y, T *partials,
-                                                   unsigned int *counter, T *out)
+                                                   unsigned int *counter, double *out, int root)
 {
     __shared__ T s_red[GBS_WARPS];
     __shared__ bool s_last;
@@ -883,61 +884,83 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_dot(int64_t n, const T *__restric
         T tot[1];
         gbs_grid_sum<T, 1>(partials, 0, gridDim.x, tot, s_red);
         if (threadIdx.x == 0) {
-            out[0] = tot[0];
+            out[0] = (double)(root ? sqrt(tot[0]) : tot[0]);
             *counter = 0;
         }
     }
 }
 
-static int vec_dot_impl(gbs_vec x, gbs_vec y, double *out)
+// Launch the dot product (or norm) of x and y into dev_out on the context's
+// stream, without waiting for it.  The counter and the per-CTA partials are
+// in the context's scratch: every later user of the scratch is ordered
+// after this launch on the same stream, and growing the scratch
+// synchronises the stream first.
+static int vec_dot_launch(gbs_vec x, gbs_vec y, double *dev_out, int root)
 {
     gbs_ctx c = x->ctx;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
     if (x->n == 0) {
-        *out = 0.0;
+        GBS_CUDA_TRY(cudaMemsetAsync(dev_out, 0, sizeof(double), c->stream));
         return GBS_OK;
     }
-    GBS_CUDA_TRY(cudaSetDevice(c->device));
     const int g = grid_for(c, x->n, 4);
     void *scr = nullptr;
-    int st = gbs_ctx_reserve(c, 64 + 8 * (size_t)g + 16, &scr);
+    int st = gbs_ctx_reserve(c, 64 + 8 * (size_t)g, &scr);
     if (st) return st;
     unsigned int *counter = (unsigned int *)scr;
-    double *res = (double *)((char *)scr + 16);
     void *partials = (char *)scr + 64;
     GBS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, c->stream));
     if (x->dtype == GBS_F64)
         k_dot<double><<<g, GBS_BLOCK, 0, c->stream>>>(x->n, (const double *)x->data,
                                                       (const double *)y->data,
-                                                      (double *)partials, counter, res);
+                                                      (double *)partials, counter, dev_out, root);
     else
         k_dot<float><<<g, GBS_BLOCK, 0, c->stream>>>(x->n, (const float *)x->data,
                                                      (const float *)y->data, (float *)partials,
-                                                     counter, (float *)res);
+                                                     counter, dev_out, root);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
+    return GBS_OK;
+}
+
+// Synchronous form: the result goes through the context's small device
+// buffer and its pinned host buffer.
+static int vec_dot_sync(gbs_vec x, gbs_vec y, double *out, int root)
+{
+    gbs_ctx c = x->ctx;
+    double *res = (double *)c->devsmall + 8;   // bytes 64..71 of the small device buffer
+    int st = vec_dot_launch(x, y, res, root);
+    if (st) return st;
     GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, res, 8, cudaMemcpyDeviceToHost, c->stream));
     GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (x->dtype == GBS_F64)
-        *out = *(volatile double *)c->pinned;
-    else
-        *out = (double)*(volatile float *)c->pinned;
+    *out = *(volatile double *)c->pinned;
     return GBS_OK;
 }
 
 extern "C" int gbs_vec_dot(gbs_vec x, gbs_vec y, double *out)
 {
     if (!x || !y || !out || x->n != y->n || x->dtype != y->dtype) return GBS_ERR_ARG;
-    return vec_dot_impl(x, y, out);
+    return vec_dot_sync(x, y, out, 0);
 }
 
 extern "C" int gbs_vec_norm2(gbs_vec x, double *out)
 {
     if (!x || !out) return GBS_ERR_ARG;
-    double d = 0.0;
-    int st = vec_dot_impl(x, x, &d);
-    if (st) return st;
-    *out = x->dtype == GBS_F64 ? sqrt(d) : (double)sqrtf((float)d);
-    return GBS_OK;
+    return vec_dot_sync(x, x, out, 1);
+}
+
+extern "C" int gbs_vec_dot_async(gbs_vec x, gbs_vec y, double *dev_out)
+{
+    if (!x || !y || !dev_out || x->n != y->n || x->dtype != y->dtype) return GBS_ERR_ARG;
+    if ((uintptr_t)dev_out % alignof(double)) return GBS_ERR_ARG;
+    return vec_dot_launch(x, y, dev_out, 0);
+}
+
+extern "C" int gbs_vec_norm2_async(gbs_vec x, double *dev_out)
+{
+    if (!x || !dev_out) return GBS_ERR_ARG;
+    if ((uintptr_t)dev_out % alignof(double)) return GBS_ERR_ARG;
+    return vec_dot_launch(x, x, dev_out, 1);
 }
 
 // ------------------------------------------------------------- Jacobi --

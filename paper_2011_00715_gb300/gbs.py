@@ -118,6 +118,8 @@ _SIGS = {
     "gbs_vec_pointwise_mult": ([_VP, _VP, _VP], ctypes.c_int),
     "gbs_vec_dot": ([_VP, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "gbs_vec_norm2": ([_VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gbs_vec_dot_async": ([_VP, _VP, _VP], ctypes.c_int),
+    "gbs_vec_norm2_async": ([_VP, _VP], ctypes.c_int),
     "gbs_pc_jacobi_create": ([_VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "gbs_pc_apply": ([_VP, _VP, _VP], ctypes.c_int),
     "gbs_pc_destroy": ([_VP], ctypes.c_int),
@@ -397,6 +399,24 @@ def gbs_vec_norm2(x) -> float:
     out = ctypes.c_double()
     _check(lib().gbs_vec_norm2(x, ctypes.byref(out)), "gbs_vec_norm2")
     return out.value
+
+
+def _dev_scalar(out):
+    """Device address of a CUDA float64 tensor with at least one element."""
+    if getattr(out, "is_cuda", False) is not True or str(out.dtype) != "torch.float64" \
+            or out.numel() < 1:
+        raise ValueError("out must be a CUDA float64 tensor with at least one element")
+    return _VP(out.data_ptr())
+
+
+def gbs_vec_dot_async(x, y, out) -> None:
+    """x . y written to out[0] (a CUDA float64 tensor) in stream order."""
+    _check(lib().gbs_vec_dot_async(x, y, _dev_scalar(out)), "gbs_vec_dot_async")
+
+
+def gbs_vec_norm2_async(x, out) -> None:
+    """||x||_2 written to out[0] (a CUDA float64 tensor) in stream order."""
+    _check(lib().gbs_vec_norm2_async(x, _dev_scalar(out)), "gbs_vec_norm2_async")
 
 
 # --------------------------------------------------------- preconditioner --

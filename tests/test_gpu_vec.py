@@ -65,6 +65,46 @@ def test_dot_norm_fp64(S, orc, n):
     assert gbs.gbs_vec_dot(xv, yv) == d
 
 
+def test_dot_norm_async_stream_order(S):
+    """The asynchronous forms write the same bits as the synchronous ones
+    into caller-owned device memory, in stream order: a torch operation
+    queued after them on the same stream reads the results."""
+    import ctypes
+    import torch
+    out = torch.full((8,), -1.0, dtype=torch.float64, device="cuda")
+    res = []
+    for k, n in enumerate((31, 65537, 3_000_001)):
+        x = I.uniform_pm1(6, k, n)
+        y = I.uniform_pm1(6, k + 10, n)
+        xv, _ = S.vec(x)
+        yv, _ = S.vec(y)
+        gbs.gbs_vec_dot_async(xv, yv, out[2 * k:])
+        gbs.gbs_vec_norm2_async(xv, out[2 * k + 1:])
+        res.append((xv, yv))
+    doubled = out * 2.0            # queued behind the writes on the same stream
+    host = doubled.cpu().numpy() / 2.0
+    for k, (xv, yv) in enumerate(res):
+        assert host[2 * k] == gbs.gbs_vec_dot(xv, yv)
+        assert host[2 * k + 1] == gbs.gbs_vec_norm2(xv)
+    # FP32: the FP32 result widened
+    x32 = I.uniform_pm1(7, 0, 100_003).astype(np.float32)
+    v32, _ = S.vec(x32, np.float32)
+    gbs.gbs_vec_norm2_async(v32, out[6:])
+    gbs.gbs_vec_dot_async(v32, v32, out[7:])
+    torch.cuda.current_stream().synchronize()
+    assert out[6].item() == gbs.gbs_vec_norm2(v32)
+    assert out[7].item() == gbs.gbs_vec_dot(v32, v32)
+    # empty vectors give 0; misaligned or missing pointers are refused
+    e0 = gbs.gbs_vec_create(S.ctx, 0)
+    gbs.gbs_vec_norm2_async(e0, out[0:])
+    torch.cuda.current_stream().synchronize()
+    assert out[0].item() == 0.0
+    assert gbs.lib().gbs_vec_dot_async(res[0][0], res[0][1],
+                                       ctypes.c_void_p(out.data_ptr() + 4)) == gbs.GBS_ERR_ARG
+    assert gbs.lib().gbs_vec_norm2_async(res[0][0], None) == gbs.GBS_ERR_ARG
+    gbs.gbs_vec_destroy(e0)
+
+
 def test_dot_exact_inputs(S):
     n = 2_000_000
     x = I.exact_vector(n, seed=3)

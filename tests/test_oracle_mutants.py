@@ -47,6 +47,12 @@ MUTANTS = {
                                  "while (q >= a && tj[order[q]] >= tj[key]) {"),
     "coo_duplicates_not_merged": ("while (p < b && tj[order[p]] == c) {", "while (0) {"),
     "coo_last_duplicate_wins": ("s = s + v[order[p]];", "s = v[order[p]];"),
+    "precond_norm_of_r": ("return norm == 1 ? orc_norm2(n, w) : sqrt(orc_dot(n, v, w));",
+                          "return norm == 1 ? orc_norm2(n, v) : sqrt(orc_dot(n, v, w));"),
+    "natural_norm_without_sqrt": ("return norm == 1 ? orc_norm2(n, w) : sqrt(orc_dot(n, v, w));",
+                                  "return norm == 1 ? orc_norm2(n, w) : orc_dot(n, v, w);"),
+    "norm_reference_unpreconditioned": ("const double bnorm = orc_test_norm(norm, n, b, dinv, w);",
+                                        "const double bnorm = orc_norm2(n, b);"),
 }
 
 PINS = [
@@ -70,6 +76,8 @@ PINS = [
     lambda o: P.test_coo_assembly_equals_dense_accumulation_and_scipy(o),
     lambda o: P.test_coo_duplicates_are_summed_in_triplet_order(o),
     lambda o: P.test_coo_degenerate_and_invalid(o),
+    lambda o: P.test_pcg_norms_with_constant_diagonal_scale_exactly(o),
+    lambda o: P.test_pcg_norms_follow_their_definitions(o),
 ]
 
 

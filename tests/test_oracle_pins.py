@@ -207,6 +207,50 @@ def test_pcg_energy_error_monotone_and_history(orc):
     assert errs[-1] < 1e-6 * errs[0]
 
 
+def test_pcg_norms_with_constant_diagonal_scale_exactly(orc):
+    """D = 4I: D^-1 v = v/4 exactly, so the preconditioned norm of every
+    residual is ||r||/4 and the natural norm sqrt(r.r/4) = ||r||/2, bit for
+    bit; the three tests stop at the same iteration with the same iterate."""
+    A = I.lap2d5(20)
+    b = orc.spmv(A, I.xstar(A.n, 3))
+    runs = [orc.pcg(A, b, 1e-9, 2000, history=True, norm=m) for m in (0, 1, 2)]
+    u, pr, na = runs
+    assert u["status"] == pr["status"] == na["status"] == orc.CONVERGED
+    assert u["iters"] == pr["iters"] == na["iters"]
+    assert np.array_equal(u["x"], pr["x"]) and np.array_equal(u["x"], na["x"])
+    assert np.array_equal(pr["rhist"], u["rhist"] / 4) and pr["bnorm"] == u["bnorm"] / 4
+    assert np.array_equal(na["rhist"], u["rhist"] / 2) and na["bnorm"] == u["bnorm"] / 2
+    assert abs(u["bnorm"] - np.linalg.norm(b)) <= gamma(A.n) * u["bnorm"]
+
+
+def test_pcg_norms_follow_their_definitions(orc):
+    """Variable diagonal: each run's residual history equals the chosen norm
+    of the true residual of the k-step iterate (dense, numpy), and the run
+    stops at the first iteration whose norm passes rtol N(b)."""
+    A = I.var7(9, 8, 7, seed=12, sigma=1.0)
+    dense = A.to_dense()
+    dg = np.diag(dense)
+    b = dense @ I.xstar(A.n, 4)
+    norms = {0: lambda v: float(np.linalg.norm(v)),
+             1: lambda v: float(np.linalg.norm(v / dg)),
+             2: lambda v: math.sqrt(float(v @ (v / dg)))}
+    rtol = 1e-6
+    iterates = [orc.pcg(A, b, 0.0, k)["x"] for k in range(0, 80)]
+    true_r = [b - dense @ x for x in iterates]
+    stops = set()
+    for m, N in norms.items():
+        run = orc.pcg(A, b, rtol, 500, history=True, norm=m)
+        assert run["status"] == orc.CONVERGED
+        assert abs(run["bnorm"] - N(b)) <= 1e-13 * N(b)
+        k = run["iters"]
+        for j in range(k + 1):
+            assert abs(run["rhist"][j] - N(true_r[j])) <= 1e-7 * N(true_r[j]) + 1e-12 * N(b)
+        first = next(j for j in range(len(true_r)) if N(true_r[j]) <= rtol * N(b))
+        assert k == first
+        stops.add(k)
+    assert len(stops) > 1          # the norms disagree on this system: the pin has teeth
+
+
 @pytest.mark.parametrize("maker,steps", [
     (lambda: I.lap2d5(2), 3),        # eigenvalues {2, 4, 4, 6}: 3 distinct
     (lambda: I.lap3d7(2), 4),        # {3, 5, 7, 9}
