@@ -94,6 +94,16 @@ enum {
                                 keep such a cluster resident */
 };
 
+/* Norm of the CG stopping test.  The paper names KSPCG (Sec. 5.5) but does
+ * not fix the norm of its test; the test runs before each iteration as
+ * N(r) <= rtol N(b). */
+enum {
+    GBS_NORM_UNPRECONDITIONED = 0,  /* N(v) = ||v||_2 (default) */
+    GBS_NORM_PRECONDITIONED = 1,    /* N(v) = ||D^-1 v||_2 */
+    GBS_NORM_NATURAL = 2            /* N(v) = sqrt(v . D^-1 v); for the residual
+                                       this is sqrt(r . z), already computed */
+};
+
 typedef struct gbs_ctx_s *gbs_ctx;
 typedef struct gbs_mat_s *gbs_mat;
 typedef struct gbs_vec_s *gbs_vec;
@@ -121,7 +131,15 @@ typedef struct {
                                 of the class */
     int persistent_ctas;     /* persistent solves: CTAs of the launch (at most one per
                                 SM), or 0 (default) for the library's choice */
-    int reserved[6];
+    int norm_type;           /* GBS_NORM_* of the stopping test of the FP64
+                                single-system CG solves (every algorithm, and
+                                gbs_ksp_solve_cg_noalloc through the context's
+                                options); GBS_MODE_MIXED, the batched and serving
+                                engines and Chebyshev test the unpreconditioned
+                                norm, and a solve in GBS_MODE_MIXED with another
+                                norm is refused with GBS_ERR_ARG.
+                                Default GBS_NORM_UNPRECONDITIONED */
+    int reserved[5];
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -131,8 +149,9 @@ typedef struct {
                             over all inner solves */
     int outer_iters;     /* MIXED: refinement steps; FP64: 0 */
     double rnorm;        /* final ||r||_2: recurrence residual in FP64 mode,
-                            true FP64 residual ||b - A x||_2 in MIXED mode */
-    double bnorm;        /* ||b||_2 */
+                            true FP64 residual ||b - A x||_2 in MIXED mode;
+                            N(r) in the chosen norm_type */
+    double bnorm;        /* ||b||_2; N(b) in the chosen norm_type */
     double device_ms;    /* device time of the solve (CUDA events) */
     double model_bytes;  /* algorithmic bytes the solve moved by the library's
                             byte model (batched solves; 0 where not computed) */

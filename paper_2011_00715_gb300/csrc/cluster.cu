@@ -56,6 +56,7 @@ struct ClArgs {
     double *x;               // initial guess in, solution out (global)
     double rtol;
     int maxit;
+    int norm;                // GBS_NORM_* of the stopping test
     gbs_result_dev *res;
 };
 
@@ -163,19 +164,27 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
         r[i] = ri;
         p[i] = zi;
         acc[0] = fma(ri, zi, acc[0]);
-        acc[1] = fma(ri, ri, acc[1]);
-        acc[2] = fma(bi, bi, acc[2]);
+        const double w = a.norm == GBS_NORM_PRECONDITIONED ? zi : ri;
+        acc[1] = fma(w, w, acc[1]);
+        if (a.norm == GBS_NORM_UNPRECONDITIONED) {
+            acc[2] = fma(bi, bi, acc[2]);
+        } else {
+            const double db = __dmul_rn(di, bi);
+            acc[2] = a.norm == GBS_NORM_PRECONDITIONED ? fma(db, db, acc[2]) : fma(bi, db, acc[2]);
+        }
     }
     // every CTA of the cluster is running before the first remote access
     cl.sync();
     cta_publish<3>(acc, s.init, s, cl, rank, cs);
     cl.sync();
-    // scalar state, meaningful in thread 0 only
+    // scalar state, meaningful in thread 0 only; rr holds N(r)^2 of the
+    // stopping-test norm N (r.r, z.z, or r.z for the natural norm)
+    const bool natural = a.norm == GBS_NORM_NATURAL;
     double rho = 0.0, rr = 0.0, bnorm = 0.0;
     int k = 0, status = GBS_DIVERGED_ITS;
     if (threadIdx.x < 32) {
         rho = cluster_total(s.init, cs);
-        rr = cluster_total(s.init + kMaxCluster, cs);
+        rr = natural ? rho : cluster_total(s.init + kMaxCluster, cs);
         bnorm = cluster_total(s.init + 2 * kMaxCluster, cs);
     }
     if (threadIdx.x == 0) {
@@ -225,7 +234,8 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
             r[i] = ri;
             const double zi = __dmul_rn(dinv[i], ri);
             u[0] = fma(ri, zi, u[0]);
-            u[1] = fma(ri, ri, u[1]);
+            const double w = a.norm == GBS_NORM_PRECONDITIONED ? zi : ri;
+            u[1] = fma(w, w, u[1]);
         }
         cta_publish<2>(u, s.u, s, cl, rank, cs);
         cl.sync();
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
         }
         if (threadIdx.x == 0) {
             ++k;
-            rr = rr_new;
+            rr = natural ? rho_new : rr_new;
             if (rho_new < 0.0) {
                 status = GBS_ERR_INDEFINITE;
                 s.go = 0;
@@ -312,7 +322,8 @@ int cluster_max(int device)
 
 }  // namespace
 
-int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, gbs_solve_info *info)
+int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, int norm,
+                      gbs_solve_info *info)
 {
     gbs_ctx c = A->ctx;
     const int64_t n = A->n;
@@ -342,6 +353,7 @@ int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, g
     a.x = (double *)x->data;
     a.rtol = rtol;
     a.maxit = maxit;
+    a.norm = norm;
     a.res = (gbs_result_dev *)scr;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));

@@ -71,6 +71,8 @@ static int opts_valid(const gbs_opts *o)
         o->batched_lanes != 4)
         return 0;
     if (o->persistent_ctas < 0) return 0;
+    if (o->norm_type < GBS_NORM_UNPRECONDITIONED || o->norm_type > GBS_NORM_NATURAL) return 0;
+    if (o->norm_type != GBS_NORM_UNPRECONDITIONED && o->mode == GBS_MODE_MIXED) return 0;
     return 1;
 }
 

@@ -123,7 +123,8 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
 int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
                     const gbs_opts *o, gbs_solve_info *info, int use_graph);
 // FP64 solve of a small system in one thread-block cluster.
-int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, gbs_solve_info *info);
+int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, int norm,
+                      gbs_solve_info *info);
 int gbs_mat_ensure_f32(gbs_mat A);
 // Make the tiling for 2^li lanes per row (li = 0, 1, 2) if it does not exist.
 int gbs_mat_ensure_lane_tiling(gbs_mat A, int li);

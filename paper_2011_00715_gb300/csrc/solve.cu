@@ -84,6 +84,7 @@ struct PcgArgs {
     int maxit;
     int outer_maxit;
     int x0_zero;
+    int norm;          // GBS_NORM_* of the stopping test (FP64 loop only)
     int skip_cta;
     unsigned long long timeout_ns;
 };
@@ -127,6 +128,14 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
     // scalar state, meaningful in thread 0 only
     T rho = T(0), rr = T(0), bnorm = T(0);
     int k = 0, status = GBS_DIVERGED_ITS;
+    // Stopping-test norm N: rr holds N(r)^2 (r.r, z.z, or r.z for the
+    // natural norm), bnorm N(b).  ref_sq(b_i, i) is b_i's term of N(b)^2.
+    const int norm = a.norm;
+    auto ref_sq = [&](T bi, int64_t i) -> T {
+        if (norm == GBS_NORM_UNPRECONDITIONED) return bi * bi;
+        const T db = gbs_ld(dinv + i, pk) * bi;
+        return norm == GBS_NORM_PRECONDITIONED ? db * db : bi * db;
+    };
 
     // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b
     T acc[3] = {T(0), T(0), T(0)};
@@ -139,8 +148,9 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             gbs_st(zT + i, zi, pk);
             gbs_st(pT + i, zi, pk);
             acc[0] += ri * zi;
-            acc[1] += ri * ri;
-            acc[2] += bi * bi;
+            const T w = norm == GBS_NORM_PRECONDITIONED ? zi : ri;
+            acc[1] += w * w;
+            acc[2] += ref_sq(bi, i);
         };
         if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, xT, wsm, wq,
                               parity, cfg, ps, pk, a.timeout_ns, epi) &&
@@ -155,8 +165,9 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             gbs_st(zT + i, zi, pk);
             gbs_st(pT + i, zi, pk);
             acc[0] += bi * zi;
-            acc[1] += bi * bi;
-            acc[2] += bi * bi;
+            const T w = norm == GBS_NORM_PRECONDITIONED ? zi : bi;
+            acc[1] += w * w;
+            acc[2] += ref_sq(bi, i);
         }
     }
     gbs_block_sum_staged<T, 3, GBS_PBLOCK>(acc, sm.buf, sm.out);
@@ -173,7 +184,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         gbs_warp_grid_sum<T, 3>(part, G, G, g3);
         if (threadIdx.x == 0) {
             rho = g3[0];
-            rr = g3[1];
+            rr = norm == GBS_NORM_NATURAL ? g3[0] : g3[1];
             bnorm = sqrt(g3[2]);
             const int s = pcg_check<T>(sqrt(rr), rho, rtol * bnorm, 0, maxit);
             ctl.go = s == -100;
@@ -244,7 +255,8 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                     gbs_st(rT + i, rn_, pk);
                     gbs_st(zT + i, zn_, pk);
                     u[0] += rn_ * zn_;
-                    u[1] += rn_ * rn_;
+                    const T w = norm == GBS_NORM_PRECONDITIONED ? zn_ : rn_;
+                    u[1] += w * w;
                 }
             }
         }
@@ -261,7 +273,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             if (threadIdx.x == 0) {
                 ++k;
                 const T rho_new = g2[0];
-                rr = g2[1];
+                rr = norm == GBS_NORM_NATURAL ? g2[0] : g2[1];
                 if (rho_new < T(0)) {
                     status = GBS_ERR_INDEFINITE;
                     ctl.go = 0;
@@ -587,6 +599,7 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     a.maxit = maxit;
     a.outer_maxit = o->outer_maxit;
     a.x0_zero = 0;
+    a.norm = o->norm_type;
     a.skip_cta = o->fault_skip_arrival;
     a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
@@ -616,6 +629,7 @@ struct OpArgs {
     OpScalars *s;
     double rtol;
     int maxit;
+    int norm;      // GBS_NORM_*: s->rr holds N(r)^2 and s->bnorm N(b)
 };
 
 // Last-CTA-done reduction of K partials into tot (fixed order).  Returns
@@ -657,13 +671,19 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     double acc[3] = {0.0, 0.0, 0.0};
     auto epi = [&](int64_t i, double s) {
-        const double bi = a.b[i], ri = bi - s, zi = a.dinv[i] * ri;
+        const double bi = a.b[i], di = a.dinv[i], ri = bi - s, zi = di * ri;
         a.r[i] = ri;
         a.z[i] = zi;
         a.p[i] = zi;
         acc[0] += ri * zi;
-        acc[1] += ri * ri;
-        acc[2] += bi * bi;
+        const double w = a.norm == GBS_NORM_PRECONDITIONED ? zi : ri;
+        acc[1] += w * w;
+        if (a.norm == GBS_NORM_UNPRECONDITIONED) {
+            acc[2] += bi * bi;
+        } else {
+            const double db = di * bi;
+            acc[2] += a.norm == GBS_NORM_PRECONDITIONED ? db * db : bi * db;
+        }
     };
     const int64_t nw = (int64_t)gridDim.x * GBS_WARPS;
     for (int64_t t = (int64_t)blockIdx.x * GBS_WARPS + (threadIdx.x >> 5); t < a.ntiles; t += nw)
@@ -672,7 +692,7 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_setup(OpArgs a)
     double tot[3];
     if (op_reduce<3>(acc, a.part, &a.s->counter[0], s_red, tot, &s_last) && threadIdx.x == 0) {
         a.s->rho = tot[0];
-        a.s->rr = tot[1];
+        a.s->rr = a.norm == GBS_NORM_NATURAL ? tot[0] : tot[1];
         a.s->bnorm = sqrt(tot[2]);
         a.s->k = 0;
         a.s->done = 0;
@@ -722,12 +742,13 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_op_update(OpArgs a)
         a.r[i] = ri;
         a.z[i] = zi;
         u[0] += ri * zi;
-        u[1] += ri * ri;
+        const double w = a.norm == GBS_NORM_PRECONDITIONED ? zi : ri;
+        u[1] += w * w;
     }
     double tot[2];
     if (op_reduce<2>(u, a.part, &a.s->counter[2], s_red, tot, &s_last) && threadIdx.x == 0) {
         a.s->k += 1;
-        a.s->rr = tot[1];
+        a.s->rr = a.norm == GBS_NORM_NATURAL ? tot[0] : tot[1];
         if (tot[0] < 0.0) {
             a.s->status = GBS_ERR_INDEFINITE;
             a.s->done = 1;
@@ -801,6 +822,7 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, con
     a.x = (double *)x->data;
     a.rtol = rtol;
     a.maxit = maxit;
+    a.norm = o->norm_type;
 
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
     GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
@@ -880,6 +902,8 @@ extern "C" int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol,
     if (b->data == x->data && A->n > 0) return GBS_ERR_ARG;
     if (!(rtol >= 0.0) || maxit < 0) return GBS_ERR_ARG;
     if (o->mode != GBS_MODE_FP64 && o->mode != GBS_MODE_MIXED) return GBS_ERR_ARG;
+    if (o->norm_type < GBS_NORM_UNPRECONDITIONED || o->norm_type > GBS_NORM_NATURAL) return GBS_ERR_ARG;
+    if (o->norm_type != GBS_NORM_UNPRECONDITIONED && o->mode == GBS_MODE_MIXED) return GBS_ERR_ARG;
     gbs_solve_info tmp;
     memset(&tmp, 0, sizeof(tmp));
     int st;
@@ -901,7 +925,7 @@ extern "C" int gbs_ksp_solve_cg_ex(gbs_mat A, gbs_vec b, gbs_vec x, double rtol,
         if (alg == GBS_ALG_AUTO) alg = auto_cluster ? GBS_ALG_CLUSTER : GBS_ALG_PERSISTENT;
         st = GBS_ERR_UNSUPPORTED;
         if (alg == GBS_ALG_CLUSTER) {
-            if (fits) st = gbs_solve_cluster(A, b, x, rtol, maxit, &tmp);
+            if (fits) st = gbs_solve_cluster(A, b, x, rtol, maxit, o->norm_type, &tmp);
             if (st == GBS_ERR_UNSUPPORTED && auto_cluster) alg = GBS_ALG_PERSISTENT;
         }
         if (alg == GBS_ALG_PERSISTENT)
@@ -1026,6 +1050,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     a.rtol = rtol;
     a.maxit = maxit;
     a.skip_cta = -1;
+    a.norm = c->opts.norm_type;
     a.timeout_ns = (unsigned long long)c->opts.barrier_timeout_ms * 1000000ull;
     // the barrier and the result record must start at zero; the vectors and
     // partial sums are written before they are read

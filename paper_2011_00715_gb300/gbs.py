@@ -46,6 +46,9 @@ GBS_ALG_PERSISTENT = 1
 GBS_ALG_PEROP = 2
 GBS_ALG_GRAPH = 3
 GBS_ALG_CLUSTER = 4
+GBS_NORM_UNPRECONDITIONED = 0
+GBS_NORM_PRECONDITIONED = 1
+GBS_NORM_NATURAL = 2
 GBS_CLUSTER_MAX_ROWS = 32768
 GBS_NOALLOC_MAX_ROWS = 262144
 
@@ -61,7 +64,8 @@ class gbs_opts(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
-                ("persistent_ctas", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("persistent_ctas", ctypes.c_int), ("norm_type", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class gbs_solve_info(ctypes.Structure):

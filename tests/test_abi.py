@@ -67,7 +67,7 @@ def test_status_codes_match_header():
 def test_enums_and_limits_match_header():
     from paper_2011_00715_gb300 import gbs
     text = open(HEADER).read()
-    found = re.findall(r"\b(GBS_(?:ALG|MODE)_[A-Z0-9]+)\s*=\s*(-?\d+)", text)
+    found = re.findall(r"\b(GBS_(?:ALG|MODE|NORM)_[A-Z0-9]+)\s*=\s*(-?\d+)", text)
     found += re.findall(r"#define\s+(GBS_[A-Z_]+_MAX_ROWS)\s+(\d+)", text)
     assert any(n == "GBS_ALG_CLUSTER" for n, _ in found)
     for name, val in found:

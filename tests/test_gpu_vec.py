@@ -76,19 +76,19 @@ def test_dot_norm_async_stream_order(S):
     for k, n in enumerate((31, 65537, 3_000_001)):
         x = I.uniform_pm1(6, k, n)
         y = I.uniform_pm1(6, k + 10, n)
-        xv, _ = S.vec(x)
-        yv, _ = S.vec(y)
+        xv, xt = S.vec(x)
+        yv, yt = S.vec(y)
         gbs.gbs_vec_dot_async(xv, yv, out[2 * k:])
         gbs.gbs_vec_norm2_async(xv, out[2 * k + 1:])
-        res.append((xv, yv))
+        res.append((xv, yv, xt, yt))   # the tensors own the vectors' memory
     doubled = out * 2.0            # queued behind the writes on the same stream
     host = doubled.cpu().numpy() / 2.0
-    for k, (xv, yv) in enumerate(res):
+    for k, (xv, yv, _, _) in enumerate(res):
         assert host[2 * k] == gbs.gbs_vec_dot(xv, yv)
         assert host[2 * k + 1] == gbs.gbs_vec_norm2(xv)
     # FP32: the FP32 result widened
     x32 = I.uniform_pm1(7, 0, 100_003).astype(np.float32)
-    v32, _ = S.vec(x32, np.float32)
+    v32, t32 = S.vec(x32, np.float32)
     gbs.gbs_vec_norm2_async(v32, out[6:])
     gbs.gbs_vec_dot_async(v32, v32, out[7:])
     torch.cuda.current_stream().synchronize()
