@@ -68,6 +68,12 @@ def parse_args():
                    help="run only the vector-operation / MatMult size sweep")
     p.add_argument("--c5-pool", type=int, default=12,
                    help="distinct operators the serving requests draw from")
+    p.add_argument("--c5-sweep", action="store_true",
+                   help="run only the serving workload's arrival-rate sweep")
+    p.add_argument("--c5-warmup", type=int, default=100,
+                   help="warm-up requests of the rate sweep (not counted)")
+    p.add_argument("--c5-sweep-requests", type=int, default=2000,
+                   help="requests per rate of the sweep")
     return p.parse_args()
 
 
@@ -374,7 +380,9 @@ def run_gbs(args, rank, world, local):
                            algorithm="persistent cooperative kernel, 3 grid barriers/iteration"),
             "solve": {"status": sorted(statuses), "iters": iters[0],
                       "true_rel_residual": true_rel, "rel_err_vs_xstar": err_xs,
-                      "kernel_ms": dev_ms, "us_per_iter": dev_ms * 1e3 / iters[0]},
+                      "kernel_ms": dev_ms, "us_per_iter": dev_ms * 1e3 / iters[0],
+                      "kernel_ms_median": float(np.percentile([i.device_ms for i in infos], 50)),
+                      "kernel_ms_p99": float(np.percentile([i.device_ms for i in infos], 99))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": measured_traffic(iters[0]),
@@ -778,25 +786,18 @@ def c4_batched(g, args):
     return res
 
 
-def c5_serving(g, args):
-    """Poisson-arriving solve requests on 27-point lognormal(0,1) operators
-    (n log-uniform in [1e3, 1e6], 1-4 right-hand sides, rtol 1e-10), served
-    by the continuous-batching engine (mixed precision, 150 GB budget) and,
-    on the same stream, by plain FP64 per-solve launches."""
+def c5_workload(g, specs):
+    """Operators (distinct ones generated once) and right-hand sides b = A x*
+    (on the device, then to the host: requests carry host data)."""
     import numpy as np
     import torch
     from paper_2011_00715_gb300 import inputs as I
     gbs = g.gbs
-    nreq = args.c5_requests
-    pool = args.c5_pool
-    specs = I.c5_request_specs(count=nreq, pool=pool)
-    t_gen = time.perf_counter()
     mats = {}
     for s in specs:
         key = s["matrix_key"]
         if key not in mats:
             mats[key] = I.var27(*s["dims"], seed=s["seed"], sigma=1.0)
-    # right-hand sides b = A x* on the device, then to the host (requests carry host data)
     bs = []
     dev = {}
     for s in specs:
@@ -817,14 +818,14 @@ def c5_serving(g, args):
         bs.append(bt.cpu().numpy())
     for h in dev.values():
         gbs.gbs_mat_destroy(h)
-    t_gen = time.perf_counter() - t_gen
-    ncols = sum(s["nrhs"] for s in specs)
-    out = {"requests": nreq, "matrix_pool": pool, "columns": ncols, "setup_s": t_gen,
-           "rows_mean": float(np.mean([mats[s["matrix_key"]].n for s in specs]))}
+    return mats, bs
 
-    # the engine's autotuner runs once per class of systems and context; a
-    # server pays it at start-up, so it is timed here, outside the runs
-    t_tune = time.perf_counter()
+
+def c5_tune(g, specs, mats):
+    """The engine's autotuner, once per class of systems (a server pays it at
+    start-up, outside the timed runs)."""
+    gbs = g.gbs
+    t = time.perf_counter()
     tuned = {}
     for s in specs:
         kp = 1 if s["nrhs"] == 1 else 2 if s["nrhs"] == 2 else 4
@@ -833,102 +834,169 @@ def c5_serving(g, args):
             h = gbs.gbs_mat_create_aij(g.ctx, A.n, A.n, A.rowptr, A.colidx, A.vals)
             tuned[kp] = gbs.gbs_batched_tune(g.ctx, h, s["nrhs"], gbs.GBS_MODE_MIXED)
             gbs.gbs_mat_destroy(h)
-    out["autotune"] = {"seconds": time.perf_counter() - t_tune,
-                       "lanes_per_row_by_column_stride": {str(k): v for k, v in sorted(tuned.items())}}
-    times = {}
+    return {"seconds": time.perf_counter() - t,
+            "lanes_per_row_by_column_stride": {str(k): v for k, v in sorted(tuned.items())}}
 
-    def serve_batched(arrivals):
-        srv = gbs.gbs_server_create(g.ctx, 150 << 30, 0, gbs.GBS_MODE_MIXED)
-        lat = [None] * nreq
-        tickets = {}
-        nxt = 0
-        t0 = time.perf_counter()
-        done = 0
-        worst = 0.0
-        while done < nreq:
-            now = time.perf_counter() - t0
-            while nxt < nreq and arrivals[nxt] <= now:
-                s = specs[nxt]
-                A = mats[s["matrix_key"]]
-                # the request's arrays stay alive in mats / bs until it is done
-                tickets[nxt] = gbs.gbs_server_submit_borrowed(srv, A.n, A.rowptr, A.colidx, A.vals,
-                                                              s["nrhs"], bs[nxt], 1e-10, 20000)
-                nxt += 1
-            q, running, fin, used = gbs.gbs_server_stats(srv)
-            if running == 0 and q == 0 and nxt < nreq:
-                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
-                continue
-            gbs.gbs_server_progress(srv)
-            tnow = time.perf_counter() - t0
-            for i, t in list(tickets.items()):
-                if gbs.gbs_server_poll(srv, t):
-                    s = specs[i]
-                    A = mats[s["matrix_key"]]
-                    x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, s["nrhs"])
-                    lat[i] = tnow - arrivals[i]
-                    worst = max(worst, float(np.max(rns / np.maximum(
-                        [np.linalg.norm(bs[i][c * A.n:(c + 1) * A.n]) for c in range(s["nrhs"])],
-                        1e-300))))
-                    if not np.all(sts == 0):
-                        worst = float("inf")
-                    del tickets[i]
-                    done += 1
-        total = time.perf_counter() - t0
-        ta, tq, tr, nq = gbs.gbs_server_times(srv)
-        gbs.gbs_server_destroy(srv)
-        times["batched"] = {"admit_s": ta, "quanta_s": tq, "retire_s": tr, "quanta": nq}
-        return total, np.array(lat), worst
 
-    def serve_perop(arrivals):
-        lat = [None] * nreq
-        t0 = time.perf_counter()
-        o = gbs.gbs_opts_default(mode=gbs.GBS_MODE_FP64, algorithm=gbs.GBS_ALG_PERSISTENT)
-        worst = 0.0
-        for i, s in enumerate(specs):
-            now = time.perf_counter() - t0
-            if arrivals[i] > now:
-                time.sleep(arrivals[i] - now)
+def serve_batched(g, specs, mats, bs, arrivals):
+    """Continuous batching: requests are submitted (borrowed host arrays) as
+    they arrive and fetched as they finish.  Returns (wall s, latencies s,
+    worst relative residual, engine time split)."""
+    import numpy as np
+    gbs = g.gbs
+    nreq = len(specs)
+    srv = gbs.gbs_server_create(g.ctx, 150 << 30, 0, gbs.GBS_MODE_MIXED)
+    lat = [None] * nreq
+    tickets = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    done = 0
+    worst = 0.0
+    while done < nreq:
+        now = time.perf_counter() - t0
+        while nxt < nreq and arrivals[nxt] <= now:
+            s = specs[nxt]
             A = mats[s["matrix_key"]]
-            h = gbs.gbs_mat_create_aij(g.ctx, A.n, A.n, A.rowptr, A.colidx, A.vals)
-            bt = torch.from_numpy(bs[i]).cuda()
-            xt = torch.zeros_like(bt)
-            for c in range(s["nrhs"]):
-                bv = gbs.gbs_vec_wrap(g.ctx, bt[c * A.n:(c + 1) * A.n])
-                xv = gbs.gbs_vec_wrap(g.ctx, xt[c * A.n:(c + 1) * A.n])
-                info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, 1e-10, 20000, o)
-                worst = max(worst, info.rnorm / info.bnorm if info.status == 0 else float("inf"))
-                gbs.gbs_vec_destroy(bv)
-                gbs.gbs_vec_destroy(xv)
-            xt.cpu()
-            gbs.gbs_mat_destroy(h)
-            lat[i] = time.perf_counter() - t0 - arrivals[i]
-        total = time.perf_counter() - t0
-        return total, np.array(lat), worst
+            # the request's arrays stay alive in mats / bs until it is done
+            tickets[nxt] = gbs.gbs_server_submit_borrowed(srv, A.n, A.rowptr, A.colidx, A.vals,
+                                                          s["nrhs"], bs[nxt], 1e-10, 20000)
+            nxt += 1
+        q, running, fin, used = gbs.gbs_server_stats(srv)
+        if running == 0 and q == 0 and nxt < nreq:
+            time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+            continue
+        gbs.gbs_server_progress(srv)
+        tnow = time.perf_counter() - t0
+        for i, t in list(tickets.items()):
+            if gbs.gbs_server_poll(srv, t):
+                s = specs[i]
+                A = mats[s["matrix_key"]]
+                x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, s["nrhs"])
+                lat[i] = tnow - arrivals[i]
+                worst = max(worst, float(np.max(rns / np.maximum(
+                    [np.linalg.norm(bs[i][c * A.n:(c + 1) * A.n]) for c in range(s["nrhs"])],
+                    1e-300))))
+                if not np.all(sts == 0):
+                    worst = float("inf")
+                del tickets[i]
+                done += 1
+    total = time.perf_counter() - t0
+    ta, tq, tr, nq = gbs.gbs_server_times(srv)
+    gbs.gbs_server_destroy(srv)
+    return total, np.array(lat), worst, {"admit_s": ta, "quanta_s": tq, "retire_s": tr,
+                                         "quanta": nq}
+
+
+def serve_perop(g, specs, mats, bs, arrivals):
+    """Plain FP64 per-solve launches in arrival order (one persistent solve
+    per right-hand side).  Returns (wall s, latencies s, worst relative
+    residual)."""
+    import numpy as np
+    import torch
+    gbs = g.gbs
+    nreq = len(specs)
+    lat = [None] * nreq
+    t0 = time.perf_counter()
+    o = gbs.gbs_opts_default(mode=gbs.GBS_MODE_FP64, algorithm=gbs.GBS_ALG_PERSISTENT)
+    worst = 0.0
+    for i, s in enumerate(specs):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        A = mats[s["matrix_key"]]
+        h = gbs.gbs_mat_create_aij(g.ctx, A.n, A.n, A.rowptr, A.colidx, A.vals)
+        bt = torch.from_numpy(bs[i]).cuda()
+        xt = torch.zeros_like(bt)
+        for c in range(s["nrhs"]):
+            bv = gbs.gbs_vec_wrap(g.ctx, bt[c * A.n:(c + 1) * A.n])
+            xv = gbs.gbs_vec_wrap(g.ctx, xt[c * A.n:(c + 1) * A.n])
+            info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, 1e-10, 20000, o)
+            worst = max(worst, info.rnorm / info.bnorm if info.status == 0 else float("inf"))
+            gbs.gbs_vec_destroy(bv)
+            gbs.gbs_vec_destroy(xv)
+        xt.cpu()
+        gbs.gbs_mat_destroy(h)
+        lat[i] = time.perf_counter() - t0 - arrivals[i]
+    total = time.perf_counter() - t0
+    return total, np.array(lat), worst
+
+
+def _served(ncols, nreq, total, lat, worst):
+    import numpy as np
+    return {"solves_per_s": ncols / total, "requests_per_s": nreq / total,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_rel_residual": worst}
+
+
+def c5_serving(g, args):
+    """Poisson-arriving solve requests on 27-point lognormal(0,1) operators
+    (n log-uniform in [1e3, 1e6], 1-4 right-hand sides, rtol 1e-10), served
+    by the continuous-batching engine (mixed precision, 150 GB budget) and,
+    on the same stream, by plain FP64 per-solve launches."""
+    import numpy as np
+    from paper_2011_00715_gb300 import inputs as I
+    nreq = args.c5_requests
+    pool = args.c5_pool
+    specs = I.c5_request_specs(count=nreq, pool=pool)
+    t_gen = time.perf_counter()
+    mats, bs = c5_workload(g, specs)
+    t_gen = time.perf_counter() - t_gen
+    ncols = sum(s["nrhs"] for s in specs)
+    out = {"requests": nreq, "matrix_pool": pool, "columns": ncols, "setup_s": t_gen,
+           "rows_mean": float(np.mean([mats[s["matrix_key"]].n for s in specs]))}
+    out["autotune"] = c5_tune(g, specs, mats)
 
     # saturation (every request present at t = 0), then a Poisson stream at
     # half the batched engine's saturated request rate
     zero = np.zeros(nreq)
-    tb, lb, wb = serve_batched(zero)
-    rate = 0.5 * nreq / tb
+    sat = serve_batched(g, specs, mats, bs, zero)
+    rate = 0.5 * nreq / sat[0]
     arr = I.poisson_arrivals(5, rate, nreq)
     runs = {"saturation": zero, f"poisson_{rate:.1f}_req_per_s": arr}
     for name, arrivals in runs.items():
-        if name == "saturation":
-            t_b, l_b, w_b = tb, lb, wb
-        else:
-            t_b, l_b, w_b = serve_batched(arrivals)
-        t_p, l_p, w_p = serve_perop(arrivals)
-        out[name] = {
-            "batched_mixed": {"solves_per_s": ncols / t_b, "requests_per_s": nreq / t_b,
-                              "p50_ms": float(np.percentile(l_b, 50) * 1e3),
-                              "p99_ms": float(np.percentile(l_b, 99) * 1e3),
-                              "max_rel_residual": w_b},
-            "perop_fp64": {"solves_per_s": ncols / t_p, "requests_per_s": nreq / t_p,
-                           "p50_ms": float(np.percentile(l_p, 50) * 1e3),
-                           "p99_ms": float(np.percentile(l_p, 99) * 1e3),
-                           "max_rel_residual": w_p},
-            "speedup_solves_per_s": t_p / t_b,
-            "batched_engine_time": dict(times["batched"])}
+        t_b, l_b, w_b, eng = sat if name == "saturation" else \
+            serve_batched(g, specs, mats, bs, arrivals)
+        t_p, l_p, w_p = serve_perop(g, specs, mats, bs, arrivals)
+        out[name] = {"batched_mixed": _served(ncols, nreq, t_b, l_b, w_b),
+                     "perop_fp64": _served(ncols, nreq, t_p, l_p, w_p),
+                     "speedup_solves_per_s": t_p / t_b,
+                     "batched_engine_time": eng}
+    return out
+
+
+def c5_sweep(g, args):
+    """The serving workload's arrival-rate sweep: a warm-up of W requests
+    served by both engines and discarded, then N further requests at Poisson
+    rates lambda_sat / 4, / 2, x 1 and x 2 (geometric, into saturation),
+    where lambda_sat is the batched engine's request rate with every request
+    present at once; both engines at every rate."""
+    import numpy as np
+    from paper_2011_00715_gb300 import inputs as I
+    W, N = args.c5_warmup, args.c5_sweep_requests
+    specs = I.c5_request_specs(count=W + N, pool=args.c5_pool)
+    mats, bs = c5_workload(g, specs)
+    out = {"warmup_requests": W, "requests": N, "matrix_pool": args.c5_pool,
+           "autotune": c5_tune(g, specs, mats)}
+    warm, main_ = specs[:W], specs[W:]
+    serve_batched(g, warm, mats, bs[:W], np.zeros(W))
+    serve_perop(g, warm, mats, bs[:W], np.zeros(W))
+    bsm = bs[W:]
+    ncols = sum(s["nrhs"] for s in main_)
+    out["columns"] = ncols
+    sat = serve_batched(g, main_, mats, bsm, np.zeros(N))
+    lam_sat = N / sat[0]
+    out["saturation_batched"] = _served(ncols, N, sat[0], sat[1], sat[2])
+    out["lambda_sat_req_per_s"] = lam_sat
+    rates = []
+    for f in (0.25, 0.5, 1.0, 2.0):
+        lam = f * lam_sat
+        arr = I.poisson_arrivals(6, lam, N)
+        tb, lb, wb, _eng = serve_batched(g, main_, mats, bsm, arr)
+        tp, lp, wp = serve_perop(g, main_, mats, bsm, arr)
+        rates.append({"lambda_req_per_s": lam, "lambda_over_sat": f,
+                      "batched_mixed": _served(ncols, N, tb, lb, wb),
+                      "perop_fp64": _served(ncols, N, tp, lp, wp)})
+    out["rates"] = rates
     return out
 
 
@@ -966,6 +1034,12 @@ def main():
         B.build()
         g = Gpu(local)
         print(json.dumps({"c2_sweep": c2_sweep(g, args)}), flush=True)
+        return
+    if args.c5_sweep:
+        from paper_2011_00715_gb300 import build as B
+        B.build()
+        g = Gpu(local)
+        print(json.dumps({"c5_sweep": c5_sweep(g, args)}), flush=True)
         return
     if args.c5_only:
         from paper_2011_00715_gb300 import build as B
