@@ -111,8 +111,8 @@ struct gbs_result_dev {
 
 // Software grid barrier for cooperative persistent kernels.
 struct gbs_grid_barrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count;  // arrivals since the launch (zeroed before it)
+    unsigned int gen;    // unused
     int error;           // 0, or a negative GBS_ERR_* set by the CTA that gave up
     int where;
 };
@@ -342,31 +342,41 @@ __device__ __forceinline__ void gbs_grid_sum(const T *partials, int stride, int 
 // Grid-wide barrier with a bounded wait.  Returns false if this CTA or
 // another one gave up (bar->error set); the caller must then leave its
 // loop.  `skip` makes this CTA not arrive (fault-injection for tests).
+//
+// One monotonic arrival counter, zeroed before the launch: barrier number
+// `where` (0, 1, 2, ... in the order every CTA meets them) is complete once
+// the counter reaches (where + 1) * gridDim.x.  Thread 0 of each CTA
+// arrives with one release add (the CTA's writes, ordered before it by the
+// CTA barrier, become visible to every CTA that observes the count) and
+// waits with acquire loads of the same word: no generation word to read
+// before arriving and no reset, so a barrier costs one round trip to L2
+// plus the polling (1.2 us on 152 CTAs, against 2.0 us for a counter plus a
+// generation word).  Counts are compared by signed difference, so the
+// 32-bit counter may wrap.
+__device__ __forceinline__ void gbs_red_add_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool gbs_grid_sync(gbs_grid_barrier *bar, unsigned long long timeout_ns,
                                               int where, bool skip, int *s_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int gen = gbs_ld_acquire(&bar->gen);
-        if (!skip) {
-            __threadfence();
-            const unsigned int arrived = atomicAdd(&bar->count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&bar->count, 0u);
-                __threadfence();
-                gbs_st_release(&bar->gen, gen + 1);
-            }
-        }
+        if (!skip) gbs_red_add_release(&bar->count, 1u);
+        const unsigned int target = (unsigned int)(where + 1) * gridDim.x;
         const unsigned long long t0 = gbs_globaltimer();
-        while (gbs_ld_acquire(&bar->gen) == gen) {
-            if (gbs_ld_relaxed_int(&bar->error) != 0) { ok = 0; break; }
-            if (gbs_globaltimer() - t0 > timeout_ns) {
-                if (atomicCAS(&bar->error, 0, GBS_ERR_TIMEOUT) == 0) bar->where = where;
-                ok = 0;
-                break;
+        for (unsigned int spin = 1; (int)(gbs_ld_acquire(&bar->count) - target) < 0; ++spin) {
+            if ((spin & 15u) == 0) {
+                if (gbs_ld_relaxed_int(&bar->error) != 0) { ok = 0; break; }
+                if (gbs_globaltimer() - t0 > timeout_ns) {
+                    if (atomicCAS(&bar->error, 0, GBS_ERR_TIMEOUT) == 0) bar->where = where;
+                    ok = 0;
+                    break;
+                }
             }
-            __nanosleep(32);
+            __nanosleep(20);
         }
         // a failure recorded by any CTA before it arrived (e.g. a bulk copy
         // that did not complete) fails the barrier for everyone
