@@ -68,6 +68,8 @@ def parse_args():
                    help="run only the vector-operation / MatMult size sweep")
     p.add_argument("--c5-pool", type=int, default=12,
                    help="distinct operators the serving requests draw from")
+    p.add_argument("--c1-only", action="store_true",
+                   help="run only the C1 solves (profiling of the one-cluster kernel)")
     p.add_argument("--c5-sweep", action="store_true",
                    help="run only the serving workload's arrival-rate sweep")
     p.add_argument("--c5-warmup", type=int, default=100,
@@ -454,26 +456,12 @@ def e2e_c2(g, A, xs, args, iters_full):
                     "gbs_ksp_solve_cg_ex + gbs_vec_get_values(x) + gbs_mat_destroy"}
 
 
-def extras(g, args, A, Ah, xsv):
-    import numpy as np
+def c1_solves(g):
+    """C1: the 64x64 2D Laplacian at rtol 1e-8 through the four launch
+    algorithms (one cluster, persistent grid, per-op kernels, CUDA graph)."""
     import torch
     from paper_2011_00715_gb300 import inputs as I
     gbs = g.gbs
-    out = {}
-    hbm, _ = peaks()
-    # --- standalone MatMult on the 128^3 matrix
-    yt = torch.empty(A.n, dtype=torch.float64, device="cuda")
-    yv = gbs.gbs_vec_wrap(g.ctx, yt)
-    for _ in range(3):
-        gbs.gbs_mat_mult(Ah, xsv, yv)
-    reps = 50
-    el = event_time(torch, lambda: gbs.gbs_mat_mult(Ah, xsv, yv), reps)
-    bb = bytes_spmv_fp64(A.n, A.nnz)
-    out["spmv_c2_fp64"] = {"us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
-                           "frac": bb / (el / reps) / 1e9 / hbm,
-                           "bytes_model": "12 nnz + 4(n+1) + 8n + 8n"}
-    gbs.gbs_vec_destroy(yv)
-    # --- C1: 64x64 2D Laplacian, rtol 1e-8
     C1 = I.lap2d5(64)
     h = g.mat(C1)
     xs = I.xstar(C1.n, 1)
@@ -499,10 +487,33 @@ def extras(g, args, A, Ah, xsv):
         el = event_time(torch, st, n_rep)
         res[name] = {"solves_per_s": n_rep / el, "iters": info.iters,
                      "us_per_iter": el / n_rep / info.iters * 1e6, "status": info.status}
-    out["c1_lap2d5_64_fp64"] = res
     for v in (xsv1, b1v, x1v):
         gbs.gbs_vec_destroy(v)
     gbs.gbs_mat_destroy(h)
+    return res
+
+
+def extras(g, args, A, Ah, xsv):
+    import numpy as np
+    import torch
+    from paper_2011_00715_gb300 import inputs as I
+    gbs = g.gbs
+    out = {}
+    hbm, _ = peaks()
+    # --- standalone MatMult on the 128^3 matrix
+    yt = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    yv = gbs.gbs_vec_wrap(g.ctx, yt)
+    for _ in range(3):
+        gbs.gbs_mat_mult(Ah, xsv, yv)
+    reps = 50
+    el = event_time(torch, lambda: gbs.gbs_mat_mult(Ah, xsv, yv), reps)
+    bb = bytes_spmv_fp64(A.n, A.nnz)
+    out["spmv_c2_fp64"] = {"us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
+                           "frac": bb / (el / reps) / 1e9 / hbm,
+                           "bytes_model": "12 nnz + 4(n+1) + 8n + 8n"}
+    gbs.gbs_vec_destroy(yv)
+    # --- C1: 64x64 2D Laplacian, rtol 1e-8
+    out["c1_lap2d5_64_fp64"] = c1_solves(g)
     # --- C3: 96^3 27-point variable coefficient, mixed vs FP64 at rtol 1e-10
     C3 = I.var27(96, seed=3, sigma=1.0)
     h = g.mat(C3)
@@ -1034,6 +1045,12 @@ def main():
         B.build()
         g = Gpu(local)
         print(json.dumps({"c2_sweep": c2_sweep(g, args)}), flush=True)
+        return
+    if args.c1_only:
+        from paper_2011_00715_gb300 import build as B
+        B.build()
+        g = Gpu(local)
+        print(json.dumps({"c1_lap2d5_64_fp64": c1_solves(g)}), flush=True)
         return
     if args.c5_sweep:
         from paper_2011_00715_gb300 import build as B

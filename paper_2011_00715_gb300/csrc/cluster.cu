@@ -4,7 +4,7 @@
 //
 // The grid-wide persistent kernel pays three software grid barriers per
 // iteration across all 152 SMs.  A small system instead runs in one cluster
-// of up to 16 CTAs: CTA k owns the rows [k R, (k+1) R) (R a power of two)
+// of up to 16 CTAs: CTA k owns the rows [k R, (k+1) R), R = ceil(n / CTAs),
 // and keeps x, r, p, A p and D^-1 of those rows in its shared memory.  The
 // SpMV reads the direction vector p of other CTAs' rows through distributed
 // shared memory, and the CTAs synchronise with the hardware cluster
@@ -46,11 +46,13 @@ constexpr int kMinRows = 128;            // rows per CTA at least
 constexpr int kMaxRowsPerCta = GBS_CLUSTER_MAX_ROWS / kPortableCluster;
 constexpr size_t kMaxSmem = (size_t)5 * kMaxRowsPerCta * sizeof(double);
 static_assert(kMaxSmem <= 200 * 1024, "five FP64 vectors of R rows fit in shared memory");
-static_assert((kMaxRowsPerCta & (kMaxRowsPerCta - 1)) == 0, "rows per CTA is a power of two");
+static_assert((uint64_t)GBS_CLUSTER_MAX_ROWS * kMaxRowsPerCta < (1ull << 32),
+              "column / R by a multiply-high is exact");
 
 struct ClArgs {
     int n;
-    int rows, log_rows;      // rows per CTA (a power of two)
+    int rows;                // rows per CTA (R)
+    unsigned int rmagic;     // floor(2^32 / R) + 1: c / R = umulhi(c, rmagic) for c < n
     const int32_t *rowptr, *colidx;
     const double *vals, *dinv, *b;
     double *x;               // initial guess in, solution out (global)
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
     }
     __syncthreads();
 
-    const int R1 = R - 1, lg = a.log_rows;
+    const unsigned int rm = a.rmagic;
     for (int kk = 0; s.go && kk <= a.maxit; ++kk) {
         // ---- S: q = A p (p of other CTAs' rows through distributed shared
         // memory), partial p.q
@@ -205,7 +207,8 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
             double sum = 0.0;
             const int e1 = __ldg(a.rowptr + gi + 1);
             for (int e = __ldg(a.rowptr + gi); e < e1; ++e) {
-                const int c = __ldg(a.colidx + e), owner = c >> lg, off = c & R1;
+                const int c = __ldg(a.colidx + e);
+                const int owner = (int)__umulhi((unsigned int)c, rm), off = c - owner * R;
                 const double pc = owner == rank ? p[off] : s.pseg[owner][off];
                 sum = fma(__ldg(a.vals + e), pc, sum);
             }
@@ -330,13 +333,11 @@ int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, i
     if (n <= 0 || n > GBS_CLUSTER_MAX_ROWS) return GBS_ERR_UNSUPPORTED;
     const int csmax = cluster_max(c->device);
     if (csmax == 0) return GBS_ERR_UNSUPPORTED;
-    int rows = kMinRows, lg = 7;
-    while ((n + rows - 1) / rows > csmax) {
-        rows *= 2;
-        ++lg;
-    }
+    // as many CTAs as the cluster allows while each keeps kMinRows rows
+    int64_t want = (n + kMinRows - 1) / kMinRows;
+    const int cs = (int)(want < csmax ? want : csmax);
+    const int rows = (int)((n + cs - 1) / cs);
     if (rows > kMaxRowsPerCta) return GBS_ERR_UNSUPPORTED;
-    const int cs = (int)((n + rows - 1) / rows);
     void *scr = nullptr;
     const int st = gbs_ctx_reserve(c, 256, &scr);
     if (st) return st;
@@ -344,7 +345,9 @@ int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, i
     memset(&a, 0, sizeof(a));
     a.n = (int)n;
     a.rows = rows;
-    a.log_rows = lg;
+    // one CTA: every column is its own (umulhi(c, 0) = 0); else rows >= 64,
+    // so the multiplier fits in 32 bits
+    a.rmagic = cs == 1 ? 0u : (unsigned int)((1ull << 32) / (uint64_t)rows) + 1u;
     a.rowptr = A->rowptr;
     a.colidx = A->colidx;
     a.vals = A->vals;
