@@ -41,8 +41,7 @@ constexpr size_t kPersistSmem = (size_t)GBS_WARP_STAGE_BYTES * GBS_PWARPS;
 
 template <typename T>
 struct PcgSmall {
-    T buf[3 * GBS_PBLOCK];   // staged block sums
-    T out[8];                // totals and part sums
+    T out[8];                // totals and part sums of a CTA sum
 };
 
 // Control block written by thread 0 of each CTA after a grid reduction and
@@ -111,13 +110,16 @@ __device__ __forceinline__ int pcg_check(T rn, T rho, T tol, int k, int maxit)
 // the same in every thread of every CTA.  The scalar recurrences (rho,
 // ||r||, alpha, beta, the stopping test) run in thread 0 of each CTA only;
 // *iters, *rnorm_out and *bnorm_out are valid in thread 0.
-template <typename T, typename IX>
+// NT: threads of the CTA; UNR: rows per thread per trip of the vector
+// phases; `stage` holds 3 NT values for the staged CTA sums.
+template <typename T, typename IX, int NT, int UNR>
 __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const T *dinv, const T *bT,
                         T *xT, T *rT,
                         T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
                         int *iters, T *rnorm_out, T *bnorm_out, int *barrier_no,
                         unsigned char *wsm, GbsWarpQ &wq, uint32_t &parity, int *s_next,
-                        const GbsPipeCfg &cfg, PcgSmall<T> &sm, PcgCtl<T> &ctl, int *s_flag)
+                        const GbsPipeCfg &cfg, PcgSmall<T> &sm, T *stage, PcgCtl<T> &ctl,
+                        int *s_flag)
 {
     const int G = gridDim.x, c = blockIdx.x, warp = threadIdx.x >> 5;
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
@@ -157,7 +159,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
     } else {
-        for (int64_t i = rb + threadIdx.x; i < re; i += GBS_PBLOCK) {
+        for (int64_t i = rb + threadIdx.x; i < re; i += NT) {
             const T bi = gbs_ld(bT + i, pk);
             const T zi = gbs_ld(dinv + i, pk) * bi;
             gbs_st(xT + i, T(0), pk);
@@ -170,7 +172,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             acc[2] += ref_sq(bi, i);
         }
     }
-    gbs_block_sum_staged<T, 3, GBS_PBLOCK>(acc, sm.buf, sm.out);
+    gbs_block_sum_staged<T, 3, NT>(acc, stage, sm.out);
     if (threadIdx.x == 0) {
         *s_next = 0;
         part[0 * G + c] = sm.out[0];
@@ -208,7 +210,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                               parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
-        gbs_block_sum_staged<T, 1, GBS_PBLOCK>(pq, sm.buf, sm.out);
+        gbs_block_sum_staged<T, 1, NT>(pq, stage, sm.out);
         if (threadIdx.x == 0) {
             *s_next = 0;
             part[3 * G + c] = sm.out[0];
@@ -230,14 +232,14 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         const T alpha = ctl.alpha;
 
         // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
-        // (four rows per thread per trip: all 20 loads are issued before the
-        // first use)
+        // (UNR rows per thread per trip: all 5 UNR loads are issued before
+        // the first use)
         T u[2] = {T(0), T(0)};
-        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 4 * GBS_PBLOCK) {
-            T pv[4], xv[4], rv[4], qv[4], dv[4];
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
+            T pv[UNR], xv[UNR], rv[UNR], qv[UNR], dv[UNR];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int64_t i = i0 + h * GBS_PBLOCK;
+            for (int h = 0; h < UNR; ++h) {
+                const int64_t i = i0 + h * NT;
                 if (i < re) {
                     pv[h] = gbs_ld(pT + i, pk);
                     xv[h] = gbs_ld(xT + i, pk);
@@ -247,8 +249,8 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 }
             }
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int64_t i = i0 + h * GBS_PBLOCK;
+            for (int h = 0; h < UNR; ++h) {
+                const int64_t i = i0 + h * NT;
                 if (i < re) {
                     const T rn_ = rv[h] - alpha * qv[h], zn_ = dv[h] * rn_;
                     gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
@@ -260,7 +262,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 }
             }
         }
-        gbs_block_sum_staged<T, 2, GBS_PBLOCK>(u, sm.buf, sm.out);
+        gbs_block_sum_staged<T, 2, NT>(u, stage, sm.out);
         if (threadIdx.x == 0) {
             part[4 * G + c] = sm.out[0];
             part[5 * G + c] = sm.out[1];
@@ -291,19 +293,19 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         const T beta = ctl.beta;
 
         // ---- P: p = z + beta p
-        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += 4 * GBS_PBLOCK) {
-            T zv[4], pv[4];
+        for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
+            T zv[UNR], pv[UNR];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int64_t i = i0 + h * GBS_PBLOCK;
+            for (int h = 0; h < UNR; ++h) {
+                const int64_t i = i0 + h * NT;
                 if (i < re) {
                     zv[h] = gbs_ld(zT + i, pk);
                     pv[h] = gbs_ld(pT + i, pk);
                 }
             }
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int64_t i = i0 + h * GBS_PBLOCK;
+            for (int h = 0; h < UNR; ++h) {
+                const int64_t i = i0 + h * NT;
                 if (i < re) gbs_st(pT + i, zv[h] + beta * pv[h], pk);
             }
         }
@@ -322,12 +324,20 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
     return status;
 }
 
-__global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
+// NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp, UNR
+// rows per thread per trip of the vector phases.  With 1024 threads (32
+// warps, 64 registers, 6 KB rings) the SpMV hides its gathers' latency
+// better; the staged CTA sums then live in dynamic shared memory after the
+// rings.
+template <int NT, int WB, int UNR>
+__global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
 {
+    constexpr bool WIDE = NT > GBS_PBLOCK;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PcgSmall<double> sm;
+    __shared__ double s_stage[WIDE ? 1 : 3 * NT];
     __shared__ PcgCtl<double> ctl;
-    __shared__ GbsWarpQ s_q[GBS_PWARPS];
+    __shared__ GbsWarpQ s_q[NT / 32];
     __shared__ int s_next;
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5;
@@ -337,11 +347,11 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_fp64(PcgArgs a)
     uint32_t parity = 0;
     int iters = 0, barrier_no = 0;
     double rn = 0.0, bn = 0.0;
-    int st = pcg_loop<double, int32_t>(a, a.colidx, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q,
-                                       a.part64, a.rtol,
-                              a.maxit, a.x0_zero != 0, &iters, &rn, &bn, &barrier_no,
-                              smem + (size_t)warp * GBS_WARP_STAGE_BYTES, s_q[warp], parity,
-                              &s_next, a.pipe64, sm, ctl, &s_flag);
+    double *stage = WIDE ? reinterpret_cast<double *>(smem + (size_t)WB * (NT / 32)) : s_stage;
+    int st = pcg_loop<double, int32_t, NT, UNR>(
+        a, a.colidx, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol, a.maxit,
+        a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, smem + (size_t)warp * WB, s_q[warp],
+        parity, &s_next, a.pipe64, sm, stage, ctl, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.res->status = st;
         a.res->iters = iters;
@@ -361,6 +371,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PcgSmall<double> sm64;
+    __shared__ double s_stage[3 * GBS_PBLOCK];
     __shared__ PcgCtl<float> ctl32;
     __shared__ GbsWarpQ s_q[GBS_PWARPS];
     __shared__ double s_scale;
@@ -408,7 +419,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
                 (threadIdx.x & 31) == 0)
                 atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         }
-        gbs_block_sum_staged<double, 2, GBS_PBLOCK>(acc, sm64.buf, sm64.out);
+        gbs_block_sum_staged<double, 2, GBS_PBLOCK>(acc, s_stage, sm64.out);
         double *part = a.part64 + (it & 1) * 2 * G;
         if (threadIdx.x == 0) {
             s_next = 0;
@@ -448,10 +459,10 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
         float rin = 0.f, bin = 0.f;
         const IX *col32 = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
                                           : (const IX *)(const void *)a.colidx;
-        const int sti = pcg_loop<float, IX>(a, col32, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32,
-                                        a.q32, a.part32, (float)a.inner_rtol, a.maxit, true, &kin,
-                                        &rin, &bin, &barrier_no, wsm, s_q[warp], parity, &s_next,
-                                        a.pipe32, sm32, ctl32, &s_flag);
+        const int sti = pcg_loop<float, IX, GBS_PBLOCK, 4>(
+            a, col32, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32, a.q32, a.part32,
+            (float)a.inner_rtol, a.maxit, true, &kin, &rin, &bin, &barrier_no, wsm, s_q[warp],
+            parity, &s_next, a.pipe32, sm32, reinterpret_cast<float *>(s_stage), ctl32, &s_flag);
         inner_total += kin;
         if (sti < 0) { st = sti; break; }
         // ---- FP64 update x += ||r|| d (own rows), then a barrier so the next
@@ -481,31 +492,31 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Cooperative grid for a persistent kernel: as many co-resident CTAs as
 // fit, but no more than one CTA per GBS_PWARPS warp tiles (small systems
 // run on few CTAs, so their barriers are cheap).
-int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0)
+int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0,
+              size_t smem = kPersistSmem, int nt = GBS_PBLOCK)
 {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmem) !=
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, kPersistSmem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess)
         return -1;
     if (per_sm < 1) return -1;
     int64_t g = (int64_t)per_sm * c->num_sms;
     if (want > 0) return (int)(want < g ? want : g);   // the caller's choice, within residency
-    const int64_t need = (ntiles + GBS_PWARPS - 1) / GBS_PWARPS;
+    const int64_t need = (ntiles + nt / 32 - 1) / (nt / 32);
     if (g > need) g = need;
     return g < 1 ? 1 : (int)g;
 }
 
 // Launch a persistent kernel and read its result record (one host
 // synchronisation per solve).
-int launch_persistent(gbs_ctx c, const void *fn, int G, PcgArgs &a, gbs_solve_info *info)
+int launch_persistent(gbs_ctx c, const void *fn, int G, PcgArgs &a, gbs_solve_info *info,
+                      size_t smem = kPersistSmem, int nt = GBS_PBLOCK)
 {
     GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
     void *args[] = {&a};
-    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(GBS_PBLOCK), args, kPersistSmem,
-                                             c->stream));
+    GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(nt), args, smem, c->stream));
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
     GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
@@ -540,6 +551,41 @@ void fill_matrix_args(PcgArgs &a, gbs_mat A)
     a.pipe32 = A->pipe32;
 }
 
+// Launch shape of the FP64 persistent kernel.  Large systems (at least 32
+// warp tiles per SM) run one CTA of 32 warps per SM with 6 KB copy rings
+// wherever one stage of the matrix's largest tile fits in 6 KB: 32 warps
+// hide the SpMV gathers' latency better than 16 (the SpMV phase of the
+// 128^3 7-point solve takes 42.9 instead of 50.7 us), while the CTA-wide
+// sums and barriers of a 1024-thread CTA cost more, which small systems
+// feel.  Otherwise one CTA of 16 warps per SM with 12.8 KB rings.
+struct Fp64Shape {
+    const void *fn;
+    size_t smem;
+    int nt;
+    GbsPipeCfg cfg;
+};
+
+Fp64Shape fp64_shape(gbs_mat A)
+{
+    constexpr int kSmallRing = 6144;
+    constexpr int kWide = 2 * GBS_PBLOCK;
+    Fp64Shape s;
+    s.cfg = A->pipe64;
+    const int stages = kSmallRing / A->pipe64.sbytes;
+    const bool large = A->ntiles >= (int64_t)A->ctx->num_sms * (kWide / 32);
+    if (stages >= 1 && large) {
+        s.cfg.stages = stages < GBS_MAX_STAGES ? stages : GBS_MAX_STAGES;
+        s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2>;
+        s.smem = (size_t)kSmallRing * (kWide / 32) + 3 * kWide * sizeof(double);
+        s.nt = kWide;
+    } else {
+        s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4>;
+        s.smem = kPersistSmem;
+        s.nt = GBS_PBLOCK;
+    }
+    return s;
+}
+
 }  // namespace
 
 int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
@@ -552,9 +598,12 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         if (st) return st;
     }
     const bool rel16 = mixed && A->colrel16;
-    const void *fn = !mixed ? (const void *)k_pcg_fp64
+    const Fp64Shape shape = fp64_shape(A);
+    const void *fn = !mixed ? shape.fn
                      : rel16 ? (const void *)k_pcg_mixed<int16_t> : (const void *)k_pcg_mixed<int32_t>;
-    const int G = coop_grid(c, fn, A->ntiles, o->persistent_ctas);
+    const size_t smem = mixed ? kPersistSmem : shape.smem;
+    const int nt = mixed ? GBS_PBLOCK : shape.nt;
+    const int G = coop_grid(c, fn, A->ntiles, o->persistent_ctas, smem, nt);
     if (G < 0) return GBS_ERR_CUDA;
     const int64_t n = A->n;
     const size_t vec64 = align256(sizeof(double) * (size_t)n);
@@ -602,8 +651,9 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     a.norm = o->norm_type;
     a.skip_cta = o->fault_skip_arrival;
     a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
+    if (!mixed) a.pipe64 = shape.cfg;
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
-    return launch_persistent(c, fn, G, a, info);
+    return launch_persistent(c, fn, G, a, info, smem, nt);
 }
 
 // ----------------------------------------------------------------------
@@ -1030,7 +1080,8 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     void *scr = nullptr;
     int st = noalloc_address(c->device, &scr);
     if (st) return st;
-    int G = coop_grid(c, (const void *)k_pcg_fp64, A->ntiles);
+    const Fp64Shape shape = fp64_shape(A);
+    int G = coop_grid(c, shape.fn, A->ntiles, 0, shape.smem, shape.nt);
     if (G < 0) return GBS_ERR_CUDA;
     if (G > kNoAllocMaxCtas) G = kNoAllocMaxCtas;
     char *base = (char *)scr;
@@ -1055,5 +1106,6 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     // the barrier and the result record must start at zero; the vectors and
     // partial sums are written before they are read
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocHead, c->stream));
-    return launch_persistent(c, (const void *)k_pcg_fp64, G, a, info);
+    a.pipe64 = shape.cfg;
+    return launch_persistent(c, shape.fn, G, a, info, shape.smem, shape.nt);
 }
