@@ -162,6 +162,36 @@ def lap2d5(nx: int, ny: int | None = None) -> CSR:
     return m
 
 
+def lap3d7_torch(nx: int, device):
+    """The nx^3 3D 7-point Dirichlet Laplacian of ``lap3d7`` laid out with
+    torch on ``device`` (same rows, columns in ascending order and values),
+    for operators too large to lay out on the host.  Returns (rowptr,
+    colidx, vals) as int32, int32, float64 tensors."""
+    import torch
+    n = nx ** 3
+    cell = torch.arange(n, dtype=torch.int64, device=device)
+    x = cell % nx
+    y = (cell // nx) % nx
+    z = cell // (nx * nx)
+    # ascending column order: -nx^2, -nx, -1, 0, +1, +nx, +nx^2
+    steps = (-nx * nx, -nx, -1, 0, 1, nx, nx * nx)
+    valid = torch.stack([z > 0, y > 0, x > 0, torch.ones_like(x, dtype=torch.bool),
+                         x < nx - 1, y < nx - 1, z < nx - 1], dim=1)
+    del x, y, z
+    counts = valid.sum(dim=1)
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=rowptr[1:])
+    if int(rowptr[-1]) > np.iinfo(np.int32).max:
+        raise ValueError("nnz exceeds int32 range")
+    del counts
+    cols = cell[:, None] + torch.tensor(steps, dtype=torch.int64, device=device)[None, :]
+    colidx = cols[valid].to(torch.int32)
+    del cols
+    vals = torch.where(torch.tensor([s == 0 for s in steps], device=device)[None, :].expand(n, 7),
+                       6.0, -1.0)[valid].to(torch.float64)
+    return rowptr.to(torch.int32), colidx, vals
+
+
 def lap3d7(nx: int, ny: int | None = None, nz: int | None = None) -> CSR:
     """3D 7-point Dirichlet Laplacian (diag 6, off-diagonals -1)."""
     ny = nx if ny is None else ny

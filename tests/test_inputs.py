@@ -159,3 +159,17 @@ def test_c4_and_c5_specs():
     assert {s["nrhs"] for s in s5} <= {1, 2, 3, 4}
     t = I.poisson_arrivals(1, 100.0, 20000)
     assert abs(np.diff(t).mean() - 0.01) < 5e-4
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 9, 16])
+def test_lap3d7_torch_layout_equals_host_layout(N):
+    """The torch layout of the 7-point Laplacian (used for operators too
+    large for the host) is the host generator's CSR, array for array."""
+    torch = pytest.importorskip("torch")
+    A = I.lap3d7(N)
+    rp, ci, v = I.lap3d7_torch(N, "cpu")
+    assert rp.dtype == torch.int32 and ci.dtype == torch.int32 and v.dtype == torch.float64
+    assert np.array_equal(A.rowptr, rp.numpy())
+    assert np.array_equal(A.colidx, ci.numpy())
+    assert np.array_equal(A.vals, v.numpy())
+    assert int(rp[-1]) == 7 * N ** 3 - 6 * N ** 2
