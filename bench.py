@@ -166,6 +166,18 @@ WORKLOAD = (f"3D 7-point Dirichlet Laplacian {N_GRID}^3 (n=2,097,152, nnz=14,581
             "b=A x*, x* uniform[-1,1) seed 2")
 
 
+# GB300's FP64 rate, nominal: 1.25 TFLOP/s, i.e. 625 G FP64 fused multiply-adds
+# (or other FP64 instruction lanes) per second.
+FP64_NOMINAL_GOPS = 625.0
+
+
+def ops_per_iter_fp64(n, nnz):
+    """FP64 operations of one fused PCG iteration: one per nonzero in the
+    SpMV, one per row for p.q, five per row in the update (x, r, z, r.z,
+    r.r) and one per row for the direction."""
+    return nnz + 7 * n
+
+
 def bytes_per_iter_fp64(n, nnz):
     """Fused FP64 PCG iteration: 12 nnz (vals + colidx) + 108 n (rowptr 4n,
     p gather 8n, q write 8n, update phase 64n, p update 24n)."""
@@ -390,6 +402,14 @@ def run_gbs(args, rank, world, local):
                          "traffic": measured_traffic(iters[0]),
                          "kernel": "k_pcg_fp64 (one launch per solve)",
                          "bytes_model": "iters x (12 nnz + 108 n)", "peak_kind": peak_kind},
+            "roofline_fp64": {"bound": "alu", "achieved": ops_per_iter_fp64(n, nnz) * iters[0]
+                              / (dev_ms / 1e3) / 1e9,
+                              "peak": FP64_NOMINAL_GOPS, "unit": "G FP64 ops/s",
+                              "frac": ops_per_iter_fp64(n, nnz) * iters[0] / (dev_ms / 1e3) / 1e9
+                              / FP64_NOMINAL_GOPS,
+                              "ops_model": "iters x (nnz + 7n): SpMV nnz, p.q n, update 5n, "
+                                           "direction n (one FP64 instruction lane each)",
+                              "peak_kind": "nominal 1.25 TFLOP/s = 625 G FMA/s"},
             "gpu_launches": int(l1 - l0),
             "clocks": clk}
     gbs.gbs_vec_destroy(rv)
