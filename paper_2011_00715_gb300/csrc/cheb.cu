@@ -47,8 +47,9 @@ struct RowVals {
     double x, r, dinv;
 };
 
+template <int NT>
 struct ChebShared {
-    double buf[2 * GBS_PBLOCK];
+    double buf[2 * NT];
     double out[8];   // totals and part sums
     double rn, bn;
     int status;   // -100 while the iteration goes on
@@ -64,11 +65,15 @@ __device__ __forceinline__ int cheb_check(double rn, double tol, int k, int maxi
     return -100;
 }
 
-__global__ void __launch_bounds__(GBS_PBLOCK) k_chebyshev(ChebArgs a)
+// NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp: 32
+// warps with 6 KB rings for large systems (more gathers in flight), else
+// 16 warps with 12.8 KB rings.
+template <int NT, int WB>
+__global__ void __launch_bounds__(NT, 1) k_chebyshev(ChebArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ ChebShared sh;
-    __shared__ GbsWarpQ s_q[GBS_PWARPS];
+    __shared__ ChebShared<NT> sh;
+    __shared__ GbsWarpQ s_q[NT / 32];
     __shared__ int s_next;
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5, G = gridDim.x, cta = blockIdx.x;
@@ -77,14 +82,14 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_chebyshev(ChebArgs a)
     __syncthreads();
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     uint32_t parity = 0;
-    unsigned char *wsm = smem + (size_t)warp * GBS_WARP_STAGE_BYTES;
+    unsigned char *wsm = smem + (size_t)warp * WB;
     const int64_t t0 = a.ntiles * cta / G, t1 = a.ntiles * (cta + 1) / G;
     const double theta = a.theta, delta = a.delta;
     int bno = 0, k = 0, status = GBS_ERR_TIMEOUT;
 
     // after each pass: CTA partials, grid barrier, every CTA's stopping test
     auto finish_pass = [&](double (&acc)[2], int par, int kk) -> bool {
-        gbs_block_sum_staged<double, 2, GBS_PBLOCK>(acc, sh.buf, sh.out);
+        gbs_block_sum_staged<double, 2, NT>(acc, sh.buf, sh.out);
         if (threadIdx.x == 0) {
             s_next = 0;
             a.part[(2 * par + 0) * G + cta] = sh.out[0];
@@ -199,14 +204,24 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
     } else {
         GBS_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->coop_supported) return GBS_ERR_UNSUPPORTED;
-        const void *fn = (const void *)k_chebyshev;
+        // launch shape: 32 warps with 6 KB rings when a stage of the largest
+        // tile fits and there are at least 32 tiles per SM
+        constexpr int kWide = 2 * GBS_PBLOCK, kRing = 6144;
+        GbsPipeCfg cfg = A->pipe64;
+        const int st6 = kRing / cfg.sbytes;
+        const bool wide = st6 >= 1 && A->ntiles >= (int64_t)c->num_sms * (kWide / 32);
+        const void *fn = wide ? (const void *)k_chebyshev<kWide, kRing>
+                              : (const void *)k_chebyshev<GBS_PBLOCK, GBS_WARP_STAGE_BYTES>;
+        const int nt = wide ? kWide : GBS_PBLOCK;
+        const size_t smem = wide ? (size_t)kRing * (kWide / 32) : kChebSmem;
+        if (wide) cfg.stages = st6 < GBS_MAX_STAGES ? st6 : GBS_MAX_STAGES;
         GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kChebSmem));
+                                          (int)smem));
         int per_sm = 0;
-        GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, kChebSmem));
+        GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
         int64_t g = (int64_t)per_sm * c->num_sms;
-        const int64_t need = (A->ntiles + GBS_PWARPS - 1) / GBS_PWARPS;
+        const int64_t need = (A->ntiles + nt / 32 - 1) / (nt / 32);
         if (g > need) g = need;
         const int G = g < 1 ? 1 : (int)g;
         const size_t head = 512;   // barrier + result record
@@ -232,7 +247,7 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
         a.colidx = A->colidx;
         a.vals = A->vals;
         a.dinv = A->dinv;
-        a.pipe = A->pipe64;
+        a.pipe = cfg;
         a.b = (const double *)b->data;
         a.x = (double *)x->data;
         a.theta = 0.5 * (emax + emin);
@@ -243,8 +258,7 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
         GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
         GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         void *args[] = {&a};
-        GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(GBS_PBLOCK), args, kChebSmem,
-                                                 c->stream));
+        GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(nt), args, smem, c->stream));
         gbs_count_launch(c);
         GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
         GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev),
