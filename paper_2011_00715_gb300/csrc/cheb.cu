@@ -66,7 +66,7 @@ __device__ __forceinline__ int cheb_check(double rn, double tol, int k, int maxi
 }
 
 // NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp: 32
-// warps with 6 KB rings for large systems (more gathers in flight), else
+// warps with 6.4 KB rings for large systems (more gathers in flight), else
 // 16 warps with 12.8 KB rings.
 template <int NT, int WB>
 __global__ void __launch_bounds__(NT, 1) k_chebyshev(ChebArgs a)
@@ -204,12 +204,12 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
     } else {
         GBS_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->coop_supported) return GBS_ERR_UNSUPPORTED;
-        // launch shape: 32 warps with 6 KB rings when a stage of the largest
-        // tile fits and there are at least 32 tiles per SM
-        constexpr int kWide = 2 * GBS_PBLOCK, kRing = 6144;
+        // launch shape: 32 warps with 6.4 KB rings when two stages of the largest
+        // tile fit and there are at least 32 tiles per SM
+        constexpr int kWide = 2 * GBS_PBLOCK, kRing = GBS_WARP_STAGE_BYTES / 2;
         GbsPipeCfg cfg = A->pipe64;
         const int st6 = kRing / cfg.sbytes;
-        const bool wide = st6 >= 1 && A->ntiles >= (int64_t)c->num_sms * (kWide / 32);
+        const bool wide = st6 >= 2 && A->ntiles >= (int64_t)c->num_sms * (kWide / 32);
         const void *fn = wide ? (const void *)k_chebyshev<kWide, kRing>
                               : (const void *)k_chebyshev<GBS_PBLOCK, GBS_WARP_STAGE_BYTES>;
         const int nt = wide ? kWide : GBS_PBLOCK;

@@ -111,7 +111,8 @@ __device__ __forceinline__ int pcg_check(T rn, T rho, T tol, int k, int maxit)
 // ||r||, alpha, beta, the stopping test) run in thread 0 of each CTA only;
 // *iters, *rnorm_out and *bnorm_out are valid in thread 0.
 // NT: threads of the CTA; UNR: rows per thread per trip of the vector
-// phases; `stage` holds 3 NT values for the staged CTA sums.
+// phases; `stage` holds the staged CTA sums: 3 NT values for a 512-thread
+// CTA, 2 NT for a wider one.
 template <typename T, typename IX, int NT, int UNR>
 __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const T *dinv, const T *bT,
                         T *xT, T *rT,
@@ -172,13 +173,25 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             acc[2] += ref_sq(bi, i);
         }
     }
-    gbs_block_sum_staged<T, 3, NT>(acc, stage, sm.out);
-    if (threadIdx.x == 0) {
-        *s_next = 0;
-        part[0 * G + c] = sm.out[0];
-        part[1 * G + c] = sm.out[1];
-        part[2 * G + c] = sm.out[2];
+    if (NT <= GBS_PBLOCK) {
+        gbs_block_sum_staged<T, 3, NT>(acc, stage, sm.out);
+        if (threadIdx.x == 0) {
+            part[0 * G + c] = sm.out[0];
+            part[1 * G + c] = sm.out[1];
+            part[2 * G + c] = sm.out[2];
+        }
+    } else {
+        // a wide CTA stages at most two values at a time (`stage` holds 2 NT)
+        const T a01[2] = {acc[0], acc[1]}, a2[1] = {acc[2]};
+        gbs_block_sum_staged<T, 2, NT>(a01, stage, sm.out);
+        if (threadIdx.x == 0) {
+            part[0 * G + c] = sm.out[0];
+            part[1 * G + c] = sm.out[1];
+        }
+        gbs_block_sum_staged<T, 1, NT>(a2, stage, sm.out);
+        if (threadIdx.x == 0) part[2 * G + c] = sm.out[0];
     }
+    if (threadIdx.x == 0) *s_next = 0;
     const bool skip = (a.skip_cta == c) && (*barrier_no == 0);
     if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, skip, s_flag)) return GBS_ERR_TIMEOUT;
     if (warp == 0) {
@@ -326,7 +339,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
 
 // NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp, UNR
 // rows per thread per trip of the vector phases.  With 1024 threads (32
-// warps, 64 registers, 6 KB rings) the SpMV hides its gathers' latency
+// warps, 64 registers, 6.4 KB rings) the SpMV hides its gathers' latency
 // better; the staged CTA sums then live in dynamic shared memory after the
 // rings.
 template <int NT, int WB, int UNR>
@@ -552,8 +565,10 @@ void fill_matrix_args(PcgArgs &a, gbs_mat A)
 }
 
 // Launch shape of the FP64 persistent kernel.  Large systems (at least 32
-// warp tiles per SM) run one CTA of 32 warps per SM with 6 KB copy rings
-// wherever one stage of the matrix's largest tile fits in 6 KB: 32 warps
+// warp tiles per SM) run one CTA of 32 warps per SM with 6.4 KB copy rings
+// wherever two stages of the matrix's largest tile fit in 6.4 KB (with a
+// single stage a warp cannot overlap its copy and its compute, and the
+// 32-warp shape measured slower on 27-point operators): 32 warps
 // hide the SpMV gathers' latency better than 16 (the SpMV phase of the
 // 128^3 7-point solve takes 42.9 instead of 50.7 us), while the CTA-wide
 // sums and barriers of a 1024-thread CTA cost more, which small systems
@@ -567,16 +582,16 @@ struct Fp64Shape {
 
 Fp64Shape fp64_shape(gbs_mat A)
 {
-    constexpr int kSmallRing = 6144;
+    constexpr int kSmallRing = GBS_WARP_STAGE_BYTES / 2;
     constexpr int kWide = 2 * GBS_PBLOCK;
     Fp64Shape s;
     s.cfg = A->pipe64;
     const int stages = kSmallRing / A->pipe64.sbytes;
     const bool large = A->ntiles >= (int64_t)A->ctx->num_sms * (kWide / 32);
-    if (stages >= 1 && large) {
+    if (stages >= 2 && large) {
         s.cfg.stages = stages < GBS_MAX_STAGES ? stages : GBS_MAX_STAGES;
         s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2>;
-        s.smem = (size_t)kSmallRing * (kWide / 32) + 3 * kWide * sizeof(double);
+        s.smem = (size_t)kSmallRing * (kWide / 32) + 2 * kWide * sizeof(double);
         s.nt = kWide;
     } else {
         s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4>;
