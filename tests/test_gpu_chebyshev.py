@@ -50,9 +50,15 @@ def solve(S, A, b, emin, emax, rtol, maxit):
     return info, x
 
 
-@pytest.mark.parametrize("case", ["lap2d5_40", "lap3d7_20", "var7", "var27", "wide"])
+@pytest.mark.parametrize("case", ["lap2d5_40", "lap3d7_20", "var7", "var27", "wide",
+                                  "lap3d7_56"])
 def test_chebyshev_against_oracle(S, orc, case):
-    if case == "lap2d5_40":
+    lmin = None
+    if case == "lap3d7_56":     # large enough for the 32-warp launch shape
+        N = 56
+        A, (lo, hi) = I.lap3d7(N), laplacian_bounds(N, 3)
+        lmin = 6 * (1 - math.cos(math.pi / (N + 1)))
+    elif case == "lap2d5_40":
         A, (lo, hi) = I.lap2d5(40), laplacian_bounds(40, 2)
     elif case == "lap3d7_20":
         A, (lo, hi) = I.lap3d7(20), laplacian_bounds(20, 3)
@@ -77,10 +83,11 @@ def test_chebyshev_against_oracle(S, orc, case):
     assert abs(info.bnorm - bn) <= 1e-12 * bn
     # two vectors with residuals r, r_ref differ by at most (||r|| + ||r_ref||) / lambda_min(A)
     trr = np.linalg.norm(b - orc.spmv(A, ref["x"]))
-    sp = pytest.importorskip("scipy.sparse")
-    sla = pytest.importorskip("scipy.sparse.linalg")
-    M = sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.n, A.n))
-    lmin = float(sla.eigsh(M, k=1, sigma=0, which="LM", return_eigenvectors=False)[0])
+    if lmin is None:
+        sp = pytest.importorskip("scipy.sparse")
+        sla = pytest.importorskip("scipy.sparse.linalg")
+        M = sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.n, A.n))
+        lmin = float(sla.eigsh(M, k=1, sigma=0, which="LM", return_eigenvectors=False)[0])
     tol = max(1e-8, (tr + trr) / (lmin * np.linalg.norm(ref["x"])))
     assert np.linalg.norm(x - ref["x"]) <= tol * np.linalg.norm(ref["x"])
 

@@ -110,6 +110,34 @@ def test_fp64_rtol_1e10(S, orc, alg, maker):
     assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
 
 
+def unit_laplacian_lmin(dims):
+    """Smallest eigenvalue of the unit 7-point Dirichlet Laplacian on an
+    nx x ny x nz grid: the sum over the axes of 2 - 2 cos(pi / (n + 1))."""
+    return sum(2 - 2 * math.cos(math.pi / (d + 1)) for d in dims)
+
+
+@pytest.mark.parametrize("case", ["lap3d7_56", "var7_60x56x52"])
+def test_wide_shape_matches_oracle(S, orc, case):
+    """Systems with at least 32 warp tiles per SM and 7-point rows run the
+    32-warp launch shape of the persistent kernel: same bar as the smaller
+    systems, with the solution bound taken from a closed-form lambda_min
+    (A - w_min L_unit is a sum of positive semidefinite link terms)."""
+    if case == "lap3d7_56":
+        A, lmin = I.lap3d7(56), unit_laplacian_lmin((56, 56, 56))
+    else:
+        A = I.var7(60, 56, 52, seed=11)
+        lmin = float(A.meta["w_min"]) * unit_laplacian_lmin((60, 56, 52))
+    assert A.n // 32 >= 152 * 32
+    b = orc.spmv(A, I.xstar(A.n, 2))
+    ref = orc.pcg(A, b, 1e-10, 20000)
+    info, x = solve(S, A, b, 1e-10, 20000, algorithm=ALGS["persistent"])
+    assert info.status == gbs.GBS_OK
+    assert abs(info.iters - ref["iters"]) <= 2
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
+    assert rel(x, ref["x"]) <= solution_tol(orc, A, b, x, ref["x"], lmin)
+    assert abs(info.bnorm - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
+
+
 @pytest.mark.parametrize("maker", [lambda: I.var27(22, seed=3), lambda: I.lap3d7(40),
                                    lambda: I.var5(150, 130, seed=4)])
 def test_mixed_matches_fp64_oracle(S, orc, maker):
