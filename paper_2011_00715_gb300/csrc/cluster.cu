@@ -38,8 +38,8 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kCT = 512;                 // threads per CTA
-constexpr int kCW = kCT / 32;            // warps per CTA
+constexpr int kCT = 512;                 // threads per CTA (256 when a CTA owns at most 256 rows)
+constexpr int kCTSmall = 256;
 constexpr int kMaxCluster = 16;          // the opt-in (non-portable) cluster size
 constexpr int kPortableCluster = 8;
 constexpr int kMinRows = 128;            // rows per CTA at least
@@ -62,12 +62,13 @@ struct ClArgs {
     gbs_result_dev *res;
 };
 
+template <int CT>
 struct ClShared {
     double *pseg[kMaxCluster];           // each rank's p segment, as this CTA addresses it
     double init[3 * kMaxCluster];        // set-up partials r.z, r.r, b.b; slot = writing rank
     double pq[kMaxCluster];              // p.Ap partials
     double u[2 * kMaxCluster];           // r.z, r.r partials after the update
-    double stage[3][kCT];                // per-thread values of a CTA sum
+    double stage[3][CT];                 // per-thread values of a CTA sum
     double part[3][4];                   // per-warp sums of a CTA sum
     double alpha, beta;
     int go, status;
@@ -90,20 +91,20 @@ __device__ __forceinline__ int cl_check(double rn, double rho, double tol, int k
 // warps per value (one per SM partition where possible) each add their
 // share of the entries per lane and finish with a shuffle tree; one lane
 // per value adds the W part sums.  A fixed order throughout.
-template <int K>
-__device__ __forceinline__ void cta_publish(const double (&v)[K], double *dst, ClShared &s,
+template <int K, int CT>
+__device__ __forceinline__ void cta_publish(const double (&v)[K], double *dst, ClShared<CT> &s,
                                             cg::cluster_group &cl, int rank, int cs)
 {
     constexpr int W = K >= 3 ? 1 : 4 / K;   // warps per value
-    constexpr int PER = kCT / 32 / W;       // entries per lane
-    static_assert(W * K <= kCW && W <= 4, "warps per value");
+    constexpr int PER = CT / 32 / W;        // entries per lane
+    static_assert(W * K <= CT / 32 && W <= 4, "warps per value");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) s.stage[k][threadIdx.x] = v[k];
     __syncthreads();
     if (warp < W * K) {
         const int k = warp / W, j = warp % W;
-        const double *src = s.stage[k] + j * (kCT / W) + lane;
+        const double *src = s.stage[k] + j * (CT / W) + lane;
         double t = src[0];
 #pragma unroll
         for (int m = 1; m < PER; ++m) t += src[32 * m];
@@ -140,10 +141,11 @@ __device__ __forceinline__ double cluster_total(const double *slots, int cs)
     return t;
 }
 
-__global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
+template <int CT>
+__global__ void __launch_bounds__(CT, 1) k_pcg_cluster(ClArgs a)
 {
     extern __shared__ __align__(16) double sm[];
-    __shared__ ClShared s;
+    __shared__ ClShared<CT> s;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
     const int R = a.rows, lo = rank * R;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
 
     // ---- set-up: r = b - A x0 (x0 read from global memory), p = z = D^-1 r
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < nl; i += kCT) {
+    for (int i = threadIdx.x; i < nl; i += CT) {
         const int gi = lo + i;
         double sum = 0.0;
         const int e1 = __ldg(a.rowptr + gi + 1);
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
     }
     // every CTA of the cluster is running before the first remote access
     cl.sync();
-    cta_publish<3>(acc, s.init, s, cl, rank, cs);
+    cta_publish<3, CT>(acc, s.init, s, cl, rank, cs);
     cl.sync();
     // scalar state, meaningful in thread 0 only; rr holds N(r)^2 of the
     // stopping-test norm N (r.r, z.z, or r.z for the natural norm)
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
         // ---- S: q = A p (p of other CTAs' rows through distributed shared
         // memory), partial p.q
         double pq[1] = {0.0};
-        for (int i = threadIdx.x; i < nl; i += kCT) {
+        for (int i = threadIdx.x; i < nl; i += CT) {
             const int gi = lo + i;
             double sum = 0.0;
             const int e1 = __ldg(a.rowptr + gi + 1);
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
             q[i] = sum;
             pq[0] = fma(p[i], sum, pq[0]);
         }
-        cta_publish<1>(pq, s.pq, s, cl, rank, cs);
+        cta_publish<1, CT>(pq, s.pq, s, cl, rank, cs);
         cl.sync();
         double pi = 0.0;
         if (threadIdx.x < 32) pi = cluster_total(s.pq, cs);
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
 
         // ---- U: x += alpha p; r -= alpha q; partials r.z, r.r
         double u[2] = {0.0, 0.0};
-        for (int i = threadIdx.x; i < nl; i += kCT) {
+        for (int i = threadIdx.x; i < nl; i += CT) {
             x[i] = fma(alpha, p[i], x[i]);
             const double ri = fma(-alpha, q[i], r[i]);
             r[i] = ri;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
             const double w = a.norm == GBS_NORM_PRECONDITIONED ? zi : ri;
             u[1] = fma(w, w, u[1]);
         }
-        cta_publish<2>(u, s.u, s, cl, rank, cs);
+        cta_publish<2, CT>(u, s.u, s, cl, rank, cs);
         cl.sync();
         double rho_new = 0.0, rr_new = 0.0;
         if (threadIdx.x < 32) {
@@ -267,10 +269,10 @@ __global__ void __launch_bounds__(kCT, 1) k_pcg_cluster(ClArgs a)
 
         // ---- P: p = z + beta p on this CTA's rows; the barrier publishes
         // them to the next SpMV of every CTA
-        for (int i = threadIdx.x; i < nl; i += kCT) p[i] = fma(beta, p[i], __dmul_rn(dinv[i], r[i]));
+        for (int i = threadIdx.x; i < nl; i += CT) p[i] = fma(beta, p[i], __dmul_rn(dinv[i], r[i]));
         cl.sync();
     }
-    for (int i = threadIdx.x; i < nl; i += kCT) a.x[lo + i] = x[i];
+    for (int i = threadIdx.x; i < nl; i += CT) a.x[lo + i] = x[i];
     if (rank == 0 && threadIdx.x == 0) {
         a.res->status = status;
         a.res->iters = k;
@@ -293,11 +295,16 @@ int cluster_max(int device)
     if (device < 0 || device >= 64) return 0;
     int v = g_cluster_max[device].load();
     if (v) return v > 0 ? v : 0;
-    const void *fn = (const void *)k_pcg_cluster;
+    const void *fn = (const void *)k_pcg_cluster<kCT>;
+    const void *fn_small = (const void *)k_pcg_cluster<kCTSmall>;
     int found = -1;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(fn_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxSmem) == cudaSuccess &&
+        cudaFuncSetAttribute(fn_small, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
         for (int cs : {kMaxCluster, kPortableCluster}) {
             cudaLaunchConfig_t cfg;
             memset(&cfg, 0, sizeof(cfg));
@@ -358,10 +365,13 @@ int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, i
     a.maxit = maxit;
     a.norm = norm;
     a.res = (gbs_result_dev *)scr;
+    // one row per thread where the CTA owns at most 256 rows: fewer warps
+    // make the CTA-wide sums and barriers cheaper
+    const bool small = rows <= kCTSmall;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(kCT);
+    cfg.blockDim = dim3(small ? kCTSmall : kCT);
     cfg.dynamicSmemBytes = (size_t)5 * rows * sizeof(double);
     cfg.stream = c->stream;
     cudaLaunchAttribute at[1];
@@ -372,7 +382,10 @@ int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, i
     cfg.attrs = at;
     cfg.numAttrs = 1;
     GBS_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    GBS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pcg_cluster, a));
+    if (small)
+        GBS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pcg_cluster<kCTSmall>, a));
+    else
+        GBS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pcg_cluster<kCT>, a));
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
     GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, a.res, sizeof(gbs_result_dev), cudaMemcpyDeviceToHost,
