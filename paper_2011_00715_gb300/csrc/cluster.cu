@@ -71,6 +71,7 @@ struct ClShared {
     double stage[3][CT];                 // per-thread values of a CTA sum
     double part[3][4];                   // per-warp sums of a CTA sum
     double alpha, beta;
+    double rn;                           // square root of the stopping test (warp 1)
     int go, status;
 };
 
@@ -129,7 +130,7 @@ __device__ __forceinline__ void cta_publish(const double (&v)[K], double *dst, C
 }
 
 // Sum of the cs published partials by a fixed tree over the slots (the
-// same in every CTA); called by all of warp 0, the total is in lane 0.  A
+// same in every CTA); called by a whole warp, the total is in its lane 0.  A
 // tree rather than a running sum: each dependent FP64 step costs a full
 // pass of the warp through the narrow FP64 pipe.
 __device__ __forceinline__ double cluster_total(const double *slots, int cs)
@@ -244,11 +245,16 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(ClArgs a)
         }
         cta_publish<2, CT>(u, s.u, s, cl, rank, cs);
         cl.sync();
+        // warps 0 and 1 form the same totals; warp 0 divides for beta while
+        // warp 1 takes the stopping test's square root, side by side
         double rho_new = 0.0, rr_new = 0.0;
-        if (threadIdx.x < 32) {
+        if (threadIdx.x < 64) {
             rho_new = cluster_total(s.u, cs);
             rr_new = cluster_total(s.u + kMaxCluster, cs);
+            if (threadIdx.x == 32) s.rn = sqrt(natural ? rho_new : rr_new);
+            if (threadIdx.x == 0) s.beta = rho_new / rho;
         }
+        __syncthreads();
         if (threadIdx.x == 0) {
             ++k;
             rr = natural ? rho_new : rr_new;
@@ -256,9 +262,8 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_cluster(ClArgs a)
                 status = GBS_ERR_INDEFINITE;
                 s.go = 0;
             } else {
-                s.beta = rho_new / rho;
                 rho = rho_new;
-                const int st = cl_check(sqrt(rr), rho, a.rtol * bnorm, k, a.maxit);
+                const int st = cl_check(s.rn, rho, a.rtol * bnorm, k, a.maxit);
                 s.go = st == -100;
                 if (!s.go) status = st;
             }

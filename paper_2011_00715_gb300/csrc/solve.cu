@@ -50,6 +50,7 @@ struct PcgSmall {
 template <typename T>
 struct PcgCtl {
     T alpha, beta;
+    T rn;        // square root of the stopping test, taken by warp 1
     int go;
     int status;
 };
@@ -282,23 +283,29 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
-        if (warp == 0) {
-            T g2[2];
+        // warps 0 and 1 form the same grid sums (same order, same bits);
+        // warp 0 divides for beta while warp 1 takes the stopping test's
+        // square root, on different SM partitions: each is a long chain of
+        // dependent FP64 steps
+        T g2[2] = {T(0), T(0)};
+        if (warp < 2) {
             gbs_warp_grid_sum<T, 2>(part + 4 * G, G, G, g2);
-            if (threadIdx.x == 0) {
-                ++k;
-                const T rho_new = g2[0];
-                rr = norm == GBS_NORM_NATURAL ? g2[0] : g2[1];
-                if (rho_new < T(0)) {
-                    status = GBS_ERR_INDEFINITE;
-                    ctl.go = 0;
-                } else {
-                    ctl.beta = rho_new / rho;
-                    rho = rho_new;
-                    const int s = pcg_check<T>(sqrt(rr), rho, rtol * bnorm, k, maxit);
-                    ctl.go = s == -100;
-                    if (!ctl.go) status = s;
-                }
+            if (threadIdx.x == 32) ctl.rn = sqrt(norm == GBS_NORM_NATURAL ? g2[0] : g2[1]);
+            if (threadIdx.x == 0) ctl.beta = g2[0] / rho;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ++k;
+            const T rho_new = g2[0];
+            rr = norm == GBS_NORM_NATURAL ? g2[0] : g2[1];
+            if (rho_new < T(0)) {
+                status = GBS_ERR_INDEFINITE;
+                ctl.go = 0;
+            } else {
+                rho = rho_new;
+                const int s = pcg_check<T>(ctl.rn, rho, rtol * bnorm, k, maxit);
+                ctl.go = s == -100;
+                if (!ctl.go) status = s;
             }
         }
         __syncthreads();
