@@ -13,8 +13,10 @@ unpreconditioned residual).
 
 The driver is written once over a small "local operations" interface, so
 the partition, the halo plan and the collective schedule are the same code
-whether the local work runs in the library on a GPU (GbsOps, NCCL) or, in
-the CPU tests, in another implementation (gloo ranks).
+whether the local work runs in the library on a GPU (GbsOps, NCCL: the
+SpMV, Jacobi apply, AXPY/AYPX, copies and dots all in the library's
+kernels) or, in the CPU tests, in another implementation (gloo ranks).
+The scalar recurrence runs here, on the host, on the all-reduced sums.
 """
 from __future__ import annotations
 
@@ -103,11 +105,22 @@ def exchange_plans(blk: LocalBlock, group=None) -> LocalBlock:
 
 
 class NumpyOps:
-    """Local operations on host arrays (numpy); `spmv(blk, v)` must be given
-    (the tests pass the oracle's)."""
+    """Local operations on host arrays (CPU tensors); `spmv(blk, v)` must be
+    given (the tests pass the oracle's)."""
     def __init__(self, spmv):
         self._spmv = spmv
         self.device = "cpu"
+        self._dinv = None
+
+    def setup(self, blk):
+        diag = np.zeros(blk.n_own)
+        for i in range(blk.n_own):
+            seg = slice(blk.rowptr[i], blk.rowptr[i + 1])
+            hit = np.nonzero(blk.colidx[seg] == i)[0]
+            diag[i] = blk.vals[seg][hit[0]] if len(hit) else 0.0
+        if np.any(diag <= 0.0):
+            raise ValueError("Jacobi needs a positive diagonal")
+        self._dinv = self.vec(1.0 / diag)
 
     def vec(self, a):
         import torch
@@ -120,10 +133,24 @@ class NumpyOps:
     def dot(self, a, b):
         return float(a[: len(b)].numpy() @ b.numpy())
 
+    def axpy(self, y, alpha, x):       # y <- alpha x + y
+        y += alpha * x
+
+    def aypx(self, y, beta, x):        # y <- x + beta y
+        y.mul_(beta).add_(x)
+
+    def jacobi(self, r, z):            # z <- D^-1 r
+        z.copy_(self._dinv * r)
+
+    def copy(self, x, y):              # y <- x
+        y.copy_(x)
+
 
 class GbsOps:
     """Local operations in the library on this rank's GPU: the local block as
-    a gbs matrix over [own | ghosts] columns, vectors as CUDA tensors."""
+    a gbs matrix over [own | ghosts] columns (its Jacobi inverse diagonal made
+    at creation), vectors as CUDA tensors wrapped per call; every vector
+    operation runs in the library's kernels."""
     def __init__(self, ctx, blk: LocalBlock):
         import torch
         from . import gbs
@@ -132,26 +159,43 @@ class GbsOps:
         self.device = "cuda"
         self.torch = torch
         self.A = gbs.gbs_mat_create_aij(ctx, blk.n_own, blk.ncols, blk.rowptr, blk.colidx, blk.vals)
+        self.pc = None
+
+    def setup(self, blk):
+        self.pc = self.gbs.gbs_pc_jacobi_create(self.A)   # GBS_ERR_DIAG -> GbsError
 
     def vec(self, a):
         return self.torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
 
+    def _call(self, fn, *tensors, scalar=None):
+        vs = [self.gbs.gbs_vec_wrap(self.ctx, t) for t in tensors]
+        try:
+            return fn(*vs) if scalar is None else fn(vs[0], scalar, *vs[1:])
+        finally:
+            for v in vs:
+                self.gbs.gbs_vec_destroy(v)
+
     def spmv(self, blk, v, out):
-        gbs = self.gbs
-        xv, yv = gbs.gbs_vec_wrap(self.ctx, v), gbs.gbs_vec_wrap(self.ctx, out)
-        gbs.gbs_mat_mult(self.A, xv, yv)
-        gbs.gbs_vec_destroy(xv)
-        gbs.gbs_vec_destroy(yv)
+        self._call(lambda xv, yv: self.gbs.gbs_mat_mult(self.A, xv, yv), v, out)
 
     def dot(self, a, b):
-        gbs = self.gbs
-        av, bv = gbs.gbs_vec_wrap(self.ctx, a[: len(b)]), gbs.gbs_vec_wrap(self.ctx, b)
-        d = gbs.gbs_vec_dot(av, bv)
-        gbs.gbs_vec_destroy(av)
-        gbs.gbs_vec_destroy(bv)
-        return d
+        return self._call(self.gbs.gbs_vec_dot, a[: len(b)], b)
+
+    def axpy(self, y, alpha, x):
+        self._call(self.gbs.gbs_vec_axpy, y, x, scalar=alpha)
+
+    def aypx(self, y, beta, x):
+        self._call(self.gbs.gbs_vec_aypx, y, x, scalar=beta)
+
+    def jacobi(self, r, z):
+        self._call(lambda rv, zv: self.gbs.gbs_pc_apply(self.pc, rv, zv), r, z)
+
+    def copy(self, x, y):
+        self._call(self.gbs.gbs_vec_copy, x, y)
 
     def close(self):
+        if self.pc is not None:
+            self.gbs.gbs_pc_destroy(self.pc)
         self.gbs.gbs_mat_destroy(self.A)
 
 
@@ -187,23 +231,19 @@ def allreduce_sum(vals, device, group=None):
 def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None):
     """Jacobi-PCG on the distributed system from x0 = 0.  Returns
     (x_own, status, iterations, ||r||, ||b||) with status 0 converged, 1
-    iteration limit, -5 indefinite, -6 NaN (the library's codes)."""
+    iteration limit, -5 indefinite, -6 NaN (the library's codes).  The
+    vector work runs in `ops`; the scalar recurrence (alpha, beta, the
+    stopping test) runs here, on the all-reduced sums."""
     import math
     n = blk.n_own
-    diag = np.zeros(n)
-    for i in range(n):
-        seg = slice(blk.rowptr[i], blk.rowptr[i + 1])
-        hit = np.nonzero(blk.colidx[seg] == i)[0]
-        diag[i] = blk.vals[seg][hit[0]] if len(hit) else 0.0
-    if np.any(diag <= 0.0):
-        raise ValueError("Jacobi needs a positive diagonal")
-    dinv = ops.vec(1.0 / diag)
+    ops.setup(blk)
     b = ops.vec(b_own)
     x = ops.vec(np.zeros(n))
-    r = b.clone()
-    z = dinv * r
+    r = ops.vec(b_own)
+    z = ops.vec(np.zeros(n))
+    ops.jacobi(r, z)
     p = ops.vec(np.zeros(blk.ncols))
-    p[:n] = z
+    ops.copy(z, p[:n])
     q = ops.vec(np.zeros(n))
     rho, rr, bb = allreduce_sum([ops.dot(r, z), ops.dot(r, r), ops.dot(b, b)], ops.device, group)
     bnorm = math.sqrt(bb)
@@ -229,9 +269,9 @@ def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None
             status = -5
             break
         alpha = rho / pq
-        x += alpha * p[:n]
-        r -= alpha * q
-        z = dinv * r
+        ops.axpy(x, alpha, p[:n])
+        ops.axpy(r, -alpha, q)
+        ops.jacobi(r, z)
         rho_new, rr = allreduce_sum([ops.dot(r, z), ops.dot(r, r)], ops.device, group)
         k += 1
         if rho_new < 0.0:
@@ -239,5 +279,5 @@ def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None
             break
         beta = rho_new / rho
         rho = rho_new
-        p[:n] = z + beta * p[:n]
+        ops.aypx(p[:n], beta, z)
     return x, status, k, math.sqrt(rr), bnorm

@@ -110,7 +110,8 @@ def test_sharded_pcg_matches_single_domain(tmp_path, orc, world, maker):
 
 @pytest.mark.gpu
 def test_sharded_pcg_library_backend_one_rank(orc):
-    """The library backend (local SpMV and dots in the library on the GPU,
+    """The library backend (local SpMV, Jacobi, AXPY/AYPX and dots in the
+    library on the GPU,
     NCCL collectives) on a one-rank group: the same iteration as the
     single-GPU solve, within rounding."""
     import torch
