@@ -11,6 +11,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "gbs_impl.cuh"
@@ -391,18 +393,22 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     if (nrows >= (int64_t)INT32_MAX || ncols >= (int64_t)INT32_MAX) return GBS_ERR_ARG;
     *out = nullptr;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
-    // the row pointers are needed on the host for tiling
-    std::vector<int32_t> hrp((size_t)nrows + 1);
-    if (memspace == GBS_MEM_HOST) {
-        memcpy(hrp.data(), rowptr, sizeof(int32_t) * (nrows + 1));
-    } else {
-        GBS_CUDA_TRY(cudaMemcpyAsync(hrp.data(), rowptr, sizeof(int32_t) * (nrows + 1),
+    // the row pointers are needed on the host for tiling: the caller's own
+    // array when it is host memory (read, not copied), else a copy
+    std::unique_ptr<int32_t[]> hrp_copy;
+    const int32_t *hrp = rowptr;
+    if (memspace == GBS_MEM_DEVICE) {
+        hrp_copy.reset(new (std::nothrow) int32_t[(size_t)nrows + 1]);
+        if (!hrp_copy) return GBS_ERR_OOM;
+        GBS_CUDA_TRY(cudaMemcpyAsync(hrp_copy.get(), rowptr, sizeof(int32_t) * (nrows + 1),
                                      cudaMemcpyDeviceToHost, c->stream));
         GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        hrp = hrp_copy.get();
     }
     if (hrp[0] != 0) return GBS_ERR_CSR;
-    for (int64_t i = 0; i < nrows; ++i)
-        if (hrp[i + 1] < hrp[i]) return GBS_ERR_CSR;
+    int bad = 0;   // monotone row pointers (one pass without early exit)
+    for (int64_t i = 0; i < nrows; ++i) bad |= hrp[i + 1] < hrp[i];
+    if (bad) return GBS_ERR_CSR;
     const int64_t nnz = hrp[nrows];
     if (nnz > 0 && (!colidx || !vals)) return GBS_ERR_ARG;
 
@@ -413,7 +419,7 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     A->ncols = ncols;
     A->nnz = nnz;
     std::vector<int32_t> tiles;
-    make_tiles(hrp.data(), nrows, tiles, &A->max_row_nnz);
+    make_tiles(hrp, nrows, tiles, &A->max_row_nnz);
     A->ntiles = (int64_t)tiles.size() - 1;
     // allocations padded to 16 bytes so vector loads never leave the buffer
     const size_t pad_nnz = (size_t)((nnz + 4) & ~(int64_t)3);
@@ -423,9 +429,9 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     if (e == cudaSuccess) e = cudaMalloc(&A->vals, sizeof(double) * pad_nnz);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv, sizeof(double) * pad_n);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
-    A->pipe64 = make_pipe_cfg(tiles, hrp.data(), 8);
-    A->pipe32 = make_pipe_cfg(tiles, hrp.data(), 4);
-    A->pipe16 = make_pipe_cfg(tiles, hrp.data(), 4, 2);
+    A->pipe64 = make_pipe_cfg(tiles, hrp, 8);
+    A->pipe32 = make_pipe_cfg(tiles, hrp, 4);
+    A->pipe16 = make_pipe_cfg(tiles, hrp, 4, 2);
     std::vector<int32_t> tdesc(2 * tiles.size());
     for (size_t t = 0; t < tiles.size(); ++t) {
         tdesc[2 * t] = tiles[t];
@@ -433,12 +439,15 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     }
     if (e == cudaSuccess) e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&A->tdesc, sizeof(int32_t) * tdesc.size());
-    if (e == cudaSuccess) e = cudaMemsetAsync(A->colidx, 0, sizeof(int32_t) * pad_nnz, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(A->vals, 0, sizeof(double) * pad_nnz, c->stream);
+    // only the padding after the nnz entries needs zeros: the copies fill the rest
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(A->colidx + nnz, 0, sizeof(int32_t) * (pad_nnz - nnz), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(A->vals + nnz, 0, sizeof(double) * (pad_nnz - nnz), c->stream);
     const cudaMemcpyKind kind =
         memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(A->rowptr, hrp.data(), sizeof(int32_t) * (nrows + 1),
+        e = cudaMemcpyAsync(A->rowptr, hrp, sizeof(int32_t) * (nrows + 1),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpyAsync(A->colidx, colidx, sizeof(int32_t) * nnz, kind, c->stream);
