@@ -161,6 +161,8 @@ def config_for(world):
     return {"workload": WORKLOAD,
             "l2": "inputs larger than L2 (matrix 175 MB + 5 vectors of 16.8 MB)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 WORKLOAD = (f"3D 7-point Dirichlet Laplacian {N_GRID}^3 (n=2,097,152, nnz=14,581,760), FP64 CSR, "
             "one Jacobi-PCG solve per step, rtol 1e-10 (unpreconditioned ||r||<=rtol||b||), x0=0, "
             "b=A x*, x* uniform[-1,1) seed 2")
