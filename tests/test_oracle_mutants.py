@@ -53,6 +53,13 @@ MUTANTS = {
                                   "return norm == 1 ? orc_norm2(n, w) : orc_dot(n, v, w);"),
     "norm_reference_unpreconditioned": ("const double bnorm = orc_test_norm(norm, n, b, dinv, w);",
                                         "const double bnorm = orc_norm2(n, b);"),
+    "f32_beta_inverted": ("float beta = rho_new / rho;", "float beta = rho / rho_new;"),
+    "f32_no_preconditioner_in_loop": (
+        "for (int64_t i = 0; i < n; ++i) z[i] = dinv32[i] * r[i];\n        float rho_new",
+        "for (int64_t i = 0; i < n; ++i) z[i] = r[i];\n        float rho_new"),
+    "mixed_residual_sign": ("r[i] = b[i] - r[i];", "r[i] = r[i] - b[i];"),
+    "mixed_rhs_not_normalised": ("r32[i] = (float)(r[i] / rn);", "r32[i] = (float)r[i];"),
+    "mixed_stagnation_test_inverted": ("if (rn > 0.5 * prev)", "if (rn < 0.5 * prev)"),
 }
 
 PINS = [
