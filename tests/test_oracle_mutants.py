@@ -60,6 +60,13 @@ MUTANTS = {
     "mixed_residual_sign": ("r[i] = b[i] - r[i];", "r[i] = r[i] - b[i];"),
     "mixed_rhs_not_normalised": ("r32[i] = (float)(r[i] / rn);", "r32[i] = (float)r[i];"),
     "mixed_stagnation_test_inverted": ("if (rn > 0.5 * prev)", "if (rn < 0.5 * prev)"),
+    "spmv_f32_row_index_for_column": (
+        "float s = 0.0f;\n        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)\n"
+        "            s += vals[k] * x[colidx[k]];",
+        "float s = 0.0f;\n        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)\n"
+        "            s += vals[k] * x[i];"),
+    "aypx_fused_roles_swapped": ("y[i] = fma(beta, y[i], x[i]);", "y[i] = fma(beta, x[i], y[i]);"),
+    "axpy_fused_rounds_twice": ("y[i] = fma(alpha, x[i], y[i]);", "y[i] = alpha * x[i] + y[i];"),
 }
 
 PINS = [
@@ -70,6 +77,8 @@ PINS = [
     lambda o: P.test_dot_norm_exact(o),
     lambda o: P.test_dot2_is_twice_working_precision(o),
     lambda o: P.test_axpy_aypx_roles(o),
+    lambda o: P.test_fused_axpy_aypx_round_the_exact_value_once(o),
+    lambda o: P.test_spmv_f32_matches_rounded_double(o),
     lambda o: P.test_jacobi_dinv(o),
     lambda o: P.test_pcg_iterates_are_krylov_minimisers(o, 3),
     lambda o: P.test_pcg_finite_termination(o, lambda: P.I.lap2d5(2), 3),
