@@ -55,7 +55,8 @@ def parse_args():
     p.add_argument("--maxit", type=int, default=20000,
                    help="iteration cap of the headline solve (profiling runs use a small cap)")
     p.add_argument("--c4-systems", type=int, default=512, help="systems in the batched workload")
-    p.add_argument("--c5-requests", type=int, default=300, help="requests in the serving workload")
+    p.add_argument("--c5-requests", type=int, default=2000,
+                   help="requests of the serving workload after its warm-up (a quarter per rate)")
     p.add_argument("--c4-only", action="store_true",
                    help="run only the batched workload (profiling of the batched kernel)")
     p.add_argument("--c5-only", action="store_true",
@@ -70,12 +71,8 @@ def parse_args():
                    help="distinct operators the serving requests draw from")
     p.add_argument("--c1-only", action="store_true",
                    help="run only the C1 solves (profiling of the one-cluster kernel)")
-    p.add_argument("--c5-sweep", action="store_true",
-                   help="run only the serving workload's arrival-rate sweep")
     p.add_argument("--c5-warmup", type=int, default=100,
-                   help="warm-up requests of the rate sweep (not counted)")
-    p.add_argument("--c5-sweep-requests", type=int, default=2000,
-                   help="requests per rate of the sweep")
+                   help="warm-up requests of the serving workload (not counted)")
     return p.parse_args()
 
 
@@ -197,26 +194,70 @@ def bytes_spmv_fp64(n, nnz):
 
 # ---------------------------------------------------------------- CPU oracle --
 
-def oracle_rate(A, b, full_iters, budget_s):
-    """Time the oracle's FP64 PCG on a bounded number of iterations and
-    extrapolate to a full solve of `full_iters` iterations (solves/s)."""
+def host_info():
+    """Host CPU count (os.cpu_count()) and model (lscpu)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_sample(A, b, full_iters, budget_s, threaded):
+    """Time the oracle's FP64 PCG (sequential build, or the OpenMP build on
+    all host cores) on a bounded number of iterations m.  Returns (seconds
+    of the sample, iterations m, threads, solves/s extrapolated to a full
+    solve of `full_iters` iterations)."""
     import oracle
-    oracle.build()
+
+    def run(m):
+        if threaded:
+            r = oracle.pcg_threaded(A, b, 0.0, m)
+            return r["threads"]
+        oracle.pcg(A, b, 0.0, m)
+        return 1
+
     t = time.perf_counter()
-    oracle.pcg(A, b, 0.0, 2)
-    t2 = time.perf_counter() - t
-    per_it = max(t2 / 3.0, 1e-6)          # set-up costs about one iteration
+    run(2)
+    per_it = max((time.perf_counter() - t) / 3.0, 1e-6)   # set-up costs about one iteration
     m = int(max(3, min(full_iters, budget_s / per_it - 1)))
     t = time.perf_counter()
-    r = oracle.pcg(A, b, 0.0, m)
+    threads = run(m)
     el = time.perf_counter() - t
     per_it = el / (m + 1)
-    return {"value": 1.0 / (per_it * (full_iters + 1)), "unit": "solves/s", "cores": 1,
-            "kind": "oracle",
-            "sample": (f"oracle FP64 Jacobi-PCG (plain C, 1 thread) on the same {N_GRID}^3 system: "
-                       f"{m} iterations timed ({el:.1f} s), {per_it*1e3:.1f} ms/iteration, "
-                       f"extrapolated to the {full_iters}-iteration solve"),
-            "iters_sampled": int(r["iters"]), "seconds": el}
+    return el, m, threads, 1.0 / (per_it * (full_iters + 1))
+
+
+def cpu_baseline_full(A, b):
+    """The oracle's full FP64 solve of the headline system, timed once with
+    the sequential build (its solution is also the parity reference) and
+    once with the OpenMP build on all host cores.  `value` is the all-core
+    rate; both are whole solves, nothing is extrapolated."""
+    import oracle
+    oracle.build()
+    oracle.build_omp()
+    t = time.perf_counter()
+    ref = oracle.pcg(A, b, RTOL, MAXIT)
+    el1 = time.perf_counter() - t
+    t = time.perf_counter()
+    par = oracle.pcg_threaded(A, b, RTOL, MAXIT)
+    eln = time.perf_counter() - t
+    cpu = dict({"value": 1.0 / eln, "unit": "solves/s", "cores": par["threads"], "kind": "oracle",
+                "sample": (f"one full FP64 Jacobi-PCG solve of the same {N_GRID}^3 system by the "
+                           f"oracle (plain C; {ref['iters']} iterations) on {par['threads']} host "
+                           f"threads (OpenMP build of the same source): {eln:.2f} s; the "
+                           f"sequential build: {el1:.2f} s"),
+                "single_thread": {"value": 1.0 / el1, "unit": "solves/s", "cores": 1,
+                                  "seconds": el1, "iters": int(ref["iters"])},
+                "all_cores": {"value": 1.0 / eln, "unit": "solves/s", "cores": par["threads"],
+                              "seconds": eln, "iters": int(par["iters"])}},
+               **host_info())
+    return cpu, ref
 
 
 def run_reference(args, rank, world):
@@ -224,33 +265,39 @@ def run_reference(args, rank, world):
         return
     import oracle
     oracle.build()
+    oracle.build_omp()
     A, xs = c2_problem()
     b = oracle.spmv(A, xs)
     # one full, untimed oracle solve gives the iteration count that each
     # timed step's bounded sample is extrapolated to
     full = oracle.pcg(A, b, RTOL, MAXIT)
     full_iters = int(full["iters"])
-    per_step_budget = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    per_step_budget = max(0.5, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_rate(A, b, full_iters, per_step_budget / 2)
-    vals = []
+        oracle_sample(A, b, full_iters, per_step_budget / 2, True)
     t0 = time.perf_counter()
-    samples = []
+    secs, rates = [], []
     for _ in range(args.steps):
-        r = oracle_rate(A, b, full_iters, per_step_budget)
-        vals.append(1.0 / r["value"])
-        samples.append(r)
-    el = time.perf_counter() - t0
-    sec_per_solve = statistics.mean(vals)
-    value = 1.0 / sec_per_solve
+        el, m, threads, rate = oracle_sample(A, b, full_iters, per_step_budget, True)
+        secs.append(el)
+        rates.append(rate)
+    total = time.perf_counter() - t0
+    value = 1.0 / statistics.mean(1.0 / r for r in rates)
+    sample = (f"oracle FP64 Jacobi-PCG (plain C, OpenMP build on {threads} host threads) on the "
+              f"same {N_GRID}^3 system: each step runs {m} of the {full_iters} iterations of a full "
+              f"solve ({statistics.mean(secs):.2f} s); solves/s extrapolated to the full solve; "
+              f"{args.steps} steps in {total:.1f} s")
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
+            "ms_per_solve_extrapolated": 1e3 / value,
+            "iters_per_step": m, "iters_per_solve": full_iters,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded stencil matrix and manufactured solution)",
-            "config": dict(config_for(world), algorithm="CPU oracle: plain C, one thread"),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[-1]["sample"] + f"; {args.steps} steps in {el:.1f} s"},
+            "config": config_for(world),
+            "algorithm": "CPU oracle: plain C, OpenMP on all host cores",
+            "cpu_baseline": dict({"value": value, "unit": "solves/s", "cores": threads,
+                                  "kind": "oracle", "sample": sample}, **host_info()),
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -392,8 +439,8 @@ def run_gbs(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded stencil matrix and manufactured solution)",
-            "config": dict(config_for(world),
-                           algorithm="persistent cooperative kernel, 3 grid barriers/iteration"),
+            "config": config_for(world),
+            "algorithm": "persistent cooperative kernel, 3 grid barriers/iteration",
             "solve": {"status": sorted(statuses), "iters": iters[0],
                       "true_rel_residual": true_rel, "rel_err_vs_xstar": err_xs,
                       "kernel_ms": dev_ms, "us_per_iter": dev_ms * 1e3 / iters[0],
@@ -418,11 +465,18 @@ def run_gbs(args, rank, world, local):
 
     if rank == 0 and world == 1 and not args.quick:
         line["e2e"] = e2e_c2(g, A, xs, args, infos[0].iters)
-        if not args.no_extras:
-            line["extras"] = extras(g, args, A, Ah, xsv)
         import oracle
         b_host = oracle.spmv(A, xs)
-        line["cpu_baseline"] = oracle_rate(A, b_host, iters[0], args.cpu_seconds)
+        # the oracle's full solve: the CPU baseline (sequential and all
+        # cores) and the FP64 reference the GPU solution is compared with
+        line["cpu_baseline"], ref = cpu_baseline_full(A, b_host)
+        x_ref = torch.from_numpy(ref["x"]).cuda()
+        line["solve"]["rel_err_vs_oracle"] = float(torch.linalg.norm(xt - x_ref) /
+                                                   torch.linalg.norm(x_ref))
+        line["solve"]["oracle_iters"] = int(ref["iters"])
+        del x_ref
+        if not args.no_extras:
+            line["extras"] = extras(g, args, A, Ah, xsv)
     for v in (xsv, bv, xv):
         gbs.gbs_vec_destroy(v)
     gbs.gbs_mat_destroy(Ah)
@@ -572,6 +626,17 @@ def extras(g, args, A, Ah, xsv):
                     "kernel_GBps": info.iters * bpi / (info.device_ms / 1e3) / 1e9}
     c3["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(sols["mixed"] - sols["fp64"]) /
                                          torch.linalg.norm(sols["fp64"]))
+    # error of both results against the oracle's FP64 solution (untimed)
+    import oracle
+    t = time.perf_counter()
+    ref3 = oracle.pcg(C3, oracle.spmv(C3, xs3), 1e-10, MAXIT)
+    c3["oracle_fp64"] = {"iters": int(ref3["iters"]), "status": int(ref3["status"]),
+                         "seconds": time.perf_counter() - t}
+    xr3 = torch.from_numpy(ref3["x"]).cuda()
+    for name in ("fp64", "mixed"):
+        c3[name]["rel_err_vs_oracle"] = float(torch.linalg.norm(sols[name] - xr3) /
+                                              torch.linalg.norm(xr3))
+    del xr3
     c3["speedup_mixed_over_fp64"] = c3["fp64"]["ms_to_solution"] / c3["mixed"]["ms_to_solution"]
     out["c3_var27_96_rtol1e-10"] = c3
     for v in (xs3v, b3v, x3v, r3v):
@@ -823,6 +888,23 @@ def c4_batched(g, args):
     diff = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
                for a, b in zip(sols["mixed"], sols["fp64"]))
     res["max_rel_diff_mixed_vs_fp64_per_system"] = diff
+    # error against the oracle's FP64 solution on a seeded sample of
+    # (system, column) pairs (untimed)
+    import oracle
+    u = I.uniform01(44, 901, np.arange(8))
+    sample = []
+    for j in range(4):
+        i = int(u[2 * j] * nsys)
+        _, A, k = mats[i]
+        c = int(u[2 * j + 1] * k)
+        sl = slice(c * A.n, (c + 1) * A.n)
+        ref = oracle.pcg(A, bts[i][sl].cpu().numpy(), 1e-10, 20000)
+        xr = torch.from_numpy(ref["x"]).cuda()
+        sample.append({"system": i, "column": c, "n": A.n, "oracle_iters": int(ref["iters"]),
+                       **{f"rel_err_vs_oracle_{m}": float(torch.linalg.norm(sols[m][i][sl] - xr) /
+                                                           torch.linalg.norm(xr))
+                          for m in ("mixed", "fp64")}})
+    res["oracle_sample"] = sample
     res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
     for (h, _, _), bv, xv in zip(mats, bvs, xvs):
         gbs.gbs_vec_destroy(bv)
@@ -883,10 +965,11 @@ def c5_tune(g, specs, mats):
             "lanes_per_row_by_column_stride": {str(k): v for k, v in sorted(tuned.items())}}
 
 
-def serve_batched(g, specs, mats, bs, arrivals):
+def serve_batched(g, specs, mats, bs, arrivals, keep=None):
     """Continuous batching: requests are submitted (borrowed host arrays) as
     they arrive and fetched as they finish.  Returns (wall s, latencies s,
-    worst relative residual, engine time split)."""
+    worst relative residual, engine time split); the solutions of the
+    requests listed in `keep` (a dict) are stored in it."""
     import numpy as np
     gbs = g.gbs
     nreq = len(specs)
@@ -918,6 +1001,8 @@ def serve_batched(g, specs, mats, bs, arrivals):
                 A = mats[s["matrix_key"]]
                 x, its, rns, sts = gbs.gbs_server_fetch(srv, t, A.n, s["nrhs"])
                 lat[i] = tnow - arrivals[i]
+                if keep is not None and i in keep:
+                    keep[i] = x
                 worst = max(worst, float(np.max(rns / np.maximum(
                     [np.linalg.norm(bs[i][c * A.n:(c + 1) * A.n]) for c in range(s["nrhs"])],
                     1e-300))))
@@ -932,10 +1017,11 @@ def serve_batched(g, specs, mats, bs, arrivals):
                                          "quanta": nq}
 
 
-def serve_perop(g, specs, mats, bs, arrivals):
+def serve_perop(g, specs, mats, bs, arrivals, keep=None):
     """Plain FP64 per-solve launches in arrival order (one persistent solve
     per right-hand side).  Returns (wall s, latencies s, worst relative
-    residual)."""
+    residual); the solutions of the requests listed in `keep` are stored
+    in it."""
     import numpy as np
     import torch
     gbs = g.gbs
@@ -959,9 +1045,11 @@ def serve_perop(g, specs, mats, bs, arrivals):
             worst = max(worst, info.rnorm / info.bnorm if info.status == 0 else float("inf"))
             gbs.gbs_vec_destroy(bv)
             gbs.gbs_vec_destroy(xv)
-        xt.cpu()
+        xh = xt.cpu()
         gbs.gbs_mat_destroy(h)
         lat[i] = time.perf_counter() - t0 - arrivals[i]
+        if keep is not None and i in keep:
+            keep[i] = xh.numpy()
     total = time.perf_counter() - t0
     return total, np.array(lat), worst
 
@@ -974,73 +1062,84 @@ def _served(ncols, nreq, total, lat, worst):
 
 
 def c5_serving(g, args):
-    """Poisson-arriving solve requests on 27-point lognormal(0,1) operators
-    (n log-uniform in [1e3, 1e6], 1-4 right-hand sides, rtol 1e-10), served
-    by the continuous-batching engine (mixed precision, 150 GB budget) and,
-    on the same stream, by plain FP64 per-solve launches."""
+    """The serving workload: Poisson-arriving solve requests on 27-point
+    lognormal(0,1) operators (n log-uniform in [1e3, 1e6], 1-4 right-hand
+    sides, rtol 1e-10), served by the continuous-batching engine (mixed
+    precision, 150 GB budget) and, on the same stream, by plain FP64
+    per-solve launches.
+
+    W warm-up requests are served by both engines and discarded.  The next
+    N requests form four segments of N/4; segment f is offered at the
+    Poisson rate f * lambda_sat for f = 1/4, 1/2, 1, 2 (geometric, into
+    saturation), where lambda_sat is the batched engine's request rate with
+    every request of the first segment present at once (both engines are
+    also timed on that saturated run).  A seeded sample of requests of the
+    first segment (n <= 2e5, one column each) is checked against the
+    oracle's FP64 solution."""
     import numpy as np
+    import oracle
     from paper_2011_00715_gb300 import inputs as I
-    nreq = args.c5_requests
-    pool = args.c5_pool
-    specs = I.c5_request_specs(count=nreq, pool=pool)
+    W, N, pool = args.c5_warmup, args.c5_requests, args.c5_pool
+    specs = I.c5_request_specs(count=W + N, pool=pool)
     t_gen = time.perf_counter()
     mats, bs = c5_workload(g, specs)
     t_gen = time.perf_counter() - t_gen
-    ncols = sum(s["nrhs"] for s in specs)
-    out = {"requests": nreq, "matrix_pool": pool, "columns": ncols, "setup_s": t_gen,
-           "rows_mean": float(np.mean([mats[s["matrix_key"]].n for s in specs]))}
+    main_specs, main_bs = specs[W:], bs[W:]
+    seg = N // 4
+    out = {"warmup_requests": W, "requests": 4 * seg, "requests_per_rate": seg,
+           "matrix_pool": pool, "distinct_sizes": len({mats[s["matrix_key"]].n for s in specs}),
+           "setup_s": t_gen,
+           "rows_mean": float(np.mean([mats[s["matrix_key"]].n for s in main_specs]))}
     out["autotune"] = c5_tune(g, specs, mats)
+    serve_batched(g, specs[:W], mats, bs[:W], np.zeros(W))
+    serve_perop(g, specs[:W], mats, bs[:W], np.zeros(W))
 
-    # saturation (every request present at t = 0), then a Poisson stream at
-    # half the batched engine's saturated request rate
-    zero = np.zeros(nreq)
-    sat = serve_batched(g, specs, mats, bs, zero)
-    rate = 0.5 * nreq / sat[0]
-    arr = I.poisson_arrivals(5, rate, nreq)
-    runs = {"saturation": zero, f"poisson_{rate:.1f}_req_per_s": arr}
-    for name, arrivals in runs.items():
-        t_b, l_b, w_b, eng = sat if name == "saturation" else \
-            serve_batched(g, specs, mats, bs, arrivals)
-        t_p, l_p, w_p = serve_perop(g, specs, mats, bs, arrivals)
-        out[name] = {"batched_mixed": _served(ncols, nreq, t_b, l_b, w_b),
-                     "perop_fp64": _served(ncols, nreq, t_p, l_p, w_p),
-                     "speedup_solves_per_s": t_p / t_b,
-                     "batched_engine_time": eng}
-    return out
+    def segment(j):
+        sp = main_specs[j * seg:(j + 1) * seg]
+        # renumbered so that the engines index them from 0
+        return sp, main_bs[j * seg:(j + 1) * seg], sum(x["nrhs"] for x in sp)
 
-
-def c5_sweep(g, args):
-    """The serving workload's arrival-rate sweep: a warm-up of W requests
-    served by both engines and discarded, then N further requests at Poisson
-    rates lambda_sat / 4, / 2, x 1 and x 2 (geometric, into saturation),
-    where lambda_sat is the batched engine's request rate with every request
-    present at once; both engines at every rate."""
-    import numpy as np
-    from paper_2011_00715_gb300 import inputs as I
-    W, N = args.c5_warmup, args.c5_sweep_requests
-    specs = I.c5_request_specs(count=W + N, pool=args.c5_pool)
-    mats, bs = c5_workload(g, specs)
-    out = {"warmup_requests": W, "requests": N, "matrix_pool": args.c5_pool,
-           "autotune": c5_tune(g, specs, mats)}
-    warm, main_ = specs[:W], specs[W:]
-    serve_batched(g, warm, mats, bs[:W], np.zeros(W))
-    serve_perop(g, warm, mats, bs[:W], np.zeros(W))
-    bsm = bs[W:]
-    ncols = sum(s["nrhs"] for s in main_)
-    out["columns"] = ncols
-    sat = serve_batched(g, main_, mats, bsm, np.zeros(N))
-    lam_sat = N / sat[0]
-    out["saturation_batched"] = _served(ncols, N, sat[0], sat[1], sat[2])
+    sp0, bs0, nc0 = segment(0)
+    zero = np.zeros(seg)
+    t_b, l_b, w_b, eng = serve_batched(g, sp0, mats, bs0, zero)
+    t_p, l_p, w_p = serve_perop(g, sp0, mats, bs0, zero)
+    lam_sat = seg / t_b
     out["lambda_sat_req_per_s"] = lam_sat
+    out["saturation"] = {"batched_mixed": _served(nc0, seg, t_b, l_b, w_b),
+                         "perop_fp64": _served(nc0, seg, t_p, l_p, w_p),
+                         "speedup_solves_per_s": t_p / t_b, "batched_engine_time": eng}
+    # seeded oracle sample among the first segment's requests of n <= 2e5
+    small = [i for i, x in enumerate(sp0) if mats[x["matrix_key"]].n <= 200000]
+    u = I.uniform01(55, 902, np.arange(3))
+    pick = sorted({small[int(v * len(small))] for v in u}) if small else []
     rates = []
-    for f in (0.25, 0.5, 1.0, 2.0):
+    for j, f in enumerate((0.25, 0.5, 1.0, 2.0)):
+        sp, bsj, nc = segment(j)
         lam = f * lam_sat
-        arr = I.poisson_arrivals(6, lam, N)
-        tb, lb, wb, _eng = serve_batched(g, main_, mats, bsm, arr)
-        tp, lp, wp = serve_perop(g, main_, mats, bsm, arr)
+        arr = I.poisson_arrivals(6 + j, lam, seg)
+        kb = {i: None for i in pick} if j == 0 else None
+        kp = {i: None for i in pick} if j == 0 else None
+        tb, lb, wb, _eng = serve_batched(g, sp, mats, bsj, arr, keep=kb)
+        tp, lp, wp = serve_perop(g, sp, mats, bsj, arr, keep=kp)
         rates.append({"lambda_req_per_s": lam, "lambda_over_sat": f,
-                      "batched_mixed": _served(ncols, N, tb, lb, wb),
-                      "perop_fp64": _served(ncols, N, tp, lp, wp)})
+                      "batched_mixed": _served(nc, seg, tb, lb, wb),
+                      "perop_fp64": _served(nc, seg, tp, lp, wp)})
+        if j == 0:
+            sample = []
+            for i in pick:
+                x = sp[i]
+                A = mats[x["matrix_key"]]
+                c = int(I.uniform01(55, 903, [i])[0] * x["nrhs"])
+                sl = slice(c * A.n, (c + 1) * A.n)
+                ref = oracle.pcg(A, bsj[i][sl], 1e-10, 20000)
+                nr = np.linalg.norm(ref["x"])
+                sample.append({"request": W + i, "n": A.n, "column": c,
+                               "oracle_iters": int(ref["iters"]),
+                               "rel_err_vs_oracle_batched_mixed":
+                                   float(np.linalg.norm(kb[i][sl] - ref["x"]) / nr),
+                               "rel_err_vs_oracle_perop_fp64":
+                                   float(np.linalg.norm(kp[i][sl] - ref["x"]) / nr)})
+            out["oracle_sample"] = sample
     out["rates"] = rates
     return out
 
@@ -1085,12 +1184,6 @@ def main():
         B.build()
         g = Gpu(local)
         print(json.dumps({"c1_lap2d5_64_fp64": c1_solves(g)}), flush=True)
-        return
-    if args.c5_sweep:
-        from paper_2011_00715_gb300 import build as B
-        B.build()
-        g = Gpu(local)
-        print(json.dumps({"c5_sweep": c5_sweep(g, args)}), flush=True)
         return
     if args.c5_only:
         from paper_2011_00715_gb300 import build as B

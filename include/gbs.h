@@ -214,6 +214,10 @@ int gbs_mat_set_values(gbs_mat A, const double *vals, int memspace);
 /* Sizes of a matrix; any output pointer may be NULL. */
 int gbs_mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz);
 
+/* CUDA device ordinal of the context the matrix belongs to (where its
+ * arrays live and its solves run).  GBS_ERR_ARG for a NULL argument. */
+int gbs_mat_get_device(gbs_mat A, int *device);
+
 /* Free a matrix (NULL is allowed). */
 int gbs_mat_destroy(gbs_mat A);
 
@@ -373,8 +377,13 @@ int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double
  * have been created beforehand (that allocates, once).
  *
  * Same arithmetic, stopping rule and statuses as gbs_ksp_solve_cg_ex with
- * GBS_MODE_FP64 and GBS_ALG_PERSISTENT.  b (read) and x (initial guess in,
- * solution out) are caller-owned FP64 device arrays of nrows entries;
+ * GBS_MODE_FP64 and GBS_ALG_PERSISTENT, with the context's options
+ * (stopping norm, barrier time limit, persistent_ctas capped at 2048 CTAs);
+ * the result is also kept as the context's last solve (gbs_ksp_last_info).
+ * b (read) and x (initial guess in, solution out) are caller-owned FP64
+ * device arrays of nrows entries on the context's device: the C entry
+ * point receives bare pointers and cannot check their length or device,
+ * so the caller must (the Python binding does, from the tensors).
  * *info receives the result.  The solver's workspace (four FP64 vectors of
  * GBS_NOALLOC_MAX_ROWS entries, per-CTA partial sums, barrier and result
  * record: about 8.1 MB) is one fixed array in the library's device image;
@@ -387,11 +396,11 @@ int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double
  *    overlap on the GPU (other streams or threads of the same device) race
  *    on the array: serialise them.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *    (cudaGetSymbolAddress) with that device current; later calls reuse it.
  *  - Calls no cudaMalloc, no cudaFree and no other allocating routine; it
  *    uses the context's stream, events and pinned result buffer (created
- *    with the context) and synchronises the stream once, at the end. */
+ *    with the context) and synchronises the stream once, at the end, to
+ *    read the result record. */
 int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, double rtol, int maxit,
                              gbs_solve_info *info);
 

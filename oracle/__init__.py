@@ -41,14 +41,52 @@ ERR_CSR = -10
 CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast-math"]
 
 
+def _compile(out: str, extra, force: bool) -> str:
+    with _lock:
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            tmp = out + f".{os.getpid()}.tmp"
+            subprocess.run(["gcc", *CFLAGS, *extra, _SRC, "-o", tmp, "-lm"], check=True)
+            os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc)."""
-    with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
-            os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [], force)
+
+
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with OpenMP (liboracle_omp.so): its SpMV and
+    vector loops run on all host cores.  Used only to time the oracle on
+    every core (the CPU baseline); nothing is checked against it."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
+
+
+def pcg_threaded(A, b, rtol, maxit):
+    """oracle pcg() through the OpenMP build, for timing on all host cores.
+    Returns dict(status, iters, rnorm, threads)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build_omp()
+        lib = ctypes.CDLL(_LIB_OMP)
+        i64, vp = ctypes.c_int64, ctypes.c_void_p
+        lib.orc_pcg.argtypes = [i64, vp, vp, vp, vp, vp, ctypes.c_double, i64,
+                                ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double), vp]
+        lib.orc_pcg.restype = ctypes.c_int
+        lib.orc_threads.restype = ctypes.c_int
+        _lib_omp = lib
+    rp, ci, v, bb = _i32(A.rowptr), _i32(A.colidx), _f64(A.vals), _f64(b)
+    x = np.zeros(A.n)
+    it = ctypes.c_int64(0)
+    rn = ctypes.c_double(0.0)
+    st = _lib_omp.orc_pcg(A.n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), float(rtol), int(maxit),
+                          ctypes.byref(it), ctypes.byref(rn), None)
+    threads = int(_lib_omp.orc_threads())
+    return {"status": st, "iters": it.value, "rnorm": rn.value, "threads": threads}
 
 
 def _load():

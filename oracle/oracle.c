@@ -28,6 +28,13 @@
  *    preconditioner; a NaN in any scalar is reported as such.
  *  - FP32 inner reductions accumulate in FP32 by pairwise summation.
  *
+ * Threads: compiled as is (the build the tests and every check use) the
+ * file is sequential.  The benchmark's CPU-baseline leg also times a second
+ * build of the same source with -fopenmp, in which the loops marked
+ * ORC_PAR_FOR / ORC_PAR_SUM are split across the host's cores (static
+ * schedule; the sums then add in another order).  That build is only
+ * timed, never used to check anything.
+ *
  * Status codes (defined here independently of the CUDA library):
  *   0 converged, 1 iteration limit, -1 bad argument, -4 missing or
  *   non-positive diagonal, -5 indefinite, -6 NaN, -8 stagnation, -10 bad CSR.
@@ -37,6 +44,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#define ORC_PAR_SUM _Pragma("omp parallel for schedule(static) reduction(+:s)")
+#else
+#define ORC_PAR_FOR
+#define ORC_PAR_SUM
+#endif
+
 #define ORC_CONVERGED 0
 #define ORC_DIVERGED_ITS 1
 #define ORC_ERR_ARG (-1)
@@ -45,6 +61,17 @@
 #define ORC_ERR_NAN (-6)
 #define ORC_ERR_STAGNATION (-8)
 #define ORC_ERR_CSR (-10)
+
+/* Host threads that the loops marked ORC_PAR_FOR / ORC_PAR_SUM run on:
+ * 1 in the sequential build. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------- CSR --- */
 
@@ -68,6 +95,7 @@ int orc_csr_check(int64_t n, int64_t ncols, const int32_t *rowptr, const int32_t
 void orc_spmv(int64_t n, const int32_t *rowptr, const int32_t *colidx,
               const double *vals, const double *x, double *y)
 {
+    ORC_PAR_FOR
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
@@ -94,6 +122,7 @@ void orc_spmv_f32(int64_t n, const int32_t *rowptr, const int32_t *colidx,
 double orc_dot(int64_t n, const double *x, const double *y)
 {
     double s = 0.0;
+    ORC_PAR_SUM
     for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
     return s;
 }
@@ -126,12 +155,14 @@ double orc_dot2(int64_t n, const double *x, const double *y)
 /* VecAXPY: y <- alpha x + y. */
 void orc_axpy(int64_t n, double alpha, const double *x, double *y)
 {
+    ORC_PAR_FOR
     for (int64_t i = 0; i < n; ++i) y[i] = alpha * x[i] + y[i];
 }
 
 /* VecAYPX: y <- x + beta y. */
 void orc_aypx(int64_t n, double beta, const double *x, double *y)
 {
+    ORC_PAR_FOR
     for (int64_t i = 0; i < n; ++i) y[i] = x[i] + beta * y[i];
 }
 
@@ -239,7 +270,9 @@ int orc_pcg_norm(int64_t n, const int32_t *rowptr, const int32_t *colidx, const 
     int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
     if (status == 0) {
         orc_spmv(n, rowptr, colidx, vals, x, q);
+        ORC_PAR_FOR
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        ORC_PAR_FOR
         for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
         memcpy(p, z, sizeof(double) * n);
         double rho = orc_dot(n, r, z);
@@ -261,6 +294,7 @@ int orc_pcg_norm(int64_t n, const int32_t *rowptr, const int32_t *colidx, const 
             double alpha = rho / pi;
             orc_axpy(n, alpha, p, x);
             orc_axpy(n, -alpha, q, r);
+            ORC_PAR_FOR
             for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
             double rho_new = orc_dot(n, r, z);
             ++k;

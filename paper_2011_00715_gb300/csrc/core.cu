@@ -596,6 +596,13 @@ extern "C" int gbs_mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64
     return GBS_OK;
 }
 
+extern "C" int gbs_mat_get_device(gbs_mat A, int *device)
+{
+    if (!A || !device) return GBS_ERR_ARG;
+    *device = A->ctx->device;
+    return GBS_OK;
+}
+
 extern "C" int gbs_mat_destroy(gbs_mat A)
 {
     if (!A) return GBS_OK;

@@ -1103,7 +1103,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     int st = noalloc_address(c->device, &scr);
     if (st) return st;
     const Fp64Shape shape = fp64_shape(A);
-    int G = coop_grid(c, shape.fn, A->ntiles, 0, shape.smem, shape.nt);
+    int G = coop_grid(c, shape.fn, A->ntiles, c->opts.persistent_ctas, shape.smem, shape.nt);
     if (G < 0) return GBS_ERR_CUDA;
     if (G > kNoAllocMaxCtas) G = kNoAllocMaxCtas;
     char *base = (char *)scr;
@@ -1129,5 +1129,8 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     // partial sums are written before they are read
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocHead, c->stream));
     a.pipe64 = shape.cfg;
-    return launch_persistent(c, shape.fn, G, a, info, shape.smem, shape.nt);
+    st = launch_persistent(c, shape.fn, G, a, info, shape.smem, shape.nt);
+    if (st == GBS_ERR_CUDA) info->status = st;
+    c->last = *info;
+    return st;
 }

@@ -107,6 +107,7 @@ _SIGS = {
     "gbs_mat_set_values_coo": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
     "gbs_mat_get_csr": ([_VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "gbs_mat_get_info": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "gbs_mat_get_device": ([_VP, _I32P], ctypes.c_int),
     "gbs_mat_destroy": ([_VP], ctypes.c_int),
     "gbs_mat_mult": ([_VP, _VP, _VP], ctypes.c_int),
     "gbs_vec_create": ([_VP, _I64, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -323,6 +324,12 @@ def gbs_mat_get_info(A):
     return n.value, m.value, z.value
 
 
+def gbs_mat_get_device(A) -> int:
+    d = ctypes.c_int32()
+    _check(lib().gbs_mat_get_device(A, ctypes.byref(d)), "gbs_mat_get_device")
+    return d.value
+
+
 def gbs_mat_destroy(A):
     _check(lib().gbs_mat_destroy(A), "gbs_mat_destroy")
 
@@ -494,6 +501,14 @@ def gbs_ksp_solve_cg_noalloc(A, b, x, rtol: float, maxit: int) -> SolveInfo:
         raise ValueError("b and x must be device tensors")
     if _dtype_code(b) != GBS_F64 or _dtype_code(x) != GBS_F64:
         raise TypeError("b and x must be float64")
+    # the C entry point gets bare pointers: the length and the device are
+    # checked here, where the tensors are known
+    n, _m, _z = gbs_mat_get_info(A)
+    if b.numel() != n or x.numel() != n:
+        raise ValueError(f"b and x must have {n} entries (got {b.numel()} and {x.numel()})")
+    dev = gbs_mat_get_device(A)
+    if b.device.index != dev or x.device.index != dev:
+        raise ValueError(f"b and x must be on cuda:{dev}, the matrix's device")
     info = gbs_solve_info()
     st = lib().gbs_ksp_solve_cg_noalloc(A, _VP(pb), _VP(px), float(rtol), int(maxit),
                                         ctypes.byref(info))

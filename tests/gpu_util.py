@@ -39,3 +39,17 @@ class Session:
     def host(self, t):
         self.torch.cuda.synchronize()
         return t.cpu().numpy()
+
+
+def record(test: str, quantity: str, value: float, bound: float) -> None:
+    """Append a measured parity figure (and the bound the test holds it to)
+    to the JSON-lines file named by GBS_PARITY_LOG, when that is set; the
+    worst value per family is what the design notes quote."""
+    import json
+    import os
+    path = os.environ.get("GBS_PARITY_LOG")
+    print(f"{test}: {quantity} = {value:.3e} (bound {bound:.3e})")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": test, "quantity": quantity, "value": float(value),
+                                "bound": float(bound)}) + "\n")

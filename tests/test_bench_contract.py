@@ -26,7 +26,12 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert "workload" in d["config"] and "model" not in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host_cpus"] == os.cpu_count()
+    # ms_per_step is the time of what each step ran (a bounded sample of the
+    # solve); the extrapolation to a whole solve is its own field
+    assert d["ms_per_step"] < d["ms_per_solve_extrapolated"] or d["iters_per_step"] >= d["iters_per_solve"]
+    assert abs(d["ms_per_solve_extrapolated"] - 1e3 / d["value"]) <= 1e-6 * d["ms_per_solve_extrapolated"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 

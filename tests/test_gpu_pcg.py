@@ -1,12 +1,17 @@
 """Jacobi-PCG parity: the CUDA solves against the CPU oracle.
 
-Tolerances: iteration counts within +-2 of the oracle; solutions within
-1e-8 relative of the oracle's FP64 solution at rtol 1e-10 (1e-6 at rtol
-1e-8); the true residual ||b - A x||_2, recomputed by the oracle's SpMV,
-within rtol ||b||_2 (1 + 1e-3).  At full size the oracle is too slow to
-solve, so the full-size cases check properties that hold at any size:
-the true residual, the forward error against the manufactured solution
-(<= kappa * rtol), and the closed-form CG iteration bound.
+Tolerances: iteration counts within +-2 of the oracle; FP64 solutions
+within 1e-8 relative of the oracle's FP64 solution at rtol 1e-10 (1e-6 at
+rtol 1e-8), at every size including the full 128^3 and 96^3 workloads the
+benchmark times (the oracle solves those in seconds); the true residual
+||b - A x||_2, recomputed by the oracle's SpMV, within rtol ||b||_2
+(1 + 1e-3).  Mixed-precision solutions are held to the oracle's FP64
+solution within the larger of 1e-8 and the guarantee of the stopping rule
+(two solutions with residuals r and r_ref differ by at most
+(||r|| + ||r_ref||) / lambda_min); the measured difference is recorded
+beside the bound.  The full-size cases also check the forward error
+against the manufactured solution (<= kappa * rtol) and the closed-form CG
+iteration bound.
 """
 import math
 
@@ -26,6 +31,11 @@ ALGS = {"persistent": gbs.GBS_ALG_PERSISTENT, "perop": gbs.GBS_ALG_PEROP,
 def S():
     from gpu_util import Session
     return Session()
+
+
+def record(*a):
+    from gpu_util import record as rec
+    rec(*a)
 
 
 def solve(S, A, b, rtol, maxit, x0=None, **opts):
@@ -106,6 +116,7 @@ def test_fp64_rtol_1e10(S, orc, alg, maker):
     info, x = solve(S, A, b, 1e-10, 20000, algorithm=ALGS[alg])
     assert info.status == gbs.GBS_OK
     assert abs(info.iters - ref["iters"]) <= 2
+    record(f"fp64_rtol_1e10[{alg},n={A.n}]", "rel_err_vs_oracle", rel(x, ref["x"]), 1e-8)
     assert rel(x, ref["x"]) <= 1e-8
     assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
 
@@ -119,9 +130,11 @@ def unit_laplacian_lmin(dims):
 @pytest.mark.parametrize("case", ["lap3d7_56", "var7_60x56x52"])
 def test_wide_shape_matches_oracle(S, orc, case):
     """Systems with at least 32 warp tiles per SM and 7-point rows run the
-    32-warp launch shape of the persistent kernel: same bar as the smaller
-    systems, with the solution bound taken from a closed-form lambda_min
-    (A - w_min L_unit is a sum of positive semidefinite link terms)."""
+    32-warp launch shape of the persistent kernel (the benchmark's shape):
+    the same 1e-8 bar against the oracle's FP64 solution as the smaller
+    systems.  The stopping rule's own guarantee, from a closed-form
+    lambda_min (A - w_min L_unit is a sum of positive semidefinite link
+    terms), is recorded beside it."""
     if case == "lap3d7_56":
         A, lmin = I.lap3d7(56), unit_laplacian_lmin((56, 56, 56))
     else:
@@ -134,7 +147,9 @@ def test_wide_shape_matches_oracle(S, orc, case):
     assert info.status == gbs.GBS_OK
     assert abs(info.iters - ref["iters"]) <= 2
     assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
-    assert rel(x, ref["x"]) <= solution_tol(orc, A, b, x, ref["x"], lmin)
+    record(f"wide_shape[{case}]", "rel_err_vs_oracle", rel(x, ref["x"]),
+           solution_tol(orc, A, b, x, ref["x"], lmin))
+    assert rel(x, ref["x"]) <= 1e-8
     assert abs(info.bnorm - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
 
 
@@ -147,7 +162,9 @@ def test_mixed_matches_fp64_oracle(S, orc, maker):
     info, x = solve(S, A, b, 1e-10, 20000, mode=gbs.GBS_MODE_MIXED)
     assert info.status == gbs.GBS_OK, gbs.gbs_status_string(info.status)
     assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b)
-    assert rel(x, ref["x"]) <= solution_tol(orc, A, b, x, ref["x"], lambda_min(A))
+    tol = solution_tol(orc, A, b, x, ref["x"], lambda_min(A))
+    record(f"mixed[n={A.n}]", "rel_err_vs_oracle", rel(x, ref["x"]), tol)
+    assert rel(x, ref["x"]) <= tol
     assert 1 <= info.outer_iters <= math.ceil(math.log(1e-10) / math.log(1e-4)) + 2
     assert abs(info.rnorm - true_res(orc, A, b, x)) <= 1e-3 * info.rnorm + 1e-300
     m = orc.pcg_mixed(A, b, 1e-10, 1e-4)
@@ -212,14 +229,21 @@ def test_barrier_timeout_is_reported_and_context_survives(S, orc):
 
 
 def test_c2_full_size_fp64(S, orc):
-    """128^3 7-point Laplacian, rtol 1e-10, the configuration the benchmark
-    times: true residual, forward error <= kappa rtol, and the CG bound."""
+    """128^3 7-point Laplacian, rtol 1e-10, the configuration and launch
+    shape the benchmark times: within 1e-8 of the oracle's FP64 solution
+    (the oracle solves it in about 7 s), iterations within 2 of the
+    oracle's, true residual, forward error <= kappa rtol, and the CG
+    bound."""
     N = 128
     A = I.lap3d7(N)
     xs = I.xstar(A.n, 2)
     b = orc.spmv(A, xs)
-    info, x = solve(S, A, b, 1e-10, 5000)
-    assert info.status == gbs.GBS_OK
+    ref = orc.pcg(A, b, 1e-10, 5000)
+    info, x = solve(S, A, b, 1e-10, 5000, algorithm=ALGS["persistent"])
+    assert info.status == gbs.GBS_OK and ref["status"] == 0
+    assert abs(info.iters - ref["iters"]) <= 2
+    record("c2_full_size_fp64", "rel_err_vs_oracle", rel(x, ref["x"]), 1e-8)
+    assert rel(x, ref["x"]) <= 1e-8
     c = math.cos(math.pi / (N + 1))
     kappa = (1 + c) / (1 - c)
     s = math.sqrt(kappa)
@@ -230,20 +254,29 @@ def test_c2_full_size_fp64(S, orc):
 
 
 def test_c3_full_size_mixed_vs_fp64(S, orc):
-    """96^3 27-point variable-coefficient operator at rtol 1e-10: mixed and
-    FP64 both reach the true FP64 residual and agree to 1e-8."""
+    """96^3 27-point variable-coefficient operator at rtol 1e-10, the
+    benchmark's mixed-precision workload: the FP64 solve within 1e-8 of the
+    oracle's FP64 solution, the mixed solve within the stopping rule's
+    guarantee of it (recorded with its measured value), both at the true
+    FP64 residual."""
     A = I.var27(96, seed=3, sigma=1.0)
     b = orc.spmv(A, I.xstar(A.n, 3))
+    ref = orc.pcg(A, b, 1e-10, 20000)
     i64, x64 = solve(S, A, b, 1e-10, 20000)
     imx, xmx = solve(S, A, b, 1e-10, 20000, mode=gbs.GBS_MODE_MIXED)
-    assert i64.status == gbs.GBS_OK and imx.status == gbs.GBS_OK
+    assert i64.status == gbs.GBS_OK and imx.status == gbs.GBS_OK and ref["status"] == 0
+    assert abs(i64.iters - ref["iters"]) <= 2
     nb = np.linalg.norm(b)
     assert true_res(orc, A, b, x64) <= 1e-10 * nb * (1 + 1e-3)
     assert true_res(orc, A, b, xmx) <= 1e-10 * nb
+    record("c3_full_size_fp64", "rel_err_vs_oracle", rel(x64, ref["x"]), 1e-8)
+    assert rel(x64, ref["x"]) <= 1e-8
     # lambda_min(A) >= w_min * lambda_min(unit-weight operator) (A minus
     # w_min times the unit operator is a sum of PSD link terms); the unit
     # 27-point operator has the closed-form minimum 14 - 6c - 6c^2 - 2c^3,
     # c = cos(pi / (N + 1))
     c = math.cos(math.pi / 97)
     lmin = (14 - 6 * c - 6 * c * c - 2 * c ** 3) * float(A.meta["w_min"])
-    assert rel(xmx, x64) <= solution_tol(orc, A, b, xmx, x64, lmin)
+    tol = solution_tol(orc, A, b, xmx, ref["x"], lmin)
+    record("c3_full_size_mixed", "rel_err_vs_oracle", rel(xmx, ref["x"]), tol)
+    assert rel(xmx, ref["x"]) <= tol

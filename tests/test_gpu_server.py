@@ -45,6 +45,10 @@ def check(orc, A, b, k, x, sts):
                     - 2 * cs[0] * cs[1] * cs[2])
         lmin = A.meta["w_min"] * lam_unit
         bound = (np.linalg.norm(bc - orc.spmv(A, xc)) + np.linalg.norm(bc - orc.spmv(A, ref["x"]))) / lmin
+        from gpu_util import record
+        nr = np.linalg.norm(ref["x"])
+        record(f"server[n={A.n},col={c}]", "rel_err_vs_oracle", np.linalg.norm(xc - ref["x"]) / nr,
+               max(1e-8, bound / nr))
         assert np.linalg.norm(xc - ref["x"]) <= max(1e-8 * np.linalg.norm(ref["x"]), bound)
 
 

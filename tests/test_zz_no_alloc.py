@@ -52,6 +52,23 @@ def test_noalloc_solve_matches_regular_solve_twice(orc):
         assert np.linalg.norm(b - orc.spmv(A, x)) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
         assert abs(info.bnorm - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
 
+    # the binding refuses vectors of the wrong length or on another device
+    # before the C entry point (which sees bare pointers) could run past
+    # their ends
+    short = torch.zeros(A.n - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        gbs.gbs_ksp_solve_cg_noalloc(h, short, x_t, 1e-10, 100)
+    with pytest.raises(ValueError):
+        gbs.gbs_ksp_solve_cg_noalloc(h, bt, short, 1e-10, 100)
+    assert gbs.gbs_mat_get_device(h) == 0
+    if torch.cuda.device_count() > 1:
+        other = torch.zeros(A.n, dtype=torch.float64, device="cuda:1")
+        with pytest.raises(ValueError):
+            gbs.gbs_ksp_solve_cg_noalloc(h, other, x_t, 1e-10, 100)
+    # the result is the context's last solve as well
+    last = gbs.gbs_ksp_last_info(ctx)
+    assert last.status == gbs.GBS_OK and last.iters == info.iters
+
     # sizes beyond the fixed workspace are refused with GBS_ERR_ARG
     big = I.lap3d7(65)                                      # 274,625 rows > 262,144
     hb = gbs.gbs_mat_create_aij(ctx, big.n, big.n, big.rowptr, big.colidx, big.vals)
