@@ -172,24 +172,31 @@ FP64_NOMINAL_GOPS = 625.0
 
 def ops_per_iter_fp64(n, nnz):
     """FP64 operations of one fused PCG iteration: one per nonzero in the
-    SpMV, one per row for p.q, five per row in the update (x, r, z, r.z,
-    r.r) and one per row for the direction."""
-    return nnz + 7 * n
+    SpMV, one per row for p.q, four per row in the update (x, r, z, r.z)
+    and one per row for the direction.  The r.r sum of the stopping test
+    (one more per row) runs only in the iterations where r.z cannot rule
+    the test out, the last few of a solve, and is not counted."""
+    return nnz + 6 * n
 
 
-def bytes_per_iter_fp64(n, nnz):
-    """Fused FP64 PCG iteration: 12 nnz (vals + colidx) + 108 n (rowptr 4n,
-    p gather 8n, q write 8n, update phase 64n, p update 24n)."""
-    return 12 * nnz + 108 * n
+def bytes_per_iter_fp64(n, nnz, index_bytes=4):
+    """Fused FP64 PCG iteration: (8 + index bytes) nnz (values + column
+    indices: 12 nnz with 32-bit indices, 10 with the 16-bit column offsets
+    the library streams where they fit) + 108 n (rowptr 4n, p gather 8n,
+    q write 8n, update phase 64n, p update 24n)."""
+    return (8 + index_bytes) * nnz + 108 * n
 
 
-def bytes_per_iter_mixed(n, nnz):
-    """FP32 inner iteration: 8 nnz + 56 n."""
-    return 8 * nnz + 56 * n
+def bytes_spmv_fp64(n, nnz, index_bytes=4):
+    """FP64 MatMult: (8 + index bytes) nnz + 4(n+1) row pointers + 8n x
+    gather + 8n y write."""
+    return (8 + index_bytes) * nnz + 4 * (n + 1) + 8 * n + 8 * n
 
 
-def bytes_spmv_fp64(n, nnz):
-    return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
+def stencil_index_bytes(N):
+    """Column index bytes the library streams for the 7-point operator on
+    an N^3 grid: 16-bit offsets col - row fit while N^2 <= 32767."""
+    return 2 if N * N <= 32767 else 4
 
 
 # ---------------------------------------------------------------- CPU oracle --
@@ -424,8 +431,12 @@ def run_gbs(args, rank, world, local):
         else args.steps / el
     n, nnz = A.n, A.nnz
     hbm, peak_kind = peaks()
-    bpl = iters[0] * bytes_per_iter_fp64(n, nnz)
+    # the library's byte model of the launch (set-up pass + iterations, with
+    # the column index width it streamed); the 12-byte-per-nonzero CSR
+    # figure (32-bit indices) is reported beside it
+    bpl = statistics.mean(i.model_bytes for i in infos)
     achieved = bpl / (dev_ms / 1e3) / 1e9
+    achieved_csr32 = iters[0] * bytes_per_iter_fp64(n, nnz, 4) / (dev_ms / 1e3) / 1e9
     # true residual of the last solve, on the device with the library's SpMV
     rt = torch.empty_like(bt)
     rv = gbs.gbs_vec_wrap(g.ctx, rt)
@@ -440,7 +451,8 @@ def run_gbs(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded stencil matrix and manufactured solution)",
             "config": config_for(world),
-            "algorithm": "persistent cooperative kernel, 3 grid barriers/iteration",
+            "algorithm": "persistent cooperative kernel, 3 grid barriers/iteration, "
+                         "16-bit column offsets",
             "solve": {"status": sorted(statuses), "iters": iters[0],
                       "true_rel_residual": true_rel, "rel_err_vs_xstar": err_xs,
                       "kernel_ms": dev_ms, "us_per_iter": dev_ms * 1e3 / iters[0],
@@ -450,14 +462,20 @@ def run_gbs(args, rank, world, local):
                          "frac": achieved / hbm,
                          "traffic": measured_traffic(iters[0]),
                          "kernel": "k_pcg_fp64 (one launch per solve)",
-                         "bytes_model": "iters x (12 nnz + 108 n)", "peak_kind": peak_kind},
+                         "bytes_model": "set-up (10 nnz + 52 n) + iters x (10 nnz + 108 n): "
+                                        "8-byte values and 16-bit column offsets",
+                         "bytes_per_launch": bpl,
+                         "frac_by_csr32_model": achieved_csr32 / hbm,
+                         "csr32_model": "iters x (12 nnz + 108 n), 32-bit column indices",
+                         "peak_kind": peak_kind},
             "roofline_fp64": {"bound": "alu", "achieved": ops_per_iter_fp64(n, nnz) * iters[0]
                               / (dev_ms / 1e3) / 1e9,
                               "peak": FP64_NOMINAL_GOPS, "unit": "G FP64 ops/s",
                               "frac": ops_per_iter_fp64(n, nnz) * iters[0] / (dev_ms / 1e3) / 1e9
                               / FP64_NOMINAL_GOPS,
-                              "ops_model": "iters x (nnz + 7n): SpMV nnz, p.q n, update 5n, "
-                                           "direction n (one FP64 instruction lane each)",
+                              "ops_model": "iters x (nnz + 6n): SpMV nnz, p.q n, update 4n, "
+                                           "direction n (one FP64 instruction lane each; the "
+                                           "r.r sum of the last iterations is not counted)",
                               "peak_kind": "nominal 1.25 TFLOP/s = 625 G FMA/s"},
             "gpu_launches": int(l1 - l0),
             "clocks": clk}
@@ -583,10 +601,12 @@ def extras(g, args, A, Ah, xsv):
         gbs.gbs_mat_mult(Ah, xsv, yv)
     reps = 50
     el = event_time(torch, lambda: gbs.gbs_mat_mult(Ah, xsv, yv), reps)
-    bb = bytes_spmv_fp64(A.n, A.nnz)
+    bb = bytes_spmv_fp64(A.n, A.nnz, stencil_index_bytes(N_GRID))
+    bb32 = bytes_spmv_fp64(A.n, A.nnz, 4)
     out["spmv_c2_fp64"] = {"us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
                            "frac": bb / (el / reps) / 1e9 / hbm,
-                           "bytes_model": "12 nnz + 4(n+1) + 8n + 8n"}
+                           "bytes_model": "10 nnz + 4(n+1) + 8n + 8n (16-bit column offsets)",
+                           "frac_by_csr32_model": bb32 / (el / reps) / 1e9 / hbm}
     gbs.gbs_vec_destroy(yv)
     # --- C1: 64x64 2D Laplacian, rtol 1e-8
     out["c1_lap2d5_64_fp64"] = c1_solves(g)
@@ -618,12 +638,12 @@ def extras(g, args, A, Ah, xsv):
         gbs.gbs_mat_mult(h, x3v, r3v)
         torch.cuda.synchronize()
         sols[name] = x3.clone()
-        bpi = (bytes_per_iter_fp64 if name == "fp64" else bytes_per_iter_mixed)(C3.n, C3.nnz)
         c3[name] = {"ms_to_solution": el / n_rep * 1e3, "status": info.status,
                     "iters": info.iters, "outer_iters": info.outer_iters,
                     "true_rel_residual": float(torch.linalg.norm(b3 - r3) / torch.linalg.norm(b3)),
                     "rel_err_vs_xstar": float(torch.linalg.norm(x3 - xs3t) / torch.linalg.norm(xs3t)),
-                    "kernel_GBps": info.iters * bpi / (info.device_ms / 1e3) / 1e9}
+                    "kernel_GBps": info.model_bytes / (info.device_ms / 1e3) / 1e9,
+                    "kernel_hbm_frac": info.model_bytes / (info.device_ms / 1e3) / 1e9 / hbm}
     c3["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(sols["mixed"] - sols["fp64"]) /
                                          torch.linalg.norm(sols["fp64"]))
     # error of both results against the oracle's FP64 solution (untimed)
@@ -780,12 +800,13 @@ def c2_sweep(g, args):
         yt = torch.empty_like(xt)
         xv, yv = gbs.gbs_vec_wrap(g.ctx, xt), gbs.gbs_vec_wrap(g.ctx, yt)
         f = lambda: gbs.gbs_mat_mult(h, xv, yv)
-        nbytes = bytes_spmv_fp64(n, nnz)
+        nbytes = bytes_spmv_fp64(n, nnz, stencil_index_bytes(N))
         reps = int(min(2000, max(10, 4e9 // nbytes)))
         for _ in range(3):
             f()
         el = event_time(torch, f, reps) / reps
-        rows.append({"op": "MatMult", "n": n, "nnz": nnz, "us": el * 1e6, "GBps": nbytes / el / 1e9})
+        rows.append({"op": "MatMult", "n": n, "nnz": nnz, "index_bytes": stencil_index_bytes(N),
+                     "us": el * 1e6, "GBps": nbytes / el / 1e9})
         gbs.gbs_vec_destroy(xv)
         gbs.gbs_vec_destroy(yv)
         gbs.gbs_mat_destroy(h)

@@ -139,7 +139,14 @@ typedef struct {
                                 norm, and a solve in GBS_MODE_MIXED with another
                                 norm is refused with GBS_ERR_ARG.
                                 Default GBS_NORM_UNPRECONDITIONED */
-    int reserved[5];
+    int no_rel16;            /* 1: single-system MatMult, CG and Chebyshev solves
+                                stream the 32-bit column indices; 0 (default):
+                                they stream 16-bit offsets col - row instead
+                                wherever every |col - row| of the matrix is at
+                                most 32767 (made on the first such use; Sec. 3,
+                                Challenge A7: the index bytes cap what narrower
+                                values save) */
+    int reserved[4];
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -154,7 +161,10 @@ typedef struct {
     double bnorm;        /* ||b||_2; N(b) in the chosen norm_type */
     double device_ms;    /* device time of the solve (CUDA events) */
     double model_bytes;  /* algorithmic bytes the solve moved by the library's
-                            byte model (batched solves; 0 where not computed) */
+                            byte model: persistent single-system CG solves
+                            (FP64 and MIXED; a nonzero counts its value and
+                            the column index width actually streamed) and
+                            batched solves; 0 where not computed */
 } gbs_solve_info;
 
 /* Library version string (static storage). */
@@ -386,7 +396,7 @@ int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double
  * so the caller must (the Python binding does, from the tensors).
  * *info receives the result.  The solver's workspace (four FP64 vectors of
  * GBS_NOALLOC_MAX_ROWS entries, per-CTA partial sums, barrier and result
- * record: about 8.1 MB) is one fixed array in the library's device image;
+ * record: about 8.6 MB) is one fixed array in the library's device image;
  * every GPU that loads the library holds it until the process exits.
  * Limits and behaviour:
  *  - GBS_ERR_ARG if nrows > GBS_NOALLOC_MAX_ROWS, the matrix is not

@@ -31,6 +31,7 @@ constexpr size_t kChebSmem = (size_t)GBS_WARP_STAGE_BYTES * GBS_PWARPS;
 struct ChebArgs {
     int64_t n, ntiles;
     const int32_t *tiles, *tdesc, *rowptr, *colidx;
+    const int16_t *colrel16;   // col - row, streamed instead of colidx when set
     const double *vals, *dinv, *b;
     double *x, *r, *d0, *d1;
     double *part;   // [parity][r.r, b.b][G]
@@ -68,9 +69,12 @@ __device__ __forceinline__ int cheb_check(double rn, double tol, int k, int maxi
 // NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp: 32
 // warps with 6.4 KB rings for large systems (more gathers in flight), else
 // 16 warps with 12.8 KB rings.
-template <int NT, int WB>
+// IX: the column indices the SpMV streams (int32, or 16-bit col - row).
+template <int NT, int WB, typename IX>
 __global__ void __launch_bounds__(NT, 1) k_chebyshev(ChebArgs a)
 {
+    const IX *cols = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
+                                     : (const IX *)(const void *)a.colidx;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ChebShared<NT> sh;
     __shared__ GbsWarpQ s_q[NT / 32];
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(NT, 1) k_chebyshev(ChebArgs a)
             acc[0] += ri * ri;
             acc[1] += bi * bi;
         };
-        if (!gbs_spmv_pipe<double>(a.tdesc, t0, t1, &s_next, a.rowptr, a.colidx, a.vals, a.x, wsm,
+        if (!gbs_spmv_pipe<double, IX>(a.tdesc, t0, t1, &s_next, a.rowptr, cols, a.vals, a.x, wsm,
                                    s_q[warp], parity, a.pipe, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(NT, 1) k_chebyshev(ChebArgs a)
                 gbs_st(dn + i, fma(a1, di, a2 * (v.dinv * ri)), pk);
                 acc[0] += ri * ri;
             };
-            if (!gbs_spmv_pipe_pre<double>(a.tdesc, t0, t1, &s_next, a.rowptr, a.colidx, a.vals, dc,
+            if (!gbs_spmv_pipe_pre<double, IX>(a.tdesc, t0, t1, &s_next, a.rowptr, cols, a.vals, dc,
                                            wsm, s_q[warp], parity, a.pipe, ps, pk, a.timeout_ns, pre,
                                            epi) &&
                 (threadIdx.x & 31) == 0)
@@ -207,11 +211,19 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
         // launch shape: 32 warps with 6.4 KB rings when two stages of the largest
         // tile fit and there are at least 32 tiles per SM
         constexpr int kWide = 2 * GBS_PBLOCK, kRing = GBS_WARP_STAGE_BYTES / 2;
-        GbsPipeCfg cfg = A->pipe64;
+        if (!c->opts.no_rel16) {
+            st = gbs_mat_ensure_rel16(A);
+            if (st) return st;
+        }
+        const bool rel = A->colrel16 && !c->opts.no_rel16;
+        GbsPipeCfg cfg = rel ? A->pipe64r : A->pipe64;
         const int st6 = kRing / cfg.sbytes;
         const bool wide = st6 >= 2 && A->ntiles >= (int64_t)c->num_sms * (kWide / 32);
-        const void *fn = wide ? (const void *)k_chebyshev<kWide, kRing>
-                              : (const void *)k_chebyshev<GBS_PBLOCK, GBS_WARP_STAGE_BYTES>;
+        const void *fn =
+            rel ? (wide ? (const void *)k_chebyshev<kWide, kRing, int16_t>
+                        : (const void *)k_chebyshev<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, int16_t>)
+                : (wide ? (const void *)k_chebyshev<kWide, kRing, int32_t>
+                        : (const void *)k_chebyshev<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, int32_t>);
         const int nt = wide ? kWide : GBS_PBLOCK;
         const size_t smem = wide ? (size_t)kRing * (kWide / 32) : kChebSmem;
         if (wide) cfg.stages = st6 < GBS_MAX_STAGES ? st6 : GBS_MAX_STAGES;
@@ -245,6 +257,7 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
         a.tdesc = A->tdesc;
         a.rowptr = A->rowptr;
         a.colidx = A->colidx;
+        a.colrel16 = rel ? A->colrel16 : nullptr;
         a.vals = A->vals;
         a.dinv = A->dinv;
         a.pipe = cfg;
@@ -275,9 +288,10 @@ extern "C" int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double e
         tmp.device_ms = ms;
         // algorithmic bytes: the set-up pass (matrix, rowptr, x gather, b and
         // D^-1 read, r and d written), then per iteration the matrix, rowptr,
-        // the d gather, x and r read and written, D^-1 read, d written
-        const double n = (double)A->n, nnz = (double)A->nnz;
-        tmp.model_bytes = (12 * nnz + 4 * (n + 1) + 40 * n) + r.iters * (12 * nnz + 4 * (n + 1) + 56 * n);
+        // the d gather, x and r read and written, D^-1 read, d written; a
+        // nonzero is 8 bytes of value and 4 or 2 of column index
+        const double n = (double)A->n, nnz = (double)A->nnz, bnz = rel ? 10.0 : 12.0;
+        tmp.model_bytes = (bnz * nnz + 4 * (n + 1) + 40 * n) + r.iters * (bnz * nnz + 4 * (n + 1) + 56 * n);
         st = r.status;
     }
     c->last = tmp;

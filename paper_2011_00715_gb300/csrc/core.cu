@@ -75,6 +75,7 @@ static int opts_valid(const gbs_opts *o)
     if (o->persistent_ctas < 0) return 0;
     if (o->norm_type < GBS_NORM_UNPRECONDITIONED || o->norm_type > GBS_NORM_NATURAL) return 0;
     if (o->norm_type != GBS_NORM_UNPRECONDITIONED && o->mode == GBS_MODE_MIXED) return 0;
+    if (o->no_rel16 != 0 && o->no_rel16 != 1) return 0;
     return 1;
 }
 
@@ -443,6 +444,7 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     A->pipe64 = make_pipe_cfg(tiles, hrp, 8);
     A->pipe32 = make_pipe_cfg(tiles, hrp, 4);
     A->pipe16 = make_pipe_cfg(tiles, hrp, 4, 2);
+    A->pipe64r = make_pipe_cfg(tiles, hrp, 8, 2);
     std::vector<int32_t> tdesc(2 * tiles.size());
     for (size_t t = 0; t < tiles.size(); ++t) {
         tdesc[2 * t] = tiles[t];
@@ -497,21 +499,17 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     return GBS_OK;
 }
 
-int gbs_mat_ensure_f32(gbs_mat A)
+// The compressed column indices (Challenge A7: with 32-bit indices an FP64
+// nonzero streams 12 bytes and an FP32 one 8; 16-bit offsets from the row
+// make that 10 and 6) where every |col - row| of the matrix fits in int16.
+int gbs_mat_ensure_rel16(gbs_mat A)
 {
-    if (A->vals32 || A->nnz == 0) {
-        if (!A->vals32) GBS_CUDA_TRY(cudaMalloc(&A->vals32, 16));
+    if (A->rel16_state != 0) return GBS_OK;
+    if (A->nnz == 0 || A->n > (int64_t)INT32_MAX) {
+        A->rel16_state = -1;
         return GBS_OK;
     }
     gbs_ctx c = A->ctx;
-    const size_t pad_nnz = (size_t)((A->nnz + 4) & ~(int64_t)3);
-    GBS_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float) * pad_nnz));
-    GBS_CUDA_TRY(cudaMemsetAsync(A->vals32, 0, sizeof(float) * pad_nnz, c->stream));
-    k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals, A->vals32);
-    gbs_count_launch(c);
-    GBS_CUDA_TRY(cudaGetLastError());
-    // the compressed column indices of the FP32 paths (Challenge A7: with
-    // 32-bit indices FP32 values save only a third of the matrix bytes)
     const size_t pad16 = (size_t)((A->nnz + 15) & ~(int64_t)7);
     int16_t *rel = nullptr;
     GBS_CUDA_TRY(cudaMalloc(&rel, sizeof(int16_t) * pad16));
@@ -531,9 +529,30 @@ int gbs_mat_ensure_f32(gbs_mat A)
         cudaFree(rel);
         return gbs_cuda_fail(e);
     }
-    if (*(volatile int *)c->pinned) cudaFree(rel);
-    else A->colrel16 = rel;
+    if (*(volatile int *)c->pinned) {
+        cudaFree(rel);
+        A->rel16_state = -1;
+    } else {
+        A->colrel16 = rel;
+        A->rel16_state = 1;
+    }
     return GBS_OK;
+}
+
+int gbs_mat_ensure_f32(gbs_mat A)
+{
+    if (A->vals32 || A->nnz == 0) {
+        if (!A->vals32) GBS_CUDA_TRY(cudaMalloc(&A->vals32, 16));
+        return gbs_mat_ensure_rel16(A);
+    }
+    gbs_ctx c = A->ctx;
+    const size_t pad_nnz = (size_t)((A->nnz + 4) & ~(int64_t)3);
+    GBS_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float) * pad_nnz));
+    GBS_CUDA_TRY(cudaMemsetAsync(A->vals32, 0, sizeof(float) * pad_nnz, c->stream));
+    k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals, A->vals32);
+    gbs_count_launch(c);
+    GBS_CUDA_TRY(cudaGetLastError());
+    return gbs_mat_ensure_rel16(A);
 }
 
 extern "C" int gbs_mat_get_csr(gbs_mat A, int32_t *rowptr, int32_t *colidx, double *vals,
@@ -696,13 +715,19 @@ extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
     gbs_ctx c = A->ctx;
     if (A->n == 0) return GBS_OK;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
-    if (x->dtype == GBS_F64)
+    if (x->dtype == GBS_F64) {
+        int st = gbs_mat_ensure_rel16(A);
+        if (st) return st;
+        if (A->colrel16 && !c->opts.no_rel16)
+            return spmv_launch<double, int16_t>(c, A, A->vals, A->colrel16, A->pipe64r,
+                                                (const double *)x->data, (double *)y->data);
         return spmv_launch<double, int32_t>(c, A, A->vals, A->colidx, A->pipe64,
                                             (const double *)x->data, (double *)y->data);
+    }
     int st = gbs_mat_ensure_f32(A);
     if (st) return st;
     // FP32: the compressed 16-bit column indices where the matrix allows them
-    if (A->colrel16)
+    if (A->colrel16 && !c->opts.no_rel16)
         return spmv_launch<float, int16_t>(c, A, A->vals32, A->colrel16, A->pipe16,
                                            (const float *)x->data, (float *)y->data);
     return spmv_launch<float, int32_t>(c, A, A->vals32, A->colidx, A->pipe32, (const float *)x->data,

@@ -71,11 +71,13 @@ struct gbs_mat_s {
     int32_t *tdesc_lanes[3];
     int64_t ntiles_lanes[3];
     GbsPipeCfg pipe64_lanes[3], pipe32_lanes[3];
-    // compressed column indices for the FP32 paths: col - row as int16, made
-    // with vals32 when every |col - row| <= 32767 (else NULL); their stage
-    // geometry (FP32 values, 16-bit indices) per tiling
+    // compressed column indices: col - row as int16, made on first use
+    // (rel16_state 0 = not yet, 1 = made, -1 = some |col - row| > 32767,
+    // colrel16 NULL); their stage geometry per tiling for FP32 values
+    // (pipe16) and for FP64 values (pipe64r, the one-lane tiling)
     int16_t *colrel16;
-    GbsPipeCfg pipe16, pipe16_lanes[3];
+    int rel16_state;
+    GbsPipeCfg pipe16, pipe16_lanes[3], pipe64r;
     // made from coordinate triplets: their count, the triplet indices in
     // sorted (row, column, index) order and each entry's segment of them
     int64_t coo_m;
@@ -126,6 +128,8 @@ int gbs_solve_perop(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
 int gbs_solve_cluster(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit, int norm,
                       gbs_solve_info *info);
 int gbs_mat_ensure_f32(gbs_mat A);
+// Make the compressed 16-bit column indices if the matrix allows them.
+int gbs_mat_ensure_rel16(gbs_mat A);
 // Make the tiling for 2^li lanes per row (li = 0, 1, 2) if it does not exist.
 int gbs_mat_ensure_lane_tiling(gbs_mat A, int li);
 

@@ -52,7 +52,13 @@ struct PcgCtl {
     T alpha, beta;
     T rn;        // square root of the stopping test, taken by warp 1
     int go;
-    int status;
+    int need_rr;   // this iteration's update phase sums N(r)^2 as well
+    int fallback;  // N(r)^2 is needed but was not summed: one extra pass
+    int stale;     // the last N(r)^2 is not that of the current residual
+    // the scalar recurrences, used by thread 0 only (kept in shared memory
+    // rather than in registers that every thread would reserve)
+    T rho, rr, bnorm, lbf, tol2;
+    int k, st, rr_current;
 };
 
 // Arguments of the persistent kernels.
@@ -79,6 +85,9 @@ struct PcgArgs {
     GbsPipeCfg pipe64, pipe32;
     gbs_grid_barrier *bar;
     gbs_result_dev *res;
+    // grid-wide bounds of D^-1 as bit patterns of positive doubles (max of
+    // the bits, max of the complemented bits = min), zeroed before the launch
+    unsigned long long *dbound;
     double rtol;
     double inner_rtol;
     int maxit;
@@ -130,8 +139,14 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
     const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
     const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
     // scalar state, meaningful in thread 0 only
-    T rho = T(0), rr = T(0), bnorm = T(0);
-    int k = 0, status = GBS_DIVERGED_ITS;
+    T &rho = ctl.rho, &rr = ctl.rr, &bnorm = ctl.bnorm, &lbf = ctl.lbf, &tol2 = ctl.tol2;
+    int &k = ctl.k, &status = ctl.st, &rr_current = ctl.rr_current;
+    if (threadIdx.x == 0) {
+        rho = rr = bnorm = lbf = tol2 = T(0);
+        k = 0;
+        status = GBS_DIVERGED_ITS;
+        rr_current = 1;
+    }
     // Stopping-test norm N: rr holds N(r)^2 (r.r, z.z, or r.z for the
     // natural norm), bnorm N(b).  ref_sq(b_i, i) is b_i's term of N(b)^2.
     const int norm = a.norm;
@@ -141,13 +156,23 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         return norm == GBS_NORM_PRECONDITIONED ? db * db : bi * db;
     };
 
-    // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b
+    // ---- set-up: r = b - A x, z = D^-1 r, p = z; partials r.z, r.r, b.b;
+    // the extreme entries of D^-1 (their bit patterns: D^-1 > 0, so the
+    // order of the bits is the order of the values)
     T acc[3] = {T(0), T(0), T(0)};
+    unsigned long long dmx = 0ull, dmn_c = 0ull;
+    auto dtrack = [&](T di) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)di);
+        dmx = bits > dmx ? bits : dmx;
+        dmn_c = ~bits > dmn_c ? ~bits : dmn_c;
+    };
     if (!x0_zero) {
         auto epi = [&](int64_t i, T s, T) {
             const T bi = gbs_ld(bT + i, pk);
             const T ri = bi - s;
-            const T zi = gbs_ld(dinv + i, pk) * ri;
+            const T di = gbs_ld(dinv + i, pk);
+            dtrack(di);
+            const T zi = di * ri;
             gbs_st(rT + i, ri, pk);
             gbs_st(zT + i, zi, pk);
             gbs_st(pT + i, zi, pk);
@@ -163,7 +188,9 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
     } else {
         for (int64_t i = rb + threadIdx.x; i < re; i += NT) {
             const T bi = gbs_ld(bT + i, pk);
-            const T zi = gbs_ld(dinv + i, pk) * bi;
+            const T di = gbs_ld(dinv + i, pk);
+            dtrack(di);
+            const T zi = di * bi;
             gbs_st(xT + i, T(0), pk);
             gbs_st(rT + i, bi, pk);
             gbs_st(zT + i, zi, pk);
@@ -193,8 +220,44 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         if (threadIdx.x == 0) part[2 * G + c] = sm.out[0];
     }
     if (threadIdx.x == 0) *s_next = 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long m = __shfl_xor_sync(0xffffffffu, dmx, off);
+        const unsigned long long mc = __shfl_xor_sync(0xffffffffu, dmn_c, off);
+        dmx = m > dmx ? m : dmx;
+        dmn_c = mc > dmn_c ? mc : dmn_c;
+    }
+    if ((threadIdx.x & 31) == 0 && dmx != 0ull) {
+        atomicMax(a.dbound, dmx);
+        atomicMax(a.dbound + 1, dmn_c);
+    }
     const bool skip = (a.skip_cta == c) && (*barrier_no == 0);
     if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, skip, s_flag)) return GBS_ERR_TIMEOUT;
+    // Lower bound of N(r)^2 by r.z: r.r >= r.z / max(D^-1) and
+    // ||D^-1 r||^2 >= min(D^-1) r.z (natural norm: N(r)^2 is r.z).  While
+    // lbf * r.z alone shows the stopping test fails, the update phase skips
+    // the N(r)^2 sum (one FP64 operation per row); the test itself is
+    // unchanged: it is decided on the summed N(r)^2 whenever it could pass.
+    // N(r)^2 of the current residual over the grid in an extra pass (thread
+    // 0 gets it); false if a barrier timed out
+    auto sum_nr2 = [&](T &out) -> bool {
+        T w2[1] = {T(0)};
+        for (int64_t i = rb + threadIdx.x; i < re; i += NT) {
+            const T ri = gbs_ld(rT + i, pk);
+            const T w = norm == GBS_NORM_PRECONDITIONED ? gbs_ld(dinv + i, pk) * ri : ri;
+            w2[0] += w * w;
+        }
+        gbs_block_sum_staged<T, 1, NT>(w2, stage, sm.out);
+        if (threadIdx.x == 0) part[5 * G + c] = sm.out[0];
+        if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag)) return false;
+        if (warp == 0) {
+            T g1[1];
+            gbs_warp_grid_sum<T, 1>(part + 5 * G, G, G, g1);
+            if (threadIdx.x == 0) out = g1[0];
+        }
+        __syncthreads();
+        return true;
+    };
     if (warp == 0) {
         T g3[3];
         gbs_warp_grid_sum<T, 3>(part, G, G, g3);
@@ -202,6 +265,11 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             rho = g3[0];
             rr = norm == GBS_NORM_NATURAL ? g3[0] : g3[1];
             bnorm = sqrt(g3[2]);
+            const T dmax = (T)__longlong_as_double((long long)__ldcg(a.dbound));
+            const T dmin = (T)__longlong_as_double((long long)~__ldcg(a.dbound + 1));
+            lbf = norm == GBS_NORM_UNPRECONDITIONED ? T(1) / dmax
+                  : norm == GBS_NORM_PRECONDITIONED ? dmin : T(1);
+            tol2 = (rtol * bnorm) * (rtol * bnorm);
             const int s = pcg_check<T>(sqrt(rr), rho, rtol * bnorm, 0, maxit);
             ctl.go = s == -100;
             if (!ctl.go) status = s;
@@ -221,7 +289,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             pq[0] += p_i * s;
         };
         if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, pT, wsm, wq,
-                              parity, cfg, ps, pk, a.timeout_ns, epi) &&
+                                  parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         gbs_block_sum_staged<T, 1, NT>(pq, stage, sm.out);
@@ -239,15 +307,30 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 else if (pi[0] <= T(0)) status = GBS_ERR_INDEFINITE;
                 ctl.go = !(isnan(pi[0]) || pi[0] <= T(0));
                 ctl.alpha = rho / pi[0];
+                // sum N(r)^2 in this update unless the current r.z is well
+                // clear of the test (a margin of 16 for one step's drop) and
+                // the iteration limit is not next
+                ctl.need_rr = norm != GBS_NORM_NATURAL &&
+                              (k + 1 >= maxit || !(lbf * rho > T(16) * tol2));
+                ctl.stale = !rr_current;
             }
         }
         __syncthreads();
-        if (!ctl.go) break;
+        if (!ctl.go) {
+            // breakdown: report N(r) of the current residual
+            if (ctl.stale) {
+                T t = T(0);
+                if (!sum_nr2(t)) return GBS_ERR_TIMEOUT;
+                if (threadIdx.x == 0) rr = t;
+            }
+            break;
+        }
         const T alpha = ctl.alpha;
 
         // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
         // (UNR rows per thread per trip: all 5 UNR loads are issued before
         // the first use)
+        const bool need_rr = ctl.need_rr != 0;
         T u[2] = {T(0), T(0)};
         for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
             T pv[UNR], xv[UNR], rv[UNR], qv[UNR], dv[UNR];
@@ -271,15 +354,23 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                     gbs_st(rT + i, rn_, pk);
                     gbs_st(zT + i, zn_, pk);
                     u[0] += rn_ * zn_;
-                    const T w = norm == GBS_NORM_PRECONDITIONED ? zn_ : rn_;
-                    u[1] += w * w;
+                    if (need_rr) {
+                        const T w = norm == GBS_NORM_PRECONDITIONED ? zn_ : rn_;
+                        u[1] += w * w;
+                    }
                 }
             }
         }
-        gbs_block_sum_staged<T, 2, NT>(u, stage, sm.out);
-        if (threadIdx.x == 0) {
-            part[4 * G + c] = sm.out[0];
-            part[5 * G + c] = sm.out[1];
+        if (need_rr) {
+            gbs_block_sum_staged<T, 2, NT>(u, stage, sm.out);
+            if (threadIdx.x == 0) {
+                part[4 * G + c] = sm.out[0];
+                part[5 * G + c] = sm.out[1];
+            }
+        } else {
+            const T u0[1] = {u[0]};
+            gbs_block_sum_staged<T, 1, NT>(u0, stage, sm.out);
+            if (threadIdx.x == 0) part[4 * G + c] = sm.out[0];
         }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
@@ -288,17 +379,46 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         // square root, on different SM partitions: each is a long chain of
         // dependent FP64 steps
         T g2[2] = {T(0), T(0)};
-        if (warp < 2) {
-            gbs_warp_grid_sum<T, 2>(part + 4 * G, G, G, g2);
-            if (threadIdx.x == 32) ctl.rn = sqrt(norm == GBS_NORM_NATURAL ? g2[0] : g2[1]);
-            if (threadIdx.x == 0) ctl.beta = g2[0] / rho;
+        if (need_rr || norm == GBS_NORM_NATURAL) {
+            if (warp < 2) {
+                gbs_warp_grid_sum<T, 2>(part + 4 * G, G, G, g2);
+                if (threadIdx.x == 32) ctl.rn = sqrt(norm == GBS_NORM_NATURAL ? g2[0] : g2[1]);
+                if (threadIdx.x == 0) ctl.beta = g2[0] / rho;
+            }
+        } else if (warp == 0) {
+            T g1[1];
+            gbs_warp_grid_sum<T, 1>(part + 4 * G, G, G, g1);
+            g2[0] = g1[0];
+            if (threadIdx.x == 0) {
+                ctl.beta = g1[0] / rho;
+                // N(r)^2 was not summed: go on only if r.z proves the test
+                // fails (with a margin of 2 for the rounding of both sums);
+                // otherwise sum it in an extra pass below
+                ctl.fallback = !(g1[0] >= T(0) && lbf * g1[0] > T(2) * tol2);
+            }
         }
         __syncthreads();
+        if (!need_rr && norm != GBS_NORM_NATURAL && ctl.fallback) {
+            // extra pass (rare: the one-step prediction above missed)
+            T t = T(0);
+            if (!sum_nr2(t)) return GBS_ERR_TIMEOUT;
+            if (threadIdx.x == 0) {
+                g2[1] = t;
+                ctl.rn = sqrt(t);
+            }
+        }
         if (threadIdx.x == 0) {
             ++k;
             const T rho_new = g2[0];
-            rr = norm == GBS_NORM_NATURAL ? g2[0] : g2[1];
-            if (rho_new < T(0)) {
+            const bool have_rr = need_rr || norm == GBS_NORM_NATURAL || ctl.fallback;
+            rr_current = have_rr;
+            if (have_rr) rr = norm == GBS_NORM_NATURAL ? g2[0] : g2[1];
+            if (!have_rr) {
+                // r.z proved the test fails; the limit was not reached
+                // (need_rr is set for the last allowed iteration)
+                rho = rho_new;
+                ctl.go = 1;
+            } else if (rho_new < T(0)) {
                 status = GBS_ERR_INDEFINITE;
                 ctl.go = 0;
             } else {
@@ -332,16 +452,17 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
             return GBS_ERR_TIMEOUT;
     }
-    *iters = k;
-    *rnorm_out = sqrt(rr);
-    *bnorm_out = bnorm;
-    // the status decides the caller's control flow in every thread: hand
-    // thread 0's value to the whole CTA so that all threads take one path
-    if (threadIdx.x == 0) ctl.status = status;
+    // the status decides the caller's control flow in every thread: every
+    // thread takes thread 0's value (kept in shared memory) after a barrier
     __syncthreads();
-    status = ctl.status;
+    if (threadIdx.x == 0) {
+        *iters = k;
+        *rnorm_out = sqrt(rr);
+        *bnorm_out = bnorm;
+    }
+    const int st_all = status;
     __syncthreads();
-    return status;
+    return st_all;
 }
 
 // NT threads per CTA (one CTA per SM), WB bytes of copy ring per warp, UNR
@@ -349,7 +470,9 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
 // warps, 64 registers, 6.4 KB rings) the SpMV hides its gathers' latency
 // better; the staged CTA sums then live in dynamic shared memory after the
 // rings.
-template <int NT, int WB, int UNR>
+// IX: the column indices the SpMV streams (int32, or the compressed 16-bit
+// col - row when the matrix has them).
+template <int NT, int WB, int UNR, typename IX>
 __global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
 {
     constexpr bool WIDE = NT > GBS_PBLOCK;
@@ -368,8 +491,10 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
     int iters = 0, barrier_no = 0;
     double rn = 0.0, bn = 0.0;
     double *stage = WIDE ? reinterpret_cast<double *>(smem + (size_t)WB * (NT / 32)) : s_stage;
-    int st = pcg_loop<double, int32_t, NT, UNR>(
-        a, a.colidx, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol, a.maxit,
+    const IX *cols = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
+                                     : (const IX *)(const void *)a.colidx;
+    int st = pcg_loop<double, IX, NT, UNR>(
+        a, cols, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol, a.maxit,
         a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, smem + (size_t)warp * WB, s_q[warp],
         parity, &s_next, a.pipe64, sm, stage, ctl, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -529,6 +654,30 @@ int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0,
     return g < 1 ? 1 : (int)g;
 }
 
+// Algorithmic bytes of a persistent solve (gbs_solve_info.model_bytes): a
+// nonzero streams its value and its column index (ib = 4 or 2 bytes); every
+// vector entry is counted once per pass that reads or writes it.
+//  FP64: the set-up pass (r = b - A x: matrix, row pointers, x gather, b
+//  and D^-1 read, r, z, p written) and per iteration the S phase (matrix,
+//  row pointers, p gather, q written: 4n + 16n), U (x, p, r, q, D^-1 read,
+//  x, r, z written: 64n) and P (z, p read, p written: 24n), i.e.
+//  (8 + ib) nnz + 108 n per iteration.
+//  Mixed: per refinement step the FP64 residual (12 nnz with 32-bit
+//  indices + 4n row pointers + 8n gather + 8n b read + 8n r written), the
+//  scaling to FP32 (8n read, 4n written) and the FP64 update (16n x, 4n
+//  FP32 solution); per inner solve its set-up (b32, D^-1 read, x, r, z, p
+//  written: 24n) and per inner iteration (4 + ib) nnz + 56 n.
+double persistent_model_bytes(gbs_mat A, bool mixed, int ib, const gbs_solve_info &r)
+{
+    const double n = (double)A->n, nnz = (double)A->nnz;
+    if (!mixed)
+        return ((8.0 + ib) * nnz + 52.0 * n + 4.0) + (double)r.iters * ((8.0 + ib) * nnz + 108.0 * n);
+    const double outer = (double)r.outer_iters + 1.0;   // residual passes
+    const double inner_solves = (double)r.outer_iters;
+    return outer * (12.0 * nnz + 36.0 * n) + inner_solves * (12.0 * n + 20.0 * n + 24.0 * n) +
+           (double)r.iters * ((4.0 + ib) * nnz + 56.0 * n);
+}
+
 // Launch a persistent kernel and read its result record (one host
 // synchronisation per solve).
 int launch_persistent(gbs_ctx c, const void *fn, int G, PcgArgs &a, gbs_solve_info *info,
@@ -587,25 +736,32 @@ struct Fp64Shape {
     GbsPipeCfg cfg;
 };
 
-Fp64Shape fp64_shape(gbs_mat A)
+// rel: stream the compressed 16-bit column indices (the matrix has them).
+template <typename IX>
+Fp64Shape fp64_shape_ix(gbs_mat A, const GbsPipeCfg &cfg)
 {
     constexpr int kSmallRing = GBS_WARP_STAGE_BYTES / 2;
     constexpr int kWide = 2 * GBS_PBLOCK;
     Fp64Shape s;
-    s.cfg = A->pipe64;
-    const int stages = kSmallRing / A->pipe64.sbytes;
+    s.cfg = cfg;
+    const int stages = kSmallRing / cfg.sbytes;
     const bool large = A->ntiles >= (int64_t)A->ctx->num_sms * (kWide / 32);
     if (stages >= 2 && large) {
         s.cfg.stages = stages < GBS_MAX_STAGES ? stages : GBS_MAX_STAGES;
-        s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2>;
+        s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2, IX>;
         s.smem = (size_t)kSmallRing * (kWide / 32) + 2 * kWide * sizeof(double);
         s.nt = kWide;
     } else {
-        s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4>;
+        s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4, IX>;
         s.smem = kPersistSmem;
         s.nt = GBS_PBLOCK;
     }
     return s;
+}
+
+Fp64Shape fp64_shape(gbs_mat A, bool rel)
+{
+    return rel ? fp64_shape_ix<int16_t>(A, A->pipe64r) : fp64_shape_ix<int32_t>(A, A->pipe64);
 }
 
 }  // namespace
@@ -619,8 +775,12 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         int st = gbs_mat_ensure_f32(A);
         if (st) return st;
     }
-    const bool rel16 = mixed && A->colrel16;
-    const Fp64Shape shape = fp64_shape(A);
+    if (!mixed && !o->no_rel16) {
+        int st = gbs_mat_ensure_rel16(A);
+        if (st) return st;
+    }
+    const bool rel16 = A->colrel16 && !o->no_rel16;
+    const Fp64Shape shape = fp64_shape(A, rel16);
     const void *fn = !mixed ? shape.fn
                      : rel16 ? (const void *)k_pcg_mixed<int16_t> : (const void *)k_pcg_mixed<int32_t>;
     const size_t smem = mixed ? kPersistSmem : shape.smem;
@@ -631,7 +791,7 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     const size_t vec64 = align256(sizeof(double) * (size_t)n);
     const size_t vec32 = align256(sizeof(float) * (size_t)n);
     const size_t part = align256(sizeof(double) * kSlots * (size_t)G);
-    const size_t head = 512;  // barrier + result
+    const size_t head = 512;  // barrier (offset 0), D^-1 bounds (128), result (256)
     const size_t total = head + 2 * part + (mixed ? vec64 + 6 * vec32 : 4 * vec64);
     void *scr = nullptr;
     int st = gbs_ctx_reserve(c, total, &scr);
@@ -640,6 +800,7 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     PcgArgs a;
     memset(&a, 0, sizeof(a));
     a.bar = (gbs_grid_barrier *)base;
+    a.dbound = (unsigned long long *)(base + 128);
     a.res = (gbs_result_dev *)(base + 256);
     a.part64 = (double *)(base + head);
     a.part32 = (float *)(base + head + part);
@@ -659,9 +820,9 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         a.q = (double *)v; v += vec64;
     }
     fill_matrix_args(a, A);
-    if (rel16) {   // the FP32 inner loop streams 16-bit column indices
+    if (rel16) {   // the SpMV (FP64, or the FP32 inner loop) streams 16-bit column indices
         a.colrel16 = A->colrel16;
-        a.pipe32 = A->pipe16;
+        if (mixed) a.pipe32 = A->pipe16;
     }
     a.b = (const double *)b->data;
     a.x = (double *)x->data;
@@ -675,7 +836,9 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
     a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
     if (!mixed) a.pipe64 = shape.cfg;
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
-    return launch_persistent(c, fn, G, a, info, smem, nt);
+    st = launch_persistent(c, fn, G, a, info, smem, nt);
+    info->model_bytes = persistent_model_bytes(A, mixed, rel16 ? 2 : 4, *info);
+    return st;
 }
 
 // ----------------------------------------------------------------------
@@ -1051,7 +1214,7 @@ namespace {
 
 constexpr int64_t kNoAllocMaxRows = GBS_NOALLOC_MAX_ROWS;
 constexpr int kNoAllocMaxCtas = 2048;
-constexpr size_t kNoAllocHead = 512;  // barrier (offset 0) + result record (offset 256)
+constexpr size_t kNoAllocHead = 512;  // barrier (offset 0), D^-1 bounds (128), result record (256)
 constexpr size_t kNoAllocPart = sizeof(double) * kSlots * kNoAllocMaxCtas;
 constexpr size_t kNoAllocVec = sizeof(double) * kNoAllocMaxRows;
 constexpr size_t kNoAllocBytes = kNoAllocHead + kNoAllocPart + 4 * kNoAllocVec;
@@ -1102,7 +1265,10 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     void *scr = nullptr;
     int st = noalloc_address(c->device, &scr);
     if (st) return st;
-    const Fp64Shape shape = fp64_shape(A);
+    // the compressed column indices only if the matrix already has them
+    // (making them would allocate)
+    const bool rel16 = A->colrel16 && !c->opts.no_rel16;
+    const Fp64Shape shape = fp64_shape(A, rel16);
     int G = coop_grid(c, shape.fn, A->ntiles, c->opts.persistent_ctas, shape.smem, shape.nt);
     if (G < 0) return GBS_ERR_CUDA;
     if (G > kNoAllocMaxCtas) G = kNoAllocMaxCtas;
@@ -1110,6 +1276,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     PcgArgs a;
     memset(&a, 0, sizeof(a));
     a.bar = (gbs_grid_barrier *)base;
+    a.dbound = (unsigned long long *)(base + 128);
     a.res = (gbs_result_dev *)(base + 256);
     a.part64 = (double *)(base + kNoAllocHead);
     char *v = base + kNoAllocHead + kNoAllocPart;
@@ -1118,6 +1285,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     a.p = (double *)(v + 2 * kNoAllocVec);
     a.q = (double *)(v + 3 * kNoAllocVec);
     fill_matrix_args(a, A);
+    if (rel16) a.colrel16 = A->colrel16;
     a.b = b;
     a.x = x;
     a.rtol = rtol;
@@ -1131,6 +1299,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     a.pipe64 = shape.cfg;
     st = launch_persistent(c, shape.fn, G, a, info, shape.smem, shape.nt);
     if (st == GBS_ERR_CUDA) info->status = st;
+    else info->model_bytes = persistent_model_bytes(A, false, rel16 ? 2 : 4, *info);
     c->last = *info;
     return st;
 }

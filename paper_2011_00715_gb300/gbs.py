@@ -65,7 +65,7 @@ class gbs_opts(ctypes.Structure):
                 ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
                 ("persistent_ctas", ctypes.c_int), ("norm_type", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("no_rel16", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class gbs_solve_info(ctypes.Structure):

@@ -41,7 +41,9 @@ def test_roofline_models():
     import bench
     n, nnz = 2_097_152, 14_581_760                   # the 128^3 7-point Laplacian
     assert bench.bytes_per_iter_fp64(n, nnz) == 12 * nnz + 108 * n
-    assert bench.ops_per_iter_fp64(n, nnz) == nnz + 7 * n
+    assert bench.bytes_per_iter_fp64(n, nnz, 2) == 10 * nnz + 108 * n
+    assert bench.stencil_index_bytes(128) == 2 and bench.stencil_index_bytes(464) == 4
+    assert bench.ops_per_iter_fp64(n, nnz) == nnz + 6 * n
     assert bench.FP64_NOMINAL_GOPS == 625.0          # 1.25 TFLOP/s in fused multiply-adds
     cfg = bench.config_for(1)
     assert "128^3" in cfg["workload"] and cfg["parallelism"] == "single GPU"

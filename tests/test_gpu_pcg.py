@@ -280,3 +280,23 @@ def test_c3_full_size_mixed_vs_fp64(S, orc):
     tol = solution_tol(orc, A, b, xmx, ref["x"], lmin)
     record("c3_full_size_mixed", "rel_err_vs_oracle", rel(xmx, ref["x"]), tol)
     assert rel(xmx, ref["x"]) <= tol
+
+
+@pytest.mark.parametrize("no_rel16", [0, 1])
+@pytest.mark.parametrize("case", ["lap3d7_56", "var27_22", "far_chain_40000"])
+def test_fp64_index_widths_match_oracle(S, orc, case, no_rel16):
+    """The persistent FP64 kernel on 16-bit column offsets (default, where
+    every |col - row| fits) and on the 32-bit indices (no_rel16, and the
+    automatic fallback of a matrix with a coupling 39,999 rows away): the
+    same 1e-8 bar against the oracle's FP64 solution."""
+    from test_gpu_spmv import far_coupled_chain
+    A = {"lap3d7_56": lambda: I.lap3d7(56), "var27_22": lambda: I.var27(22, seed=3),
+         "far_chain_40000": lambda: far_coupled_chain(40000, 5)}[case]()
+    b = orc.spmv(A, I.xstar(A.n, 2))
+    ref = orc.pcg(A, b, 1e-10, 50000)
+    info, x = solve(S, A, b, 1e-10, 50000, algorithm=ALGS["persistent"], no_rel16=no_rel16)
+    assert info.status == gbs.GBS_OK and ref["status"] == 0
+    assert abs(info.iters - ref["iters"]) <= 2
+    record(f"index_widths[{case},no_rel16={no_rel16}]", "rel_err_vs_oracle", rel(x, ref["x"]), 1e-8)
+    assert rel(x, ref["x"]) <= 1e-8
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)

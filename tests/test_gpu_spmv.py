@@ -240,3 +240,37 @@ def test_fp32_paths_with_and_without_compressed_indices(S, orc, n):
     xs = S.host(xt)
     assert np.linalg.norm(b - orc.spmv(A, xs)) <= 1e-10 * np.linalg.norm(b)
     gbs.gbs_mat_destroy(h)
+
+
+@pytest.mark.parametrize("n", [30000, 40000])
+def test_fp64_matmult_both_index_widths(S, orc, n):
+    """FP64 MatMult streams 16-bit offsets col - row wherever they fit
+    (n = 30000) and falls back to the 32-bit indices otherwise (n = 40000):
+    bitwise the oracle's product on exact inputs either way, and bitwise the
+    same as the 32-bit path (no_rel16) on any input, since the arithmetic
+    and its order do not depend on the index width."""
+    from gpu_util import Session
+    A = far_coupled_chain(n, 5)
+    xe = (I.counter_u64(9, 1, np.arange(n)) % np.uint64(17)).astype(np.float64) - 8.0
+    Ae = I.CSR(n, A.rowptr, A.colidx, np.round(A.vals * 8.0) / 8.0)
+    assert np.array_equal(run(S, Ae, xe), orc.spmv(Ae, xe))
+    S32 = Session(gbs.gbs_opts_default(no_rel16=1))
+    x = I.uniform_pm1(8, 1, n)
+    assert np.array_equal(run(S, A, x), run(S32, A, x))
+    assert np.array_equal(run(S32, Ae, xe), orc.spmv(Ae, xe))
+    gbs.gbs_ctx_destroy(S32.ctx)
+
+
+def test_fp64_matmult_index_widths_on_stencils(S, orc):
+    """The 7-point and 27-point operators (every offset fits 16 bits): the
+    16-bit and 32-bit FP64 MatMult agree bitwise, and both meet the 1e-13
+    bound against the oracle."""
+    from gpu_util import Session
+    S32 = Session(gbs.gbs_opts_default(no_rel16=1))
+    for A in (I.lap3d7(40), I.var27(22, seed=3)):
+        x = I.uniform_pm1(4, 2, A.n)
+        y16, y32 = run(S, A, x), run(S32, A, x)
+        assert np.array_equal(y16, y32)
+        ref = orc.spmv(A, x)
+        assert np.linalg.norm(y16 - ref) <= 1e-13 * np.linalg.norm(ref)
+    gbs.gbs_ctx_destroy(S32.ctx)
