@@ -68,7 +68,7 @@ enum { MODE_OUTER = 0, MODE_INNER = 1 };
 // vector load.
 struct BSys {
     const int32_t *rowptr, *colidx, *tdesc;   // tdesc: {row start, nonzero start} per warp tile
-    const int16_t *colrel16;                  // col - row, for FP32 INNER tiles (may be NULL)
+    const int16_t *colrel16;                  // col - row, for INNER tiles (may be NULL)
     const double *vals, *dinv;
     const float *vals32, *dinv32;
     const double *b;    // n x kp
@@ -132,10 +132,11 @@ struct BArgs {
     double *cpartS, *cpartU;   // chunk * 16: per-chunk sums
     int *cntS, *cntU;          // per chunk: units arrived (zero between phases)
     int *sysS, *sysU;          // per active system: chunks arrived
-    int *claim;                // 3 per global iteration of the quantum: next unclaimed unit of S, U, P
+    int *claim;                // next unclaimed unit of S, U, P: 4 rotating sets of 3
+    int *nfin;                 // active systems finished during the launch
     gbs_grid_barrier *bar;
     GbsPipeCfg cfg;     // stage geometry covering every active system's tiles
-    int quantum;
+    int quantum;        // global iterations at most (even)
     int iter0;          // parity of the global iteration count at launch
     double inner_rtol;
     int outer_maxit;
@@ -524,7 +525,10 @@ __device__ __noinline__ void s_finish_outer(const BArgs &a, int slot, double rr,
         P.run = m;
         P.upd = m;
         a.dyn[slot].osteps += 1;
-        if (!m) a.dyn[slot].finished = 1;
+        if (!m) {
+            a.dyn[slot].finished = 1;
+            atomicAdd(a.nfin, 1);
+        }
     }
 }
 
@@ -552,7 +556,10 @@ __device__ __noinline__ void s_finish_inner(const BArgs &a, int slot, TI pq)
     if (lane == 0 && m) {
         P.upd = upd & ~m;
         P.run &= ~m;
-        if (!P.run) a.dyn[slot].finished = 1;
+        if (!P.run) {
+            a.dyn[slot].finished = 1;
+            atomicAdd(a.nfin, 1);
+        }
     }
 }
 
@@ -612,8 +619,12 @@ __device__ __noinline__ void u_finish_inner(const BArgs &a, int slot, int nxt, T
         P.upd = mw;
         a.dyn[slot].isteps += 1;
         // refinement once every running column's inner solve has stopped
-        if (!run) a.dyn[slot].finished = 1;
-        else a.dyn[slot].mode[nxt] = mw ? MODE_INNER : MODE_OUTER;
+        if (!run) {
+            a.dyn[slot].finished = 1;
+            atomicAdd(a.nfin, 1);
+        } else {
+            a.dyn[slot].mode[nxt] = mw ? MODE_INNER : MODE_OUTER;
+        }
     }
 }
 
@@ -689,6 +700,23 @@ __device__ __forceinline__ bool s_unit(const BArgs &a, BWarpQ &q, unsigned char 
     return true;
 }
 
+// Active index of the system holding unit u: the last i with cum[i] <= u
+// (cum: non-decreasing prefix sums of the active systems' units, n + 1
+// entries), searched from i0 on; a warp's units only grow, so it keeps its
+// last index.  One probe when u is still in system i0, else a binary search
+// (late in a long launch most systems have finished and are passed over).
+__device__ __forceinline__ int find_sys(const int *cum, int i0, int n, int u)
+{
+    if (__ldg(cum + i0 + 1) > u) return i0;
+    int lo = i0 + 1, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cum + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // A unit is `tg` consecutive warp tiles of one system.  Lane 0 of each warp
 // claims the next unit of [gb, ge) from the counter *next (shared by the
 // whole grid, so the work balances across SMs), keeps the next tile
@@ -732,7 +760,7 @@ __device__ bool phase_s(const BArgs &a, int cur, int gb, int ge, int *next, unsi
                 p_unit = -1;
                 return;
             }
-            while (__ldg(a.scum + cai + 1) <= u) ++cai;
+            cai = find_sys(a.scum, cai, a.nact, u);
             const int slot = __ldg(a.act + cai);
             const BSysDyn &D = a.dyn[slot];
             if (D.finished) {   // skip the rest of a finished system
@@ -1017,7 +1045,7 @@ __device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int g
         const int u = __shfl_sync(0xffffffffu, pend, 0);
         if (u >= ge) break;
         if (lane == 0) pend = gb + atomicAdd(next, 1);
-        while (__ldg(a.ucum + cai + 1) <= u) ++cai;
+        cai = find_sys(a.ucum, cai, a.nact, u);
         const int slot = __ldg(a.act + cai);
         const BSysDyn &D = a.dyn[slot];
         // nothing to do for a finished system, nor in P after an OUTER step
@@ -1055,16 +1083,30 @@ __global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
     const uint64_t ps = gbs_policy_stream();
     uint32_t parity = 0;
     int bno = 0;
+    // The launch ends after `quantum` global iterations, or earlier once
+    // every active system has finished.  Systems finish only in the S and U
+    // phases (their scalar steps), so the count of finished systems read
+    // between the U and P barriers is the same in every CTA, and all CTAs
+    // leave after the same P barrier.  The claim counters rotate over 4
+    // sets: the set of iteration q + 2 is zeroed in iteration q, two
+    // barriers after its last use (all 4 are zeroed before the launch).
+    __shared__ int s_done;
     for (int q = 0; q < a.quantum; ++q) {
         const int cur = (a.iter0 + q) & 1, nxt = cur ^ 1;
-        int *ctr = a.claim + 3 * q;
+        int *ctr = a.claim + 3 * (q & 3);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            int *z = a.claim + 3 * ((q + 2) & 3);
+            z[0] = z[1] = z[2] = 0;
+        }
         if (!phase_s<TI>(a, cur, 0, a.nsu, ctr, wsm, s_q[warp], parity, ps) && lane == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
         phase_up<TI, true>(a, cur, nxt, 0, a.nuu, ctr + 1);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
+        if (threadIdx.x == 0) s_done = gbs_ld_relaxed_int(a.nfin) >= a.nact;
         phase_up<TI, false>(a, cur, nxt, 0, a.nuu, ctr + 2);
         if (!gbs_grid_sync(a.bar, a.timeout_ns, bno++, false, &s_flag)) break;
+        if (s_done) break;
     }
 }
 
@@ -1080,7 +1122,41 @@ __global__ void k_interleave(int64_t n, int k, int kp, const double *src, double
     }
 }
 
+// Many interleavings in one launch: job j moves n * kp entries (dir 0:
+// column-major src -> interleaved dst; dir 1: back, padding dropped);
+// off[j] is the first flat index of job j, off[njobs] the total.
+struct IlvJob {
+    const double *src;
+    double *dst;
+    int64_t n, off;
+    int k, kp;
+};
+
+__global__ void k_interleave_many(const IlvJob *jobs, int njobs, int64_t total, int dir)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = njobs - 1;   // the job holding e: last j with off[j] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].off <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const IlvJob J = jobs[lo];
+        const int64_t le = e - J.off, i = le / J.kp, cc = le % J.kp;
+        if (dir == 0) J.dst[le] = cc < J.k ? J.src[cc * J.n + i] : 0.0;
+        else if (cc < J.k) J.dst[cc * J.n + i] = J.src[le];
+    }
+}
+
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Global iterations per launch of gbs_ksp_solve_cg_batched.  Long quanta
+// keep the launch count low; a single launch to the end was measured
+// slower (512 systems: 2.82 against 2.35 s) because the units of finished
+// systems are skipped one claim at a time until the host compacts the
+// active list, which it does between launches.
+constexpr int kBatchQuantum = 384;
 
 // Column stride of a system with k right-hand sides: k rounded up to a power of two.
 int padded_k(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
@@ -1136,6 +1212,15 @@ struct Engine {
     size_t cnt_bytes = 0;
     BArgs g_args;
     int G = 0;
+    // slots added since the last launch: their records (staged on the host
+    // in h_sys / h_col / h_dyn) and their right-hand sides and initial
+    // guesses go to the device together, before the next launch
+    std::vector<BSys> h_sys;
+    std::vector<BCol> h_col;
+    std::vector<int> pending;
+    std::vector<IlvJob> ilv_in;
+    IlvJob *d_jobs = nullptr;
+    size_t cap_jobs = 0;
 };
 
 void engine_free_graph(Engine &E)
@@ -1157,6 +1242,8 @@ int engine_init(Engine &E, gbs_ctx c, int nslots, int fp64, int quantum)
     E.nslots = nslots;
     E.slots.assign(nslots, SlotHost());
     E.h_dyn.assign(nslots, BSysDyn());
+    E.h_sys.assign(nslots, BSys());
+    E.h_col.assign((size_t)nslots * GBS_KMAX, BCol());
     const size_t ns = (size_t)std::max(nslots, 1);
     GBS_CUDA_TRY(cudaMalloc(&E.d_sys, sizeof(BSys) * ns));
     GBS_CUDA_TRY(cudaMalloc(&E.d_col, sizeof(BCol) * ns * GBS_KMAX));
@@ -1187,6 +1274,7 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_cpartS);
     cudaFree(E.d_cpartU);
     cudaFree(E.d_bar);
+    cudaFree(E.d_jobs);
     E = Engine();
 }
 
@@ -1213,7 +1301,7 @@ double slot_model_bytes(const Engine &E, int slot)
     if (!H.used || !H.A) return 0.0;
     const BSysDyn &D = E.h_dyn[slot];
     const double n = (double)H.A->n, nnz = (double)H.A->nnz, kp = H.kp, tsz = E.fp64 ? 8 : 4;
-    const double isz = (!E.fp64 && H.A->colrel16) ? 2 : 4;   // index bytes of INNER tiles
+    const double isz = H.A->colrel16 ? 2 : 4;   // index bytes of INNER tiles
     const double inner = (tsz + isz) * nnz + 4 * (n + 1) + tsz * n * (8 * kp + 2);
     const double outer = 12 * nnz + 4 * (n + 1) + 32 * n * kp + tsz * n * (3 * kp + 1);
     return D.isteps * inner + D.osteps * outer;
@@ -1248,8 +1336,8 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     }
     const int64_t ntiles = A->ntiles_lanes[li];
     const size_t nk = (size_t)A->n * kp, tsz = E.fp64 ? 8 : 4;
-    if (!E.fp64) {
-        int st = gbs_mat_ensure_f32(A);
+    {   // FP32 values (mixed) and the 16-bit column offsets of the INNER tiles
+        int st = E.fp64 ? gbs_mat_ensure_rel16(A) : gbs_mat_ensure_f32(A);
         if (st) return st;
     }
     const size_t bytes = 3 * a256(nk * 8) + 4 * a256(nk * tsz);
@@ -1281,7 +1369,7 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     S.rowptr = A->rowptr;
     S.colidx = A->colidx;
     S.tdesc = A->tdesc_lanes[li];
-    S.colrel16 = E.fp64 ? nullptr : A->colrel16;
+    S.colrel16 = A->colrel16;
     S.vals = A->vals;
     S.vals32 = A->vals32;
     S.dinv = A->dinv;
@@ -1304,12 +1392,9 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     S.usub = usub;
     S.rtol = rtol;
     S.maxit = maxit;
-    if (nk) {
-        const int g = (int)std::min<int64_t>((int64_t)(nk + 255) / 256, (int64_t)c->num_sms * 8);
-        k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, kp, b, (double *)S.b, 0);
-        if (x0) k_interleave<<<g, 256, 0, c->stream>>>(A->n, k, kp, x0, S.x, 0);
-        gbs_count_launch(c, x0 ? 2 : 1);
-        GBS_CUDA_TRY(cudaGetLastError());
+    if (nk) {   // interleaved at the next flush, with every other added slot's
+        E.ilv_in.push_back(IlvJob{b, (double *)S.b, A->n, 0, k, kp});
+        if (x0) E.ilv_in.push_back(IlvJob{x0, S.x, A->n, 0, k, kp});
     }
     BSysDyn D;
     memset(&D, 0, sizeof(D));
@@ -1326,14 +1411,56 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     }
     H.finished = bad;
     E.h_dyn[slot] = D;
-    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_sys + slot, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
-    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_col + (size_t)slot * GBS_KMAX, C, sizeof(C),
-                                 cudaMemcpyHostToDevice, c->stream));
-    GBS_CUDA_TRY(cudaMemsetAsync(E.d_ph + slot, 0, sizeof(BPh), c->stream));
-    GBS_CUDA_TRY(cudaMemcpyAsync(E.d_dyn + slot, &D, sizeof(D), cudaMemcpyHostToDevice, c->stream));
-    // the host arrays above are copied from pageable memory: make sure they
-    // are consumed before they go out of scope
-    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    E.h_sys[slot] = S;
+    memcpy(&E.h_col[(size_t)slot * GBS_KMAX], C, sizeof(C));
+    E.pending.push_back(slot);
+    return GBS_OK;
+}
+
+// Send the records of the slots added since the last flush to the device
+// (one copy per run of consecutive slots) and interleave all their
+// right-hand sides and initial guesses in one launch.
+int engine_flush(Engine &E)
+{
+    gbs_ctx c = E.c;
+    if (!E.pending.empty()) {
+        std::vector<int> ps = E.pending;
+        std::sort(ps.begin(), ps.end());
+        for (size_t i = 0; i < ps.size();) {
+            size_t j = i + 1;
+            while (j < ps.size() && ps[j] == ps[j - 1] + 1) ++j;
+            const int s0 = ps[i], cnt = ps[j - 1] - s0 + 1;
+            GBS_CUDA_TRY(cudaMemcpyAsync(E.d_sys + s0, &E.h_sys[s0], sizeof(BSys) * cnt,
+                                         cudaMemcpyHostToDevice, c->stream));
+            GBS_CUDA_TRY(cudaMemcpyAsync(E.d_col + (size_t)s0 * GBS_KMAX,
+                                         &E.h_col[(size_t)s0 * GBS_KMAX],
+                                         sizeof(BCol) * GBS_KMAX * cnt, cudaMemcpyHostToDevice,
+                                         c->stream));
+            GBS_CUDA_TRY(cudaMemsetAsync(E.d_ph + s0, 0, sizeof(BPh) * cnt, c->stream));
+            GBS_CUDA_TRY(cudaMemcpyAsync(E.d_dyn + s0, &E.h_dyn[s0], sizeof(BSysDyn) * cnt,
+                                         cudaMemcpyHostToDevice, c->stream));
+            i = j;
+        }
+        E.pending.clear();
+    }
+    if (!E.ilv_in.empty()) {
+        int64_t tot = 0;
+        for (IlvJob &J : E.ilv_in) {
+            J.off = tot;
+            tot += J.n * J.kp;
+        }
+        int st = ensure_cap(E.d_jobs, E.cap_jobs, E.ilv_in.size());
+        if (st) return st;
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_jobs, E.ilv_in.data(), sizeof(IlvJob) * E.ilv_in.size(),
+                                     cudaMemcpyHostToDevice, c->stream));
+        const int g = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 8);
+        k_interleave_many<<<g, 256, 0, c->stream>>>(E.d_jobs, (int)E.ilv_in.size(), tot, 0);
+        gbs_count_launch(c);
+        GBS_CUDA_TRY(cudaGetLastError());
+        // the job list is host memory the next flush rewrites
+        GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        E.ilv_in.clear();
+    }
     return GBS_OK;
 }
 
@@ -1343,6 +1470,10 @@ int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters,
                    int *status)
 {
     gbs_ctx c = E.c;
+    {
+        const int st = engine_flush(E);
+        if (st) return st;
+    }
     SlotHost &H = E.slots[slot];
     BCol C[GBS_KMAX];
     GBS_CUDA_TRY(cudaMemcpyAsync(C, E.d_col + (size_t)slot * GBS_KMAX, sizeof(C),
@@ -1375,6 +1506,52 @@ int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters,
     return GBS_OK;
 }
 
+// Results of slots 0 .. ns-1 at once: every x (column-major, device
+// arrays x_out[s]) in one launch, every column record in one copy.  Column
+// j of slot s goes to position off[s] + j of iters / rnorm / status.
+int engine_collect_all(Engine &E, int ns, double *const *x_out, const int64_t *off, int *iters,
+                       double *rnorm, int *status)
+{
+    gbs_ctx c = E.c;
+    int st = engine_flush(E);
+    if (st) return st;
+    std::vector<BCol> C((size_t)ns * GBS_KMAX);
+    if (ns) GBS_CUDA_TRY(cudaMemcpyAsync(C.data(), E.d_col, sizeof(BCol) * C.size(),
+                                         cudaMemcpyDeviceToHost, c->stream));
+    std::vector<IlvJob> jobs;
+    int64_t tot = 0;
+    for (int s = 0; s < ns; ++s) {
+        const SlotHost &H = E.slots[s];
+        const int64_t nk = H.A->n * H.kp;
+        if (!nk || !x_out[s]) continue;
+        jobs.push_back(IlvJob{(const double *)(H.work + a256((size_t)nk * 8)), x_out[s], H.A->n, tot,
+                              H.k, H.kp});
+        tot += nk;
+    }
+    if (!jobs.empty()) {
+        st = ensure_cap(E.d_jobs, E.cap_jobs, jobs.size());
+        if (st) return st;
+        GBS_CUDA_TRY(cudaMemcpyAsync(E.d_jobs, jobs.data(), sizeof(IlvJob) * jobs.size(),
+                                     cudaMemcpyHostToDevice, c->stream));
+        const int g = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 8);
+        k_interleave_many<<<g, 256, 0, c->stream>>>(E.d_jobs, (int)jobs.size(), tot, 1);
+        gbs_count_launch(c);
+        GBS_CUDA_TRY(cudaGetLastError());
+    }
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < ns; ++s) {
+        const SlotHost &H = E.slots[s];
+        for (int cc = 0; cc < H.k; ++cc) {
+            const BCol &B = C[(size_t)s * GBS_KMAX + cc];
+            const int cs = B.status == GBS_RUNNING ? GBS_DIVERGED_ITS : B.status;
+            if (iters) iters[off[s] + cc] = B.iters;
+            if (rnorm) rnorm[off[s] + cc] = B.rn;
+            if (status) status[off[s] + cc] = cs;
+        }
+    }
+    return GBS_OK;
+}
+
 void engine_release(Engine &E, int slot)
 {
     E.dirty = true;
@@ -1390,9 +1567,9 @@ GbsPipeCfg engine_pipe_cfg(const Engine &E, const std::vector<int> &act)
     int v = 16, cl = 16, r = 16;
     for (int s : act) {
         const SlotHost &H = E.slots[s];
-        // FP32 tiles may carry 16-bit or 32-bit indices: cover both geometries
-        for (int w = 0; w < (E.fp64 ? 1 : 2); ++w) {
-            const GbsPipeCfg &p = E.fp64 ? H.A->pipe64_lanes[H.li]
+        // tiles may carry 16-bit or 32-bit indices: cover both geometries
+        for (int w = 0; w < 2; ++w) {
+            const GbsPipeCfg &p = E.fp64 ? (w == 0 ? H.A->pipe64_lanes[H.li] : H.A->pipe64r_lanes[H.li])
                                  : w == 0 ? H.A->pipe32_lanes[H.li] : H.A->pipe16_lanes[H.li];
             v = std::max(v, p.coloff);
             cl = std::max(cl, p.rpoff - p.coloff);
@@ -1412,6 +1589,10 @@ int engine_step(Engine &E, int *ran)
 {
     gbs_ctx c = E.c;
     *ran = 0;
+    {
+        const int st = engine_flush(E);
+        if (st) return st;
+    }
     std::vector<int> act;
     for (int s = 0; s < E.nslots; ++s) {
         const SlotHost &H = E.slots[s];
@@ -1441,7 +1622,8 @@ int engine_step(Engine &E, int *ran)
         if (!st) st = ensure_cap(E.d_partU, E.cap_partU, (size_t)nuu * 2 * GBS_KMAX);
         if (!st) st = ensure_cap(E.d_cpartS, E.cap_cpartS, (size_t)nchs * 2 * GBS_KMAX);
         if (!st) st = ensure_cap(E.d_cpartU, E.cap_cpartU, (size_t)nchu * 2 * GBS_KMAX);
-        const size_t ncnt = (size_t)nchs + nchu + 2 * (size_t)nact + 3 * (size_t)E.quantum;
+        const size_t nclaim = 12;
+        const size_t ncnt = (size_t)nchs + nchu + 2 * (size_t)nact + nclaim + 1;
         if (!st) st = ensure_cap(E.d_cnt, E.cap_cnt, ncnt);
         if (st) return st;
         E.cnt_bytes = ncnt * sizeof(int);
@@ -1478,6 +1660,7 @@ int engine_step(Engine &E, int *ran)
         a.sysS = E.d_cnt + nchs + nchu;
         a.sysU = E.d_cnt + nchs + nchu + nact;
         a.claim = E.d_cnt + nchs + nchu + 2 * nact;
+        a.nfin = a.claim + nclaim;
         a.bar = E.d_bar;
         a.cfg = engine_pipe_cfg(E, act);
         a.quantum = E.quantum;   // even: the parity of the global iteration is unchanged
@@ -1659,7 +1842,7 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
     if (nsys == 0) return GBS_OK;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
     Engine E;
-    int rc = engine_init(E, c, nsys, mode == GBS_MODE_FP64, 64);
+    int rc = engine_init(E, c, nsys, mode == GBS_MODE_FP64, kBatchQuantum);
     for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
         int li = 0;
         rc = choose_lanes(c, A[s], nrhs[s], mode == GBS_MODE_FP64, &li);
@@ -1667,24 +1850,31 @@ extern "C" int gbs_ksp_solve_cg_batched(gbs_ctx c, int nsys, const gbs_mat *A, c
             rc = engine_add(E, s, A[s], nrhs[s], rtol[s], maxit, (const double *)B[s]->data,
                             (const double *)X[s]->data, false, 0, li);
     }
+    // the slots' set-up goes to the device in one flush, then launches of
+    // up to kBatchQuantum global iterations each (the last ends as soon as
+    // every system has finished); between launches the host drops finished
+    // systems from the active list, so their units are not claimed again
+    if (rc == GBS_OK) rc = engine_flush(E);
     if (rc == GBS_OK) {
         cudaEventRecord(c->ev0, c->stream);
         for (int ran = 1; rc == GBS_OK && ran;) rc = engine_step(E, &ran);
         cudaEventRecord(c->ev1, c->stream);
     }
     int first_bad = GBS_OK;
-    int64_t o = 0;
     double model = 0.0;
     for (int s = 0; s < nsys; ++s) model += slot_model_bytes(E, s);
-    for (int s = 0; s < nsys && rc == GBS_OK; ++s) {
-        int it[GBS_KMAX], stc[GBS_KMAX];
-        double rn[GBS_KMAX];
-        rc = engine_collect(E, s, (double *)X[s]->data, GBS_MEM_DEVICE, it, rn, stc);
-        for (int cc = 0; cc < nrhs[s] && rc == GBS_OK; ++cc, ++o) {
-            if (iters) iters[o] = it[cc];
-            if (rnorm) rnorm[o] = rn[cc];
-            if (status) status[o] = stc[cc];
-            if (stc[cc] != GBS_OK && first_bad == GBS_OK) first_bad = stc[cc];
+    std::vector<int64_t> off(nsys + 1, 0);
+    std::vector<double *> xo(nsys);
+    for (int s = 0; s < nsys; ++s) {
+        off[s + 1] = off[s] + nrhs[s];
+        xo[s] = (double *)X[s]->data;
+    }
+    std::vector<int> stc(off[nsys]);
+    if (rc == GBS_OK) rc = engine_collect_all(E, nsys, xo.data(), off.data(), iters, rnorm, stc.data());
+    if (rc == GBS_OK) {
+        for (int64_t o = 0; o < off[nsys]; ++o) {
+            if (status) status[o] = stc[o];
+            if (stc[o] != GBS_OK && first_bad == GBS_OK) first_bad = stc[o];
         }
     }
     memset(&c->last, 0, sizeof(c->last));
@@ -1879,7 +2069,9 @@ static int server_admit(gbs_server srv)
         int li = 0;
         st = choose_lanes(srv->c, A, r.k, srv->mode == GBS_MODE_FP64, &li);
         if (st == GBS_OK) st = engine_add(E, slot, A, r.k, r.rtol, r.maxit, db, nullptr, true, r.ticket, li);
-        cudaFree(db);   // engine_add synchronised the stream after interleaving b
+        // interleave b now: the flush synchronises the stream, so db can go
+        if (st == GBS_OK) st = engine_flush(E);
+        cudaFree(db);
         if (st) {
             gbs_mat_destroy(A);
             return st;

@@ -364,6 +364,7 @@ int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
         A->pipe64_lanes[0] = A->pipe64;
         A->pipe32_lanes[0] = A->pipe32;
         A->pipe16_lanes[0] = A->pipe16;
+        A->pipe64r_lanes[0] = A->pipe64r;
         return GBS_OK;
     }
     if (A->tdesc_lanes[li]) return GBS_OK;
@@ -393,6 +394,7 @@ int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
     A->pipe64_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 8);
     A->pipe32_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 4);
     A->pipe16_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 4, 2);
+    A->pipe64r_lanes[li] = make_pipe_cfg(tiles, hrp.data(), 8, 2);
     return GBS_OK;
 }
 

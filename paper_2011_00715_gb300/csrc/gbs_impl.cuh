@@ -74,10 +74,10 @@ struct gbs_mat_s {
     // compressed column indices: col - row as int16, made on first use
     // (rel16_state 0 = not yet, 1 = made, -1 = some |col - row| > 32767,
     // colrel16 NULL); their stage geometry per tiling for FP32 values
-    // (pipe16) and for FP64 values (pipe64r, the one-lane tiling)
+    // (pipe16) and for FP64 values (pipe64r)
     int16_t *colrel16;
     int rel16_state;
-    GbsPipeCfg pipe16, pipe16_lanes[3], pipe64r;
+    GbsPipeCfg pipe16, pipe16_lanes[3], pipe64r, pipe64r_lanes[3];
     // made from coordinate triplets: their count, the triplet indices in
     // sorted (row, column, index) order and each entry's segment of them
     int64_t coo_m;
