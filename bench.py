@@ -479,6 +479,11 @@ def run_gbs(args, rank, world, local):
                               "peak_kind": "nominal 1.25 TFLOP/s = 625 G FMA/s"},
             "gpu_launches": int(l1 - l0),
             "clocks": clk}
+    # the tuner's decision for this class (made during the warm-up solves)
+    sh, ln = gbs.gbs_ksp_tune(Ah, gbs.GBS_MODE_FP64)
+    line["autotune"] = {"persistent_fp64": {"shape": {1: "16 warps/SM, 12.8 KB rings",
+                                                      2: "32 warps/SM, 6.4 KB rings"}[sh],
+                                            "lanes_per_row": ln, "rows_per_warp_tile": 32 // ln}}
     gbs.gbs_vec_destroy(rv)
 
     if rank == 0 and world == 1 and not args.quick:
@@ -658,6 +663,11 @@ def extras(g, args, A, Ah, xsv):
                                               torch.linalg.norm(xr3))
     del xr3
     c3["speedup_mixed_over_fp64"] = c3["fp64"]["ms_to_solution"] / c3["mixed"]["ms_to_solution"]
+    c3["autotune"] = {}
+    for name, mode in (("fp64", gbs.GBS_MODE_FP64), ("mixed", gbs.GBS_MODE_MIXED)):
+        sh, ln = gbs.gbs_ksp_tune(h, mode)
+        c3["autotune"][name] = {"warps_per_sm": 16 * sh, "lanes_per_row": ln,
+                                "rows_per_warp_tile": 32 // ln}
     out["c3_var27_96_rtol1e-10"] = c3
     for v in (xs3v, b3v, x3v, r3v):
         gbs.gbs_vec_destroy(v)
@@ -927,6 +937,15 @@ def c4_batched(g, args):
                           for m in ("mixed", "fp64")}})
     res["oracle_sample"] = sample
     res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+    # the batched engine's tuner decisions (cached per class during the
+    # solves): one system of each stencil family
+    tuned = {}
+    for (h, A, k), sp in zip(mats, specs):
+        key = f"{sp['family']}_k{k}"
+        if key not in tuned:
+            tuned[key] = {m: gbs.gbs_batched_tune(g.ctx, h, k, mode) for m, mode in
+                          (("mixed", gbs.GBS_MODE_MIXED), ("fp64", gbs.GBS_MODE_FP64))}
+    res["autotune_lanes_per_row"] = tuned
     for (h, _, _), bv, xv in zip(mats, bvs, xvs):
         gbs.gbs_vec_destroy(bv)
         gbs.gbs_vec_destroy(xv)

@@ -146,7 +146,15 @@ typedef struct {
                                 most 32767 (made on the first such use; Sec. 3,
                                 Challenge A7: the index bytes cap what narrower
                                 values save) */
-    int reserved[4];
+    int persistent_shape;    /* persistent single-system CG solves: 1 = one CTA of
+                                16 warps per SM (12.8 KB copy rings), 2 = one CTA of
+                                32 warps (6.4 KB rings; FP64 only, where two stages
+                                of the largest tile fit), 0 (default) = the tuner's
+                                choice for the system's class (gbs_ksp_tune) */
+    int persistent_lanes;    /* persistent single-system CG solves: lanes per matrix
+                                row in the SpMV, 1 (warp tiles of 32 rows) or 2 (16
+                                rows), or 0 (default) for the tuner's choice */
+    int reserved[2];
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -370,6 +378,22 @@ int gbs_ksp_last_info(gbs_ctx ctx, gbs_solve_info *info);
  * barrier per iteration. */
 int gbs_ksp_solve_chebyshev(gbs_mat A, gbs_vec b, gbs_vec x, double emin, double emax,
                             double rtol, int maxit, gbs_solve_info *info);
+
+/* Autotuner of the persistent single-system CG kernels (the library's
+ * own; the paper has no counterpart: its kernels come from vendor
+ * libraries).  For the class of A (mode, column index width, row length up
+ * to 8 / 16 / 32 / more nonzeros, log2 of the warp tiles per SM) it times a
+ * solve capped at 24 iterations of every candidate launch shape (one CTA of
+ * 16 or of 32 warps per SM; FP64 only for the latter) and SpMV tiling (1 or
+ * 2 lanes per row: warp tiles of 32 or 16 rows) on A itself, median of
+ * three, and keeps the fastest (the fixed rule's choice unless another is
+ * at least 3 % faster).  The decision is cached in the context, so every
+ * system of the class gets the same kernel; GBS_ALG_PERSISTENT and AUTO
+ * solves call it on first use of a class unless gbs_opts fixes the shape
+ * and lanes.  Outputs: *shape (1 or 2) and *lanes (1 or 2).  Allocates two
+ * vectors of nrows entries while tuning.  GBS_ERR_ARG for a NULL argument
+ * or an unknown mode. */
+int gbs_ksp_tune(gbs_mat A, int mode, int *shape, int *lanes);
 
 /* Largest system GBS_ALG_CLUSTER takes (rows): 8 CTAs (the portable
  * cluster size) of 4096 rows, x, r, p, A p and D^-1 in FP64 shared memory. */

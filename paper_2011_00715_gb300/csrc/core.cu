@@ -76,6 +76,8 @@ static int opts_valid(const gbs_opts *o)
     if (o->norm_type < GBS_NORM_UNPRECONDITIONED || o->norm_type > GBS_NORM_NATURAL) return 0;
     if (o->norm_type != GBS_NORM_UNPRECONDITIONED && o->mode == GBS_MODE_MIXED) return 0;
     if (o->no_rel16 != 0 && o->no_rel16 != 1) return 0;
+    if (o->persistent_shape < 0 || o->persistent_shape > 2) return 0;
+    if (o->persistent_lanes != 0 && o->persistent_lanes != 1 && o->persistent_lanes != 2) return 0;
     return 1;
 }
 

@@ -37,6 +37,10 @@ struct gbs_ctx_s {
     // batched engines' lanes-per-row decisions, per precision, column stride
     // and row-length class: 0 = not tuned yet, else 1 + log2(lanes)
     signed char lane_choice[2][4][8];
+    // persistent single-system CG: the tuner's shape and tiling decisions,
+    // per precision, index width, row-length class and log2 of the warp
+    // tiles per SM: 0 = not tuned yet, else 1 + 2 (shape - 1) + log2(lanes)
+    signed char pcg_choice[2][2][4][12];
 };
 
 // Geometry of the bulk-copy pipeline of one matrix for one value type,
@@ -583,7 +587,7 @@ __device__ __forceinline__ int gbs_col(int16_t c, int row) { return row + (int)c
 // gbs_spmv_pipe_pre is the same with a per-row prefetch: pre(row) runs before
 // the row's nonzeros are gathered (so the loads it issues are in flight with
 // the gathers) and its value is handed to epi(row, sum, vdiag, pre_value).
-template <typename V, typename IX, typename Pre, typename Epi>
+template <typename V, typename IX, int LOG_L = 0, typename Pre, typename Epi>
 __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ tdesc, int64_t t_begin,
                                                   int64_t t_end, int *s_next,
                                                   const int32_t *__restrict__ rowptr,
@@ -670,20 +674,52 @@ __device__ __forceinline__ bool gbs_spmv_pipe_pre(const int32_t *__restrict__ td
             const IX *scol = reinterpret_cast<const IX *>(st + cfg.coloff);
             const int32_t *srp = reinterpret_cast<const int32_t *>(st + cfg.rpoff);
             const int nrows = r1 - r0;
-            if (lane < nrows) {
-                const int row = r0 + lane;
-                const int vb = k0 & ~(E - 1), cb = k0 & ~(CE - 1), rb = r0 & ~3;
-                const auto pv = pre((int64_t)row);
-                const int beg = srp[row - rb], end = srp[row - rb + 1];
-                V sum = V(0), vd = V(0);
+            if constexpr (LOG_L == 0) {
+                if (lane < nrows) {
+                    const int row = r0 + lane;
+                    const int vb = k0 & ~(E - 1), cb = k0 & ~(CE - 1), rb = r0 & ~3;
+                    const auto pv = pre((int64_t)row);
+                    const int beg = srp[row - rb], end = srp[row - rb + 1];
+                    V sum = V(0), vd = V(0);
 #pragma unroll 8
-                for (int k = beg; k < end; ++k) {
-                    const int c = gbs_col(scol[k - cb], row);
-                    const V xv = gbs_ld(v + c, pol_keep);
-                    if (c == row) vd = xv;
-                    sum = gbs_mac(sval[k - vb], xv, sum);
+                    for (int k = beg; k < end; ++k) {
+                        const int c = gbs_col(scol[k - cb], row);
+                        const V xv = gbs_ld(v + c, pol_keep);
+                        if (c == row) vd = xv;
+                        sum = gbs_mac(sval[k - vb], xv, sum);
+                    }
+                    epi((int64_t)row, sum, vd, pv);
                 }
-                epi((int64_t)row, sum, vd, pv);
+            } else {
+                // L = 2^LOG_L lanes per row (tiles of at most 32 / L rows):
+                // lane l takes row r0 + l / L and every L-th nonzero of it
+                // from l mod L on; the L partial sums meet in a fixed
+                // shuffle tree and the group's first lane finishes the row
+                constexpr int L = 1 << LOG_L;
+                const int sub = lane & (L - 1);
+                const bool act = (lane >> LOG_L) < nrows;
+                const int row = r0 + (lane >> LOG_L);
+                V sum = V(0), vd = V(0);
+                if (act) {
+                    const int vb = k0 & ~(E - 1), cb = k0 & ~(CE - 1), rb = r0 & ~3;
+                    const int beg = srp[row - rb], end = srp[row - rb + 1];
+#pragma unroll 4
+                    for (int k = beg + sub; k < end; k += L) {
+                        const int c = gbs_col(scol[k - cb], row);
+                        const V xv = gbs_ld(v + c, pol_keep);
+                        if (c == row) vd = xv;
+                        sum = gbs_mac(sval[k - vb], xv, sum);
+                    }
+                }
+#pragma unroll
+                for (int off = L / 2; off > 0; off >>= 1) {
+                    sum += __shfl_xor_sync(0xffffffffu, sum, off);
+                    vd += __shfl_xor_sync(0xffffffffu, vd, off);
+                }
+                if (act && sub == 0) {
+                    const auto pv = pre((int64_t)row);
+                    epi((int64_t)row, sum, vd, pv);
+                }
             }
         }
         __syncwarp();
@@ -706,7 +742,7 @@ struct GbsNoPre {
     __device__ __forceinline__ int operator()(int64_t) const { return 0; }
 };
 
-template <typename V, typename IX, typename Epi>
+template <typename V, typename IX, int LOG_L = 0, typename Epi>
 __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc, int64_t t_begin,
                                               int64_t t_end, int *s_next,
                                               const int32_t *__restrict__ rowptr,
@@ -719,8 +755,9 @@ __device__ __forceinline__ bool gbs_spmv_pipe(const int32_t *__restrict__ tdesc,
 {
     GbsNoPre pre;
     auto e = [&](int64_t row, V sum, V vd, int) { epi(row, sum, vd); };
-    return gbs_spmv_pipe_pre<V, IX>(tdesc, t_begin, t_end, s_next, rowptr, colidx, vals, v, wsm, q,
-                                    parity, cfg, pol_stream, pol_keep, timeout_ns, pre, e);
+    return gbs_spmv_pipe_pre<V, IX, LOG_L>(
+        tdesc, t_begin, t_end, s_next, rowptr, colidx, vals, v, wsm, q, parity, cfg, pol_stream,
+        pol_keep, timeout_ns, pre, e);
 }
 
 #endif  // __CUDACC__

@@ -30,6 +30,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gbs_impl.cuh"
@@ -65,8 +66,7 @@ struct PcgCtl {
 struct PcgArgs {
     int64_t n;
     int64_t ntiles;
-    const int32_t *tiles;
-    const int32_t *tdesc;
+    const int32_t *tdesc;   // {row start, nonzero start} per warp tile (the chosen tiling)
     const int32_t *rowptr;
     const int32_t *colidx;
     const int16_t *colrel16;   // col - row (FP32 inner loop, when the matrix has it)
@@ -123,7 +123,7 @@ __device__ __forceinline__ int pcg_check(T rn, T rho, T tol, int k, int maxit)
 // NT: threads of the CTA; UNR: rows per thread per trip of the vector
 // phases; `stage` holds the staged CTA sums: 3 NT values for a 512-thread
 // CTA, 2 NT for a wider one.
-template <typename T, typename IX, int NT, int UNR>
+template <typename T, typename IX, int NT, int UNR, int LOG_L>
 __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const T *dinv, const T *bT,
                         T *xT, T *rT,
                         T *zT, T *pT, T *qT, T *part, T rtol, int maxit, bool x0_zero,
@@ -136,8 +136,8 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     int64_t t0, t1;
     cta_tiles(a, t0, t1);
-    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
-    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
+    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tdesc + 2 * t0) : 0;
+    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tdesc + 2 * t1) : 0;
     // scalar state, meaningful in thread 0 only
     T &rho = ctl.rho, &rr = ctl.rr, &bnorm = ctl.bnorm, &lbf = ctl.lbf, &tol2 = ctl.tol2;
     int &k = ctl.k, &status = ctl.st, &rr_current = ctl.rr_current;
@@ -181,7 +181,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             acc[1] += w * w;
             acc[2] += ref_sq(bi, i);
         };
-        if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, xT, wsm, wq,
+        if (!gbs_spmv_pipe<T, IX, LOG_L>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, xT, wsm, wq,
                               parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
@@ -288,7 +288,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             gbs_st(qT + i, s, pk);
             pq[0] += p_i * s;
         };
-        if (!gbs_spmv_pipe<T, IX>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, pT, wsm, wq,
+        if (!gbs_spmv_pipe<T, IX, LOG_L>(a.tdesc, t0, t1, s_next, a.rowptr, colidx, vals, pT, wsm, wq,
                                   parity, cfg, ps, pk, a.timeout_ns, epi) &&
             (threadIdx.x & 31) == 0)
             atomicCAS(&a.bar->error, 0, GBS_ERR_TIMEOUT);
@@ -471,8 +471,9 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
 // better; the staged CTA sums then live in dynamic shared memory after the
 // rings.
 // IX: the column indices the SpMV streams (int32, or the compressed 16-bit
-// col - row when the matrix has them).
-template <int NT, int WB, int UNR, typename IX>
+// col - row when the matrix has them); 2^LOG_L lanes share a row of the
+// SpMV (the tiling in a.tdesc has at most 32 / 2^LOG_L rows per tile).
+template <int NT, int WB, int UNR, typename IX, int LOG_L>
 __global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
 {
     constexpr bool WIDE = NT > GBS_PBLOCK;
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
     double *stage = WIDE ? reinterpret_cast<double *>(smem + (size_t)WB * (NT / 32)) : s_stage;
     const IX *cols = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
                                      : (const IX *)(const void *)a.colidx;
-    int st = pcg_loop<double, IX, NT, UNR>(
+    int st = pcg_loop<double, IX, NT, UNR, LOG_L>(
         a, cols, a.vals, a.dinv, a.b, a.x, a.r, a.z, a.p, a.q, a.part64, a.rtol, a.maxit,
         a.x0_zero != 0, &iters, &rn, &bn, &barrier_no, smem + (size_t)warp * WB, s_q[warp],
         parity, &s_next, a.pipe64, sm, stage, ctl, &s_flag);
@@ -511,7 +512,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_fp64(PcgArgs a)
 // The refinement scalars live in thread 0 of each CTA, like the inner ones.
 // IX: the column indices of the FP32 inner loop (int32, or the compressed
 // 16-bit col - row); the FP64 residual always reads the int32 indices.
-template <typename IX>
+// 2^LOG_L lanes share a row of the inner SpMV (the FP64 residual takes one
+// lane per row of the same tiles).
+template <typename IX, int LOG_L>
 __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
     const uint64_t ps = gbs_policy_stream(), pk = gbs_policy_keep();
     int64_t t0, t1;
     cta_tiles(a, t0, t1);
-    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tiles + t0) : 0;
-    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tiles + t1) : 0;
+    const int64_t rb = t0 < t1 ? (int64_t)__ldg(a.tdesc + 2 * t0) : 0;
+    const int64_t re = t0 < t1 ? (int64_t)__ldg(a.tdesc + 2 * t1) : 0;
     int barrier_no = 0, inner_total = 0, outer = 0, st = GBS_DIVERGED_ITS;
     double rn = 0.0, bnorm = 0.0, prev = INFINITY;   // thread 0
     for (int it = 0; it <= a.outer_maxit; ++it) {
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
         float rin = 0.f, bin = 0.f;
         const IX *col32 = sizeof(IX) == 2 ? (const IX *)(const void *)a.colrel16
                                           : (const IX *)(const void *)a.colidx;
-        const int sti = pcg_loop<float, IX, GBS_PBLOCK, 4>(
+        const int sti = pcg_loop<float, IX, GBS_PBLOCK, 4, LOG_L>(
             a, col32, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32, a.q32, a.part32,
             (float)a.inner_rtol, a.maxit, true, &kin, &rin, &bin, &barrier_no, wsm, s_q[warp],
             parity, &s_next, a.pipe32, sm32, reinterpret_cast<float *>(s_stage), ctl32, &s_flag);
@@ -704,88 +707,123 @@ int launch_persistent(gbs_ctx c, const void *fn, int G, PcgArgs &a, gbs_solve_in
     return r.status;
 }
 
-void fill_matrix_args(PcgArgs &a, gbs_mat A)
+// Tiling li (2^li lanes per row: tiles of at most 32 >> li rows) and its
+// stage geometries.
+void fill_matrix_args(PcgArgs &a, gbs_mat A, int li)
 {
     a.n = A->n;
-    a.ntiles = A->ntiles;
-    a.tiles = A->tiles;
-    a.tdesc = A->tdesc;
+    a.ntiles = A->ntiles_lanes[li];
+    a.tdesc = A->tdesc_lanes[li];
     a.rowptr = A->rowptr;
     a.colidx = A->colidx;
     a.vals = A->vals;
     a.vals32 = A->vals32;
     a.dinv = A->dinv;
     a.dinv32 = A->dinv32;
-    a.pipe64 = A->pipe64;
-    a.pipe32 = A->pipe32;
+    a.pipe64 = A->pipe64_lanes[li];
+    a.pipe32 = A->pipe32_lanes[li];
 }
 
-// Launch shape of the FP64 persistent kernel.  Large systems (at least 32
-// warp tiles per SM) run one CTA of 32 warps per SM with 6.4 KB copy rings
-// wherever two stages of the matrix's largest tile fit in 6.4 KB (with a
-// single stage a warp cannot overlap its copy and its compute, and the
-// 32-warp shape measured slower on 27-point operators): 32 warps
-// hide the SpMV gathers' latency better than 16 (the SpMV phase of the
-// 128^3 7-point solve takes 42.9 instead of 50.7 us), while the CTA-wide
-// sums and barriers of a 1024-thread CTA cost more, which small systems
-// feel.  Otherwise one CTA of 16 warps per SM with 12.8 KB rings.
-struct Fp64Shape {
+// Launch shapes of the persistent kernels.  FP64: one CTA of 16 warps per
+// SM with 12.8 KB copy rings per warp (shape 1), or one CTA of 32 warps
+// with 6.4 KB rings (shape 2: more warps hide the SpMV gathers' latency
+// better, while the CTA-wide sums and barriers of a 1024-thread CTA cost
+// more; it needs two stages of the largest tile in 6.4 KB).  The mixed
+// kernel has shape 1 only.  Either runs the SpMV with 1 or 2 lanes per row
+// (tilings of 32- and 16-row tiles).
+struct PcgShape {
     const void *fn;
     size_t smem;
     int nt;
-    GbsPipeCfg cfg;
+    GbsPipeCfg cfg;     // stage geometry of the SpMV the kernel's loop runs
 };
 
-// rel: stream the compressed 16-bit column indices (the matrix has them).
-template <typename IX>
-Fp64Shape fp64_shape_ix(gbs_mat A, const GbsPipeCfg &cfg)
+template <typename IX, int LOG_L>
+PcgShape fp64_shape_l(int shape, GbsPipeCfg cfg)
 {
     constexpr int kSmallRing = GBS_WARP_STAGE_BYTES / 2;
     constexpr int kWide = 2 * GBS_PBLOCK;
-    Fp64Shape s;
+    PcgShape s;
     s.cfg = cfg;
-    const int stages = kSmallRing / cfg.sbytes;
-    const bool large = A->ntiles >= (int64_t)A->ctx->num_sms * (kWide / 32);
-    if (stages >= 2 && large) {
+    if (shape == 2) {
+        const int stages = kSmallRing / cfg.sbytes;
         s.cfg.stages = stages < GBS_MAX_STAGES ? stages : GBS_MAX_STAGES;
-        s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2, IX>;
+        s.fn = (const void *)k_pcg_fp64<kWide, kSmallRing, 2, IX, LOG_L>;
         s.smem = (size_t)kSmallRing * (kWide / 32) + 2 * kWide * sizeof(double);
         s.nt = kWide;
     } else {
-        s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4, IX>;
+        s.fn = (const void *)k_pcg_fp64<GBS_PBLOCK, GBS_WARP_STAGE_BYTES, 4, IX, LOG_L>;
         s.smem = kPersistSmem;
         s.nt = GBS_PBLOCK;
     }
     return s;
 }
 
-Fp64Shape fp64_shape(gbs_mat A, bool rel)
+// The kernel and geometry for (mode, index width, shape, lanes 2^li).
+PcgShape pcg_shape(gbs_mat A, bool mixed, bool rel, int shape, int li)
 {
-    return rel ? fp64_shape_ix<int16_t>(A, A->pipe64r) : fp64_shape_ix<int32_t>(A, A->pipe64);
+    if (mixed) {
+        PcgShape s;
+        s.fn = rel ? (li ? (const void *)k_pcg_mixed<int16_t, 1> : (const void *)k_pcg_mixed<int16_t, 0>)
+                   : (li ? (const void *)k_pcg_mixed<int32_t, 1> : (const void *)k_pcg_mixed<int32_t, 0>);
+        s.smem = kPersistSmem;
+        s.nt = GBS_PBLOCK;
+        s.cfg = rel ? A->pipe16_lanes[li] : A->pipe32_lanes[li];
+        return s;
+    }
+    const GbsPipeCfg cfg = rel ? A->pipe64r_lanes[li] : A->pipe64_lanes[li];
+    if (rel) return li ? fp64_shape_l<int16_t, 1>(shape, cfg) : fp64_shape_l<int16_t, 0>(shape, cfg);
+    return li ? fp64_shape_l<int32_t, 1>(shape, cfg) : fp64_shape_l<int32_t, 0>(shape, cfg);
 }
 
-}  // namespace
+// Shape 2 is possible where two stages of the tiling's largest tile fit in
+// a 6.4 KB ring and there are at least 32 tiles per SM.
+bool wide_shape_fits(gbs_mat A, bool rel, int li)
+{
+    const GbsPipeCfg &cfg = rel ? A->pipe64r_lanes[li] : A->pipe64_lanes[li];
+    return (GBS_WARP_STAGE_BYTES / 2) / cfg.sbytes >= 2 &&
+           A->ntiles_lanes[li] >= (int64_t)A->ctx->num_sms * 32;
+}
 
-int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
-                         const gbs_opts *o, gbs_solve_info *info)
+// The fixed rule used before a class is tuned and where tuning is not
+// possible: the 32-warp shape wherever it fits, one lane per row.
+void rule_shape(gbs_mat A, bool mixed, bool rel, int *shape, int *li)
+{
+    *li = 0;
+    *shape = !mixed && wide_shape_fits(A, rel, 0) ? 2 : 1;
+}
+
+// Class of a system for the tuner's decisions: precision, index width,
+// row length (at most 8, 16, 32 or more nonzeros) and log2 of the warp
+// tiles per SM.
+void pcg_class(gbs_mat A, bool mixed, bool rel, int *i0, int *i1, int *i2, int *i3)
+{
+    const int m = A->max_row_nnz;
+    int64_t t = A->ntiles / (A->ctx->num_sms > 0 ? A->ctx->num_sms : 1);
+    int lg = 0;
+    while (t > 1 && lg < 11) {
+        t >>= 1;
+        ++lg;
+    }
+    *i0 = mixed ? 1 : 0;
+    *i1 = rel ? 1 : 0;
+    *i2 = m <= 8 ? 0 : m <= 16 ? 1 : m <= 32 ? 2 : 3;
+    *i3 = lg;
+}
+
+// Launch a persistent solve of A with right-hand side b into x (device
+// arrays of n entries) with the given shape and tiling; the caller made
+// the FP32 copy and the compressed indices it asks for.
+int persistent_run(gbs_mat A, const double *b, double *x, double rtol, int maxit, const gbs_opts *o,
+                   bool mixed, bool rel16, int shape, int li, int outer_maxit, gbs_solve_info *info)
 {
     gbs_ctx c = A->ctx;
-    const bool mixed = o->mode == GBS_MODE_MIXED;
-    if (mixed) {
-        int st = gbs_mat_ensure_f32(A);
+    {
+        const int st = gbs_mat_ensure_lane_tiling(A, li);
         if (st) return st;
     }
-    if (!mixed && !o->no_rel16) {
-        int st = gbs_mat_ensure_rel16(A);
-        if (st) return st;
-    }
-    const bool rel16 = A->colrel16 && !o->no_rel16;
-    const Fp64Shape shape = fp64_shape(A, rel16);
-    const void *fn = !mixed ? shape.fn
-                     : rel16 ? (const void *)k_pcg_mixed<int16_t> : (const void *)k_pcg_mixed<int32_t>;
-    const size_t smem = mixed ? kPersistSmem : shape.smem;
-    const int nt = mixed ? GBS_PBLOCK : shape.nt;
-    const int G = coop_grid(c, fn, A->ntiles, o->persistent_ctas, smem, nt);
+    const PcgShape sh = pcg_shape(A, mixed, rel16, shape, li);
+    const int G = coop_grid(c, sh.fn, A->ntiles_lanes[li], o->persistent_ctas, sh.smem, sh.nt);
     if (G < 0) return GBS_ERR_CUDA;
     const int64_t n = A->n;
     const size_t vec64 = align256(sizeof(double) * (size_t)n);
@@ -819,26 +857,158 @@ int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit
         a.p = (double *)v; v += vec64;
         a.q = (double *)v; v += vec64;
     }
-    fill_matrix_args(a, A);
-    if (rel16) {   // the SpMV (FP64, or the FP32 inner loop) streams 16-bit column indices
-        a.colrel16 = A->colrel16;
-        if (mixed) a.pipe32 = A->pipe16;
-    }
-    a.b = (const double *)b->data;
-    a.x = (double *)x->data;
+    fill_matrix_args(a, A, li);
+    if (rel16) a.colrel16 = A->colrel16;   // the SpMV (FP64, or FP32 inner) streams 16-bit offsets
+    if (mixed) a.pipe32 = sh.cfg;
+    else a.pipe64 = sh.cfg;
+    a.b = b;
+    a.x = x;
     a.rtol = rtol;
     a.inner_rtol = o->inner_rtol;
     a.maxit = maxit;
-    a.outer_maxit = o->outer_maxit;
+    a.outer_maxit = outer_maxit;
     a.x0_zero = 0;
     a.norm = o->norm_type;
     a.skip_cta = o->fault_skip_arrival;
     a.timeout_ns = (unsigned long long)o->barrier_timeout_ms * 1000000ull;
-    if (!mixed) a.pipe64 = shape.cfg;
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
-    st = launch_persistent(c, fn, G, a, info, smem, nt);
+    st = launch_persistent(c, sh.fn, G, a, info, sh.smem, sh.nt);
     info->model_bytes = persistent_model_bytes(A, mixed, rel16 ? 2 : 4, *info);
     return st;
+}
+
+// The tuner: for a class not yet decided on this context, time a solve
+// capped at kTuneIters iterations (rtol 0, so none stops early; mixed: one
+// refinement step) of every candidate (shape x lanes per row) on this
+// system, median of three runs each, and keep the fastest; the rule's
+// choice is kept unless another is at least 3 % faster.  The decision is
+// cached per class, so every system of the class gets the same kernel.
+constexpr int kTuneIters = 24;
+
+int pcg_tune(gbs_mat A, bool mixed, bool rel16, const gbs_opts *o, int *shape, int *li)
+{
+    gbs_ctx c = A->ctx;
+    int k0, k1, k2, k3;
+    pcg_class(A, mixed, rel16, &k0, &k1, &k2, &k3);
+    signed char &dec = c->pcg_choice[k0][k1][k2][k3];
+    if (dec > 0) {
+        *shape = 1 + ((dec - 1) >> 1);
+        *li = (dec - 1) & 1;
+        return GBS_OK;
+    }
+    int rshape, rli;
+    rule_shape(A, mixed, rel16, &rshape, &rli);
+    if (A->n == 0 || !A->diag_ok) {
+        *shape = rshape;
+        *li = rli;
+        return GBS_OK;
+    }
+    double *bx = nullptr;   // b = D^-1 (any nonzero right-hand side), x
+    GBS_CUDA_TRY(cudaMalloc(&bx, 2 * sizeof(double) * (size_t)A->n));
+    GBS_CUDA_TRY(cudaMemcpyAsync(bx, A->dinv, sizeof(double) * A->n, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    float best = 0.f, rule_ms = 0.f;
+    int bs = rshape, bl = rli, st = GBS_OK;
+    gbs_opts to = *o;
+    to.persistent_ctas = 0;
+    to.fault_skip_arrival = -1;
+    to.inner_rtol = 1e-300;   // mixed: the inner solve runs its kTuneIters iterations too
+    for (int cl = 0; cl < 2 && st == GBS_OK; ++cl) {
+        for (int cs = 1; cs <= (mixed ? 1 : 2) && st == GBS_OK; ++cs) {
+            if (cs == 2 && !wide_shape_fits(A, rel16, cl)) continue;
+            st = gbs_mat_ensure_lane_tiling(A, cl);
+            float t[3];
+            for (int r = 0; r < 3 && st == GBS_OK; ++r) {
+                gbs_solve_info ti;
+                memset(&ti, 0, sizeof(ti));
+                cudaMemsetAsync(bx + A->n, 0, sizeof(double) * A->n, c->stream);
+                const int rs = persistent_run(A, bx, bx + A->n, 0.0, kTuneIters, &to, mixed, rel16, cs,
+                                              cl, 1, &ti);
+                // a timing run's own status (limit reached, stagnation) is
+                // of no interest; only a failure of the device stops tuning
+                if (rs == GBS_ERR_CUDA || rs == GBS_ERR_OOM || rs == GBS_ERR_TIMEOUT ||
+                    rs == GBS_ERR_UNSUPPORTED)
+                    st = rs;
+                t[r] = (float)ti.device_ms;
+            }
+            if (st != GBS_OK) break;
+            std::sort(t, t + 3);
+            if (cs == rshape && cl == rli) rule_ms = t[1];
+            if (best == 0.f || t[1] < best) {
+                best = t[1];
+                bs = cs;
+                bl = cl;
+            }
+        }
+    }
+    cudaFree(bx);
+    if (st != GBS_OK) return st;
+    if (rule_ms > 0.f && best > 0.97f * rule_ms) {
+        bs = rshape;
+        bl = rli;
+    }
+    dec = (signed char)(1 + 2 * (bs - 1) + bl);
+    *shape = bs;
+    *li = bl;
+    return GBS_OK;
+}
+
+// Shape and lanes for a solve: the options' fixed choice, else the tuned
+// decision of the class.
+int pcg_choice(gbs_mat A, bool mixed, bool rel16, const gbs_opts *o, int *shape, int *li)
+{
+    if (o->persistent_shape == 0 || o->persistent_lanes == 0) {
+        int st = pcg_tune(A, mixed, rel16, o, shape, li);
+        if (st) return st;
+    }
+    if (o->persistent_shape != 0) *shape = mixed ? 1 : o->persistent_shape;
+    if (o->persistent_lanes != 0) *li = o->persistent_lanes == 2 ? 1 : 0;
+    if (*shape == 2 && !wide_shape_fits(A, rel16, *li)) *shape = 1;
+    return GBS_OK;
+}
+
+}  // namespace
+
+int gbs_solve_persistent(gbs_mat A, gbs_vec b, gbs_vec x, double rtol, int maxit,
+                         const gbs_opts *o, gbs_solve_info *info)
+{
+    const bool mixed = o->mode == GBS_MODE_MIXED;
+    if (mixed) {
+        int st = gbs_mat_ensure_f32(A);
+        if (st) return st;
+    }
+    if (!mixed && !o->no_rel16) {
+        int st = gbs_mat_ensure_rel16(A);
+        if (st) return st;
+    }
+    const bool rel16 = A->colrel16 && !o->no_rel16;
+    int shape = 1, li = 0;
+    int st = pcg_choice(A, mixed, rel16, o, &shape, &li);
+    if (st) {   // the tuner's device failure is the solve's
+        info->status = st;
+        return st;
+    }
+    return persistent_run(A, (const double *)b->data, (double *)x->data, rtol, maxit, o, mixed,
+                          rel16, shape, li, o->outer_maxit, info);
+}
+
+extern "C" int gbs_ksp_tune(gbs_mat A, int mode, int *shape, int *lanes)
+{
+    if (!A || !shape || !lanes || (mode != GBS_MODE_FP64 && mode != GBS_MODE_MIXED)) return GBS_ERR_ARG;
+    gbs_ctx c = A->ctx;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const bool mixed = mode == GBS_MODE_MIXED;
+    int st = mixed ? gbs_mat_ensure_f32(A) : (c->opts.no_rel16 ? GBS_OK : gbs_mat_ensure_rel16(A));
+    if (st) return st;
+    const bool rel16 = A->colrel16 && !c->opts.no_rel16;
+    gbs_opts o = c->opts;
+    o.mode = mode;
+    int sh = 1, li = 0;
+    st = pcg_choice(A, mixed, rel16, &o, &sh, &li);
+    if (st) return st;
+    *shape = sh;
+    *lanes = 1 << li;
+    return GBS_OK;
 }
 
 // ----------------------------------------------------------------------
@@ -1268,8 +1438,32 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     // the compressed column indices only if the matrix already has them
     // (making them would allocate)
     const bool rel16 = A->colrel16 && !c->opts.no_rel16;
-    const Fp64Shape shape = fp64_shape(A, rel16);
-    int G = coop_grid(c, shape.fn, A->ntiles, c->opts.persistent_ctas, shape.smem, shape.nt);
+    // the class's tuned shape and tiling if this context has decided it and
+    // the tiling exists (tuning and making a tiling would allocate), else
+    // the fixed rule
+    int shp = 1, li = 0;
+    {
+        int k0, k1, k2, k3;
+        pcg_class(A, false, rel16, &k0, &k1, &k2, &k3);
+        const signed char dec = c->pcg_choice[k0][k1][k2][k3];
+        if (dec > 0 && A->tdesc_lanes[(dec - 1) & 1]) {
+            shp = 1 + ((dec - 1) >> 1);
+            li = (dec - 1) & 1;
+        } else {
+            rule_shape(A, false, rel16, &shp, &li);
+        }
+        if (li == 0 && !A->tdesc_lanes[0]) {   // tiling 0 is the creation tiling
+            A->tdesc_lanes[0] = A->tdesc;
+            A->ntiles_lanes[0] = A->ntiles;
+            A->pipe64_lanes[0] = A->pipe64;
+            A->pipe32_lanes[0] = A->pipe32;
+            A->pipe16_lanes[0] = A->pipe16;
+            A->pipe64r_lanes[0] = A->pipe64r;
+        }
+        if (shp == 2 && !wide_shape_fits(A, rel16, li)) shp = 1;
+    }
+    const PcgShape shape = pcg_shape(A, false, rel16, shp, li);
+    int G = coop_grid(c, shape.fn, A->ntiles_lanes[li], c->opts.persistent_ctas, shape.smem, shape.nt);
     if (G < 0) return GBS_ERR_CUDA;
     if (G > kNoAllocMaxCtas) G = kNoAllocMaxCtas;
     char *base = (char *)scr;
@@ -1284,7 +1478,7 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     a.z = (double *)(v + kNoAllocVec);
     a.p = (double *)(v + 2 * kNoAllocVec);
     a.q = (double *)(v + 3 * kNoAllocVec);
-    fill_matrix_args(a, A);
+    fill_matrix_args(a, A, li);
     if (rel16) a.colrel16 = A->colrel16;
     a.b = b;
     a.x = x;

@@ -65,7 +65,8 @@ class gbs_opts(ctypes.Structure):
                 ("barrier_timeout_ms", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
                 ("persistent_ctas", ctypes.c_int), ("norm_type", ctypes.c_int),
-                ("no_rel16", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("no_rel16", ctypes.c_int), ("persistent_shape", ctypes.c_int),
+                ("persistent_lanes", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class gbs_solve_info(ctypes.Structure):
@@ -146,6 +147,7 @@ _SIGS = {
     "gbs_server_submit_borrowed": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "gbs_batched_tune": ([_VP, _VP, ctypes.c_int, ctypes.c_int, _I32P], ctypes.c_int),
+    "gbs_ksp_tune": ([_VP, ctypes.c_int, _I32P, _I32P], ctypes.c_int),
     "gbs_server_progress": ([_VP, _I32P], ctypes.c_int),
     "gbs_server_poll": ([_VP, ctypes.c_uint64, _I32P], ctypes.c_int),
     "gbs_server_wait": ([_VP, ctypes.c_uint64], ctypes.c_int),
@@ -484,6 +486,13 @@ def gbs_ksp_solve_chebyshev(A, b, x, emin: float, emax: float, rtol: float, maxi
     if st not in _RESULT_STATUSES:
         _check(st, "gbs_ksp_solve_chebyshev")
     return _info(info)
+
+
+def gbs_ksp_tune(A, mode: int):
+    """(shape, lanes per row) the tuner picks for A's class in this mode."""
+    sh, ln = ctypes.c_int(), ctypes.c_int()
+    _check(lib().gbs_ksp_tune(A, int(mode), ctypes.byref(sh), ctypes.byref(ln)), "gbs_ksp_tune")
+    return sh.value, ln.value
 
 
 def gbs_ksp_last_info(ctx) -> SolveInfo:

@@ -300,3 +300,57 @@ def test_fp64_index_widths_match_oracle(S, orc, case, no_rel16):
     record(f"index_widths[{case},no_rel16={no_rel16}]", "rel_err_vs_oracle", rel(x, ref["x"]), 1e-8)
     assert rel(x, ref["x"]) <= 1e-8
     assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("lanes", [1, 2])
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("case", ["lap3d7_56", "var27_40"])
+def test_every_tuner_candidate_meets_the_oracle_bar(S, orc, case, shape, lanes):
+    """Every launch shape and SpMV tiling the tuner chooses among (one CTA of
+    16 or 32 warps per SM; 1 or 2 lanes per row), forced through the
+    options: FP64 within 1e-8 of the oracle's solution, mixed precision
+    (16-warp shape) within the stopping rule's guarantee, both at the true
+    residual."""
+    A = I.lap3d7(56) if case == "lap3d7_56" else I.var27(40, seed=5)
+    b = orc.spmv(A, I.xstar(A.n, 2))
+    ref = orc.pcg(A, b, 1e-10, 20000)
+    info, x = solve(S, A, b, 1e-10, 20000, algorithm=ALGS["persistent"], persistent_shape=shape,
+                    persistent_lanes=lanes)
+    assert info.status == gbs.GBS_OK and abs(info.iters - ref["iters"]) <= 2
+    record(f"candidate[{case},shape={shape},lanes={lanes}]", "rel_err_vs_oracle",
+           rel(x, ref["x"]), 1e-8)
+    assert rel(x, ref["x"]) <= 1e-8
+    assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-3)
+    if shape == 1:
+        info, x = solve(S, A, b, 1e-10, 20000, mode=gbs.GBS_MODE_MIXED, persistent_lanes=lanes)
+        assert info.status == gbs.GBS_OK
+        assert true_res(orc, A, b, x) <= 1e-10 * np.linalg.norm(b)
+        if case == "lap3d7_56":
+            lmin = unit_laplacian_lmin((56, 56, 56))
+        else:
+            c = math.cos(math.pi / 41)
+            lmin = (14 - 6 * c - 6 * c * c - 2 * c ** 3) * float(A.meta["w_min"])
+        tol = solution_tol(orc, A, b, x, ref["x"], lmin)
+        record(f"candidate_mixed[{case},lanes={lanes}]", "rel_err_vs_oracle", rel(x, ref["x"]), tol)
+        assert rel(x, ref["x"]) <= tol
+
+
+def test_tuner_decides_per_class(S, orc):
+    """gbs_ksp_tune returns one of its candidates, the same decision for a
+    second system of the same class, and a persistent solve with the
+    default options gets the oracle's solution."""
+    A = I.lap3d7(48)
+    h = S.mat(A)
+    shape, lanes = gbs.gbs_ksp_tune(h, gbs.GBS_MODE_FP64)
+    assert shape in (1, 2) and lanes in (1, 2)
+    B = I.var7(48, 48, 48, seed=4)            # same class: 7-point rows, same size
+    hb = S.mat(B)
+    assert gbs.gbs_ksp_tune(hb, gbs.GBS_MODE_FP64) == (shape, lanes)
+    ms, ml = gbs.gbs_ksp_tune(h, gbs.GBS_MODE_MIXED)
+    assert ms == 1 and ml in (1, 2)
+    gbs.gbs_mat_destroy(h)
+    gbs.gbs_mat_destroy(hb)
+    b = orc.spmv(B, I.xstar(B.n, 3))
+    ref = orc.pcg(B, b, 1e-10, 20000)
+    info, x = solve(S, B, b, 1e-10, 20000, algorithm=ALGS["persistent"])
+    assert info.status == gbs.GBS_OK and rel(x, ref["x"]) <= 1e-8
