@@ -134,6 +134,9 @@ def _load():
                                       ctypes.c_double, i64, i64, ctypes.POINTER(i64),
                                       ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
         lib.orc_pcg_mixed.restype = ctypes.c_int
+        lib.orc_block_pcg.argtypes = [i64, i32p, i32p, f64p, ctypes.c_int, f64p, f64p,
+                                      ctypes.c_double, i64, ctypes.POINTER(i64), f64p, f64p]
+        lib.orc_block_pcg.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -302,3 +305,22 @@ def pcg_mixed(A, b, rtol, inner_rtol=1e-4, inner_maxit=10000, outer_maxit=30, x0
                                float(inner_rtol), int(inner_maxit), int(outer_maxit),
                                ctypes.byref(o), ctypes.byref(i), ctypes.byref(rn))
     return {"x": x, "status": st, "outer": o.value, "inner": i.value, "rnorm": rn.value}
+
+
+def block_pcg(A, B, rtol, maxit, X0=None):
+    """Block Jacobi-PCG (O'Leary) in FP64 for the k columns of B (an n x k
+    array, or k * n values column by column).  Returns dict(x (n x k),
+    status, iters (block iterations), rnorm[k], bnorm[k])."""
+    rp, ci, v = _i32(A.rowptr), _i32(A.colidx), _f64(A.vals)
+    Bc = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(A.n, -1, order="F"))
+    k = Bc.shape[1]
+    bb = np.ascontiguousarray(Bc.T).reshape(-1)          # column j at j * n
+    X = np.zeros(A.n * k) if X0 is None else np.ascontiguousarray(
+        np.asarray(X0, dtype=np.float64).reshape(A.n, -1, order="F").T).reshape(-1).copy()
+    it = ctypes.c_int64(0)
+    rn = np.zeros(k)
+    bn = np.zeros(k)
+    st = _load().orc_block_pcg(A.n, _p(rp), _p(ci), _p(v), int(k), _p(bb), _p(X), float(rtol),
+                               int(maxit), ctypes.byref(it), _p(rn), _p(bn))
+    return {"x": X.reshape(k, A.n).T.copy(), "status": st, "iters": it.value, "rnorm": rn,
+            "bnorm": bn}

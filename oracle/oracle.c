@@ -432,6 +432,147 @@ int orc_pcg_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, const
 }
 
 /*
+ * Solve S Y = C for Y (k x k, column-major, k <= 8) with the symmetric
+ * positive definite S (its lower triangle is used) factored as L D L^T,
+ * L unit lower triangular, without square roots, so that for k = 1 the
+ * solution is the single division C / S.  Returns 0, or -1 if a pivot of D
+ * is not positive (S not positive definite: a breakdown of the block
+ * method).
+ */
+static int orc_ldl_solve(int k, const double *S, const double *C, double *Y)
+{
+    double L[64], D[8];
+    for (int j = 0; j < k; ++j) {
+        double d = S[j + j * k];
+        for (int m = 0; m < j; ++m) d -= L[j + m * k] * L[j + m * k] * D[m];
+        if (!(d > 0.0)) return -1;
+        D[j] = d;
+        L[j + j * k] = 1.0;
+        for (int i = j + 1; i < k; ++i) {
+            double v = S[i + j * k];
+            for (int m = 0; m < j; ++m) v -= L[i + m * k] * L[j + m * k] * D[m];
+            L[i + j * k] = v / d;
+        }
+    }
+    for (int c = 0; c < k; ++c) {
+        double y[8];
+        for (int i = 0; i < k; ++i) {          /* L y = C(:, c) */
+            double v = C[i + c * k];
+            for (int m = 0; m < i; ++m) v -= L[i + m * k] * y[m];
+            y[i] = v;
+        }
+        for (int i = 0; i < k; ++i) y[i] = y[i] / D[i];
+        for (int i = k - 1; i >= 0; --i) {     /* L^T Y(:, c) = y */
+            double v = y[i];
+            for (int m = i + 1; m < k; ++m) v -= L[m + i * k] * Y[m + c * k];
+            Y[i + c * k] = v;
+        }
+    }
+    return 0;
+}
+
+/* G = U^T V for n x k blocks (column-major), entry (a, b) = sum_i U_ia V_ib
+ * left to right. */
+static void orc_gram(int64_t n, int k, const double *U, const double *V, double *G)
+{
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) G[a + b * k] = orc_dot(n, U + a * n, V + b * n);
+}
+
+/*
+ * Block Jacobi-preconditioned CG for k right-hand sides at once (O'Leary,
+ * "The block conjugate gradient algorithm and related methods", Linear
+ * Algebra Appl. 29, 1980), FP64; the paper's Challenge F2 / KSPHPDDM point
+ * that methods for several right-hand sides raise arithmetic intensity.
+ * B, X: n x k column-major (column j at B + j n), X the initial guess in
+ * and the solution out; 1 <= k <= 8.
+ *
+ *   R = B - A X;  Z = D^-1 R;  P = Z;  rho = Z^T R                (k x k)
+ *   for it = 0, 1, ...:
+ *       if ||R_j|| <= rtol ||B_j|| for every column j: converged
+ *       Q = A P;  pi = P^T Q;  alpha = pi^-1 rho
+ *       X += P alpha;  R -= Q alpha;  Z = D^-1 R
+ *       rho' = Z^T R;  beta = rho^-1 rho';  P = Z + P beta;  rho = rho'
+ *
+ * The k x k systems are solved by orc_ldl_solve (pi or rho not positive
+ * definite: ORC_ERR_INDEFINITE).  The products X + P alpha etc. add the k
+ * terms left to right onto the first operand, so for k = 1 every operation
+ * is the one orc_pcg does.  *iters = block iterations (SpMV passes over
+ * the block); rnorm[j] = ||R_j|| at the end, bnorm[j] = ||B_j||.
+ */
+int orc_block_pcg(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                  int k, const double *B, double *X, double rtol, int64_t maxit,
+                  int64_t *iters, double *rnorm, double *bnorm)
+{
+    *iters = 0;
+    if (n < 0 || k < 1 || k > 8 || maxit < 0 || !(rtol >= 0.0)) return ORC_ERR_ARG;
+    for (int j = 0; j < k; ++j) rnorm[j] = bnorm[j] = 0.0;
+    if (n == 0) return ORC_CONVERGED;
+    const size_t nk = (size_t)n * k;
+    double *dinv = malloc(sizeof(double) * n);
+    double *R = malloc(sizeof(double) * nk);
+    double *Z = malloc(sizeof(double) * nk);
+    double *P = malloc(sizeof(double) * nk);
+    double *Q = malloc(sizeof(double) * nk);
+    double rho[64], pi[64], alpha[64], rho2[64], beta[64], t[8];
+    int status = orc_jacobi_dinv(n, rowptr, colidx, vals, dinv);
+    if (status == 0) {
+        for (int j = 0; j < k; ++j) {
+            orc_spmv(n, rowptr, colidx, vals, X + j * n, Q + j * n);
+            for (int64_t i = 0; i < n; ++i) R[i + j * n] = B[i + j * n] - Q[i + j * n];
+            for (int64_t i = 0; i < n; ++i) Z[i + j * n] = dinv[i] * R[i + j * n];
+            bnorm[j] = orc_norm2(n, B + j * n);
+        }
+        memcpy(P, Z, sizeof(double) * nk);
+        orc_gram(n, k, Z, R, rho);
+        int64_t it = 0;
+        status = ORC_DIVERGED_ITS;
+        for (;;) {
+            int done = 1, bad = 0;
+            for (int j = 0; j < k; ++j) {
+                rnorm[j] = orc_norm2(n, R + j * n);
+                if (isnan(rnorm[j])) bad = 1;
+                if (!(rnorm[j] <= rtol * bnorm[j])) done = 0;
+            }
+            if (bad) { status = ORC_ERR_NAN; break; }
+            if (done) { status = ORC_CONVERGED; break; }
+            if (it >= maxit) break;
+            for (int j = 0; j < k; ++j) orc_spmv(n, rowptr, colidx, vals, P + j * n, Q + j * n);
+            orc_gram(n, k, P, Q, pi);
+            if (orc_ldl_solve(k, pi, rho, alpha)) { status = ORC_ERR_INDEFINITE; break; }
+            for (int64_t i = 0; i < n; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double x = X[i + j * n], r = R[i + j * n];
+                    for (int m = 0; m < k; ++m) {
+                        x = x + P[i + m * n] * alpha[m + j * k];
+                        r = r - Q[i + m * n] * alpha[m + j * k];
+                    }
+                    X[i + j * n] = x;
+                    R[i + j * n] = r;
+                }
+            for (size_t e = 0; e < nk; ++e) Z[e] = dinv[e % (size_t)n] * R[e];
+            orc_gram(n, k, Z, R, rho2);
+            ++it;
+            if (orc_ldl_solve(k, rho, rho2, beta)) { status = ORC_ERR_INDEFINITE; break; }
+            for (int64_t i = 0; i < n; ++i) {
+                for (int j = 0; j < k; ++j) {
+                    double p = Z[i + j * n];
+                    for (int m = 0; m < k; ++m) p = p + P[i + m * n] * beta[m + j * k];
+                    t[j] = p;
+                }
+                for (int j = 0; j < k; ++j) P[i + j * n] = t[j];
+            }
+            memcpy(rho, rho2, sizeof(rho));
+        }
+        if (status == ORC_ERR_INDEFINITE)
+            for (int j = 0; j < k; ++j) rnorm[j] = orc_norm2(n, R + j * n);
+        *iters = it;
+    }
+    free(dinv); free(R); free(Z); free(P); free(Q);
+    return status;
+}
+
+/*
  * Jacobi-preconditioned Chebyshev iteration (KSPCHEBYSHEV with PCJACOBI,
  * the paper's multigrid smoother of Sec. 5.3): Chebyshev acceleration of
  * the preconditioned Richardson iteration for a spectrum of D^-1 A inside

@@ -67,6 +67,19 @@ MUTANTS = {
         "            s += vals[k] * x[i];"),
     "aypx_fused_roles_swapped": ("y[i] = fma(beta, y[i], x[i]);", "y[i] = fma(beta, x[i], y[i]);"),
     "axpy_fused_rounds_twice": ("y[i] = fma(alpha, x[i], y[i]);", "y[i] = alpha * x[i] + y[i];"),
+    "block_alpha_operands_swapped": ("if (orc_ldl_solve(k, pi, rho, alpha))",
+                                     "if (orc_ldl_solve(k, rho, pi, alpha))"),
+    "block_residual_sign": ("r = r - Q[i + m * n] * alpha[m + j * k];",
+                            "r = r + Q[i + m * n] * alpha[m + j * k];"),
+    "block_rho_unpreconditioned": ("orc_gram(n, k, Z, R, rho2);", "orc_gram(n, k, R, R, rho2);"),
+    "block_beta_transposed": ("p = p + P[i + m * n] * beta[m + j * k];",
+                              "p = p + P[i + m * n] * beta[j + m * k];"),
+    "block_alpha_transposed_in_x": ("x = x + P[i + m * n] * alpha[m + j * k];",
+                                    "x = x + P[i + m * n] * alpha[j + m * k];"),
+    "block_no_preconditioner": ("for (size_t e = 0; e < nk; ++e) Z[e] = dinv[e % (size_t)n] * R[e];",
+                                "for (size_t e = 0; e < nk; ++e) Z[e] = R[e];"),
+    "ldl_pivot_update_dropped": ("for (int m = 0; m < j; ++m) d -= L[j + m * k] * L[j + m * k] * D[m];",
+                                 "for (int m = 0; m < j; ++m) d -= L[j + m * k] * D[m];"),
 }
 
 PINS = [
@@ -94,6 +107,9 @@ PINS = [
     lambda o: P.test_coo_degenerate_and_invalid(o),
     lambda o: P.test_pcg_norms_with_constant_diagonal_scale_exactly(o),
     lambda o: P.test_pcg_norms_follow_their_definitions(o),
+    lambda o: P.test_block_pcg_iterates_are_block_krylov_minimisers(o, 2),
+    lambda o: P.test_block_pcg_finite_termination(o, 2, 3),
+    lambda o: P.test_block_pcg_against_dense_solve_and_fewer_steps(o),
 ]
 
 

@@ -559,3 +559,94 @@ def test_coo_assembly_of_edge_contributions_is_the_laplacian(orc):
         assert st == 0
         assert np.array_equal(rp, A.rowptr) and np.array_equal(ci, A.colidx)
         assert np.array_equal(vals, A.vals)
+
+
+# -------------------------------------------------------------- block CG --
+
+def block_rhs(orc, A, k, seed):
+    return np.stack([orc.spmv(A, I.xstar(A.n, seed + 17 * j)) for j in range(k)], axis=1)
+
+
+@pytest.mark.parametrize("maker", [lambda: I.lap2d5(20), lambda: I.var7(9, 8, 7, seed=3),
+                                   lambda: I.var27(6, seed=5)])
+def test_block_pcg_with_one_column_is_pcg_bitwise(orc, maker):
+    """k = 1: every block operation reduces to the PCG operation (the 1 x 1
+    LDL solve is one division), so the iterates are bitwise the PCG ones."""
+    A = maker()
+    b = block_rhs(orc, A, 1, 3)[:, 0]
+    for rtol, maxit in ((1e-10, 5000), (0.0, 7)):
+        r = orc.pcg(A, b, rtol, maxit)
+        q = orc.block_pcg(A, b, rtol, maxit)
+        assert q["status"] == r["status"] and q["iters"] == r["iters"]
+        assert np.array_equal(q["x"][:, 0], r["x"])
+        assert q["rnorm"][0] == r["rnorm"]
+
+
+def block_krylov_minimiser(A, B, j):
+    """Dense reference for the j-th block PCG iterate from X0 = 0: the
+    minimiser of trace((X - X*)^T A (X - X*)) over X in the block Krylov
+    space span{Z0, (D^-1 A) Z0, ..., (D^-1 A)^(j-1) Z0} (each column a
+    combination of all jk basis vectors), Z0 = D^-1 B, by Galerkin
+    projection on an orthonormal basis."""
+    d = A.to_dense()
+    dinv = 1.0 / np.diag(d)
+    V = dinv[:, None] * B
+    basis = []
+    for _ in range(j):
+        basis.append(V)
+        V = dinv[:, None] * (d @ V)
+    Q, _ = np.linalg.qr(np.concatenate(basis, axis=1))
+    return Q @ np.linalg.solve(Q.T @ d @ Q, Q.T @ B)
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 4])
+def test_block_pcg_iterates_are_block_krylov_minimisers(orc, j):
+    A = I.var5(9, 8, seed=31, sigma=0.5)                # non-constant diagonal
+    B = block_rhs(orc, A, 3, 5)
+    r = orc.block_pcg(A, B, rtol=0.0, maxit=j)
+    assert r["status"] == orc.DIVERGED_ITS and r["iters"] == j
+    ref = block_krylov_minimiser(A, B, j)
+    assert np.linalg.norm(r["x"] - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("k,steps", [(1, 6), (2, 3), (3, 2), (6, 1)])
+def test_block_pcg_finite_termination(orc, k, steps):
+    """The 1D tridiagonal of 6 rows has 6 distinct eigenvalues (simple):
+    the block Krylov space of k generic columns holds the solution after
+    ceil(6 / k) block steps, and not one step earlier."""
+    A = I.lap2d5(6, 1)
+    B = block_rhs(orc, A, k, 2)
+    r = orc.block_pcg(A, B, rtol=1e-12, maxit=50)
+    assert r["status"] == orc.CONVERGED and r["iters"] == steps
+    if steps > 1:
+        r1 = orc.block_pcg(A, B, rtol=1e-12, maxit=steps - 1)
+        assert r1["status"] == orc.DIVERGED_ITS
+        assert np.max(r1["rnorm"] / r1["bnorm"]) > 1e-6
+
+
+def test_block_pcg_against_dense_solve_and_fewer_steps(orc):
+    A = I.var7(7, 6, 5, seed=8)
+    B = block_rhs(orc, A, 4, 9)
+    r = orc.block_pcg(A, B, rtol=1e-12, maxit=1000)
+    X = np.linalg.solve(A.to_dense(), B)
+    assert r["status"] == orc.CONVERGED
+    assert np.linalg.norm(r["x"] - X) <= 1e-9 * np.linalg.norm(X)
+    assert np.all(r["rnorm"] <= 1e-12 * r["bnorm"])
+    # the shared block space needs fewer steps than the slowest single column
+    single = max(orc.pcg(A, B[:, j], 1e-12, 1000)["iters"] for j in range(4))
+    assert r["iters"] < single
+
+
+def test_block_pcg_breakdown_and_degenerate(orc):
+    A = I.lap2d5(5)
+    b = block_rhs(orc, A, 1, 4)[:, 0]
+    # two equal columns: P^T A P is singular at the first step
+    r = orc.block_pcg(A, np.stack([b, b], axis=1), 1e-10, 100)
+    assert r["status"] == orc.ERR_INDEFINITE
+    # zero right-hand sides converge at once
+    r = orc.block_pcg(A, np.zeros((A.n, 3)), 1e-10, 100)
+    assert r["status"] == orc.CONVERGED and r["iters"] == 0 and not r["x"].any()
+    # iteration limit
+    B = block_rhs(orc, A, 2, 1)
+    r = orc.block_pcg(A, B, 1e-14, 2)
+    assert r["status"] == orc.DIVERGED_ITS and r["iters"] == 2
