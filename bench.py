@@ -876,6 +876,7 @@ def c4_batched(g, args):
     res = {"systems": nsys, "rhs_per_system": 8, "rows_total": n_tot, "nnz_total": nnz_tot,
            "setup_s": t_gen}
     sols = {}
+    its_by_mode = {}
     for name, mode in (("mixed", gbs.GBS_MODE_MIXED), ("fp64", gbs.GBS_MODE_FP64)):
         times, dev = [], []
         for rep in range(2):
@@ -908,6 +909,7 @@ def c4_batched(g, args):
                 sl = slice(c * A.n, (c + 1) * A.n)
                 worst = max(worst, float(torch.linalg.norm(bt[sl] - rt[sl]) / torch.linalg.norm(bt[sl])))
         sols[name] = [xt.clone() for xt in xts]
+        its_by_mode[name] = its
         res[name] = {"seconds": min(times), "solves_per_s": ncols / min(times),
                      "quanta_device_s": min(dev),
                      "model_GB": model_bytes / 1e9,
@@ -937,6 +939,45 @@ def c4_batched(g, args):
                           for m in ("mixed", "fp64")}})
     res["oracle_sample"] = sample
     res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+    # block CG (FP64): the 8 columns of a system share one search space; one
+    # cooperative launch per system, systems one after another
+    for xt in xts:
+        xt.zero_()
+    torch.cuda.synchronize()
+    l0 = g.launches()
+    t = time.perf_counter()
+    its_b, ok_b = [], 0
+    for (h, A, k), bv, xv in zip(mats, bvs, xvs):
+        info_b, _rn = gbs.gbs_ksp_solve_cg_block(h, k, bv, xv, 1e-10, 20000)
+        its_b.append(info_b.iters)
+        ok_b += info_b.status == 0
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    lb = g.launches() - l0
+    worst_b = 0.0
+    for (h, A, k), bt, xt in zip(mats, bts, xts):
+        rt = torch.empty_like(bt)
+        for c in range(k):
+            xv1 = gbs.gbs_vec_wrap(g.ctx, xt[c * A.n:(c + 1) * A.n])
+            rv1 = gbs.gbs_vec_wrap(g.ctx, rt[c * A.n:(c + 1) * A.n])
+            gbs.gbs_mat_mult(h, xv1, rv1)
+            gbs.gbs_vec_destroy(xv1)
+            gbs.gbs_vec_destroy(rv1)
+            sl = slice(c * A.n, (c + 1) * A.n)
+            worst_b = max(worst_b, float(torch.linalg.norm(bt[sl] - rt[sl]) / torch.linalg.norm(bt[sl])))
+    # independent CG per system: its slowest column's iterations (FP64 batched run)
+    indep = []
+    o = 0
+    for (h, A, k) in mats:
+        indep.append(int(max(its_by_mode["fp64"][o:o + k])))
+        o += k
+    res["block_fp64"] = {"seconds": tb, "solves_per_s": ncols / tb, "systems_ok": int(ok_b),
+                         "block_iters_mean": float(np.mean(its_b)), "block_iters_max": int(max(its_b)),
+                         "independent_cg_iters_mean": float(np.mean(indep)),
+                         "independent_cg_iters_max": int(max(indep)),
+                         "iteration_ratio_block_over_independent": float(np.sum(its_b) / np.sum(indep)),
+                         "max_true_rel_residual": worst_b, "kernel_launches": int(lb),
+                         "note": "one launch per system (the batched engine runs independent columns)"}
     # the batched engine's tuner decisions (cached per class during the
     # solves): one system of each stencil family
     tuned = {}

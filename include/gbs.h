@@ -438,6 +438,27 @@ int gbs_ksp_tune(gbs_mat A, int mode, int *shape, int *lanes);
 int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, double rtol, int maxit,
                              gbs_solve_info *info);
 
+/* Block Jacobi-preconditioned CG for k right-hand sides of one matrix at
+ * once (Sec. 3, Challenge F2: Krylov methods with multiple right-hand sides
+ * raise arithmetic intensity and converge in fewer iterations; the block
+ * method is O'Leary's block CG, which the paper reaches through KSPHPDDM).
+ * The k columns share one search space: per iteration Q = A P (one pass
+ * over the matrix for all columns), alpha = (P^T Q)^-1 (Z^T R),
+ * X += P alpha, R -= Q alpha, Z = D^-1 R, beta = (Z^T R)_old^-1 (Z^T R),
+ * P = Z + P beta, with the k x k systems solved by LDL^T.  FP64.
+ * B (read) and X (initial guess in, solution out): vectors of nrows * k
+ * entries, column-major (column j at offset j * nrows); 1 <= k <= 8.
+ * Stopping test before each iteration: every column ||R_j||_2 <= rtol
+ * ||B_j||_2.  info->iters = block iterations; info->rnorm / bnorm = the
+ * largest column norms; rnorm[k] (may be NULL) receives each column's
+ * final ||R_j||_2 (recurrence residual).  One cooperative launch.
+ * Statuses: GBS_OK, GBS_DIVERGED_ITS, GBS_ERR_INDEFINITE (P^T A P or
+ * Z^T R not positive definite: A indefinite, or the columns of B, or of
+ * the residual block, linearly dependent), GBS_ERR_NAN, GBS_ERR_DIAG,
+ * GBS_ERR_TIMEOUT; GBS_ERR_ARG for bad sizes or k out of range. */
+int gbs_ksp_solve_cg_block(gbs_mat A, int k, gbs_vec B, gbs_vec X, double rtol, int maxit,
+                           gbs_solve_info *info, double *rnorm);
+
 /* Batched solve of independent systems in one persistent launch (Response
  * A6, Sec. 4: many different-size problems at once; Challenge F2 / Sec. 4:
  * multiple right-hand sides raise arithmetic intensity).  System s has

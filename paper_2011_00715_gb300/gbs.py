@@ -148,6 +148,8 @@ _SIGS = {
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "gbs_batched_tune": ([_VP, _VP, ctypes.c_int, ctypes.c_int, _I32P], ctypes.c_int),
     "gbs_ksp_tune": ([_VP, ctypes.c_int, _I32P, _I32P], ctypes.c_int),
+    "gbs_ksp_solve_cg_block": ([_VP, ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                ctypes.POINTER(gbs_solve_info), _VP], ctypes.c_int),
     "gbs_server_progress": ([_VP, _I32P], ctypes.c_int),
     "gbs_server_poll": ([_VP, ctypes.c_uint64, _I32P], ctypes.c_int),
     "gbs_server_wait": ([_VP, ctypes.c_uint64], ctypes.c_int),
@@ -486,6 +488,19 @@ def gbs_ksp_solve_chebyshev(A, b, x, emin: float, emax: float, rtol: float, maxi
     if st not in _RESULT_STATUSES:
         _check(st, "gbs_ksp_solve_chebyshev")
     return _info(info)
+
+
+def gbs_ksp_solve_cg_block(A, k: int, B, X, rtol: float, maxit: int):
+    """Block Jacobi-PCG for the k columns of B (a gbs_vec of n * k entries,
+    column-major) into X.  Returns (SolveInfo, per-column final residual
+    norms as a numpy array)."""
+    info = gbs_solve_info()
+    rn = np.zeros(int(k))
+    st = lib().gbs_ksp_solve_cg_block(A, int(k), B, X, float(rtol), int(maxit), ctypes.byref(info),
+                                      rn.ctypes.data)
+    if st not in _RESULT_STATUSES:
+        _check(st, "gbs_ksp_solve_cg_block")
+    return _info(info), rn
 
 
 def gbs_ksp_tune(A, mode: int):
