@@ -345,14 +345,15 @@ def event_time(torch, fn, reps):
     return e0.elapsed_time(e1) / 1e3
 
 
-# DRAM traffic of one iteration of the persistent FP64 kernel on the 128^3
+# DRAM traffic of one SpMV pass of the persistent FP64 kernel on the 128^3
 # workload, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# of a launch capped at 20 iterations, divided by its 21 SpMV passes), with
-# the hash of the kernel sources it was taken on; the roofline reports the
-# traffic scaled to the full launch only while the sources are unchanged.
+# of a launch capped at 20 iterations, divided by its 21 SpMV passes: the
+# set-up and 20 iterations), with the hash of the kernel sources it was taken
+# on; the roofline reports the traffic scaled to the full launch (iterations
+# + 1 passes) only while the sources are unchanged.
 TRAFFIC_SOURCES = ("paper_2011_00715_gb300/csrc/solve.cu", "paper_2011_00715_gb300/csrc/gbs_impl.cuh")
-TRAFFIC_PER_ITER = {"sha256": "751b5f3cdc2c54dff4935090638606c5da5d5f00ec2aabdd34a397e498a95c7a",
-                    "bytes": 300391411}
+TRAFFIC_PER_ITER = {"sha256": "abfa65ad439dca936c3c1e94bc3a2462856b414a0c40da453e062454a1221a6c",
+                    "bytes": 268130000}
 
 
 def kernel_source_hash():
@@ -367,7 +368,7 @@ def kernel_source_hash():
 def measured_traffic(iters):
     if TRAFFIC_PER_ITER["bytes"] is None or TRAFFIC_PER_ITER["sha256"] != kernel_source_hash():
         return None
-    return TRAFFIC_PER_ITER["bytes"] * iters
+    return TRAFFIC_PER_ITER["bytes"] * (iters + 1)
 
 
 def run_gbs(args, rank, world, local):
