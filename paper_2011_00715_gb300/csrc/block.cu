@@ -61,6 +61,7 @@ struct BcgShared {
     double tot[kSlotsB];          // grid totals of the last reduction
     double rho[kKmax * kKmax];    // Z^T R (column-major, full)
     double mat[kKmax * kKmax];    // alpha or beta (column-major)
+    double fac[kKmax * kKmax + kKmax];   // L and 1 / D of the last LDL^T
     double bn[kKmax];
     int go, status, it, pad;
 };
@@ -69,40 +70,78 @@ struct BcgShared {
 __device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
 // Solve S Y = C (k x k, column-major, S symmetric positive definite) with
-// S = L D L^T: lane c < k solves for column c (each lane factors S itself,
-// same operations, so no exchange is needed).  Returns false in every lane
-// if a pivot is not positive.  Warp 0 only.
-__device__ __noinline__ bool ldl_solve_warp(int k, const double *S, const double *C, double *Y)
+// S = L D L^T, L unit lower triangular, no square roots.  Warp 0 only.
+// Factorisation: lane i holds row i of L; at step j every lane forms the
+// pivot d_j from row j (shuffled from lane j), then lanes i > j form
+// L_ij; one reciprocal per pivot.  The factors go to shared memory (fl,
+// 64 + 8 entries), then lane c < k solves for column c by forward and back
+// substitution.  Returns false in every lane if a pivot is not positive.
+__device__ __noinline__ bool ldl_solve_warp(int k, const double *S, const double *C, double *Y,
+                                            double *fl)
 {
     const int lane = threadIdx.x & 31;
-    double L[kKmax * kKmax], D[kKmax];
+    double Lrow[kKmax];   // this lane's row of L (lane < k), columns < lane
+    double D[kKmax], Di[kKmax];
+#pragma unroll
+    for (int m = 0; m < kKmax; ++m) Lrow[m] = 0.0;
     bool ok = true;
-    for (int j = 0; j < k; ++j) {
+#pragma unroll
+    for (int j = 0; j < kKmax; ++j) {
+        if (j >= k) break;
+        // row j of L from lane j, and the pivot
+        double lj[kKmax];
+#pragma unroll
+        for (int m = 0; m < kKmax; ++m) lj[m] = __shfl_sync(0xffffffffu, Lrow[m], j);
         double d = S[j + j * k];
-        for (int m = 0; m < j; ++m) d -= L[j + m * k] * L[j + m * k] * D[m];
+#pragma unroll
+        for (int m = 0; m < kKmax; ++m)
+            if (m < j) d -= lj[m] * lj[m] * D[m];
         if (!(d > 0.0)) ok = false;
         D[j] = d;
-        for (int i = j + 1; i < k; ++i) {
-            double v = S[i + j * k];
-            for (int m = 0; m < j; ++m) v -= L[i + m * k] * L[j + m * k] * D[m];
-            L[i + j * k] = v / d;
+        Di[j] = 1.0 / d;
+        if (lane > j && lane < k) {
+            double v = S[lane + j * k];
+#pragma unroll
+            for (int m = 0; m < kKmax; ++m)
+                if (m < j) v -= Lrow[m] * lj[m] * D[m];
+            Lrow[j] = v * Di[j];
         }
     }
+    if (lane < k)
+#pragma unroll
+        for (int m = 0; m < kKmax; ++m)
+            if (m < lane) fl[lane + m * k] = Lrow[m];
+    if (lane < k) fl[64 + lane] = Di[lane];
+    __syncwarp();
     if (ok && lane < k) {
         const int c = lane;
         double y[kKmax];
-        for (int i = 0; i < k; ++i) {
+#pragma unroll
+        for (int i = 0; i < kKmax; ++i) {
+            if (i >= k) break;
             double v = C[i + c * k];
-            for (int m = 0; m < i; ++m) v -= L[i + m * k] * y[m];
+#pragma unroll
+            for (int m = 0; m < kKmax; ++m)
+                if (m < i) v -= fl[i + m * k] * y[m];
             y[i] = v;
         }
-        for (int i = 0; i < k; ++i) y[i] = y[i] / D[i];
-        for (int i = k - 1; i >= 0; --i) {
+#pragma unroll
+        for (int i = 0; i < kKmax; ++i)
+            if (i < k) y[i] = y[i] * fl[64 + i];
+#pragma unroll
+        for (int i = kKmax - 1; i >= 0; --i) {
+            if (i >= k) continue;
             double v = y[i];
-            for (int m = i + 1; m < k; ++m) v -= L[m + i * k] * Y[m + c * k];
-            Y[i + c * k] = v;
+#pragma unroll
+            for (int m = 0; m < kKmax; ++m)
+                if (m > i && m < k) v -= fl[m + i * k] * y[m];
+            y[i] = v;
         }
+#pragma unroll
+        for (int i = 0; i < kKmax; ++i)
+            if (i < k) Y[i + c * k] = y[i];
     }
+    __syncwarp();
     return ok;
 }
 
@@ -310,7 +349,7 @@ __global__ void __launch_bounds__(kBT, 1) k_block_cg(BcgArgs a)
             double pi[kKmax * kKmax];
             for (int i = 0; i < k; ++i)
                 for (int j = 0; j <= i; ++j) pi[i + j * k] = pi[j + i * k] = sh.tot[tri(i, j)];
-            const bool ok = ldl_solve_warp(k, pi, sh.rho, sh.mat);   // alpha
+            const bool ok = ldl_solve_warp(k, pi, sh.rho, sh.mat, sh.fac);   // alpha
             if (lane == 0 && !ok) {
                 sh.status = GBS_ERR_INDEFINITE;
                 sh.go = 0;
@@ -355,7 +394,7 @@ __global__ void __launch_bounds__(kBT, 1) k_block_cg(BcgArgs a)
             double rho2[kKmax * kKmax];
             for (int i = 0; i < k; ++i)
                 for (int j = 0; j <= i; ++j) rho2[i + j * k] = rho2[j + i * k] = sh.tot[np + tri(i, j)];
-            const bool ok = ldl_solve_warp(k, sh.rho, rho2, sh.mat);   // beta
+            const bool ok = ldl_solve_warp(k, sh.rho, rho2, sh.mat, sh.fac);   // beta
             __syncwarp();
             if (lane == 0) {
                 sh.it = it + 1;
@@ -451,8 +490,11 @@ extern "C" int gbs_ksp_solve_cg_block(gbs_mat A, int k, gbs_vec B, gbs_vec X, do
         int per_sm = 0;
         GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBT, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
+        // one CTA per 4 warp tiles at most: a block iteration's vector work
+        // (about 3 k^2 + k^2 FP64 operations per row) is bound by the FP64
+        // rate, so it wants every SM well before the SpMV does
         int64_t g = (int64_t)per_sm * c->num_sms;
-        const int64_t need = (A->ntiles + kBW - 1) / kBW;
+        const int64_t need = (A->ntiles + 3) / 4;
         if (g > need) g = need;
         if (c->opts.persistent_ctas > 0 && c->opts.persistent_ctas < g) g = c->opts.persistent_ctas;
         const int G = g < 1 ? 1 : (int)g;

@@ -16,7 +16,9 @@ the partition, the halo plan and the collective schedule are the same code
 whether the local work runs in the library on a GPU (GbsOps, NCCL: the
 SpMV, Jacobi apply, AXPY/AYPX, copies and dots all in the library's
 kernels) or, in the CPU tests, in another implementation (gloo ranks).
-The scalar recurrence runs here, on the host, on the all-reduced sums.
+The scalar recurrence runs here, on the host, on the all-reduced sums: per
+iteration the host waits twice, for the results of the two all-reduces
+(the dot products feeding each are left on the device).
 """
 from __future__ import annotations
 
@@ -133,6 +135,12 @@ class NumpyOps:
     def dot(self, a, b):
         return float(a[: len(b)].numpy() @ b.numpy())
 
+    def dots(self, pairs):
+        """Local partial sums a . b of every pair, as a tensor (the input of
+        one all-reduce)."""
+        import torch
+        return torch.tensor([self.dot(a, b) for a, b in pairs], dtype=torch.float64)
+
     def axpy(self, y, alpha, x):       # y <- alpha x + y
         y += alpha * x
 
@@ -149,8 +157,11 @@ class NumpyOps:
 class GbsOps:
     """Local operations in the library on this rank's GPU: the local block as
     a gbs matrix over [own | ghosts] columns (its Jacobi inverse diagonal made
-    at creation), vectors as CUDA tensors wrapped per call; every vector
-    operation runs in the library's kernels."""
+    at creation), vectors as CUDA tensors; every vector operation runs in the
+    library's kernels.  Each tensor (or slice) is wrapped once and its handle
+    kept until close(), and the dot products of one reduction point are
+    written in stream order into a device buffer that the all-reduce then
+    sums, so no host synchronisation happens before the all-reduce."""
     def __init__(self, ctx, blk: LocalBlock):
         import torch
         from . import gbs
@@ -160,6 +171,8 @@ class GbsOps:
         self.torch = torch
         self.A = gbs.gbs_mat_create_aij(ctx, blk.n_own, blk.ncols, blk.rowptr, blk.colidx, blk.vals)
         self.pc = None
+        self._handles = {}
+        self._keep = []
 
     def setup(self, blk):
         self.pc = self.gbs.gbs_pc_jacobi_create(self.A)   # GBS_ERR_DIAG -> GbsError
@@ -167,33 +180,44 @@ class GbsOps:
     def vec(self, a):
         return self.torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
 
-    def _call(self, fn, *tensors, scalar=None):
-        vs = [self.gbs.gbs_vec_wrap(self.ctx, t) for t in tensors]
-        try:
-            return fn(*vs) if scalar is None else fn(vs[0], scalar, *vs[1:])
-        finally:
-            for v in vs:
-                self.gbs.gbs_vec_destroy(v)
+    def _h(self, t):
+        key = (t.data_ptr(), t.numel())
+        h = self._handles.get(key)
+        if h is None:
+            h = self.gbs.gbs_vec_wrap(self.ctx, t)
+            self._handles[key] = h
+            self._keep.append(t)   # the wrapped memory stays alive with its handle
+        return h
 
     def spmv(self, blk, v, out):
-        self._call(lambda xv, yv: self.gbs.gbs_mat_mult(self.A, xv, yv), v, out)
+        self.gbs.gbs_mat_mult(self.A, self._h(v), self._h(out))
 
     def dot(self, a, b):
-        return self._call(self.gbs.gbs_vec_dot, a[: len(b)], b)
+        return self.gbs.gbs_vec_dot(self._h(a[: len(b)]), self._h(b))
+
+    def dots(self, pairs):
+        out = self.torch.empty(len(pairs), dtype=self.torch.float64, device="cuda")
+        for j, (a, b) in enumerate(pairs):
+            self.gbs.gbs_vec_dot_async(self._h(a[: len(b)]), self._h(b), out[j:j + 1])
+        return out
 
     def axpy(self, y, alpha, x):
-        self._call(self.gbs.gbs_vec_axpy, y, x, scalar=alpha)
+        self.gbs.gbs_vec_axpy(self._h(y), alpha, self._h(x))
 
     def aypx(self, y, beta, x):
-        self._call(self.gbs.gbs_vec_aypx, y, x, scalar=beta)
+        self.gbs.gbs_vec_aypx(self._h(y), beta, self._h(x))
 
     def jacobi(self, r, z):
-        self._call(lambda rv, zv: self.gbs.gbs_pc_apply(self.pc, rv, zv), r, z)
+        self.gbs.gbs_pc_apply(self.pc, self._h(r), self._h(z))
 
     def copy(self, x, y):
-        self._call(self.gbs.gbs_vec_copy, x, y)
+        self.gbs.gbs_vec_copy(self._h(x), self._h(y))
 
     def close(self):
+        for h in self._handles.values():
+            self.gbs.gbs_vec_destroy(h)
+        self._handles.clear()
+        self._keep.clear()
         if self.pc is not None:
             self.gbs.gbs_pc_destroy(self.pc)
         self.gbs.gbs_mat_destroy(self.A)
@@ -221,9 +245,13 @@ def halo_exchange(blk: LocalBlock, v, group=None):
 
 
 def allreduce_sum(vals, device, group=None):
+    """Sum a list of host values, or a tensor of partial sums already on the
+    device (summed in place), over the ranks; the totals come back to the
+    host for the scalar recurrence."""
     import torch
     import torch.distributed as dist
-    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    t = vals if isinstance(vals, torch.Tensor) else torch.tensor(vals, dtype=torch.float64,
+                                                                  device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.tolist()
 
@@ -245,7 +273,7 @@ def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None
     p = ops.vec(np.zeros(blk.ncols))
     ops.copy(z, p[:n])
     q = ops.vec(np.zeros(n))
-    rho, rr, bb = allreduce_sum([ops.dot(r, z), ops.dot(r, r), ops.dot(b, b)], ops.device, group)
+    rho, rr, bb = allreduce_sum(ops.dots([(r, z), (r, r), (b, b)]), ops.device, group)
     bnorm = math.sqrt(bb)
     k = 0
     status = 1
@@ -261,7 +289,7 @@ def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None
             break
         halo_exchange(blk, p, group)
         ops.spmv(blk, p, q)
-        (pq,) = allreduce_sum([ops.dot(p, q)], ops.device, group)
+        (pq,) = allreduce_sum(ops.dots([(p, q)]), ops.device, group)
         if math.isnan(pq):
             status = -6
             break
@@ -272,7 +300,7 @@ def sharded_pcg(blk: LocalBlock, ops, b_own, rtol: float, maxit: int, group=None
         ops.axpy(x, alpha, p[:n])
         ops.axpy(r, -alpha, q)
         ops.jacobi(r, z)
-        rho_new, rr = allreduce_sum([ops.dot(r, z), ops.dot(r, r)], ops.device, group)
+        rho_new, rr = allreduce_sum(ops.dots([(r, z), (r, r)]), ops.device, group)
         k += 1
         if rho_new < 0.0:
             status = -5

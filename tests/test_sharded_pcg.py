@@ -46,6 +46,18 @@ def _local_spmv(blk, v):
     return orc.spmv(I.CSR(blk.n_own, blk.rowptr, blk.colidx, blk.vals), v)
 
 
+class _NoBlockingDotOps(sharded.NumpyOps):
+    """The driver must take its dot products through dots() (partials left
+    where the all-reduce reads them), never through a blocking dot()."""
+    def dot(self, a, b):
+        raise AssertionError("blocking dot product in the sharded driver")
+
+    def dots(self, pairs):
+        import torch
+        return torch.tensor([sharded.NumpyOps.dot(self, a, b) for a, b in pairs],
+                            dtype=torch.float64)
+
+
 def _worker(rank, world, port, out_dir, maker):
     import torch
     import torch.distributed as dist
@@ -63,7 +75,7 @@ def _worker(rank, world, port, out_dir, maker):
         assert torch.equal(v[blk.n_own:], torch.as_tensor(blk.ghosts, dtype=torch.float64))
         import oracle as orc
         b = orc.spmv(A, I.xstar(A.n, 21))
-        x, st, k, rn, bn = sharded.sharded_pcg(blk, sharded.NumpyOps(_local_spmv),
+        x, st, k, rn, bn = sharded.sharded_pcg(blk, _NoBlockingDotOps(_local_spmv),
                                                b[blk.lo:blk.hi], 1e-10, 20000)
         parts = [None] * world
         dist.all_gather_object(parts, (blk.lo, x.numpy(), st, k, rn, bn))
