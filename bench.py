@@ -179,12 +179,15 @@ def ops_per_iter_fp64(n, nnz):
     return nnz + 6 * n
 
 
-def bytes_per_iter_fp64(n, nnz, index_bytes=4):
+def bytes_per_iter_fp64(n, nnz, index_bytes=4, vector_bytes=108):
     """Fused FP64 PCG iteration: (8 + index bytes) nnz (values + column
     indices: 12 nnz with 32-bit indices, 10 with the 16-bit column offsets
-    the library streams where they fit) + 108 n (rowptr 4n, p gather 8n,
-    q write 8n, update phase 64n, p update 24n)."""
-    return (8 + index_bytes) * nnz + 108 * n
+    the library streams where they fit) + vector bytes per row: 108 n in
+    the survey's model of the iteration (rowptr 4n, p gather 8n, q write 8n,
+    update phase with x += alpha p 64n, p update 24n); 100 n as the kernel
+    orders the passes (the x update moves into the p update, which reads p
+    anyway: update 40n, p and x update 40n)."""
+    return (8 + index_bytes) * nnz + vector_bytes * n
 
 
 def bytes_spmv_fp64(n, nnz, index_bytes=4):
@@ -463,8 +466,9 @@ def run_gbs(args, rank, world, local):
                          "frac": achieved / hbm,
                          "traffic": measured_traffic(iters[0]),
                          "kernel": "k_pcg_fp64 (one launch per solve)",
-                         "bytes_model": "set-up (10 nnz + 52 n) + iters x (10 nnz + 108 n): "
-                                        "8-byte values and 16-bit column offsets",
+                         "bytes_model": "set-up (10 nnz + 52 n) + iters x (10 nnz + 100 n) + 24 n: "
+                                        "8-byte values, 16-bit column offsets, x += alpha p in "
+                                        "the p update",
                          "bytes_per_launch": bpl,
                          "frac_by_csr32_model": achieved_csr32 / hbm,
                          "csr32_model": "iters x (12 nnz + 108 n), 32-bit column indices",

@@ -327,19 +327,19 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         }
         const T alpha = ctl.alpha;
 
-        // ---- U: x += alpha p; r -= alpha q; z = D^-1 r; partials r.z, r.r
-        // (UNR rows per thread per trip: all 5 UNR loads are issued before
-        // the first use)
+        // ---- U: r -= alpha q; z = D^-1 r; partials r.z (and r.r).  The
+        // solution update x += alpha p waits for the P phase, which reads p
+        // anyway (8 bytes per row fewer than doing it here); an exit right
+        // after U applies it in a pass of its own.  (UNR rows per thread per
+        // trip: all loads are issued before the first use.)
         const bool need_rr = ctl.need_rr != 0;
         T u[2] = {T(0), T(0)};
         for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
-            T pv[UNR], xv[UNR], rv[UNR], qv[UNR], dv[UNR];
+            T rv[UNR], qv[UNR], dv[UNR];
 #pragma unroll
             for (int h = 0; h < UNR; ++h) {
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
-                    pv[h] = gbs_ld(pT + i, pk);
-                    xv[h] = gbs_ld(xT + i, pk);
                     rv[h] = gbs_ld(rT + i, pk);
                     qv[h] = gbs_ld(qT + i, pk);
                     dv[h] = gbs_ld(dinv + i, pk);
@@ -350,7 +350,6 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
                     const T rn_ = rv[h] - alpha * qv[h], zn_ = dv[h] * rn_;
-                    gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
                     gbs_st(rT + i, rn_, pk);
                     gbs_st(zT + i, zn_, pk);
                     u[0] += rn_ * zn_;
@@ -429,24 +428,33 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
             }
         }
         __syncthreads();
-        if (!ctl.go) break;
+        if (!ctl.go) {
+            // the loop ends after this update: x += alpha p on own rows
+            for (int64_t i = rb + threadIdx.x; i < re; i += NT)
+                gbs_st(xT + i, gbs_ld(xT + i, pk) + alpha * gbs_ld(pT + i, pk), pk);
+            break;
+        }
         const T beta = ctl.beta;
 
-        // ---- P: p = z + beta p
+        // ---- P: x += alpha p (the update U left), p = z + beta p
         for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
-            T zv[UNR], pv[UNR];
+            T zv[UNR], pv[UNR], xv[UNR];
 #pragma unroll
             for (int h = 0; h < UNR; ++h) {
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
                     zv[h] = gbs_ld(zT + i, pk);
                     pv[h] = gbs_ld(pT + i, pk);
+                    xv[h] = gbs_ld(xT + i, pk);
                 }
             }
 #pragma unroll
             for (int h = 0; h < UNR; ++h) {
                 const int64_t i = i0 + h * NT;
-                if (i < re) gbs_st(pT + i, zv[h] + beta * pv[h], pk);
+                if (i < re) {
+                    gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
+                    gbs_st(pT + i, zv[h] + beta * pv[h], pk);
+                }
             }
         }
         if (!gbs_grid_sync(a.bar, a.timeout_ns, (*barrier_no)++, false, s_flag))
@@ -662,23 +670,25 @@ int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0,
 // vector entry is counted once per pass that reads or writes it.
 //  FP64: the set-up pass (r = b - A x: matrix, row pointers, x gather, b
 //  and D^-1 read, r, z, p written) and per iteration the S phase (matrix,
-//  row pointers, p gather, q written: 4n + 16n), U (x, p, r, q, D^-1 read,
-//  x, r, z written: 64n) and P (z, p read, p written: 24n), i.e.
-//  (8 + ib) nnz + 108 n per iteration.
+//  row pointers, p gather, q written: 4n + 16n), U (r, q, D^-1 read, r, z
+//  written: 40n) and P (z, p, x read, p, x written: 40n), i.e.
+//  (8 + ib) nnz + 100 n per iteration, and the final x += alpha p pass.
 //  Mixed: per refinement step the FP64 residual (12 nnz with 32-bit
 //  indices + 4n row pointers + 8n gather + 8n b read + 8n r written), the
 //  scaling to FP32 (8n read, 4n written) and the FP64 update (16n x, 4n
 //  FP32 solution); per inner solve its set-up (b32, D^-1 read, x, r, z, p
-//  written: 24n) and per inner iteration (4 + ib) nnz + 56 n.
+//  written: 24n) and final x pass (12n); per inner iteration
+//  (4 + ib) nnz + 52 n.
 double persistent_model_bytes(gbs_mat A, bool mixed, int ib, const gbs_solve_info &r)
 {
     const double n = (double)A->n, nnz = (double)A->nnz;
     if (!mixed)
-        return ((8.0 + ib) * nnz + 52.0 * n + 4.0) + (double)r.iters * ((8.0 + ib) * nnz + 108.0 * n);
+        return ((8.0 + ib) * nnz + 52.0 * n + 4.0) + (double)r.iters * ((8.0 + ib) * nnz + 100.0 * n) +
+               (r.iters > 0 ? 24.0 * n : 0.0);
     const double outer = (double)r.outer_iters + 1.0;   // residual passes
     const double inner_solves = (double)r.outer_iters;
-    return outer * (12.0 * nnz + 36.0 * n) + inner_solves * (12.0 * n + 20.0 * n + 24.0 * n) +
-           (double)r.iters * ((4.0 + ib) * nnz + 56.0 * n);
+    return outer * (12.0 * nnz + 36.0 * n) + inner_solves * (12.0 * n + 20.0 * n + 24.0 * n + 12.0 * n) +
+           (double)r.iters * ((4.0 + ib) * nnz + 52.0 * n);
 }
 
 // Launch a persistent kernel and read its result record (one host
