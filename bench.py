@@ -69,6 +69,8 @@ def parse_args():
                    help="run only the vector-operation / MatMult size sweep")
     p.add_argument("--c5-pool", type=int, default=12,
                    help="distinct operators the serving requests draw from")
+    p.add_argument("--c3-only", action="store_true",
+                   help="run only the C3 solves and the 27-point MatMult sweep")
     p.add_argument("--c1-only", action="store_true",
                    help="run only the C1 solves (profiling of the one-cluster kernel)")
     p.add_argument("--c5-warmup", type=int, default=100,
@@ -172,8 +174,8 @@ FP64_NOMINAL_GOPS = 625.0
 
 def ops_per_iter_fp64(n, nnz):
     """FP64 operations of one fused PCG iteration: one per nonzero in the
-    SpMV, one per row for p.q, four per row in the update (x, r, z, r.z)
-    and one per row for the direction.  The r.r sum of the stopping test
+    SpMV, one per row for p.q, three per row in the update (r, z, r.z) and
+    two in the direction phase (x and p).  The r.r sum of the stopping test
     (one more per row) runs only in the iterations where r.z cannot rule
     the test out, the last few of a solve, and is not counted."""
     return nnz + 6 * n
@@ -348,6 +350,65 @@ def event_time(torch, fn, reps):
     return e0.elapsed_time(e1) / 1e3
 
 
+def event_time_flushed(torch, fn, reps, flush):
+    """Device time of `reps` calls of fn, each timed alone between CUDA
+    events, with `flush` (a write of a buffer larger than L2) run outside
+    the timed pairs so every call starts with a cold L2."""
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for e0, e1 in ev:
+        flush()
+        e0.record(s)
+        fn()
+        e1.record(s)
+    ev[-1][1].synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+
+
+def bytes_spmv_fp32(n, nnz, index_bytes=4):
+    """FP32 MatMult: (4 + index bytes) nnz + 4(n+1) row pointers + 4n x
+    gather + 4n y write."""
+    return (4 + index_bytes) * nnz + 4 * (n + 1) + 4 * n + 4 * n
+
+
+def spmv_lanes_sweep(g, h, n, nnz, index_bytes):
+    """Standalone MatMult of one matrix in FP64 and FP32 for each lanes-per-
+    row setting (1, 2, 4) and the default rule, L2 flushed before every
+    call; GB/s by the byte models above."""
+    import torch
+    gbs = g.gbs
+    hbm, _ = peaks()
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    res = {}
+    for name, dt, model in (("fp64", torch.float64, bytes_spmv_fp64),
+                            ("fp32", torch.float32, bytes_spmv_fp32)):
+        x = torch.rand(n, dtype=dt, device="cuda")
+        y = torch.empty(n, dtype=dt, device="cuda")
+        xv, yv = gbs.gbs_vec_wrap(g.ctx, x), gbs.gbs_vec_wrap(g.ctx, y)
+        bb = model(n, nnz, index_bytes)
+        r = {"bytes_model": f"({8 if name == 'fp64' else 4} + {index_bytes}) nnz + 4(n+1) + "
+                            f"{'16n' if name == 'fp64' else '8n'}"}
+        for lanes in (0, 1, 2, 4):
+            gbs.gbs_ctx_set_opts(g.ctx, gbs.gbs_opts_default(spmv_lanes=lanes))
+            for _ in range(3):
+                gbs.gbs_mat_mult(h, xv, yv)
+            reps = 20
+            el = event_time_flushed(torch, lambda: gbs.gbs_mat_mult(h, xv, yv), reps,
+                                    flush_buf.zero_)
+            r["default" if lanes == 0 else f"lanes_{lanes}"] = {
+                "us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
+                "frac": bb / (el / reps) / 1e9 / hbm}
+        gbs.gbs_ctx_set_opts(g.ctx, gbs.gbs_opts_default())
+        gbs.gbs_vec_destroy(xv)
+        gbs.gbs_vec_destroy(yv)
+        res[name] = r
+    res["default_rule"] = "2 lanes per row where a row has more than 16 nonzeros, else 1"
+    res["l2"] = "L2 flushed (256 MB write) before each timed call"
+    del flush_buf
+    return res
+
+
 # DRAM traffic of one SpMV pass of the persistent FP64 kernel on the 128^3
 # workload, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
 # of a launch capped at 20 iterations, divided by its 21 SpMV passes: the
@@ -355,8 +416,8 @@ def event_time(torch, fn, reps):
 # on; the roofline reports the traffic scaled to the full launch (iterations
 # + 1 passes) only while the sources are unchanged.
 TRAFFIC_SOURCES = ("paper_2011_00715_gb300/csrc/solve.cu", "paper_2011_00715_gb300/csrc/gbs_impl.cuh")
-TRAFFIC_PER_ITER = {"sha256": "06580d99e27b89678e7ab54accd9f0b641c13661abd4b415903a5baa71668a48",
-                    "bytes": 267761571}
+TRAFFIC_PER_ITER = {"sha256": "905f0a1af930d414283c6372fc9950b668ec80f6c3ce89fdd8e5b994c8190e16",
+                    "bytes": 267489182}
 
 
 def kernel_source_hash():
@@ -448,6 +509,10 @@ def run_gbs(args, rank, world, local):
     torch.cuda.synchronize()
     true_rel = float(torch.linalg.norm(bt - rt) / torch.linalg.norm(bt))
     err_xs = float(torch.linalg.norm(xt - xst) / torch.linalg.norm(xst))
+    # the FP64 FMA rate of this GPU, measured after the timed region (the
+    # denominator of the FP64 roofline; the nominal rate is kept beside it)
+    fp64_peak = gbs.gbs_probe_fp64_rate(g.ctx, 4096) / 1e9
+    fp64_achieved = ops_per_iter_fp64(n, nnz) * iters[0] / (dev_ms / 1e3) / 1e9
 
     line = {"metric": METRIC,
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -473,15 +538,17 @@ def run_gbs(args, rank, world, local):
                          "frac_by_csr32_model": achieved_csr32 / hbm,
                          "csr32_model": "iters x (12 nnz + 108 n), 32-bit column indices",
                          "peak_kind": peak_kind},
-            "roofline_fp64": {"bound": "alu", "achieved": ops_per_iter_fp64(n, nnz) * iters[0]
-                              / (dev_ms / 1e3) / 1e9,
-                              "peak": FP64_NOMINAL_GOPS, "unit": "G FP64 ops/s",
-                              "frac": ops_per_iter_fp64(n, nnz) * iters[0] / (dev_ms / 1e3) / 1e9
-                              / FP64_NOMINAL_GOPS,
-                              "ops_model": "iters x (nnz + 6n): SpMV nnz, p.q n, update 4n, "
-                                           "direction n (one FP64 instruction lane each; the "
-                                           "r.r sum of the last iterations is not counted)",
-                              "peak_kind": "nominal 1.25 TFLOP/s = 625 G FMA/s"},
+            "roofline_fp64": {"bound": "alu", "achieved": fp64_achieved,
+                              "peak": fp64_peak, "unit": "G FP64 ops/s",
+                              "frac": fp64_achieved / fp64_peak,
+                              "ops_model": "iters x (nnz + 6n): SpMV nnz, p.q n, update 3n "
+                                           "(r, z, r.z), x and p updates 2n (one FP64 "
+                                           "instruction lane each; the r.r sum of the last "
+                                           "iterations is not counted)",
+                              "peak_kind": "measured: FP64 FMA-chain kernel (gbs_probe_fp64_rate) "
+                                           "after the timed region",
+                              "nominal_peak": FP64_NOMINAL_GOPS,
+                              "frac_of_nominal": fp64_achieved / FP64_NOMINAL_GOPS},
             "gpu_launches": int(l1 - l0),
             "clocks": clk}
     # the tuner's decision for this class (made during the warm-up solves)
@@ -597,30 +664,14 @@ def c1_solves(g):
     return res
 
 
-def extras(g, args, A, Ah, xsv):
-    import numpy as np
+def c3_problem(g, out):
+    """C3: 96^3 27-point variable coefficient (lognormal sigma 1), mixed
+    against FP64 at rtol 1e-10, each result's error against the oracle's
+    FP64 solution, and the standalone MatMult of the same operator."""
     import torch
     from paper_2011_00715_gb300 import inputs as I
     gbs = g.gbs
-    out = {}
     hbm, _ = peaks()
-    # --- standalone MatMult on the 128^3 matrix
-    yt = torch.empty(A.n, dtype=torch.float64, device="cuda")
-    yv = gbs.gbs_vec_wrap(g.ctx, yt)
-    for _ in range(3):
-        gbs.gbs_mat_mult(Ah, xsv, yv)
-    reps = 50
-    el = event_time(torch, lambda: gbs.gbs_mat_mult(Ah, xsv, yv), reps)
-    bb = bytes_spmv_fp64(A.n, A.nnz, stencil_index_bytes(N_GRID))
-    bb32 = bytes_spmv_fp64(A.n, A.nnz, 4)
-    out["spmv_c2_fp64"] = {"us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
-                           "frac": bb / (el / reps) / 1e9 / hbm,
-                           "bytes_model": "10 nnz + 4(n+1) + 8n + 8n (16-bit column offsets)",
-                           "frac_by_csr32_model": bb32 / (el / reps) / 1e9 / hbm}
-    gbs.gbs_vec_destroy(yv)
-    # --- C1: 64x64 2D Laplacian, rtol 1e-8
-    out["c1_lap2d5_64_fp64"] = c1_solves(g)
-    # --- C3: 96^3 27-point variable coefficient, mixed vs FP64 at rtol 1e-10
     C3 = I.var27(96, seed=3, sigma=1.0)
     h = g.mat(C3)
     xs3 = I.xstar(C3.n, 3)
@@ -668,6 +719,8 @@ def extras(g, args, A, Ah, xsv):
                                               torch.linalg.norm(xr3))
     del xr3
     c3["speedup_mixed_over_fp64"] = c3["fp64"]["ms_to_solution"] / c3["mixed"]["ms_to_solution"]
+    # standalone MatMult of the same operator (16-bit offsets: |col - row| <= 96^2 + 97)
+    out["spmv_c3_var27_96"] = spmv_lanes_sweep(g, h, C3.n, C3.nnz, 2)
     c3["autotune"] = {}
     for name, mode in (("fp64", gbs.GBS_MODE_FP64), ("mixed", gbs.GBS_MODE_MIXED)):
         sh, ln = gbs.gbs_ksp_tune(h, mode)
@@ -677,6 +730,32 @@ def extras(g, args, A, Ah, xsv):
     for v in (xs3v, b3v, x3v, r3v):
         gbs.gbs_vec_destroy(v)
     gbs.gbs_mat_destroy(h)
+
+
+def extras(g, args, A, Ah, xsv):
+    import numpy as np
+    import torch
+    from paper_2011_00715_gb300 import inputs as I
+    gbs = g.gbs
+    out = {}
+    hbm, _ = peaks()
+    # --- standalone MatMult on the 128^3 matrix
+    yt = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    yv = gbs.gbs_vec_wrap(g.ctx, yt)
+    for _ in range(3):
+        gbs.gbs_mat_mult(Ah, xsv, yv)
+    reps = 50
+    el = event_time(torch, lambda: gbs.gbs_mat_mult(Ah, xsv, yv), reps)
+    bb = bytes_spmv_fp64(A.n, A.nnz, stencil_index_bytes(N_GRID))
+    bb32 = bytes_spmv_fp64(A.n, A.nnz, 4)
+    out["spmv_c2_fp64"] = {"us": el / reps * 1e6, "GBps": bb / (el / reps) / 1e9,
+                           "frac": bb / (el / reps) / 1e9 / hbm,
+                           "bytes_model": "10 nnz + 4(n+1) + 8n + 8n (16-bit column offsets)",
+                           "frac_by_csr32_model": bb32 / (el / reps) / 1e9 / hbm}
+    gbs.gbs_vec_destroy(yv)
+    # --- C1: 64x64 2D Laplacian, rtol 1e-8
+    out["c1_lap2d5_64_fp64"] = c1_solves(g)
+    c3_problem(g, out)
     out["c2_chebyshev"] = c2_chebyshev(g, A, Ah, xsv)
     out["c2_coo_assembly"] = c2_coo_assembly(g, A)
     out["c2_sweep"] = c2_sweep(g, args)
@@ -1264,6 +1343,14 @@ def main():
         B.build()
         g = Gpu(local)
         print(json.dumps({"c2_sweep": c2_sweep(g, args)}), flush=True)
+        return
+    if args.c3_only:
+        from paper_2011_00715_gb300 import build as B
+        B.build()
+        g = Gpu(local)
+        out = {}
+        c3_problem(g, out)
+        print(json.dumps(out), flush=True)
         return
     if args.c1_only:
         from paper_2011_00715_gb300 import build as B

@@ -154,7 +154,12 @@ typedef struct {
     int persistent_lanes;    /* persistent single-system CG solves: lanes per matrix
                                 row in the SpMV, 1 (warp tiles of 32 rows) or 2 (16
                                 rows), or 0 (default) for the tuner's choice */
-    int reserved[2];
+    int spmv_lanes;          /* gbs_mat_mult: lanes per matrix row (1, 2 or 4: warp
+                                tiles of 32, 16 or 8 rows), or 0 (default): 2 where
+                                a row has more than 16 nonzeros, else 1.  The
+                                partial sums of a row are added in a fixed order
+                                for a given setting */
+    int reserved[1];         /* must be 0 */
 } gbs_opts;
 
 /* Result of the last solve on a context. */
@@ -209,6 +214,15 @@ int gbs_ctx_synchronize(gbs_ctx ctx);
 /* Number of this library's kernel launches on the context so far (a
  * counter kept by the host code; used to report launch counts). */
 int gbs_ctx_launch_count(gbs_ctx ctx, int64_t *count);
+
+/* Measure the device's FP64 fused multiply-add rate (the denominator of the
+ * FP64 arithmetic roofline of the CG kernels): one warm-up and one timed
+ * launch of a kernel in which every thread of a full grid runs 8
+ * independent chains of `iters` FMAs (1 <= iters <= 2^24; 4096 takes a few
+ * milliseconds).  *fma_per_s receives the FMAs per second of the timed
+ * launch (CUDA events on the context's stream).  Synchronises the stream.
+ * GBS_ERR_ARG for a NULL pointer or iters out of range, GBS_ERR_CUDA. */
+int gbs_probe_fp64_rate(gbs_ctx ctx, int iters, double *fma_per_s);
 
 /* ------------------------------------------------------------ matrix --- */
 

@@ -78,6 +78,9 @@ static int opts_valid(const gbs_opts *o)
     if (o->no_rel16 != 0 && o->no_rel16 != 1) return 0;
     if (o->persistent_shape < 0 || o->persistent_shape > 2) return 0;
     if (o->persistent_lanes != 0 && o->persistent_lanes != 1 && o->persistent_lanes != 2) return 0;
+    if (o->spmv_lanes != 0 && o->spmv_lanes != 1 && o->spmv_lanes != 2 && o->spmv_lanes != 4)
+        return 0;
+    if (o->reserved[0] != 0) return 0;
     return 1;
 }
 
@@ -172,6 +175,59 @@ extern "C" int gbs_ctx_launch_count(gbs_ctx c, int64_t *count)
 {
     if (!c || !count) return GBS_ERR_ARG;
     *count = c->launches;
+    return GBS_OK;
+}
+
+// FP64 FMA issue-rate probe: every thread runs 8 independent dependent
+// chains of fused multiply-adds, enough for the FP64 pipe to stay busy.  The
+// sum is stored only if it equals an impossible value, so nothing is
+// written in practice but nothing can be elided either.
+__global__ void __launch_bounds__(512) k_fp64_fma_rate(int iters, double m, double cst, double *sink)
+{
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = 1.0 + 1e-3 * (double)(threadIdx.x + 37 * j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = fma(v[j], m, cst);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += v[j];
+    if (s == -1.0) sink[blockIdx.x & 7] = s;
+}
+
+extern "C" int gbs_probe_fp64_rate(gbs_ctx c, int iters, double *fma_per_s)
+{
+    if (!c || !fma_per_s || iters <= 0 || iters > (1 << 24)) return GBS_ERR_ARG;
+    *fma_per_s = 0.0;
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    int per_sm = 0;
+    GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp64_fma_rate, 512, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int g = c->num_sms * per_sm;
+    double *sink = (double *)c->devsmall + 32;   // bytes 256..319 of the context's small buffer
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // a warm-up launch, then the timed one
+    for (int rep = 0; e == cudaSuccess && rep < 2; ++rep) {
+        if (rep == 1) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) {
+            k_fp64_fma_rate<<<g, 512, 0, c->stream>>>(iters, 0.999999999, 1e-9, sink);
+            gbs_count_launch(c);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return gbs_cuda_fail(e);
+    if (ms <= 0.f) return GBS_ERR_CUDA;
+    *fma_per_s = (double)g * 512.0 * 8.0 * (double)iters / ((double)ms * 1e-3);
     return GBS_OK;
 }
 
@@ -653,8 +709,9 @@ struct StoreEpi {
 // a stage fits in 6.4 KB (every tile of at most 512 nonzeros does) — twice
 // the warps hide the gather latency better than deeper rings, even with a
 // single stage per warp (measured: 7-point 128^3 FP64 51 -> 41 us, 27-point
-// 96^3 FP32 43 -> 37 us).
-template <typename V, typename IX, int WB, int MINB>
+// 96^3 FP32 43 -> 37 us).  2^LOG_L lanes share a row (tiles of 32 / 2^LOG_L
+// rows, from the matching lane tiling).
+template <typename V, typename IX, int WB, int MINB, int LOG_L>
 __global__ void __launch_bounds__(GBS_BLOCK, MINB) k_spmv(int64_t ntiles, const int32_t *tdesc,
                                                           const int32_t *rowptr, const IX *colidx,
                                                           const V *vals, const V *x, V *y,
@@ -671,44 +728,68 @@ __global__ void __launch_bounds__(GBS_BLOCK, MINB) k_spmv(int64_t ntiles, const 
     StoreEpi<V> epi{y, pk};
     uint32_t parity = 0;
     const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
-    const bool ok = gbs_spmv_pipe<V, IX>(tdesc, t0, t1, &s_next, rowptr, colidx, vals, x,
+    const bool ok = gbs_spmv_pipe<V, IX, LOG_L>(tdesc, t0, t1, &s_next, rowptr, colidx, vals, x,
                                          smem + (size_t)warp * WB, s_q[warp], parity, cfg, ps, pk,
                                          2000000000ull, epi);
     if (!ok && lane == 0) atomicExch(err, 1);
 }
 
-template <typename V, typename IX, int WB, int MINB>
+template <typename V, typename IX, int WB, int MINB, int LOG_L>
 static int spmv_launch_shape(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, const V *x, V *y,
                              GbsPipeCfg cfg)
 {
-    const void *fn = (const void *)k_spmv<V, IX, WB, MINB>;
+    const void *fn = (const void *)k_spmv<V, IX, WB, MINB, LOG_L>;
     const size_t smem = (size_t)WB * GBS_WARPS;
     GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_BLOCK, smem));
     if (per_sm < 1) per_sm = 1;
-    const int64_t need = (A->ntiles + GBS_WARPS - 1) / GBS_WARPS;
+    const int64_t ntiles = A->ntiles_lanes[LOG_L];
+    const int64_t need = (ntiles + GBS_WARPS - 1) / GBS_WARPS;
     const int64_t cap = (int64_t)c->num_sms * per_sm;
     const int g = (int)(need < cap ? need : cap);
     int *err = (int *)c->devsmall + 1;   // word 1 of the context's small device buffer
-    k_spmv<V, IX, WB, MINB><<<g, GBS_BLOCK, smem, c->stream>>>(A->ntiles, A->tdesc, A->rowptr, colidx,
-                                                              vals, x, y, cfg, err);
+    k_spmv<V, IX, WB, MINB, LOG_L><<<g, GBS_BLOCK, smem, c->stream>>>(
+        ntiles, A->tdesc_lanes[LOG_L], A->rowptr, colidx, vals, x, y, cfg, err);
     gbs_count_launch(c);
     GBS_CUDA_TRY(cudaGetLastError());
     return GBS_OK;
 }
 
-template <typename V, typename IX>
-static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, GbsPipeCfg cfg,
-                       const V *x, V *y)
+template <typename V, typename IX, int LOG_L>
+static int spmv_launch_l(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, GbsPipeCfg cfg,
+                         const V *x, V *y)
 {
     constexpr int kSmallRing = GBS_WARP_STAGE_BYTES / 2;
     const int small_stages = kSmallRing / cfg.sbytes;
     if (small_stages >= 1) {
         cfg.stages = small_stages < GBS_MAX_STAGES ? small_stages : GBS_MAX_STAGES;
-        return spmv_launch_shape<V, IX, kSmallRing, 4>(c, A, vals, colidx, x, y, cfg);
+        return spmv_launch_shape<V, IX, kSmallRing, 4, LOG_L>(c, A, vals, colidx, x, y, cfg);
     }
-    return spmv_launch_shape<V, IX, GBS_WARP_STAGE_BYTES, 1>(c, A, vals, colidx, x, y, cfg);
+    return spmv_launch_shape<V, IX, GBS_WARP_STAGE_BYTES, 1, LOG_L>(c, A, vals, colidx, x, y, cfg);
+}
+
+// Lanes per row of MatMult (log2): the context's spmv_lanes, else two lanes
+// for rows of more than 16 nonzeros (27-point stencils: half the lanes of a
+// one-lane tile would idle on the tail of every row) and one otherwise.
+static int spmv_log_lanes(gbs_mat A)
+{
+    const int o = A->ctx->opts.spmv_lanes;
+    if (o > 0) return o == 1 ? 0 : o == 2 ? 1 : 2;
+    return A->max_row_nnz > 16 ? 1 : 0;
+}
+
+// MatMult with the tiling for li = log2(lanes per row); cfgs[li] is the
+// stage layout of that tiling for these values and indices.
+template <typename V, typename IX>
+static int spmv_launch(gbs_ctx c, gbs_mat A, const V *vals, const IX *colidx, const GbsPipeCfg *cfgs,
+                       int li, const V *x, V *y)
+{
+    const int st = gbs_mat_ensure_lane_tiling(A, li);
+    if (st) return st;
+    if (li == 1) return spmv_launch_l<V, IX, 1>(c, A, vals, colidx, cfgs[1], x, y);
+    if (li == 2) return spmv_launch_l<V, IX, 2>(c, A, vals, colidx, cfgs[2], x, y);
+    return spmv_launch_l<V, IX, 0>(c, A, vals, colidx, cfgs[0], x, y);
 }
 
 extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
@@ -719,23 +800,24 @@ extern "C" int gbs_mat_mult(gbs_mat A, gbs_vec x, gbs_vec y)
     gbs_ctx c = A->ctx;
     if (A->n == 0) return GBS_OK;
     GBS_CUDA_TRY(cudaSetDevice(c->device));
+    const int li = spmv_log_lanes(A);
     if (x->dtype == GBS_F64) {
         int st = gbs_mat_ensure_rel16(A);
         if (st) return st;
         if (A->colrel16 && !c->opts.no_rel16)
-            return spmv_launch<double, int16_t>(c, A, A->vals, A->colrel16, A->pipe64r,
+            return spmv_launch<double, int16_t>(c, A, A->vals, A->colrel16, A->pipe64r_lanes, li,
                                                 (const double *)x->data, (double *)y->data);
-        return spmv_launch<double, int32_t>(c, A, A->vals, A->colidx, A->pipe64,
+        return spmv_launch<double, int32_t>(c, A, A->vals, A->colidx, A->pipe64_lanes, li,
                                             (const double *)x->data, (double *)y->data);
     }
     int st = gbs_mat_ensure_f32(A);
     if (st) return st;
     // FP32: the compressed 16-bit column indices where the matrix allows them
     if (A->colrel16 && !c->opts.no_rel16)
-        return spmv_launch<float, int16_t>(c, A, A->vals32, A->colrel16, A->pipe16,
+        return spmv_launch<float, int16_t>(c, A, A->vals32, A->colrel16, A->pipe16_lanes, li,
                                            (const float *)x->data, (float *)y->data);
-    return spmv_launch<float, int32_t>(c, A, A->vals32, A->colidx, A->pipe32, (const float *)x->data,
-                                       (float *)y->data);
+    return spmv_launch<float, int32_t>(c, A, A->vals32, A->colidx, A->pipe32_lanes, li,
+                                       (const float *)x->data, (float *)y->data);
 }
 
 // --------------------------------------------------------------- vector --

@@ -327,19 +327,26 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         }
         const T alpha = ctl.alpha;
 
-        // ---- U: r -= alpha q; z = D^-1 r; partials r.z (and r.r).  The
-        // solution update x += alpha p waits for the P phase, which reads p
-        // anyway (8 bytes per row fewer than doing it here); an exit right
-        // after U applies it in a pass of its own.  (UNR rows per thread per
-        // trip: all loads are issued before the first use.)
+        // ---- U: r -= alpha q; z = D^-1 r; partials r.z (and r.r).  In
+        // FP64 the solution update x += alpha p waits for the P phase, which
+        // reads p anyway (8 bytes per row fewer than doing it here); an exit
+        // right after U applies it in a pass of its own.  The FP32 inner loop
+        // keeps it here: deferring it measured 14 % slower there (27-point
+        // 96^3, two lanes per row: 22.5 against 19.8 ms).  (UNR rows per
+        // thread per trip: all loads are issued before the first use.)
+        constexpr bool kDeferX = sizeof(T) == 8;
         const bool need_rr = ctl.need_rr != 0;
         T u[2] = {T(0), T(0)};
         for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
-            T rv[UNR], qv[UNR], dv[UNR];
+            T rv[UNR], qv[UNR], dv[UNR], pv[UNR], xv[UNR];
 #pragma unroll
             for (int h = 0; h < UNR; ++h) {
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
+                    if constexpr (!kDeferX) {
+                        pv[h] = gbs_ld(pT + i, pk);
+                        xv[h] = gbs_ld(xT + i, pk);
+                    }
                     rv[h] = gbs_ld(rT + i, pk);
                     qv[h] = gbs_ld(qT + i, pk);
                     dv[h] = gbs_ld(dinv + i, pk);
@@ -350,6 +357,7 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
                     const T rn_ = rv[h] - alpha * qv[h], zn_ = dv[h] * rn_;
+                    if constexpr (!kDeferX) gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
                     gbs_st(rT + i, rn_, pk);
                     gbs_st(zT + i, zn_, pk);
                     u[0] += rn_ * zn_;
@@ -430,13 +438,14 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
         __syncthreads();
         if (!ctl.go) {
             // the loop ends after this update: x += alpha p on own rows
-            for (int64_t i = rb + threadIdx.x; i < re; i += NT)
-                gbs_st(xT + i, gbs_ld(xT + i, pk) + alpha * gbs_ld(pT + i, pk), pk);
+            if constexpr (kDeferX)
+                for (int64_t i = rb + threadIdx.x; i < re; i += NT)
+                    gbs_st(xT + i, gbs_ld(xT + i, pk) + alpha * gbs_ld(pT + i, pk), pk);
             break;
         }
         const T beta = ctl.beta;
 
-        // ---- P: x += alpha p (the update U left), p = z + beta p
+        // ---- P: (FP64: x += alpha p, the update U left) p = z + beta p
         for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += UNR * NT) {
             T zv[UNR], pv[UNR], xv[UNR];
 #pragma unroll
@@ -445,14 +454,14 @@ __device__ int pcg_loop(const PcgArgs &a, const IX *colidx, const T *vals, const
                 if (i < re) {
                     zv[h] = gbs_ld(zT + i, pk);
                     pv[h] = gbs_ld(pT + i, pk);
-                    xv[h] = gbs_ld(xT + i, pk);
+                    if constexpr (kDeferX) xv[h] = gbs_ld(xT + i, pk);
                 }
             }
 #pragma unroll
             for (int h = 0; h < UNR; ++h) {
                 const int64_t i = i0 + h * NT;
                 if (i < re) {
-                    gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
+                    if constexpr (kDeferX) gbs_st(xT + i, xv[h] + alpha * pv[h], pk);
                     gbs_st(pT + i, zv[h] + beta * pv[h], pk);
                 }
             }
@@ -677,8 +686,8 @@ int coop_grid(gbs_ctx c, const void *fn, int64_t ntiles, int want = 0,
 //  indices + 4n row pointers + 8n gather + 8n b read + 8n r written), the
 //  scaling to FP32 (8n read, 4n written) and the FP64 update (16n x, 4n
 //  FP32 solution); per inner solve its set-up (b32, D^-1 read, x, r, z, p
-//  written: 24n) and final x pass (12n); per inner iteration
-//  (4 + ib) nnz + 52 n.
+//  written: 24n) and per inner iteration (4 + ib) nnz + 56 n (the FP32
+//  loop updates x in U).
 double persistent_model_bytes(gbs_mat A, bool mixed, int ib, const gbs_solve_info &r)
 {
     const double n = (double)A->n, nnz = (double)A->nnz;
@@ -687,8 +696,8 @@ double persistent_model_bytes(gbs_mat A, bool mixed, int ib, const gbs_solve_inf
                (r.iters > 0 ? 24.0 * n : 0.0);
     const double outer = (double)r.outer_iters + 1.0;   // residual passes
     const double inner_solves = (double)r.outer_iters;
-    return outer * (12.0 * nnz + 36.0 * n) + inner_solves * (12.0 * n + 20.0 * n + 24.0 * n + 12.0 * n) +
-           (double)r.iters * ((4.0 + ib) * nnz + 52.0 * n);
+    return outer * (12.0 * nnz + 36.0 * n) + inner_solves * (12.0 * n + 20.0 * n + 24.0 * n) +
+           (double)r.iters * ((4.0 + ib) * nnz + 56.0 * n);
 }
 
 // Launch a persistent kernel and read its result record (one host

@@ -66,7 +66,8 @@ class gbs_opts(ctypes.Structure):
                 ("fault_skip_arrival", ctypes.c_int), ("batched_lanes", ctypes.c_int),
                 ("persistent_ctas", ctypes.c_int), ("norm_type", ctypes.c_int),
                 ("no_rel16", ctypes.c_int), ("persistent_shape", ctypes.c_int),
-                ("persistent_lanes", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("persistent_lanes", ctypes.c_int), ("spmv_lanes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class gbs_solve_info(ctypes.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "gbs_ctx_set_opts": ([_VP, ctypes.POINTER(gbs_opts)], ctypes.c_int),
     "gbs_ctx_synchronize": ([_VP], ctypes.c_int),
     "gbs_ctx_launch_count": ([_VP, ctypes.POINTER(_I64)], ctypes.c_int),
+    "gbs_probe_fp64_rate": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "gbs_mat_create_aij": ([_VP, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "gbs_mat_set_values": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
     "gbs_mat_create_coo": ([_VP, _I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)],
@@ -253,6 +255,13 @@ def gbs_ctx_set_opts(ctx, opts: gbs_opts):
 
 def gbs_ctx_synchronize(ctx):
     _check(lib().gbs_ctx_synchronize(ctx), "gbs_ctx_synchronize")
+
+
+def gbs_probe_fp64_rate(ctx, iters: int = 4096) -> float:
+    """FP64 FMAs per second of the device (a timed FMA-chain kernel)."""
+    r = ctypes.c_double()
+    _check(lib().gbs_probe_fp64_rate(ctx, iters, ctypes.byref(r)), "gbs_probe_fp64_rate")
+    return r.value
 
 
 def gbs_ctx_launch_count(ctx) -> int:

@@ -4,9 +4,12 @@ FP64 rows are accumulated left to right in storage order with fused
 multiply-adds: held to ||y - y_orc|| <= 1e-13 ||y_orc|| and, per row, to the
 componentwise bound 2 gamma_m (|A||x|)_i (m = nonzeros in the row), and
 bitwise on exact inputs.  FP32 rows round each product and sum separately
-in the oracle's order, so they are bitwise equal to the oracle's FP32
-product (rows longer than one tile are reduced by a tree and use the
-bounds instead).
+in the oracle's order with one lane per row, so they are bitwise equal to
+the oracle's FP32 product (rows longer than one tile are reduced by a tree
+and use the bounds instead).  With 2 or 4 lanes per row (the default for
+rows of more than 16 nonzeros) each lane sums a share of the row and the
+shares are added by a tree: FP64 and FP32 are then bitwise on exact inputs
+and within the componentwise bound gamma_m (|A||x|) of any summation order.
 """
 import numpy as np
 import pytest
@@ -23,6 +26,13 @@ U = 2.0 ** -53
 def S():
     from gpu_util import Session
     return Session()
+
+
+@pytest.fixture(scope="module")
+def S1():
+    """One lane per row: the FP32 summation order of the oracle."""
+    from gpu_util import Session
+    return Session(gbs.gbs_opts_default(spmv_lanes=1))
 
 
 def with_empty_and_long_rows(n=3000, seed=5):
@@ -81,16 +91,16 @@ def test_spmv_fp64(S, name, orc):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_spmv_fp32_bitwise(S, name, orc):
+def test_spmv_fp32_bitwise(S1, name, orc):
     A = CASES[name]()
     ncols = A.meta.get("ncols", A.n)
     x = I.uniform_pm1(18, 0, ncols).astype(np.float32)
-    y = run(S, A, x, np.float32)
+    y = run(S1, A, x, np.float32)
     ref = orc.spmv_f32(A, x)
     assert np.array_equal(y, ref)
 
 
-def test_spmv_empty_and_long_rows(S, orc):
+def test_spmv_empty_and_long_rows(S, S1, orc):
     A = with_empty_and_long_rows()
     x = I.uniform_pm1(19, 0, A.n)
     y = run(S, A, x)
@@ -99,7 +109,7 @@ def test_spmv_empty_and_long_rows(S, orc):
     assert np.all(y[rows == 0] == 0.0)
     assert_within_bounds(orc, A, x, y, ref)
     x32 = x.astype(np.float32)
-    y32 = run(S, A, x32, np.float32)
+    y32 = run(S1, A, x32, np.float32)
     ref32 = orc.spmv_f32(A, x32)
     short = rows <= 2048
     assert np.array_equal(y32[short], ref32[short])
@@ -274,3 +284,73 @@ def test_fp64_matmult_index_widths_on_stencils(S, orc):
         ref = orc.spmv(A, x)
         assert np.linalg.norm(y16 - ref) <= 1e-13 * np.linalg.norm(ref)
     gbs.gbs_ctx_destroy(S32.ctx)
+
+
+def exact_version(A, ncols, seed):
+    """A copy of A with values on a 1/8 grid in [-64, 64] and an integer x in
+    [-8, 8]: every product and partial sum is exact in FP32 and FP64, so any
+    summation order gives the oracle's bits."""
+    Ae = I.CSR(A.n, A.rowptr, A.colidx, np.round(np.clip(A.vals, -64, 64) * 8.0) / 8.0)
+    Ae.meta["ncols"] = ncols
+    xe = (I.counter_u64(seed, 3, np.arange(ncols)) % np.uint64(17)).astype(np.float64) - 8.0
+    return Ae, xe
+
+
+LANE_CASES = {
+    "var27_13": lambda: I.var27(13, seed=3),
+    "lap3d7_20": lambda: I.lap3d7(20),
+    "random_rect": lambda: I.random_csr(700, 1300, 11, seed=2),
+    "empty_and_long_rows": with_empty_and_long_rows,
+}
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("name", sorted(LANE_CASES))
+def test_spmv_lanes_per_row(orc, name, lanes):
+    """Every lanes-per-row tiling of MatMult: bitwise the oracle on exact
+    inputs in both precisions; on random inputs FP64 within 2 gamma_m
+    (|A||x|) and FP32 within gamma_m (|A32||x32|) (u = 2^-24) of the exact
+    product of its FP32 operands."""
+    from gpu_util import Session
+    S = Session(gbs.gbs_opts_default(spmv_lanes=lanes))
+    A = LANE_CASES[name]()
+    ncols = A.meta.get("ncols", A.n)
+    Ae, xe = exact_version(A, ncols, 5)
+    assert np.array_equal(run(S, Ae, xe), orc.spmv(Ae, xe))
+    assert np.array_equal(run(S, Ae, xe.astype(np.float32), np.float32),
+                          orc.spmv_f32(Ae, xe.astype(np.float32)))
+    x = I.uniform_pm1(21, 0, ncols)
+    assert_within_bounds(orc, A, x, run(S, A, x), orc.spmv(A, x))
+    x32 = x.astype(np.float32)
+    y32 = run(S, A, x32, np.float32).astype(np.float64)
+    A32 = I.CSR(A.n, A.rowptr, A.colidx, A.vals.astype(np.float32).astype(np.float64))
+    A32.meta["ncols"] = ncols
+    ref = orc.spmv(A32, x32.astype(np.float64))
+    absA = I.CSR(A.n, A.rowptr, A.colidx, np.abs(A32.vals))
+    absA.meta["ncols"] = ncols
+    m = np.diff(A.rowptr)
+    u32 = 2.0 ** -24
+    g = m * u32 / (1 - m * u32)
+    # the FP64 reference rounds too: 2^-50 of |A||x| covers it
+    assert np.all(np.abs(y32 - ref) <= (g + 2.0 ** -50) * orc.spmv(absA, np.abs(x32.astype(np.float64))))
+    gbs.gbs_ctx_destroy(S.ctx)
+
+
+def test_spmv_default_lanes_rule(S, orc):
+    """By default rows of more than 16 nonzeros take 2 lanes and shorter rows
+    one: the default results are bitwise those of the explicit setting."""
+    from gpu_util import Session
+    S1_, S2_ = (Session(gbs.gbs_opts_default(spmv_lanes=k)) for k in (1, 2))
+    for A, same in ((I.var27(13, seed=3), S2_), (I.lap3d7(20), S1_)):
+        x = I.uniform_pm1(22, 0, A.n)
+        for dt in (np.float64, np.float32):
+            xx = x.astype(dt)
+            assert np.array_equal(run(S, A, xx, dt), run(same, A, xx, dt))
+    for s_ in (S1_, S2_):
+        gbs.gbs_ctx_destroy(s_.ctx)
+
+
+def test_spmv_lanes_option_refused():
+    from gpu_util import Session
+    with pytest.raises(Exception):
+        Session(gbs.gbs_opts_default(spmv_lanes=3))

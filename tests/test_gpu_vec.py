@@ -169,3 +169,19 @@ def test_vector_values_roundtrip_and_errors(S):
     e = gbs.gbs_vec_create(S.ctx, 0)
     assert gbs.gbs_vec_dot(e, e) == 0.0
     gbs.gbs_vec_destroy(e)
+
+
+def test_fp64_rate_probe(S):
+    """The FP64 FMA-rate probe (the FP64 roofline's denominator) returns a
+    rate between 1/20 and 2x of the nominal 625 G FMA/s of a GB300, scales
+    its work with iters, and refuses bad arguments."""
+    r1 = gbs.gbs_probe_fp64_rate(S.ctx, 2048)
+    r2 = gbs.gbs_probe_fp64_rate(S.ctx, 8192)
+    for r in (r1, r2):
+        assert 625e9 / 20 < r < 2 * 625e9, r
+    assert abs(r1 - r2) <= 0.25 * r2
+    assert gbs.lib().gbs_probe_fp64_rate(S.ctx, 0, None) == gbs.GBS_ERR_ARG
+    import ctypes
+    v = ctypes.c_double()
+    assert gbs.lib().gbs_probe_fp64_rate(S.ctx, 0, ctypes.byref(v)) == gbs.GBS_ERR_ARG
+    assert gbs.lib().gbs_probe_fp64_rate(S.ctx, (1 << 24) + 1, ctypes.byref(v)) == gbs.GBS_ERR_ARG
