@@ -136,6 +136,7 @@ struct BArgs {
     int *nfin;                 // active systems finished during the launch
     gbs_grid_barrier *bar;
     GbsPipeCfg cfg;     // stage geometry covering every active system's tiles
+    int ring;           // bytes of one warp's stage ring (cfg.stages stages, 128-aligned)
     int quantum;        // global iterations at most (even)
     int iter0;          // parity of the global iteration count at launch
     double inner_rtol;
@@ -1073,7 +1074,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
     __shared__ BWarpQ s_q[GBS_PWARPS];
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wsm = smem + (size_t)warp * GBS_BWARP_BYTES;
+    unsigned char *wsm = smem + (size_t)warp * a.ring;
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < GBS_MAX_STAGES; ++j) gbs_mbar_init(&s_q[warp].bar[j], 1);
@@ -1164,8 +1165,14 @@ int padded_k(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
 // Reduction units of a system.  Large systems group more work per unit, so
 // the per-unit completion count costs little; the grouping depends on the
 // system alone (results do not depend on the batch).
-int tiles_per_unit(int64_t ntiles) { return (int)std::min<int64_t>(8, std::max<int64_t>(1, ntiles / 256)); }
-int subs_per_unit(int64_t nsub) { return (int)std::min<int64_t>(4, std::max<int64_t>(1, nsub / 256)); }
+// Units of work of one system: S units of up to 32 warp tiles, U/P units of
+// up to 16 sub-blocks, at least 64 units per system where it is that large.
+// Each claim of a unit costs a grid-wide atomic and a walk to its system's
+// records; with 512 systems x 8 columns, units of at most 8 tiles / 4
+// sub-blocks measured S 1090 -> 1000 us, U 931 -> 792 us per iteration.
+// The sizes depend on the system alone (its reduction order with them).
+int tiles_per_unit(int64_t ntiles) { return (int)std::min<int64_t>(32, std::max<int64_t>(1, ntiles / 64)); }
+int subs_per_unit(int64_t nsub) { return (int)std::min<int64_t>(16, std::max<int64_t>(1, nsub / 64)); }
 
 // ----------------------------------------------------------------------
 // Host engine: a slot table of systems run by the kernel above.
@@ -1211,6 +1218,7 @@ struct Engine {
     bool dirty = true;        // a slot was filled or released since the capture
     size_t cnt_bytes = 0;
     BArgs g_args;
+    size_t g_smem = 0;       // dynamic shared memory of the captured launch
     int G = 0;
     // slots added since the last launch: their records (staged on the host
     // in h_sys / h_col / h_dyn) and their right-hand sides and initial
@@ -1290,11 +1298,12 @@ size_t system_bytes(int64_t n, int64_t nnz, int k, int fp64)
 
 // Algorithmic bytes of the steps a slot's system has taken: an INNER step
 // streams the inner-precision values and column indices (16-bit when the
-// matrix has the compressed form), rowptr, the p gather and q
-// (S), x, p, r, q read and x, r written plus D^-1 (U), r, p read and p
-// written plus D^-1 (P); an OUTER step streams the FP64 values and colidx,
-// rowptr, the x gather, b and r64 (S), r64 read, D^-1 and x_i, r_i, p_i
-// written (U).  Vector entries count kp per row.
+// matrix has the compressed form), rowptr, the p gather and q written (S:
+// 2 kp entries per row), x, p, r, q read and x, r written plus D^-1 (U:
+// 6 kp + 1), r, p read and p written plus D^-1 (P: 3 kp + 1); an OUTER
+// step streams the FP64 values and colidx, rowptr, the x gather, b and r64
+// (S), r64 read, D^-1 and x_i, r_i, p_i written (U).  Vector entries count
+// kp per row, once per pass that reads or writes them.
 double slot_model_bytes(const Engine &E, int slot)
 {
     const SlotHost &H = E.slots[slot];
@@ -1302,7 +1311,7 @@ double slot_model_bytes(const Engine &E, int slot)
     const BSysDyn &D = E.h_dyn[slot];
     const double n = (double)H.A->n, nnz = (double)H.A->nnz, kp = H.kp, tsz = E.fp64 ? 8 : 4;
     const double isz = H.A->colrel16 ? 2 : 4;   // index bytes of INNER tiles
-    const double inner = (tsz + isz) * nnz + 4 * (n + 1) + tsz * n * (8 * kp + 2);
+    const double inner = (tsz + isz) * nnz + 4 * (n + 1) + tsz * n * (11 * kp + 2);
     const double outer = 12 * nnz + 4 * (n + 1) + 32 * n * kp + tsz * n * (3 * kp + 1);
     return D.isteps * inner + D.osteps * outer;
 }
@@ -1580,7 +1589,10 @@ GbsPipeCfg engine_pipe_cfg(const Engine &E, const std::vector<int> &act)
     cfg.coloff = v;
     cfg.rpoff = v + cl;
     cfg.sbytes = v + cl + r;
-    cfg.stages = std::min(GBS_MAX_STAGES, std::max(1, GBS_BWARP_BYTES / cfg.sbytes));
+    // two stages: the S phase is bound by the latency of its gathers, not of
+    // its copies (4 and 8 stages measured 1.5 % and 6 % slower than 2), and
+    // the smaller rings leave more of the SM's memory to L1
+    cfg.stages = std::min(2, std::max(1, GBS_BWARP_BYTES / cfg.sbytes));
     return cfg;
 }
 
@@ -1601,7 +1613,6 @@ int engine_step(Engine &E, int *ran)
     if (act.empty()) return GBS_OK;
     const int nact = (int)act.size();
     const void *fn = E.fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
-    const size_t smem = (size_t)GBS_BWARP_BYTES * GBS_PWARPS;
     if (E.dirty || act != E.g_act) {
         engine_free_graph(E);
         E.dirty = false;
@@ -1630,7 +1641,16 @@ int engine_step(Engine &E, int *ran)
         GBS_CUDA_TRY(cudaMemcpyAsync(E.d_idx, idx.data(), sizeof(int) * idx.size(),
                                      cudaMemcpyHostToDevice, c->stream));
         GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));   // idx is a stack vector
+        // the rings take only the stages the active tiles need; the rest of
+        // the SM's on-chip memory stays L1, where the SpMV's gathers of p
+        // (each entry read by every row that couples to it) find it
+        const GbsPipeCfg cfg = engine_pipe_cfg(E, act);
+        const int ring = (cfg.stages * cfg.sbytes + 127) & ~127;
+        const size_t smem = (size_t)ring * GBS_PWARPS;
+        E.g_smem = smem;
         GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxL1));
         int per_sm = 0;
         GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
@@ -1662,7 +1682,8 @@ int engine_step(Engine &E, int *ran)
         a.claim = E.d_cnt + nchs + nchu + 2 * nact;
         a.nfin = a.claim + nclaim;
         a.bar = E.d_bar;
-        a.cfg = engine_pipe_cfg(E, act);
+        a.cfg = cfg;
+        a.ring = ring;
         a.quantum = E.quantum;   // even: the parity of the global iteration is unchanged
         a.iter0 = 0;
         a.inner_rtol = E.inner_rtol;
@@ -1678,7 +1699,7 @@ int engine_step(Engine &E, int *ran)
             cudaMemsetAsync(E.d_cnt, 0, E.cnt_bytes, cap);
             cudaMemsetAsync(E.d_bar, 0, 256, cap);
             void *args[] = {&E.g_args};
-            cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args, smem, cap);
+            cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args, E.g_smem, cap);
             e = cudaStreamEndCapture(cap, &E.graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E.gexec, E.graph, 0);
@@ -1697,7 +1718,7 @@ int engine_step(Engine &E, int *ran)
         GBS_CUDA_TRY(cudaMemsetAsync(E.d_bar, 0, 256, c->stream));
         void *args[] = {&E.g_args};
         GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args,
-                                                 smem, c->stream));
+                                                 E.g_smem, c->stream));
     }
     gbs_count_launch(c);
     E.iter += E.quantum;
