@@ -1067,11 +1067,11 @@ __device__ __forceinline__ void phase_up(const BArgs &a, int cur, int nxt, int g
 // global synchronisation.  Warps claim the units of each phase from
 // grid-wide counters (one per phase and global iteration, zeroed before
 // the launch), so SMs share the work evenly whatever the units cost.
-template <typename TI>
-__global__ void __launch_bounds__(GBS_PBLOCK, 1) k_batched(BArgs a)
+template <typename TI, int NT>
+__global__ void __launch_bounds__(NT, 1) k_batched(BArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ BWarpQ s_q[GBS_PWARPS];
+    __shared__ BWarpQ s_q[NT / 32];
     __shared__ int s_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wsm = smem + (size_t)warp * a.ring;
@@ -1158,6 +1158,15 @@ size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 // systems are skipped one claim at a time until the host compacts the
 // active list, which it does between launches.
 constexpr int kBatchQuantum = 384;
+
+// Threads per CTA of the batched kernel (one CTA per SM): 24 warps at 80
+// registers in FP32, 20 warps at 96 in FP64.  The S phase is bound by the
+// latency of its gathers, so more warps pay although the kernel spills a
+// little more; measured on the 512-system C4 batch against 16 warps at 128
+// registers: FP32 2.08 -> 1.89 s (20 warps 1.95 s), FP64 2.90 -> 2.85 s
+// (24 warps 2.92 s: its spills, 1.3 KB, cost more than the warps gain).
+constexpr int kBatchThreads32 = 768, kBatchThreads64 = 640;
+inline int batch_threads(bool fp64) { return fp64 ? kBatchThreads64 : kBatchThreads32; }
 
 // Column stride of a system with k right-hand sides: k rounded up to a power of two.
 int padded_k(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
@@ -1612,7 +1621,9 @@ int engine_step(Engine &E, int *ran)
     }
     if (act.empty()) return GBS_OK;
     const int nact = (int)act.size();
-    const void *fn = E.fp64 ? (const void *)k_batched<double> : (const void *)k_batched<float>;
+    const int nt = batch_threads(E.fp64);
+    const void *fn = E.fp64 ? (const void *)k_batched<double, kBatchThreads64>
+                            : (const void *)k_batched<float, kBatchThreads32>;
     if (E.dirty || act != E.g_act) {
         engine_free_graph(E);
         E.dirty = false;
@@ -1646,16 +1657,16 @@ int engine_step(Engine &E, int *ran)
         // (each entry read by every row that couples to it) find it
         const GbsPipeCfg cfg = engine_pipe_cfg(E, act);
         const int ring = (cfg.stages * cfg.sbytes + 127) & ~127;
-        const size_t smem = (size_t)ring * GBS_PWARPS;
+        const size_t smem = (size_t)ring * (nt / 32);
         E.g_smem = smem;
         GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         GBS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           (int)cudaSharedmemCarveoutMaxL1));
         int per_sm = 0;
-        GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GBS_PBLOCK, smem));
+        GBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
         if (per_sm < 1) return GBS_ERR_CUDA;
-        // at most one CTA per GBS_PWARPS units of the larger pass
-        const int64_t need = ((int64_t)std::max(nsu, nuu) + GBS_PWARPS - 1) / GBS_PWARPS;
+        // at most one CTA per warp-count units of the larger pass
+        const int64_t need = ((int64_t)std::max(nsu, nuu) + nt / 32 - 1) / (nt / 32);
         E.G = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, std::max<int64_t>(need, 1));
         BArgs &a = E.g_args;
         memset(&a, 0, sizeof(a));
@@ -1699,7 +1710,7 @@ int engine_step(Engine &E, int *ran)
             cudaMemsetAsync(E.d_cnt, 0, E.cnt_bytes, cap);
             cudaMemsetAsync(E.d_bar, 0, 256, cap);
             void *args[] = {&E.g_args};
-            cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args, E.g_smem, cap);
+            cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3((unsigned)nt), args, E.g_smem, cap);
             e = cudaStreamEndCapture(cap, &E.graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E.gexec, E.graph, 0);
@@ -1717,7 +1728,7 @@ int engine_step(Engine &E, int *ran)
         GBS_CUDA_TRY(cudaMemsetAsync(E.d_cnt, 0, E.cnt_bytes, c->stream));
         GBS_CUDA_TRY(cudaMemsetAsync(E.d_bar, 0, 256, c->stream));
         void *args[] = {&E.g_args};
-        GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3(GBS_PBLOCK), args,
+        GBS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.G), dim3((unsigned)nt), args,
                                                  E.g_smem, c->stream));
     }
     gbs_count_launch(c);
