@@ -178,6 +178,11 @@ typedef struct {
                             (FP64 and MIXED; a nonzero counts its value and
                             the column index width actually streamed) and
                             batched solves; 0 where not computed */
+    int cta_threads;     /* persistent single-system CG solves: threads per CTA
+                            of the launch (one CTA per SM: 512 or 1024); 0 for
+                            other algorithms */
+    int lanes_per_row;   /* persistent single-system CG solves: lanes sharing a
+                            matrix row in the SpMV (1 or 2); 0 otherwise */
 } gbs_solve_info;
 
 /* Library version string (static storage). */

@@ -555,6 +555,9 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     }
     A->diag_ok = (flags & 2) ? 0 : 1;
     if (nrows != ncols) A->diag_ok = 0;
+    // the creation tiling is the one-lane tiling: registered now, so every
+    // launch-shape decision sees its tile count from the first solve on
+    (void)gbs_mat_ensure_lane_tiling(A, 0);
     *out = A;
     return GBS_OK;
 }

@@ -800,6 +800,7 @@ PcgShape pcg_shape(gbs_mat A, bool mixed, bool rel, int shape, int li)
 bool wide_shape_fits(gbs_mat A, bool rel, int li)
 {
     const GbsPipeCfg &cfg = rel ? A->pipe64r_lanes[li] : A->pipe64_lanes[li];
+    if (!A->tdesc_lanes[li] || cfg.sbytes <= 0) return false;   // tiling not made
     return (GBS_WARP_STAGE_BYTES / 2) / cfg.sbytes >= 2 &&
            A->ntiles_lanes[li] >= (int64_t)A->ctx->num_sms * 32;
 }
@@ -893,6 +894,8 @@ int persistent_run(gbs_mat A, const double *b, double *x, double rtol, int maxit
     GBS_CUDA_TRY(cudaMemsetAsync(base, 0, head, c->stream));
     st = launch_persistent(c, sh.fn, G, a, info, sh.smem, sh.nt);
     info->model_bytes = persistent_model_bytes(A, mixed, rel16 ? 2 : 4, *info);
+    info->cta_threads = sh.nt;
+    info->lanes_per_row = 1 << li;
     return st;
 }
 
@@ -982,6 +985,10 @@ int pcg_choice(gbs_mat A, bool mixed, bool rel16, const gbs_opts *o, int *shape,
     }
     if (o->persistent_shape != 0) *shape = mixed ? 1 : o->persistent_shape;
     if (o->persistent_lanes != 0) *li = o->persistent_lanes == 2 ? 1 : 0;
+    // the check below reads the tiling's tile count: make it first (a
+    // decision cached from another system of the class finds none here)
+    const int st = gbs_mat_ensure_lane_tiling(A, *li);
+    if (st) return st;
     if (*shape == 2 && !wide_shape_fits(A, rel16, *li)) *shape = 1;
     return GBS_OK;
 }
@@ -1471,14 +1478,6 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
         } else {
             rule_shape(A, false, rel16, &shp, &li);
         }
-        if (li == 0 && !A->tdesc_lanes[0]) {   // tiling 0 is the creation tiling
-            A->tdesc_lanes[0] = A->tdesc;
-            A->ntiles_lanes[0] = A->ntiles;
-            A->pipe64_lanes[0] = A->pipe64;
-            A->pipe32_lanes[0] = A->pipe32;
-            A->pipe16_lanes[0] = A->pipe16;
-            A->pipe64r_lanes[0] = A->pipe64r;
-        }
         if (shp == 2 && !wide_shape_fits(A, rel16, li)) shp = 1;
     }
     const PcgShape shape = pcg_shape(A, false, rel16, shp, li);
@@ -1513,6 +1512,8 @@ extern "C" int gbs_ksp_solve_cg_noalloc(gbs_mat A, const double *b, double *x, d
     st = launch_persistent(c, shape.fn, G, a, info, shape.smem, shape.nt);
     if (st == GBS_ERR_CUDA) info->status = st;
     else info->model_bytes = persistent_model_bytes(A, false, rel16 ? 2 : 4, *info);
+    info->cta_threads = shape.nt;
+    info->lanes_per_row = 1 << li;
     c->last = *info;
     return st;
 }

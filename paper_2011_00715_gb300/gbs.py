@@ -73,7 +73,8 @@ class gbs_opts(ctypes.Structure):
 class gbs_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("device_ms", ctypes.c_double), ("model_bytes", ctypes.c_double)]
+                ("device_ms", ctypes.c_double), ("model_bytes", ctypes.c_double),
+                ("cta_threads", ctypes.c_int), ("lanes_per_row", ctypes.c_int)]
 
 
 @dataclass
@@ -85,6 +86,8 @@ class SolveInfo:
     bnorm: float
     device_ms: float
     model_bytes: float = 0.0
+    cta_threads: int = 0
+    lanes_per_row: int = 0
 
 
 _lib = None
@@ -462,7 +465,8 @@ def gbs_pc_destroy(pc):
 # ----------------------------------------------------------------- solver --
 
 def _info(i: gbs_solve_info) -> SolveInfo:
-    return SolveInfo(i.status, i.iters, i.outer_iters, i.rnorm, i.bnorm, i.device_ms, i.model_bytes)
+    return SolveInfo(i.status, i.iters, i.outer_iters, i.rnorm, i.bnorm, i.device_ms, i.model_bytes,
+                     i.cta_threads, i.lanes_per_row)
 
 
 _RESULT_STATUSES = (GBS_OK, GBS_DIVERGED_ITS, GBS_ERR_DIAG, GBS_ERR_INDEFINITE, GBS_ERR_NAN,

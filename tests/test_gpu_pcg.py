@@ -354,3 +354,54 @@ def test_tuner_decides_per_class(S, orc):
     ref = orc.pcg(B, b, 1e-10, 20000)
     info, x = solve(S, B, b, 1e-10, 20000, algorithm=ALGS["persistent"])
     assert info.status == gbs.GBS_OK and rel(x, ref["x"]) <= 1e-8
+
+
+def test_first_solve_on_a_new_matrix_takes_the_decided_shape(orc):
+    """The launch shape a solve reports (threads per CTA, lanes per row) is
+    the class's decision from the first solve on a freshly created matrix
+    on, in the regular and the allocation-free entry points: the check of
+    whether the 32-warp shape fits reads the tiling's tile count, which a
+    new matrix has from its creation."""
+    from gpu_util import Session
+    import torch
+    A = I.lap3d7(56)                       # 5488 warp tiles: the 32-warp shape fits
+    b = orc.spmv(A, I.xstar(A.n, 5))
+    fixed = Session(gbs.gbs_opts_default(persistent_shape=2, persistent_lanes=1))
+    for _ in range(2):                     # a new matrix each time
+        h = fixed.mat(A)
+        bv, bt = fixed.vec(b)
+        xv, xt = fixed.zeros(A.n)
+        shapes = []
+        for _ in range(2):
+            info = gbs.gbs_ksp_solve_cg_ex(h, bv, xv, 1e-10, 20000, gbs.gbs_opts_default(
+                algorithm=ALGS["persistent"], persistent_shape=2, persistent_lanes=1))
+            assert info.status == gbs.GBS_OK
+            shapes.append((info.cta_threads, info.lanes_per_row))
+        assert shapes == [(1024, 1), (1024, 1)]
+        gbs.gbs_mat_destroy(h)
+    gbs.gbs_ctx_destroy(fixed.ctx)
+    # tuned: a second, new matrix of the class gets the decision on its first solve
+    S = Session()
+    h1 = S.mat(A)
+    shape, lanes = gbs.gbs_ksp_tune(h1, gbs.GBS_MODE_FP64)
+    gbs.gbs_mat_destroy(h1)
+    h2 = S.mat(A)
+    bv, bt = S.vec(b)
+    xv, xt = S.zeros(A.n)
+    info = gbs.gbs_ksp_solve_cg_ex(h2, bv, xv, 1e-10, 20000,
+                                   gbs.gbs_opts_default(algorithm=ALGS["persistent"]))
+    assert info.status == gbs.GBS_OK
+    assert (info.cta_threads, info.lanes_per_row) == (512 * shape, lanes)
+    gbs.gbs_mat_destroy(h2)
+    # allocation-free entry point, untuned context: the fixed rule (32 warps, one lane)
+    R = Session()
+    h3 = R.mat(A)
+    bt = torch.from_numpy(b).cuda()
+    xt = torch.zeros_like(bt)
+    info = gbs.gbs_ksp_solve_cg_noalloc(h3, bt, xt, 1e-10, 20000)
+    assert info.status == gbs.GBS_OK
+    assert (info.cta_threads, info.lanes_per_row) == (1024, 1)
+    assert rel(xt.cpu().numpy(), orc.pcg(A, b, 1e-10, 20000)["x"]) <= 1e-8
+    gbs.gbs_mat_destroy(h3)
+    gbs.gbs_ctx_destroy(S.ctx)
+    gbs.gbs_ctx_destroy(R.ctx)
