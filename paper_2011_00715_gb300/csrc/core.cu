@@ -478,7 +478,9 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
         hrp = hrp_copy.get();
     }
     if (hrp[0] != 0) return GBS_ERR_CSR;
-    int bad = 0;   // monotone row pointers (one pass without early exit)
+    // monotone row pointers (one pass without early exit), checked before
+    // hrp[n] sizes any copy
+    int bad = 0;
     for (int64_t i = 0; i < nrows; ++i) bad |= hrp[i + 1] < hrp[i];
     if (bad) return GBS_ERR_CSR;
     const int64_t nnz = hrp[nrows];
@@ -490,9 +492,6 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     A->n = nrows;
     A->ncols = ncols;
     A->nnz = nnz;
-    std::vector<int32_t> tiles;
-    make_tiles(hrp, nrows, tiles, &A->max_row_nnz);
-    A->ntiles = (int64_t)tiles.size() - 1;
     // allocations padded to 16 bytes so vector loads never leave the buffer
     const size_t pad_nnz = (size_t)((nnz + 4) & ~(int64_t)3);
     const size_t pad_n = (size_t)((nrows + 4) & ~(int64_t)3);
@@ -501,6 +500,27 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     if (e == cudaSuccess) e = cudaMalloc(&A->vals, sizeof(double) * pad_nnz);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv, sizeof(double) * pad_n);
     if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
+    // the bulk of the matrix goes to the device first, so the copies run
+    // while the host cuts the tiles
+    const cudaMemcpyKind kind =
+        memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(A->colidx, colidx, sizeof(int32_t) * nnz, kind, c->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(A->vals, vals, sizeof(double) * nnz, kind, c->stream);
+    // only the padding after the nnz entries needs zeros: the copies fill the rest
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(A->colidx + nnz, 0, sizeof(int32_t) * (pad_nnz - nnz), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(A->vals + nnz, 0, sizeof(double) * (pad_nnz - nnz), c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
+        mat_free(A);
+        return gbs_cuda_fail(e);
+    }
+    std::vector<int32_t> tiles;
+    make_tiles(hrp, nrows, tiles, &A->max_row_nnz);
+    A->ntiles = (int64_t)tiles.size() - 1;
     A->pipe64 = make_pipe_cfg(tiles, hrp, 8);
     A->pipe32 = make_pipe_cfg(tiles, hrp, 4);
     A->pipe16 = make_pipe_cfg(tiles, hrp, 4, 2);
@@ -510,22 +530,11 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
         tdesc[2 * t] = tiles[t];
         tdesc[2 * t + 1] = hrp[tiles[t]];
     }
-    if (e == cudaSuccess) e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
+    e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&A->tdesc, sizeof(int32_t) * tdesc.size());
-    // only the padding after the nnz entries needs zeros: the copies fill the rest
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(A->colidx + nnz, 0, sizeof(int32_t) * (pad_nnz - nnz), c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(A->vals + nnz, 0, sizeof(double) * (pad_nnz - nnz), c->stream);
-    const cudaMemcpyKind kind =
-        memspace == GBS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(A->rowptr, hrp, sizeof(int32_t) * (nrows + 1),
                             cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && nnz > 0)
-        e = cudaMemcpyAsync(A->colidx, colidx, sizeof(int32_t) * nnz, kind, c->stream);
-    if (e == cudaSuccess && nnz > 0)
-        e = cudaMemcpyAsync(A->vals, vals, sizeof(double) * nnz, kind, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(A->tiles, tiles.data(), sizeof(int32_t) * tiles.size(),
                             cudaMemcpyHostToDevice, c->stream);
