@@ -236,8 +236,10 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[KP])
 // INNER step, tile staged in shared memory: q = A p on its rows.  L = 2^li
 // lanes share a row: lane l takes row r0 + l / L and every L-th nonzero of
 // it from l mod L on (all KP columns at once); the L partial sums are added
-// by a fixed shuffle tree.  acc[c][0] += p_row,c q_row,c (p_row from the
-// diagonal entry's gather).
+// by a fixed shuffle tree.  acc[c][0] += p_row,c q_row,c (p_row loaded once
+// per row: every row of an admitted system has its diagonal entry, so this
+// is the operand the diagonal's gather reads; picking it out of the
+// gathers instead cost KP selects per nonzero).
 template <typename TI, int KP, bool REL>
 __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char *st,
                                              const GbsPipeCfg &cfg, int4 d, TI (&acc)[KP][2])
@@ -250,9 +252,9 @@ __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char 
     const int rl = lane >> li, h = lane & (L - 1);
     const bool act = rl < r1 - r0;
     const int row = r0 + rl;
-    TI sum[KP], pd[KP];
+    TI sum[KP];
 #pragma unroll
-    for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
+    for (int i = 0; i < KP; ++i) sum[i] = TI(0);
     if (act) {
         const TI *sval = reinterpret_cast<const TI *>(st);
         const IX *scol = reinterpret_cast<const IX *>(st + cfg.coloff);
@@ -267,21 +269,16 @@ __device__ __forceinline__ void s_tile_inner(const BSys &S, const unsigned char 
             const TI a = sval[e - vb];
             TI v[KP];
             vload<TI, KP>(p + (size_t)c * KP, v);
-            const bool dg = c == row;
 #pragma unroll
-            for (int i = 0; i < KP; ++i) {
-                pd[i] = dg ? v[i] : pd[i];
-                sum[i] = fma(a, v[i], sum[i]);
-            }
+            for (int i = 0; i < KP; ++i) sum[i] = fma(a, v[i], sum[i]);
         }
     }
     for (int off = 1; off < L; off <<= 1)
 #pragma unroll
-        for (int i = 0; i < KP; ++i) {
-            sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
-            pd[i] += __shfl_xor_sync(0xffffffffu, pd[i], off);
-        }
+        for (int i = 0; i < KP; ++i) sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
     if (act && h == 0) {
+        TI pd[KP];
+        vload<TI, KP>(static_cast<const TI *>(S.pi) + (size_t)row * KP, pd);
         vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
 #pragma unroll
         for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
@@ -297,28 +294,24 @@ __device__ __forceinline__ void s_long_inner(const BSys &S, int4 d, TI (&acc)[KP
     const int row = d.x, k0 = d.y, k1 = d.w;
     const TI *vals = bvals<TI>(S);
     const TI *p = static_cast<const TI *>(S.pi);
-    TI sum[KP], pd[KP];
+    TI sum[KP];
 #pragma unroll
-    for (int i = 0; i < KP; ++i) sum[i] = pd[i] = TI(0);
+    for (int i = 0; i < KP; ++i) sum[i] = TI(0);
     for (int e = k0 + lane; e < k1; e += 32) {
         const int c = gbs_ld_stream(S.colidx + e, ps);
         const TI a = gbs_ld_stream(vals + e, ps);
         TI v[KP];
         vload<TI, KP>(p + (size_t)c * KP, v);
 #pragma unroll
-        for (int i = 0; i < KP; ++i) {
-            if (c == row) pd[i] = v[i];
-            sum[i] = fma(a, v[i], sum[i]);
-        }
+        for (int i = 0; i < KP; ++i) sum[i] = fma(a, v[i], sum[i]);
     }
 #pragma unroll
     for (int i = 0; i < KP; ++i)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
-            pd[i] += __shfl_xor_sync(0xffffffffu, pd[i], off);
-        }
+        for (int off = 16; off > 0; off >>= 1) sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], off);
     if (lane == 0) {
+        TI pd[KP];
+        vload<TI, KP>(p + (size_t)row * KP, pd);
         vstore<TI, KP>(static_cast<TI *>(S.qi) + (size_t)row * KP, sum);
 #pragma unroll
         for (int i = 0; i < KP; ++i) acc[i][0] += pd[i] * sum[i];
