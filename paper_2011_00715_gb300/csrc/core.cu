@@ -115,6 +115,9 @@ extern "C" int gbs_ctx_create(int device, void *stream, const gbs_opts *opts, gb
         e = cudaMallocHost(&c->pinned, 4096);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->devsmall, 4096);
+    // zero once: the dot products' arrival counter (word 5) is left at zero
+    // by every launch that uses it
+    if (e == cudaSuccess) e = cudaMemset(c->devsmall, 0, 4096);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e != cudaSuccess) {
@@ -1042,11 +1045,14 @@ __global__ void __launch_bounds__(GBS_BLOCK) k_dot(int64_t n, const T *__restric
     }
 }
 
-// Launch the dot product (or norm) of x and y into dev_out on the context's
-// stream, without waiting for it.  The counter and the per-CTA partials are
-// in the context's scratch: every later user of the scratch is ordered
-// after this launch on the same stream, and growing the scratch
-// synchronises the stream first.
+// Launch the dot product (or norm) of x and y into out (device memory, or
+// the context's pinned host buffer, which the device writes through the
+// unified address space) on the context's stream, without waiting for it.
+// The per-CTA partials are in the context's scratch: every later user of
+// the scratch is ordered after this launch on the same stream, and growing
+// the scratch synchronises the stream first.  The arrival counter is word 5
+// of the context's small device buffer, zero at creation and reset by the
+// last CTA of every launch, so no clearing copy precedes the kernel.
 static int vec_dot_launch(gbs_vec x, gbs_vec y, double *dev_out, int root)
 {
     gbs_ctx c = x->ctx;
@@ -1059,9 +1065,8 @@ static int vec_dot_launch(gbs_vec x, gbs_vec y, double *dev_out, int root)
     void *scr = nullptr;
     int st = gbs_ctx_reserve(c, 64 + 8 * (size_t)g, &scr);
     if (st) return st;
-    unsigned int *counter = (unsigned int *)scr;
+    unsigned int *counter = (unsigned int *)c->devsmall + 5;
     void *partials = (char *)scr + 64;
-    GBS_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, c->stream));
     if (x->dtype == GBS_F64)
         k_dot<double><<<g, GBS_BLOCK, 0, c->stream>>>(x->n, (const double *)x->data,
                                                       (const double *)y->data,
@@ -1075,15 +1080,17 @@ static int vec_dot_launch(gbs_vec x, gbs_vec y, double *dev_out, int root)
     return GBS_OK;
 }
 
-// Synchronous form: the result goes through the context's small device
-// buffer and its pinned host buffer.
+// Synchronous form: the last CTA writes the result straight into the
+// context's pinned host buffer (no copy operation after the kernel).
 static int vec_dot_sync(gbs_vec x, gbs_vec y, double *out, int root)
 {
     gbs_ctx c = x->ctx;
-    double *res = (double *)c->devsmall + 8;   // bytes 64..71 of the small device buffer
-    int st = vec_dot_launch(x, y, res, root);
+    if (x->n == 0) {
+        *out = 0.0;
+        return GBS_OK;
+    }
+    int st = vec_dot_launch(x, y, (double *)c->pinned, root);
     if (st) return st;
-    GBS_CUDA_TRY(cudaMemcpyAsync(c->pinned, res, 8, cudaMemcpyDeviceToHost, c->stream));
     GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     *out = *(volatile double *)c->pinned;
     return GBS_OK;
