@@ -120,7 +120,20 @@ extern "C" int gbs_ctx_create(int device, void *stream, const gbs_opts *opts, gb
     if (e == cudaSuccess) e = cudaMemset(c->devsmall, 0, 4096);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = ~(uint64_t)0;   // never trim at synchronisation
+            e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     if (e != cudaSuccess) {
+        if (c->pool) cudaMemPoolDestroy(c->pool);
         if (c->pinned) cudaFreeHost(c->pinned);
         if (c->devsmall) cudaFree(c->devsmall);
         free(c);
@@ -139,6 +152,7 @@ extern "C" int gbs_ctx_destroy(gbs_ctx c)
     if (c->scratch) cudaFree(c->scratch);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->devsmall) cudaFree(c->devsmall);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
     free(c);
@@ -148,6 +162,10 @@ extern "C" int gbs_ctx_destroy(gbs_ctx c)
 extern "C" int gbs_ctx_set_stream(gbs_ctx c, void *stream)
 {
     if (!c) return GBS_ERR_ARG;
+    // the matrices' arrays are ordered on the stream they were made on:
+    // finish its work before later work and frees go to the new one
+    GBS_CUDA_TRY(cudaSetDevice(c->device));
+    GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->stream = (cudaStream_t)stream;
     return GBS_OK;
 }
@@ -397,20 +415,32 @@ static GbsPipeCfg make_pipe_cfg(const std::vector<int32_t> &tiles, const int32_t
     return cfg;   // at least 2 stages: a full tile needs at most 6320 bytes
 }
 
+cudaError_t gbs_mat_alloc(gbs_ctx c, void **p, size_t bytes)
+{
+    return cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
+}
+
+void gbs_mat_release(gbs_ctx c, void *p)
+{
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
 static void mat_free(gbs_mat A)
 {
     if (!A) return;
-    cudaFree(A->rowptr);
-    cudaFree(A->colidx);
-    cudaFree(A->vals);
-    cudaFree(A->vals32);
-    cudaFree(A->dinv);
-    cudaFree(A->dinv32);
-    cudaFree(A->tiles);
-    cudaFree(A->tdesc);
-    cudaFree(A->tdesc_lanes[1]);
-    cudaFree(A->tdesc_lanes[2]);
-    cudaFree(A->colrel16);
+    gbs_ctx c = A->ctx;
+    gbs_mat_release(c, A->rowptr);
+    gbs_mat_release(c, A->colidx);
+    gbs_mat_release(c, A->vals);
+    gbs_mat_release(c, A->vals32);
+    gbs_mat_release(c, A->dinv);
+    gbs_mat_release(c, A->dinv32);
+    gbs_mat_release(c, A->tiles);
+    gbs_mat_release(c, A->tdesc);
+    gbs_mat_release(c, A->tdesc_lanes[1]);
+    gbs_mat_release(c, A->tdesc_lanes[2]);
+    gbs_mat_release(c, A->colrel16);
+    // the coordinate maps come from the assembly's own allocations
     cudaFree(A->coo_seg);
     cudaFree(A->coo_perm);
     free(A);
@@ -442,12 +472,12 @@ int gbs_mat_ensure_lane_tiling(gbs_mat A, int li)
         tdesc[2 * t + 1] = hrp[tiles[t]];
     }
     int32_t *d = nullptr;
-    GBS_CUDA_TRY(cudaMalloc(&d, sizeof(int32_t) * tdesc.size()));
+    GBS_CUDA_TRY(gbs_mat_alloc(c, (void **)&d, sizeof(int32_t) * tdesc.size()));
     cudaError_t e = cudaMemcpyAsync(d, tdesc.data(), sizeof(int32_t) * tdesc.size(),
                                     cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // tdesc is a stack vector
     if (e != cudaSuccess) {
-        cudaFree(d);
+        gbs_mat_release(c, d);
         return gbs_cuda_fail(e);
     }
     A->tdesc_lanes[li] = d;
@@ -498,11 +528,11 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
     // allocations padded to 16 bytes so vector loads never leave the buffer
     const size_t pad_nnz = (size_t)((nnz + 4) & ~(int64_t)3);
     const size_t pad_n = (size_t)((nrows + 4) & ~(int64_t)3);
-    cudaError_t e = cudaMalloc(&A->rowptr, sizeof(int32_t) * (pad_n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&A->colidx, sizeof(int32_t) * pad_nnz);
-    if (e == cudaSuccess) e = cudaMalloc(&A->vals, sizeof(double) * pad_nnz);
-    if (e == cudaSuccess) e = cudaMalloc(&A->dinv, sizeof(double) * pad_n);
-    if (e == cudaSuccess) e = cudaMalloc(&A->dinv32, sizeof(float) * pad_n);
+    cudaError_t e = gbs_mat_alloc(c, (void **)&A->rowptr, sizeof(int32_t) * (pad_n + 1));
+    if (e == cudaSuccess) e = gbs_mat_alloc(c, (void **)&A->colidx, sizeof(int32_t) * pad_nnz);
+    if (e == cudaSuccess) e = gbs_mat_alloc(c, (void **)&A->vals, sizeof(double) * pad_nnz);
+    if (e == cudaSuccess) e = gbs_mat_alloc(c, (void **)&A->dinv, sizeof(double) * pad_n);
+    if (e == cudaSuccess) e = gbs_mat_alloc(c, (void **)&A->dinv32, sizeof(float) * pad_n);
     // the bulk of the matrix goes to the device first, so the copies run
     // while the host cuts the tiles
     const cudaMemcpyKind kind =
@@ -533,8 +563,8 @@ extern "C" int gbs_mat_create_aij(gbs_ctx c, int64_t nrows, int64_t ncols, const
         tdesc[2 * t] = tiles[t];
         tdesc[2 * t + 1] = hrp[tiles[t]];
     }
-    e = cudaMalloc(&A->tiles, sizeof(int32_t) * tiles.size());
-    if (e == cudaSuccess) e = cudaMalloc(&A->tdesc, sizeof(int32_t) * tdesc.size());
+    e = gbs_mat_alloc(c, (void **)&A->tiles, sizeof(int32_t) * tiles.size());
+    if (e == cudaSuccess) e = gbs_mat_alloc(c, (void **)&A->tdesc, sizeof(int32_t) * tdesc.size());
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(A->rowptr, hrp, sizeof(int32_t) * (nrows + 1),
                             cudaMemcpyHostToDevice, c->stream);
@@ -587,7 +617,7 @@ int gbs_mat_ensure_rel16(gbs_mat A)
     gbs_ctx c = A->ctx;
     const size_t pad16 = (size_t)((A->nnz + 15) & ~(int64_t)7);
     int16_t *rel = nullptr;
-    GBS_CUDA_TRY(cudaMalloc(&rel, sizeof(int16_t) * pad16));
+    GBS_CUDA_TRY(gbs_mat_alloc(c, (void **)&rel, sizeof(int16_t) * pad16));
     int *flag = (int *)c->devsmall + 2;   // word 2 of the context's small device buffer
     cudaError_t e = cudaMemsetAsync(rel, 0, sizeof(int16_t) * pad16, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
@@ -601,11 +631,11 @@ int gbs_mat_ensure_rel16(gbs_mat A)
         e = cudaMemcpyAsync(c->pinned, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        cudaFree(rel);
+        gbs_mat_release(c, rel);
         return gbs_cuda_fail(e);
     }
     if (*(volatile int *)c->pinned) {
-        cudaFree(rel);
+        gbs_mat_release(c, rel);
         A->rel16_state = -1;
     } else {
         A->colrel16 = rel;
@@ -617,12 +647,12 @@ int gbs_mat_ensure_rel16(gbs_mat A)
 int gbs_mat_ensure_f32(gbs_mat A)
 {
     if (A->vals32 || A->nnz == 0) {
-        if (!A->vals32) GBS_CUDA_TRY(cudaMalloc(&A->vals32, 16));
+        if (!A->vals32) GBS_CUDA_TRY(gbs_mat_alloc(A->ctx, (void **)&A->vals32, 16));
         return gbs_mat_ensure_rel16(A);
     }
     gbs_ctx c = A->ctx;
     const size_t pad_nnz = (size_t)((A->nnz + 4) & ~(int64_t)3);
-    GBS_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float) * pad_nnz));
+    GBS_CUDA_TRY(gbs_mat_alloc(A->ctx, (void **)&A->vals32, sizeof(float) * pad_nnz));
     GBS_CUDA_TRY(cudaMemsetAsync(A->vals32, 0, sizeof(float) * pad_nnz, c->stream));
     k_f64_to_f32<<<grid_for(c, A->nnz), GBS_BLOCK, 0, c->stream>>>(A->nnz, A->vals, A->vals32);
     gbs_count_launch(c);

@@ -34,6 +34,10 @@ struct gbs_ctx_s {
     gbs_solve_info last;
     int64_t launches;           // kernel launches issued by this library
     cudaEvent_t ev0, ev1;
+    // stream-ordered pool for the matrices' device arrays: freed memory
+    // stays reserved for the next matrix (no mapping or unmapping per
+    // create / destroy)
+    cudaMemPool_t pool;
     // batched engines' lanes-per-row decisions, per precision, column stride
     // and row-length class: 0 = not tuned yet, else 1 + log2(lanes)
     signed char lane_choice[2][4][8];
@@ -136,6 +140,10 @@ int gbs_mat_ensure_f32(gbs_mat A);
 int gbs_mat_ensure_rel16(gbs_mat A);
 // Make the tiling for 2^li lanes per row (li = 0, 1, 2) if it does not exist.
 int gbs_mat_ensure_lane_tiling(gbs_mat A, int li);
+// Device arrays owned by a matrix: from its context's pool, in its stream's
+// order (GBS_ERR via the returned cudaError_t); freed likewise.
+cudaError_t gbs_mat_alloc(gbs_ctx c, void **p, size_t bytes);
+void gbs_mat_release(gbs_ctx c, void *p);
 
 // ------------------------------------------------------------------------
 // Device helpers
