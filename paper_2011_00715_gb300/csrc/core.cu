@@ -149,7 +149,8 @@ extern "C" int gbs_ctx_destroy(gbs_ctx c)
     if (!c) return GBS_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    if (c->scratch) cudaFree(c->scratch);
+    if (c->scratch) cudaFreeAsync(c->scratch, c->stream);
+    cudaStreamSynchronize(c->stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->devsmall) cudaFree(c->devsmall);
     if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -256,11 +257,12 @@ int gbs_ctx_reserve(gbs_ctx c, size_t bytes, void **out)
 {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes > c->scratch_bytes) {
+        // from the context's pool as well (stream-ordered)
         GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        if (c->scratch) cudaFree(c->scratch);
+        if (c->scratch) cudaFreeAsync(c->scratch, c->stream);
         c->scratch = nullptr;
         c->scratch_bytes = 0;
-        GBS_CUDA_TRY(cudaMalloc(&c->scratch, bytes));
+        GBS_CUDA_TRY(cudaMallocFromPoolAsync(&c->scratch, bytes, c->pool, c->stream));
         c->scratch_bytes = bytes;
     }
     *out = c->scratch;
