@@ -1354,7 +1354,9 @@ int engine_add(Engine &E, int slot, gbs_mat A, int k, double rtol, int maxit, co
     const size_t bytes = 3 * a256(nk * 8) + 4 * a256(nk * tsz);
     char *p = nullptr;
     if (bytes) {
-        GBS_CUDA_TRY(cudaMalloc(&p, bytes));
+        // from the context's pool, in stream order (a slot's vectors come and
+        // go with every served request)
+        GBS_CUDA_TRY(gbs_mat_alloc(c, (void **)&p, bytes));
         // padding columns and unused entries hold zeros
         GBS_CUDA_TRY(cudaMemsetAsync(p, 0, bytes, c->stream));
     }
@@ -1567,7 +1569,7 @@ void engine_release(Engine &E, int slot)
 {
     E.dirty = true;
     SlotHost &H = E.slots[slot];
-    if (H.work) cudaFree(H.work);
+    gbs_mat_release(E.c, H.work);
     if (H.own_A) gbs_mat_destroy(H.A);
     H = SlotHost();
 }
