@@ -46,6 +46,7 @@
 #include <type_traits>
 #include <chrono>
 #include <deque>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -1502,11 +1503,18 @@ int engine_collect(Engine &E, int slot, double *x_out, int memspace, int *iters,
             gbs_count_launch(c);
             GBS_CUDA_TRY(cudaGetLastError());
         } else {
-            std::vector<double> tmp(nk);
-            GBS_CUDA_TRY(cudaMemcpyAsync(tmp.data(), xil, nk * 8, cudaMemcpyDeviceToHost, c->stream));
-            GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
-            for (size_t e = 0; e < nk; ++e)
-                if ((int)(e % kp) < H.k) x_out[(e % kp) * n + e / kp] = tmp[e];
+            // column-major on the device first (a pooled temporary), then
+            // one copy to the host
+            const size_t nkk = (size_t)n * H.k;
+            double *tmp = nullptr;
+            GBS_CUDA_TRY(gbs_mat_alloc(c, (void **)&tmp, nkk * 8));
+            k_interleave<<<g, 256, 0, c->stream>>>(n, H.k, kp, xil, tmp, 1);
+            gbs_count_launch(c);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(x_out, tmp, nkk * 8, cudaMemcpyDeviceToHost, c->stream);
+            gbs_mat_release(c, tmp);
+            if (e != cudaSuccess) return gbs_cuda_fail(e);
         }
     }
     GBS_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1937,16 +1945,51 @@ struct Request {
     size_t bytes;
     int slot = -1;
     bool done = false;
-    std::vector<double> x;
+    double *x = nullptr;   // n x k column-major result, pinned (from the server's cache)
+    size_t xn = 0, xcap = 0;
     std::vector<int> iters, status;
     std::vector<double> rnorm;
 };
 
 }  // namespace
 
+// Pinned host buffers for the results: retirement copies a request's x
+// into one at the link's rate (no page faults, no zero fill), the fetch
+// copies it to the caller and returns the buffer here for the next request
+// (best fit by capacity).
+struct PinnedCache {
+    std::multimap<size_t, double *> free_;
+    double *take(size_t n, size_t *cap)
+    {
+        auto it = free_.lower_bound(n);
+        if (it != free_.end()) {
+            double *p = it->second;
+            *cap = it->first;
+            free_.erase(it);
+            return p;
+        }
+        double *p = nullptr;
+        if (cudaMallocHost((void **)&p, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        *cap = std::max<size_t>(n, 1);
+        return p;
+    }
+    void give(double *p, size_t cap)
+    {
+        if (p) free_.emplace(cap, p);
+    }
+    ~PinnedCache()
+    {
+        for (auto &kv : free_) cudaFreeHost(kv.second);
+    }
+};
+
 struct gbs_server_s {
     gbs_ctx c;
     Engine E;
+    PinnedCache pinned;
     size_t budget;
     size_t used = 0;
     int mode;
@@ -2039,6 +2082,7 @@ extern "C" int gbs_server_destroy(gbs_server srv)
     if (!srv) return GBS_OK;
     cudaSetDevice(srv->c->device);
     engine_destroy(srv->E);
+    for (auto &kv : srv->reqs) srv->pinned.give(kv.second.x, kv.second.xcap);
     delete srv;
     return GBS_OK;
 }
@@ -2074,7 +2118,10 @@ static int server_admit(gbs_server srv)
         if (st != GBS_OK) {
             // a malformed request finishes at once with that status
             r.done = true;
-            r.x.assign((size_t)r.n * r.k, 0.0);
+            r.xn = (size_t)r.n * r.k;
+            r.x = srv->pinned.take(r.xn, &r.xcap);
+            if (!r.x) return GBS_ERR_OOM;
+            memset(r.x, 0, r.xn * sizeof(double));
             r.iters.assign(r.k, 0);
             r.rnorm.assign(r.k, 0.0);
             r.status.assign(r.k, st);
@@ -2124,11 +2171,13 @@ static int server_retire(gbs_server srv, int *retired)
         SlotHost &H = E.slots[s];
         if (!H.used || !H.finished) continue;
         Request &r = srv->reqs.at(H.ticket);
-        r.x.assign((size_t)r.n * r.k, 0.0);
+        r.xn = (size_t)r.n * r.k;
+        r.x = srv->pinned.take(r.xn, &r.xcap);
+        if (!r.x) return GBS_ERR_OOM;
         r.iters.assign(r.k, 0);
         r.rnorm.assign(r.k, 0.0);
         r.status.assign(r.k, 0);
-        const int st = engine_collect(E, s, r.x.data(), GBS_MEM_HOST, r.iters.data(), r.rnorm.data(),
+        const int st = engine_collect(E, s, r.x, GBS_MEM_HOST, r.iters.data(), r.rnorm.data(),
                                       r.status.data());
         if (st) return st;
         engine_release(E, s);
@@ -2193,12 +2242,13 @@ extern "C" int gbs_server_fetch(gbs_server srv, uint64_t ticket, double *x, int 
     auto it = srv->reqs.find(ticket);
     if (it == srv->reqs.end() || !it->second.done) return GBS_ERR_NOT_FOUND;
     Request &r = it->second;
-    if (x && !r.x.empty()) memcpy(x, r.x.data(), r.x.size() * sizeof(double));
+    if (x && r.xn) memcpy(x, r.x, r.xn * sizeof(double));
     for (int cc = 0; cc < r.k; ++cc) {
         if (iters) iters[cc] = r.iters[cc];
         if (rnorm) rnorm[cc] = r.rnorm[cc];
         if (status) status[cc] = r.status[cc];
     }
+    srv->pinned.give(r.x, r.xcap);
     srv->reqs.erase(it);
     return GBS_OK;
 }
