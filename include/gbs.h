@@ -114,8 +114,11 @@ typedef struct gbs_server_s *gbs_server;
 typedef struct {
     int mode;                /* GBS_MODE_FP64 (default) or GBS_MODE_MIXED */
     int algorithm;           /* GBS_ALG_* (default GBS_ALG_AUTO) */
-    double inner_rtol;       /* MIXED: relative tolerance of each FP32 inner
-                                solve (default 1e-4) */
+    double inner_rtol;       /* MIXED: relative tolerance eta of each FP32 inner
+                                solve (default 1e-4); a refinement step j with
+                                outer residual r_j stops its inner solve at
+                                max(eta, rtol ||b|| / (2 ||r_j||)), so the last
+                                step does only the work that finishes the solve */
     int outer_maxit;         /* MIXED: refinement steps at most (default 30) */
     int barrier_timeout_ms;  /* device-side waits give up after this many
                                 milliseconds with GBS_ERR_TIMEOUT (default 2000) */

@@ -419,9 +419,13 @@ int orc_pcg_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, const
         if (it >= outer_maxit) break;
         prev = rn;
         for (int64_t i = 0; i < n; ++i) r32[i] = (float)(r[i] / rn);
+        /* the inner solve stops at eta, or sooner where half the outer
+         * target already suffices: x += rn d with ||r/rn - A d|| <= eta_j
+         * leaves an outer residual of about rn eta_j */
+        const double eta_j = fmax(inner_rtol, 0.5 * rtol * bnorm / rn);
         int64_t kin = 0;
         float rin = 0.0f;
-        int st = orc_pcg_f32(n, rowptr, colidx, vals32, dinv32, r32, d32, (float)inner_rtol,
+        int st = orc_pcg_f32(n, rowptr, colidx, vals32, dinv32, r32, d32, (float)eta_j,
                              inner_maxit, &kin, &rin);
         *inner += kin;
         if (st < 0) { status = st; break; }

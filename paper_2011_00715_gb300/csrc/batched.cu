@@ -507,8 +507,11 @@ __device__ __noinline__ void s_finish_outer(const BArgs &a, int slot, double rr,
                 C.prev = rn;
                 C.scale = 1.0 / rn;
                 C.outer += 1;
-                // FP64 inner solves aim below rtol ||b|| at once
-                C.tol_inner = a.fp64 ? 0.5 * S.rtol * C.bnorm / rn : a.inner_rtol;
+                // FP64 inner solves aim below rtol ||b|| at once; FP32 ones
+                // stop at the inner tolerance, or sooner where half the
+                // outer target already suffices (the last refinement step)
+                C.tol_inner = a.fp64 ? 0.5 * S.rtol * C.bnorm / rn
+                                     : fmax(a.inner_rtol, 0.5 * S.rtol * C.bnorm / rn);
                 P.scale[lane] = C.scale;
                 P.rn[lane] = rn;
                 run = true;

@@ -540,6 +540,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
     __shared__ PcgCtl<float> ctl32;
     __shared__ GbsWarpQ s_q[GBS_PWARPS];
     __shared__ double s_scale;
+    __shared__ double s_itol;
     __shared__ int s_go;
     __shared__ int s_next;
     __shared__ int s_flag;
@@ -612,6 +613,9 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
                 if (!s_go) st = s;
                 prev = rn;
                 s_scale = 1.0 / rn;
+                // the inner tolerance: eta, or looser where half the outer
+                // target already suffices (the last refinement step)
+                s_itol = fmax(a.inner_rtol, 0.5 * a.rtol * bnorm / rn);
             }
         }
         __syncthreads();
@@ -626,7 +630,7 @@ __global__ void __launch_bounds__(GBS_PBLOCK) k_pcg_mixed(PcgArgs a)
                                           : (const IX *)(const void *)a.colidx;
         const int sti = pcg_loop<float, IX, GBS_PBLOCK, 4, LOG_L>(
             a, col32, a.vals32, a.dinv32, a.b32, a.x32, a.r32, a.z32, a.p32, a.q32, a.part32,
-            (float)a.inner_rtol, a.maxit, true, &kin, &rin, &bin, &barrier_no, wsm, s_q[warp],
+            (float)s_itol, a.maxit, true, &kin, &rin, &bin, &barrier_no, wsm, s_q[warp],
             parity, &s_next, a.pipe32, sm32, reinterpret_cast<float *>(s_stage), ctl32, &s_flag);
         inner_total += kin;
         if (sti < 0) { st = sti; break; }

@@ -650,3 +650,26 @@ def test_block_pcg_breakdown_and_degenerate(orc):
     B = block_rhs(orc, A, 2, 1)
     r = orc.block_pcg(A, B, 1e-14, 2)
     assert r["status"] == orc.DIVERGED_ITS and r["iters"] == 2
+
+
+def test_mixed_last_step_stops_at_half_the_target(orc):
+    """Each refinement step's inner FP32 solve stops at
+    eta_j = max(eta, rtol ||b|| / (2 ||r_j||)).  With x0 = 0 and a loose
+    rtol the first step alone can finish: its inner solve is then exactly
+    the FP32 PCG of r0 / ||r0|| = b / ||b|| to the relative tolerance
+    rtol / 2, so its iteration count is that solve's, far below what the
+    fixed eta would take, and one refinement step reaches rtol."""
+    A = I.var7(14, 13, 12, seed=9, sigma=1.0)
+    b = orc.spmv(A, I.xstar(A.n, 9))
+    rtol, eta = 1e-3, 1e-6
+    m = orc.pcg_mixed(A, b, rtol, inner_rtol=eta)
+    assert m["status"] == orc.CONVERGED and m["outer"] == 1
+    alone = orc.pcg_f32(A, (b / orc.norm2(b)).astype(np.float32), 0.5 * rtol, 10000)
+    fixed = orc.pcg_f32(A, (b / orc.norm2(b)).astype(np.float32), eta, 10000)
+    assert m["inner"] == alone["iters"] < fixed["iters"]
+    assert np.linalg.norm(b - orc.spmv(A, m["x"])) <= rtol * np.linalg.norm(b)
+    # at a tight rtol every step but the last runs to eta: the count of
+    # steps stays within the fixed-eta bound
+    m2 = orc.pcg_mixed(A, b, 1e-10, inner_rtol=1e-4)
+    assert m2["status"] == orc.CONVERGED
+    assert m2["outer"] <= math.ceil(math.log(1e-10) / math.log(1e-4)) + 2
