@@ -54,8 +54,10 @@ def check(orc, A, b, k, x, sts):
 
 def test_server_continuous_batching(S, orc):
     srv = gbs.gbs_server_create(S.ctx, 8 << 30, 0, gbs.GBS_MODE_MIXED)
+    # the first request is large enough to need many quanta of the engine,
+    # so it is still running when the last two arrive
     reqs = [request(orc, i, d, k) for i, (d, k) in
-            enumerate([((14, 13, 12), 2), ((9, 9, 9), 1), ((20, 18, 17), 4), ((6, 7, 5), 3)])]
+            enumerate([((34, 32, 30), 2), ((9, 9, 9), 1), ((20, 18, 17), 4), ((6, 7, 5), 3)])]
     tickets = {}
     # the first two arrive, the engine runs, the others arrive while they are on the GPU
     for i in (0, 1):
