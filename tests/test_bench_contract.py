@@ -45,5 +45,9 @@ def test_roofline_models():
     assert bench.stencil_index_bytes(128) == 2 and bench.stencil_index_bytes(464) == 4
     assert bench.ops_per_iter_fp64(n, nnz) == nnz + 6 * n
     assert bench.FP64_NOMINAL_GOPS == 625.0          # 1.25 TFLOP/s in fused multiply-adds
+    # standalone MatMult models: values + indices per nonzero, row pointers,
+    # the x gather and the y write once per row
+    assert bench.bytes_spmv_fp64(n, nnz, 2) == 10 * nnz + 4 * (n + 1) + 16 * n
+    assert bench.bytes_spmv_fp32(n, nnz, 2) == 6 * nnz + 4 * (n + 1) + 8 * n
     cfg = bench.config_for(1)
     assert "128^3" in cfg["workload"] and cfg["parallelism"] == "single GPU"
