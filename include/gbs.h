@@ -550,7 +550,11 @@ int gbs_server_wait(gbs_server srv, uint64_t ticket);
 
 /* Copy a finished request's solution (host, nrows * k, column-major) and
  * per-column iters/rnorm/status (k entries each; any may be NULL), then
- * release it.  GBS_ERR_NOT_FOUND for unknown or already fetched tickets. */
+ * release it.  A finished request's solution waits in a pinned host buffer
+ * of the server (reused by later requests once fetched), so results that
+ * are never fetched hold pinned memory until gbs_server_destroy.  The
+ * server's calls are not thread-safe: one thread drives a server.
+ * GBS_ERR_NOT_FOUND for unknown or already fetched tickets. */
 int gbs_server_fetch(gbs_server srv, uint64_t ticket, double *x, int *iters, double *rnorm,
                      int *status);
 
