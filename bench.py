@@ -7,12 +7,17 @@ Headline workload: one Jacobi-preconditioned CG solve per step of the 3D
 rtol 1e-10 -- solves/s.  Inputs (matrix 175 MB + vectors) exceed the
 129 MB L2, so no flush is needed between steps.
 
-Also reported: the roofline of the persistent solve kernel (algorithmic
-bytes 12 nnz + 108 n per iteration over its CUDA-event time, against the
-measured HBM copy bandwidth), an end-to-end number through the C ABI with
-host buffers, the CPU oracle's rate on a bounded sample, SpMV bandwidth,
-the 64x64 2D case, mixed precision vs FP64 on the 96^3 27-point case, and
-the batched and serving workloads when they are built.
+Also reported: the roofline of the persistent solve kernel (the
+library's byte model of the launch -- 10 nnz + 100 n per iteration with
+16-bit column offsets -- over its CUDA-event time, against the measured
+HBM copy bandwidth, with the 12 nnz + 108 n CSR model beside it and the
+DRAM traffic of an ncu capture), its FP64 rate against a measured FMA
+rate, an end-to-end number through the C ABI with host buffers, the CPU
+oracle's rate on a bounded sample (one core and all cores), MatMult
+bandwidth and a size sweep, the 64x64 2D case, mixed precision vs FP64 on
+the 96^3 27-point case with its MatMult lanes sweep, Chebyshev, COO
+assembly, and the batched (512 systems x 8 right-hand sides) and serving
+(Poisson arrival-rate sweep) workloads.
 
 Multi-GPU: every rank solves its own copy of the workload (independent
 replicas, no collective on the data path); value = all ranks' solves /
