@@ -60,6 +60,11 @@ MUTANTS = {
     "mixed_residual_sign": ("r[i] = b[i] - r[i];", "r[i] = r[i] - b[i];"),
     "mixed_rhs_not_normalised": ("r32[i] = (float)(r[i] / rn);", "r32[i] = (float)r[i];"),
     "mixed_stagnation_test_inverted": ("if (rn > 0.5 * prev)", "if (rn < 0.5 * prev)"),
+    "mixed_inner_tolerance_fixed": ("const double eta_j = fmax(inner_rtol, 0.5 * rtol * bnorm / rn);",
+                                    "const double eta_j = inner_rtol;"),
+    "mixed_inner_tolerance_full_target": (
+        "const double eta_j = fmax(inner_rtol, 0.5 * rtol * bnorm / rn);",
+        "const double eta_j = fmax(inner_rtol, rtol * bnorm / rn);"),
     "spmv_f32_row_index_for_column": (
         "float s = 0.0f;\n        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)\n"
         "            s += vals[k] * x[colidx[k]];",
@@ -99,6 +104,7 @@ PINS = [
     lambda o: P.test_pcg_diagonal_matrix_one_step(o),
     lambda o: P.test_pcg_f32_close_to_fp64(o),
     lambda o: P.test_mixed_refinement_reaches_fp64_accuracy(o),
+    lambda o: P.test_mixed_last_step_stops_at_half_the_target(o),
     lambda o: P.test_chebyshev_error_is_the_scaled_chebyshev_polynomial(o, 5),
     lambda o: P.test_chebyshev_rate_with_exact_bounds(o),
     lambda o: P.test_chebyshev_single_eigenvalue_and_arguments(o),
