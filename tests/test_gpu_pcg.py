@@ -171,6 +171,24 @@ def test_mixed_matches_fp64_oracle(S, orc, maker):
     assert m["status"] == 0 and abs(m["outer"] - info.outer_iters) <= 1
 
 
+def test_mixed_last_step_stops_at_half_the_target(S, orc):
+    """A loose mixed solve (rtol 1e-3, inner tolerance 1e-6) finishes in one
+    refinement step whose FP32 inner solve stops at rtol / 2, not at the
+    inner tolerance: its inner count is that of the oracle's mixed solve
+    and of FP32 PCG on b / ||b|| to rtol / 2 (within a step or two of FP32
+    rounding), far below the count to 1e-6; the true residual meets rtol."""
+    A = I.var7(40, 36, 32, seed=9, sigma=1.0)
+    b = orc.spmv(A, I.xstar(A.n, 9))
+    info, x = solve(S, A, b, 1e-3, 20000, mode=gbs.GBS_MODE_MIXED, inner_rtol=1e-6)
+    assert info.status == gbs.GBS_OK and info.outer_iters == 1
+    assert true_res(orc, A, b, x) <= 1e-3 * np.linalg.norm(b)
+    m = orc.pcg_mixed(A, b, 1e-3, inner_rtol=1e-6)
+    alone = orc.pcg_f32(A, (b / orc.norm2(b)).astype(np.float32), 0.5e-3, 20000)
+    deep = orc.pcg_f32(A, (b / orc.norm2(b)).astype(np.float32), 1e-6, 20000)
+    assert m["outer"] == 1 and m["inner"] == alone["iters"]
+    assert abs(info.iters - alone["iters"]) <= 2 < deep["iters"] - alone["iters"]
+
+
 def test_finite_termination_and_limits(S, orc):
     A = I.lap2d5(2)
     b = orc.spmv(A, I.xstar(4, 1))
